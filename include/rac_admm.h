@@ -1,0 +1,238 @@
+/*
+ * rac_admm.h - C-ABI of the GB300 (sm_103a) RAC-MBADMM library.
+ *
+ * RAC-MBADMM is the randomly assembled cyclic multi-block ADMM of Zhu, Mihic
+ * and Ye, "On a Randomized Multi-Block ADMM for Solving Selected Machine
+ * Learning Problems" (arXiv:1907.01995).  Each iteration ("sweep", eq.
+ * RAC-ADDM of Sec. 1) randomly assembles the primal coordinates into p
+ * blocks, minimises the augmented Lagrangian (eq. lagrangian) over each block
+ * in turn, and then takes a multiplier ascent step.
+ *
+ * Problem solved (the general model eq. general_model of Sec. 1 with a
+ * separable f, in the split form Sec. 3.1 uses for the Elastic-Net):
+ *
+ *   minimise  1/2 ||A x - b||^2 + c^T x + sum_j phi(x_j)      (data form)
+ *        or   1/2 x^T H x + c^T x + sum_j phi(x_j)             (H form)
+ *   subject to  E x = d   (optional, at most one row; Sec. 3.2 eq. svm)
+ *
+ * with phi one of: none (linear regression), l1l2 = lambda1 |t| +
+ * lambda2/2 t^2 (LASSO / Elastic-Net, Sec. 3.1; the paper's lambda alpha and
+ * lambda (1 - alpha)), or the indicator of [lo, hi] (SVM dual box, Sec. 3.2).
+ * The library splits x - z = 0 (penalty gamma, dual xi) exactly as Sec. 3.1
+ * does: x is partitioned into RAC blocks, z is one block with a closed form,
+ * and E x = d carries penalty beta and dual mu.
+ *
+ * The paper's "A" of eq. general_model (the constraint matrix) is E here; the
+ * paper's "A = X / sqrt(n)" of Sec. 3.1 (the data matrix) is A here.  To solve
+ * the paper's (1/2n)||y - X beta||^2 + lambda{(1-alpha)/2 ||beta||^2 +
+ * alpha ||beta||_1} pass A = X / sqrt(n), b = y / sqrt(n), lambda1 =
+ * lambda alpha, lambda2 = lambda (1 - alpha).
+ *
+ * Conventions for every entry point:
+ *   - Every function returns rac_status; nothing throws across the ABI.
+ *   - Pointers to caller data may be host or device pointers: the library
+ *     copies with cudaMemcpyDefault, which infers the direction from the
+ *     pointer (unified addressing).  Caller data is only read during the
+ *     call and never retained.
+ *   - Matrices are column-major with an explicit leading dimension.
+ *   - All work is enqueued on options.stream (a cudaStream_t, NULL = legacy
+ *     default stream); a call returns after the result has been copied out.
+ *   - Handles own all device memory they allocate; rac_admm_destroy frees it.
+ *   - A handle is not thread-safe: one caller thread at a time.
+ */
+#ifndef RAC_ADMM_H
+#define RAC_ADMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RAC_OK = 0,
+    RAC_ERR_ARG = 1,            /* invalid argument (sizes, pointers, options) */
+    RAC_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    RAC_ERR_OOM = 3,            /* device allocation failed */
+    RAC_ERR_NOT_PD = 4,         /* a block matrix failed Cholesky (Assumption 2.1 violated) */
+    RAC_ERR_NUMERIC = 5,        /* a non-finite value appeared in the iterates */
+    RAC_ERR_TIMEOUT = 6,        /* a bounded in-kernel wait gave up (grid barrier) */
+    RAC_ERR_NOT_CONVERGED = 7,  /* max_sweeps reached before KKT <= tol */
+    RAC_ERR_STATE = 8           /* checkpoint buffer does not match the handle */
+} rac_status;
+
+typedef enum { RAC_PHI_NONE = 0, RAC_PHI_L1L2 = 1, RAC_PHI_BOX = 2 } rac_phi;
+
+/* Storage precision of the data matrix A (and of G = A^T A in the Gram form).
+ * FP64: everything in double.  FP32 / BF16: A (or G) stored in that type with
+ * FP32 accumulation; iterates, duals, the anchor gradient and the periodic
+ * exact refresh stay in FP64 (see rac_options.refresh_every). */
+typedef enum { RAC_FP64 = 0, RAC_FP32 = 1, RAC_BF16 = 2 } rac_precision;
+
+/* How the block gradient is maintained during a sweep.
+ * GRAM: g = H x + c kept as an n-vector, updated by g += G[:, S] dx per block
+ *       (G = A^T A formed once at setup, or the caller's H).
+ * RESIDUAL: the block gradient is A_S^T r computed from an m-vector kept up to
+ *       date by r += A_S dx; block matrices A_S^T A_S are formed per sweep.
+ * AUTO: GRAM when n <= m (or H is given), RESIDUAL otherwise. */
+typedef enum { RAC_FORM_AUTO = 0, RAC_FORM_GRAM = 1, RAC_FORM_RESIDUAL = 2 } rac_form;
+
+/* The problem (eq. general_model restated in split form; see above). */
+typedef struct {
+    int64_t m, n;           /* A is m x n; n = number of primal coordinates */
+    const double *A;        /* m x n column-major, or NULL when H is given */
+    int64_t lda;            /* leading dimension of A, >= m */
+    const double *b;        /* m, or NULL (= 0) */
+    const double *H;        /* n x n symmetric PSD (column-major), or NULL */
+    const double *c;        /* n, or NULL (= 0): linear term added to the smooth part */
+    const double *E;        /* 1 x n coupling row, or NULL (k = 0) */
+    const double *d;        /* 1, right-hand side of E x = d (NULL = 0) */
+    int32_t k;              /* number of coupling rows: 0 or 1 */
+    int32_t phi;            /* rac_phi */
+    double lambda1, lambda2;/* l1l2 weights (>= 0) */
+    double lo, hi;          /* box bounds (lo < hi) */
+} rac_problem;
+
+/* Run parameters (the paper's s or p, beta, iterations and tolerance). */
+typedef struct {
+    int32_t num_blocks;     /* p, 1 <= p <= n; the first (n mod p) blocks get ceil(n/p) coordinates */
+    double beta;            /* penalty of E x = d (eq. lagrangian), > 0 */
+    double gamma;           /* penalty of x - z = 0 (Sec. 3.1); 0 means gamma = beta */
+    double tol;             /* stop when KKT(z) <= tol (KKT defined in rac_info) */
+    int32_t max_sweeps;     /* sweep cap per solve call */
+    int32_t refresh_every;  /* sweeps between exact FP64 refreshes + KKT checks (>= 1) */
+    uint64_t seed;          /* seed of the random assembly stream */
+    int32_t storage;        /* rac_precision */
+    int32_t form;           /* rac_form */
+    int32_t grid;           /* CTAs of the persistent sweep kernel; 0 = choose */
+    const double *x0;       /* optional warm start for x = z (n), or NULL */
+    const double *xi0;      /* optional warm start for the dual xi (n), or NULL */
+    void *stream;           /* cudaStream_t */
+} rac_options;
+
+/* KKT measure used for the stop test, evaluated in FP64 on z with the exact
+ * A (or H): with v = A^T (A z - b) + c - E^T mu,
+ *   none: |v_j|;  l1l2: |v_j + lambda2 z_j + lambda1 sign z_j| if z_j != 0,
+ *   else max(|v_j| - lambda1, 0);  box: |v_j| inside, max(-v_j,0) at lo,
+ *   max(v_j,0) at hi;
+ * kkt = max( max_j(.) / max(1, ||c - A^T b||_inf),  |E z - d| / max(1, ||z||_1) ). */
+typedef struct {
+    int32_t sweeps;         /* sweeps run by this call */
+    int64_t block_updates;  /* sweeps * p */
+    double kkt;             /* KKT of the returned z (see above) */
+    double primal_res;      /* ||x - z||_inf */
+    double mu;              /* coupling multiplier (0 when k = 0) */
+    double seconds;         /* wall time of the call */
+    int32_t status;         /* rac_status of this problem */
+    char form[32];          /* e.g. "gram/fp32" */
+} rac_info;
+
+typedef struct rac_handle rac_handle;
+
+/* Human-readable text for a status (static storage). */
+const char *rac_status_string(int32_t status);
+
+/* Fill *opt with defaults: p = 1, beta = 1, gamma = 0, tol = 1e-6,
+ * max_sweeps = 1000, refresh_every = 10, seed = 0, FP64, AUTO form. */
+rac_status rac_options_default(rac_options *opt);
+
+/* Copy and convert the problem into device buffers owned by a new handle,
+ * form G = A^T A if the Gram form is chosen, and set the iterates to the
+ * warm start (or zero).  *out receives the handle (NULL on failure). */
+rac_status rac_admm_setup(const rac_problem *prob, const rac_options *opt, rac_handle **out);
+
+/* Run sweeps from the handle's current state until KKT(z) <= tol (checked
+ * after every refresh_every sweeps) or max_sweeps sweeps; write z (n) to
+ * x_out (host or device) and fill *info.  Calling again continues from the
+ * state left by the previous call; the sweep counter (which selects the
+ * random assembly) continues too.  Returns RAC_ERR_NOT_CONVERGED (with x_out
+ * written) if the cap was hit. */
+rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *info);
+
+/* Reset the iterates to x = z = x0, xi = xi0, mu = 0 (NULL = zeros) and the
+ * sweep counter to 0. */
+rac_status rac_admm_reset(rac_handle *h, const double *x0, const double *xi0);
+
+/* Copy the current iterates (each n; NULL to skip) and mu (1) out. */
+rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, double *xi, double *mu);
+
+/* Solve `count` independent problems in one persistent launch (Sec. 3.2's
+ * SVM duals are the intended use).  All problems share opt except that
+ * problem i uses seed opt->seed + i and, when opt->num_blocks <= 0, blocks of
+ * at most -opt->num_blocks coordinates (p_i = ceil(n_i / -num_blocks)) with
+ * beta_i = gamma_i = 0.1 p_i (the paper's SVM rule) when opt->beta <= 0.
+ * Each problem must be in data form with m <= 4096.  x_out[i] receives z_i;
+ * infos[i] its info.  Returns the first non-OK per-problem status (or OK). */
+rac_status rac_admm_batch(int32_t count, const rac_problem *probs, const rac_options *opt,
+                          double *const *x_out, rac_info *infos);
+
+/* Regularisation path on the handle's problem (phi = l1l2, data form): solve
+ * for nlambda pairs (lambda1[i], lambda2[i]) together.  All points share the
+ * assembly stream, gamma and the block factors, so each block step is a
+ * multi-right-hand-side product.  Each point starts from the handle's warm
+ * start and stops on its own.  X_out is n x nlambda column-major (host or
+ * device); infos has nlambda entries. */
+rac_status rac_admm_path(rac_handle *h, int32_t nlambda, const double *lambda1,
+                         const double *lambda2, double *X_out, rac_info *infos);
+
+/* Serialise the iterates and the sweep counter.  Call with buf = NULL to
+ * query *len.  Restoring and continuing reproduces the uninterrupted run
+ * bit for bit (the assembly is counter-based and every reduction has a fixed
+ * order). */
+rac_status rac_admm_checkpoint(rac_handle *h, void *buf, size_t *len);
+rac_status rac_admm_restore(rac_handle *h, const void *buf, size_t len);
+
+/* Free the handle and its device memory (NULL is allowed). */
+void rac_admm_destroy(rac_handle *h);
+
+/* ---- component entry points (same kernels the solver runs) ------------- */
+
+/* Random assembly for sweeps sweep0 .. sweep0 + nsweeps - 1: perm_out
+ * (device, nsweeps x n int32, row per sweep) receives the permutation pi^k
+ * (the coordinates in ascending order of their Philox4x64-10 key, counter
+ * (j, k, 0, 0), key (seed, 0), ties by j) and blk_out (device, same shape,
+ * may be NULL) the block of each coordinate. */
+rac_status rac_assembly(int64_t n, int32_t num_blocks, uint64_t seed, int64_t sweep0,
+                        int32_t nsweeps, int32_t *perm_out, int32_t *blk_out, void *stream);
+
+/* Learned warm start (per-coordinate MLP, 6 -> 128 -> 128 -> 2). */
+#define RAC_WS_FEATURES 6
+#define RAC_WS_HIDDEN 128
+#define RAC_WS_OUT 2
+/* Number of float parameters of the network (W1,b1,W2,b2,W3,b3). */
+int64_t rac_ws_num_params(void);
+
+/* Per-coordinate features of a data-form problem (device pointers):
+ * F (n x 6 row-major, float) = [A_j^T b / ||A_j||, ||A_j||, lambda1/lambda_max,
+ * lambda2, |A_j^T b| / lambda1, log(n/m)], lambda_max = ||A^T b||_inf.
+ * Also writes lambda_max to *lam_max_out (host). */
+rac_status rac_ws_features(int64_t m, int64_t n, const double *A, int64_t lda,
+                           const double *b, double lambda1, double lambda2,
+                           float *F, double *lam_max_out, void *stream);
+
+/* Forward pass for N rows of features (device): out (N x 2 row-major) =
+ * [predicted x_j / (|A_j^T b| / ||A_j||^2 + eps) scale-free target, logit of
+ * p(active)].  params has rac_ws_num_params() floats (device). */
+rac_status rac_ws_forward(int64_t N, const float *F, const float *params, float *out,
+                          void *stream);
+
+/* One training step on N samples: loss = mean((out0 - t0)^2 * mask)
+ * + mean(BCE(out1, t1)); grads accumulated into grad (zeroed first), then one
+ * Adam step (lr, beta1, beta2, eps) at step count `step` (>= 1) updating
+ * params, m1, m2 (device, rac_ws_num_params() floats each).  *loss_out
+ * receives the loss (host). */
+rac_status rac_ws_train_step(int64_t N, const float *F, const float *T, float *params,
+                             float *grad, float *m1, float *m2, int32_t step, float lr,
+                             float beta1, float beta2, float eps, float *loss_out,
+                             void *stream);
+
+/* Gradient only (no Adam step): grad (device) receives d loss / d params and
+ * *loss_out the loss; used to check the backward kernels. */
+rac_status rac_ws_loss_grad(int64_t N, const float *F, const float *T, const float *params,
+                            float *grad, float *loss_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAC_ADMM_H */

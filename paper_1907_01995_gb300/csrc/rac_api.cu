@@ -1,0 +1,633 @@
+// rac_api.cu - host runtime and C-ABI of the RAC-MBADMM library.
+//
+// A handle owns device copies of the problem (FP64 A for the exact refresh,
+// plus the storage-precision G~ = A~^T A~ or slab-layout A~ for the sweeps),
+// the FP64 iterates (x, z, xi, mu) and the per-sweep buffers.  A solve call
+// runs "periods" of refresh_every sweeps; a period is one CUDA graph:
+//   assembly for all sweeps of the period (one launch, one CTA per sweep)
+//   per sweep: block factors (p CTAs) -> persistent block chain -> prox/dual
+//   exact FP64 refresh at z, KKT reduction, anchor reset
+// and the host reads the 48-byte statistics once per period.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "rac_device.cuh"
+#include "rac_internal.h"
+
+using namespace rac;
+
+#define RAC_CK(call)                                   \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return map_cuda(e_);    \
+    } while (0)
+#define RAC_ST(call)                                   \
+    do {                                               \
+        rac_status s_ = (call);                        \
+        if (s_ != RAC_OK) return s_;                   \
+    } while (0)
+
+static rac_status map_cuda(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RAC_ERR_OOM;
+    }
+    return RAC_ERR_CUDA;
+}
+
+struct rac_handle {
+    // problem
+    int m = 0, n = 0, k = 0, phi = 0;
+    double lam1 = 0, lam2 = 0, lo = 0, hi = 0, d = 0;
+    bool has_A = false;
+    // options
+    int p = 1;
+    double beta = 1, gamma = 1, tol = 1e-6;
+    int max_sweeps = 1000, refresh_every = 10;
+    uint64_t seed = 0;
+    int store = ST_F64;
+    bool gram = true;
+    int grid = 0;
+    cudaStream_t user = nullptr, st = nullptr;
+    cudaEvent_t ev = nullptr;
+    double kkt_scale = 1.0;
+    // device buffers
+    double *A64 = nullptr, *b64 = nullptr, *c64 = nullptr, *e64 = nullptr, *H64 = nullptr;
+    void *G = nullptr, *As = nullptr;
+    int R = 0, nslab = 0, nchunk = 1;
+    double *x = nullptr, *z = nullptr, *xi = nullptr, *mu = nullptr, *t = nullptr;
+    double *g = nullptr, *gdef = nullptr, *ga = nullptr, *dres = nullptr, *dx = nullptr;
+    double *gz = nullptr, *rbuf = nullptr, *rpart = nullptr;
+    void *W = nullptr, *cpart = nullptr;
+    GridBarrier *bar = nullptr;
+    int *err = nullptr;
+    DevStats *stats = nullptr;
+    DevStats *h_stats = nullptr;  // pinned
+    int *h_err = nullptr;         // pinned
+    int *perm = nullptr, *blk = nullptr, *tidx = nullptr;
+    uint64_t *tkey = nullptr;
+    int64_t *sweep_dev = nullptr;
+    int nslots = 0;
+    int64_t sweep = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+    bool use_graph = true;
+    std::vector<void *> allocs;
+    char form[32] = {0};
+
+    template <class T> rac_status alloc(T **p_, size_t count) {
+        void *q = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) return map_cuda(e);
+        allocs.push_back(q);
+        *p_ = (T *)q;
+        return RAC_OK;
+    }
+    ~rac_handle() {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+        for (void *q : allocs) cudaFree(q);
+        if (h_stats) cudaFreeHost(h_stats);
+        if (h_err) cudaFreeHost(h_err);
+        if (ev) cudaEventDestroy(ev);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+extern "C" const char *rac_status_string(int32_t s) {
+    switch (s) {
+    case RAC_OK: return "ok";
+    case RAC_ERR_ARG: return "invalid argument";
+    case RAC_ERR_CUDA: return "CUDA runtime error";
+    case RAC_ERR_OOM: return "out of device memory";
+    case RAC_ERR_NOT_PD: return "block matrix not positive definite";
+    case RAC_ERR_NUMERIC: return "non-finite value in the iterates";
+    case RAC_ERR_TIMEOUT: return "bounded in-kernel wait timed out";
+    case RAC_ERR_NOT_CONVERGED: return "sweep cap reached before KKT <= tol";
+    case RAC_ERR_STATE: return "checkpoint does not match the handle";
+    default: return "unknown status";
+    }
+}
+
+extern "C" rac_status rac_options_default(rac_options *o) {
+    if (!o) return RAC_ERR_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->num_blocks = 1;
+    o->beta = 1.0;
+    o->gamma = 0.0;
+    o->tol = 1e-6;
+    o->max_sweeps = 1000;
+    o->refresh_every = 10;
+    o->storage = RAC_FP64;
+    o->form = RAC_FORM_AUTO;
+    return RAC_OK;
+}
+
+// enter: the handle's private stream waits for the caller's stream
+static rac_status enter(rac_handle *h) {
+    RAC_CK(cudaEventRecord(h->ev, h->user));
+    RAC_CK(cudaStreamWaitEvent(h->st, h->ev, 0));
+    return RAC_OK;
+}
+
+static rac_status copy_in(void *dst, const double *src, size_t count, cudaStream_t st) {
+    if (!src) return RAC_OK;
+    RAC_CK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, st));
+    return RAC_OK;
+}
+
+// Exact FP64 refresh at z: gz = grad(z), KKT statistics, anchor reset,
+// t = E x - d.
+static rac_status enqueue_refresh(rac_handle *h) {
+    cudaStream_t st = h->st;
+    if (h->has_A) {
+        RAC_CK(launch_resid_f64(h->m, h->n, h->A64, h->m, h->z, h->b64, h->rbuf, h->rpart,
+                                h->nchunk, st));
+        RAC_CK(launch_gemvt_f64(h->m, h->n, h->A64, h->m, h->rbuf, h->c64, h->gz, st));
+    } else {
+        RAC_CK(launch_symv_f64(h->n, h->H64, h->z, h->c64, h->gz, st));
+    }
+    RAC_CK(launch_kkt(h->n, h->gz, h->x, h->z, h->e64, h->d, h->k ? h->mu : nullptr, h->phi,
+                      h->lam1, h->lam2, h->lo, h->hi, h->stats, st));
+    if (h->gram) {
+        RAC_CK(launch_gram_anchor(h->store, h->n, h->G, h->gz, h->x, h->z, h->g, st));
+    } else {
+        RAC_CK(cudaMemcpyAsync(h->ga, h->gz, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RAC_CK(launch_slab_anchor(h->store, h->n, h->nslab, h->R, h->As, h->x, h->z, h->dres, st));
+    }
+    if (h->k)
+        RAC_CK(cudaMemcpyAsync(h->t, &h->stats->ex_minus_d, sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+    return RAC_OK;
+}
+
+static ChainArgs chain_args(rac_handle *h, int slot) {
+    ChainArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = h->n;
+    a.p = h->p;
+    a.m = h->m;
+    a.perm = h->perm + (size_t)slot * h->n;
+    a.blk = h->blk + (size_t)slot * h->n;
+    a.W = h->W;
+    a.G = h->G;
+    a.As = h->As;
+    a.R = h->R;
+    a.nslab = h->nslab;
+    a.g = h->g;
+    a.gdef = h->gdef;
+    a.ga = h->ga;
+    a.dres = h->dres;
+    a.partials = h->cpart;
+    a.x = h->x;
+    a.z = h->z;
+    a.xi = h->xi;
+    a.dx = h->dx;
+    a.e = h->e64;
+    a.t = h->t;
+    a.mu = h->k ? h->mu : nullptr;
+    a.beta = h->beta;
+    a.gamma = h->gamma;
+    a.bar = h->bar;
+    a.err = h->err;
+    return a;
+}
+
+// One period of nb sweeps followed by the refresh (enqueued on h->st).
+static rac_status enqueue_period(rac_handle *h, int nb) {
+    cudaStream_t st = h->st;
+    RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, nb, h->perm, h->blk, h->tkey,
+                           h->tidx, st));
+    for (int s = 0; s < nb; ++s) {
+        ChainArgs a = chain_args(h, s);
+        RAC_CK(launch_factor(h->store, h->gram, a, h->W, nullptr, nullptr, h->err, st));
+        RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
+        RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
+        ProxArgs pa;
+        std::memset(&pa, 0, sizeof(pa));
+        pa.n = h->n;
+        pa.x = h->x;
+        pa.z = h->z;
+        pa.xi = h->xi;
+        pa.dx = h->dx;
+        pa.g = h->gram ? h->g : nullptr;
+        pa.gdef = h->gdef;
+        pa.mu = h->k ? h->mu : nullptr;
+        pa.t = h->k ? h->t : nullptr;
+        pa.phi = h->phi;
+        pa.lam1 = h->lam1;
+        pa.lam2 = h->lam2;
+        pa.lo = h->lo;
+        pa.hi = h->hi;
+        pa.beta = h->beta;
+        pa.gamma = h->gamma;
+        RAC_CK(launch_prox(pa, st));
+    }
+    RAC_ST(enqueue_refresh(h));
+    RAC_CK(launch_advance(h->sweep_dev, nb, st));
+    return RAC_OK;
+}
+
+static rac_status run_period(rac_handle *h, int nb) {
+    if (h->use_graph) {
+        auto it = h->graphs.find(nb);
+        if (it == h->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            bool ok = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) ==
+                      cudaSuccess;
+            rac_status s = ok ? enqueue_period(h, nb) : RAC_ERR_CUDA;
+            cudaError_t ce = cudaStreamEndCapture(h->st, &graph);
+            if (ok && s == RAC_OK && ce == cudaSuccess &&
+                cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+                h->graphs[nb] = exec;
+                cudaGraphDestroy(graph);
+            } else {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                h->use_graph = false;  // fall back to direct launches
+                return enqueue_period(h, nb);
+            }
+            it = h->graphs.find(nb);
+        }
+        RAC_CK(cudaGraphLaunch(it->second, h->st));
+        return RAC_OK;
+    }
+    return enqueue_period(h, nb);
+}
+
+struct HostStats {
+    double kkt, stat, feas, xz;
+    bool nonfinite;
+};
+
+static rac_status read_stats(rac_handle *h, HostStats *hs, int *dev_err) {
+    RAC_CK(cudaMemcpyAsync(h->h_stats, h->stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->st));
+    RAC_CK(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    RAC_CK(cudaStreamSynchronize(h->st));
+    const DevStats &s = *h->h_stats;
+    hs->stat = s.stat_max / h->kkt_scale;
+    hs->feas = h->k ? std::fabs(s.ez_minus_d) / std::max(1.0, s.znorm1) : 0.0;
+    hs->kkt = std::max(hs->stat, hs->feas);
+    hs->xz = s.xz_inf;
+    hs->nonfinite = s.nonfinite != 0.0 || !std::isfinite(hs->kkt);
+    *dev_err = *h->h_err;
+    return RAC_OK;
+}
+
+static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) {
+    cudaStream_t st = h->st;
+    size_t nb = (size_t)h->n * sizeof(double);
+    if (x0) {
+        RAC_CK(cudaMemcpyAsync(h->x, x0, nb, cudaMemcpyDefault, st));
+    } else {
+        RAC_CK(cudaMemsetAsync(h->x, 0, nb, st));
+    }
+    RAC_CK(cudaMemcpyAsync(h->z, h->x, nb, cudaMemcpyDeviceToDevice, st));
+    if (xi0) {
+        RAC_CK(cudaMemcpyAsync(h->xi, xi0, nb, cudaMemcpyDefault, st));
+    } else {
+        RAC_CK(cudaMemsetAsync(h->xi, 0, nb, st));
+    }
+    RAC_CK(cudaMemsetAsync(h->mu, 0, sizeof(double), st));
+    RAC_CK(cudaMemsetAsync(h->t, 0, sizeof(double), st));
+    RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
+    h->sweep = 0;
+    RAC_CK(cudaMemsetAsync(h->sweep_dev, 0, sizeof(int64_t), st));
+    RAC_ST(enqueue_refresh(h));
+    return RAC_OK;
+}
+
+static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_handle *h) {
+    h->m = (int)pr->m;
+    h->n = (int)pr->n;
+    h->k = pr->k;
+    h->phi = pr->phi;
+    h->lam1 = pr->lambda1;
+    h->lam2 = pr->lambda2;
+    h->lo = pr->lo;
+    h->hi = pr->hi;
+    h->has_A = pr->A != nullptr;
+    h->p = o->num_blocks;
+    h->beta = o->beta;
+    h->gamma = o->gamma > 0 ? o->gamma : o->beta;
+    h->tol = o->tol;
+    h->max_sweeps = o->max_sweeps;
+    h->refresh_every = std::max(1, o->refresh_every);
+    h->seed = o->seed;
+    h->store = o->storage;
+    h->user = (cudaStream_t)o->stream;
+    h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
+    RAC_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    RAC_CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+    RAC_ST(enter(h));
+    cudaStream_t st = h->st;
+    const int m = h->m, n = h->n;
+    // FP64 copies of the data
+    if (h->has_A) {
+        RAC_ST(h->alloc(&h->A64, (size_t)m * n));
+        RAC_CK(cudaMemcpy2DAsync(h->A64, (size_t)m * sizeof(double), pr->A,
+                                 (size_t)pr->lda * sizeof(double), (size_t)m * sizeof(double), n,
+                                 cudaMemcpyDefault, st));
+        RAC_ST(h->alloc(&h->b64, m));
+        if (pr->b) {
+            RAC_ST(copy_in(h->b64, pr->b, m, st));
+        } else {
+            RAC_CK(cudaMemsetAsync(h->b64, 0, m * sizeof(double), st));
+        }
+    } else {
+        RAC_ST(h->alloc(&h->H64, (size_t)n * n));
+        RAC_CK(cudaMemcpy2DAsync(h->H64, (size_t)n * sizeof(double), pr->H, (size_t)n * sizeof(double),
+                                 (size_t)n * sizeof(double), n, cudaMemcpyDefault, st));
+    }
+    if (pr->c) {
+        RAC_ST(h->alloc(&h->c64, n));
+        RAC_ST(copy_in(h->c64, pr->c, n, st));
+    }
+    if (h->k) {
+        RAC_ST(h->alloc(&h->e64, n));
+        RAC_ST(copy_in(h->e64, pr->E, n, st));
+        if (pr->d) {
+            RAC_CK(cudaMemcpyAsync(&h->d, pr->d, sizeof(double), cudaMemcpyDefault, st));
+            RAC_CK(cudaStreamSynchronize(st));
+        }
+    }
+    // work buffers
+    RAC_ST(h->alloc(&h->x, n));
+    RAC_ST(h->alloc(&h->z, n));
+    RAC_ST(h->alloc(&h->xi, n));
+    RAC_ST(h->alloc(&h->dx, n));
+    RAC_ST(h->alloc(&h->gz, n));
+    RAC_ST(h->alloc(&h->mu, 1));
+    RAC_ST(h->alloc(&h->t, 1));
+    RAC_ST(h->alloc(&h->err, 1));
+    RAC_ST(h->alloc(&h->stats, 1));
+    RAC_ST(h->alloc(&h->bar, 1));
+    RAC_ST(h->alloc(&h->sweep_dev, 1));
+    RAC_CK(cudaMallocHost(&h->h_stats, sizeof(DevStats)));
+    RAC_CK(cudaMallocHost(&h->h_err, sizeof(int)));
+    if (h->has_A) {
+        RAC_ST(h->alloc(&h->rbuf, m));
+        int sms = 148;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int rowblocks = (m + 255) / 256;
+        h->nchunk = std::max(1, std::min(n, (4 * sms + rowblocks - 1) / rowblocks));
+        RAC_ST(h->alloc(&h->rpart, (size_t)h->nchunk * m));
+    }
+    // the scale of the KKT measure: max(1, ||grad at 0||_inf)
+    {
+        std::vector<double> g0(n);
+        if (h->has_A) {
+            RAC_CK(cudaMemsetAsync(h->z, 0, n * sizeof(double), st));
+            RAC_CK(launch_resid_f64(m, n, h->A64, m, h->z, h->b64, h->rbuf, h->rpart, h->nchunk, st));
+            RAC_CK(launch_gemvt_f64(m, n, h->A64, m, h->rbuf, h->c64, h->gz, st));
+            RAC_CK(cudaMemcpyAsync(g0.data(), h->gz, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        } else if (h->c64) {
+            RAC_CK(cudaMemcpyAsync(g0.data(), h->c64, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        RAC_CK(cudaStreamSynchronize(st));
+        double mx = 0.0;
+        for (double v : g0) mx = std::max(mx, std::fabs(v));
+        h->kkt_scale = std::max(1.0, mx);
+    }
+    // storage-precision copy for the sweeps
+    const size_t sb = store_bytes(h->store);
+    if (h->gram) {
+        RAC_CK(cudaMalloc(&h->G, (size_t)n * n * sb));
+        h->allocs.push_back(h->G);
+        if (h->has_A) {
+            RAC_CK(launch_gram_build(h->store, m, n, h->A64, m, h->G, st));
+        } else {
+            RAC_CK(launch_sym_convert(h->store, n, h->H64, h->G, st));
+        }
+        RAC_ST(h->alloc(&h->g, n));
+        RAC_ST(h->alloc(&h->gdef, n));
+    } else {
+        h->R = slab_rows(h->store);
+        h->nslab = (m + h->R - 1) / h->R;
+        RAC_CK(cudaMalloc(&h->As, (size_t)h->nslab * n * h->R * sb));
+        h->allocs.push_back(h->As);
+        RAC_CK(launch_to_slab(h->store, m, n, h->A64, m, h->R, h->nslab, h->As, st));
+        RAC_ST(h->alloc(&h->ga, n));
+        RAC_ST(h->alloc(&h->dres, (size_t)h->nslab * h->R));
+    }
+    BlockLayout lay(n, h->p);
+    const size_t ta = h->store == ST_F64 ? 8 : 4;
+    RAC_CK(cudaMalloc(&h->W, lay.factor_total() * ta));
+    h->allocs.push_back(h->W);
+    // chain grid
+    size_t smem = 0;
+    int gmax = chain_max_grid(h->store, h->gram, lay.smax(), &smem);
+    if (gmax <= 0) return RAC_ERR_ARG;
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int want = h->gram ? std::min(sms, (n + 31) / 32) : std::min(sms, h->nslab);
+    if (o->grid > 0) want = o->grid;
+    h->grid = std::max(1, std::min(want, gmax));
+    if (!h->gram) {
+        RAC_CK(cudaMalloc(&h->cpart, (size_t)2 * h->grid * lay.smax() * ta));
+        h->allocs.push_back(h->cpart);
+    }
+    // assembly slots
+    h->nslots = h->refresh_every;
+    RAC_ST(h->alloc(&h->perm, (size_t)h->nslots * n));
+    RAC_ST(h->alloc(&h->blk, (size_t)h->nslots * n));
+    RAC_ST(h->alloc(&h->tidx, (size_t)h->nslots * n));
+    RAC_ST(h->alloc(&h->tkey, (size_t)h->nslots * n));
+    std::snprintf(h->form, sizeof(h->form), "%s/%s", h->gram ? "gram" : "residual",
+                  h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"));
+    RAC_ST(set_state(h, o->x0, o->xi0));
+    RAC_CK(cudaStreamSynchronize(st));
+    return RAC_OK;
+}
+
+extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o, rac_handle **out) {
+    if (!out) return RAC_ERR_ARG;
+    *out = nullptr;
+    if (!pr || !o) return RAC_ERR_ARG;
+    if (pr->n <= 0 || pr->n > (int64_t)1 << 30) return RAC_ERR_ARG;
+    if (!pr->A && !pr->H) return RAC_ERR_ARG;
+    if (pr->A && (pr->m <= 0 || pr->lda < pr->m || pr->m > (int64_t)1 << 30)) return RAC_ERR_ARG;
+    if (pr->k < 0 || pr->k > 1 || (pr->k == 1 && !pr->E)) return RAC_ERR_ARG;
+    if (pr->phi < RAC_PHI_NONE || pr->phi > RAC_PHI_BOX) return RAC_ERR_ARG;
+    if (pr->phi == RAC_PHI_L1L2 && (pr->lambda1 < 0 || pr->lambda2 < 0)) return RAC_ERR_ARG;
+    if (pr->phi == RAC_PHI_BOX && !(pr->lo < pr->hi)) return RAC_ERR_ARG;
+    if (o->num_blocks < 1 || o->num_blocks > pr->n) return RAC_ERR_ARG;
+    if (!(o->beta > 0) || o->gamma < 0 || !(o->tol >= 0) || o->max_sweeps < 0) return RAC_ERR_ARG;
+    if (o->storage < RAC_FP64 || o->storage > RAC_BF16) return RAC_ERR_ARG;
+    if (o->form == RAC_FORM_RESIDUAL && !pr->A) return RAC_ERR_ARG;
+    int64_t smax = (pr->n + o->num_blocks - 1) / o->num_blocks;
+    if (smax > 4096) return RAC_ERR_ARG;
+    rac_handle *h = new (std::nothrow) rac_handle();
+    if (!h) return RAC_ERR_OOM;
+    rac_status s = setup_impl(pr, o, h);
+    if (s != RAC_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return RAC_OK;
+}
+
+extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *info) {
+    if (!h) return RAC_ERR_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    RAC_ST(enter(h));
+    HostStats hs;
+    int dev_err = 0;
+    RAC_ST(read_stats(h, &hs, &dev_err));
+    int done = 0;
+    rac_status status = RAC_OK;
+    if (dev_err) status = (rac_status)dev_err;
+    while (status == RAC_OK && hs.kkt > h->tol && done < h->max_sweeps) {
+        int nb = std::min(h->refresh_every, h->max_sweeps - done);
+        RAC_ST(run_period(h, nb));
+        h->sweep += nb;
+        done += nb;
+        RAC_ST(read_stats(h, &hs, &dev_err));
+        if (dev_err) status = (rac_status)dev_err;
+        else if (hs.nonfinite) status = RAC_ERR_NUMERIC;
+    }
+    if (status == RAC_OK && hs.kkt > h->tol) status = RAC_ERR_NOT_CONVERGED;
+    if (x_out) {
+        RAC_CK(cudaMemcpyAsync(x_out, h->z, (size_t)h->n * sizeof(double), cudaMemcpyDefault, h->st));
+    }
+    double mu = 0.0;
+    if (h->k) RAC_CK(cudaMemcpyAsync(&mu, h->mu, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    RAC_CK(cudaStreamSynchronize(h->st));
+    if (info) {
+        info->sweeps = done;
+        info->block_updates = (int64_t)done * h->p;
+        info->kkt = hs.kkt;
+        info->primal_res = hs.xz;
+        info->mu = mu;
+        info->seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->status = status;
+        std::memcpy(info->form, h->form, sizeof(info->form));
+    }
+    return status;
+}
+
+extern "C" rac_status rac_admm_reset(rac_handle *h, const double *x0, const double *xi0) {
+    if (!h) return RAC_ERR_ARG;
+    RAC_ST(enter(h));
+    RAC_ST(set_state(h, x0, xi0));
+    RAC_CK(cudaStreamSynchronize(h->st));
+    return RAC_OK;
+}
+
+extern "C" rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, double *xi, double *mu) {
+    if (!h) return RAC_ERR_ARG;
+    RAC_ST(enter(h));
+    size_t nb = (size_t)h->n * sizeof(double);
+    if (x) RAC_CK(cudaMemcpyAsync(x, h->x, nb, cudaMemcpyDefault, h->st));
+    if (z) RAC_CK(cudaMemcpyAsync(z, h->z, nb, cudaMemcpyDefault, h->st));
+    if (xi) RAC_CK(cudaMemcpyAsync(xi, h->xi, nb, cudaMemcpyDefault, h->st));
+    if (mu) RAC_CK(cudaMemcpyAsync(mu, h->mu, sizeof(double), cudaMemcpyDefault, h->st));
+    RAC_CK(cudaStreamSynchronize(h->st));
+    return RAC_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+struct CkptHeader {
+    char magic[8];
+    int64_t n, sweep;
+    uint64_t seed;
+    int32_t p, k, store, gram;
+};
+
+extern "C" rac_status rac_admm_checkpoint(rac_handle *h, void *buf, size_t *len) {
+    if (!h || !len) return RAC_ERR_ARG;
+    size_t need = sizeof(CkptHeader) + (3 * (size_t)h->n + 1) * sizeof(double);
+    if (!buf) {
+        *len = need;
+        return RAC_OK;
+    }
+    if (*len < need) return RAC_ERR_ARG;
+    CkptHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, "RACKPT01", 8);
+    hd.n = h->n;
+    hd.sweep = h->sweep;
+    hd.seed = h->seed;
+    hd.p = h->p;
+    hd.k = h->k;
+    hd.store = h->store;
+    hd.gram = h->gram;
+    std::memcpy(buf, &hd, sizeof(hd));
+    double *body = (double *)((char *)buf + sizeof(hd));
+    RAC_ST(enter(h));
+    size_t nb = (size_t)h->n * sizeof(double);
+    RAC_CK(cudaMemcpyAsync(body, h->x, nb, cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(body + h->n, h->z, nb, cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(body + 2 * (size_t)h->n, h->xi, nb, cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(body + 3 * (size_t)h->n, h->mu, sizeof(double), cudaMemcpyDefault, h->st));
+    RAC_CK(cudaStreamSynchronize(h->st));
+    *len = need;
+    return RAC_OK;
+}
+
+extern "C" rac_status rac_admm_restore(rac_handle *h, const void *buf, size_t len) {
+    if (!h || !buf) return RAC_ERR_ARG;
+    size_t need = sizeof(CkptHeader) + (3 * (size_t)h->n + 1) * sizeof(double);
+    if (len < need) return RAC_ERR_STATE;
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "RACKPT01", 8) != 0 || hd.n != h->n || hd.p != h->p ||
+        hd.k != h->k || hd.seed != h->seed)
+        return RAC_ERR_STATE;
+    const double *body = (const double *)((const char *)buf + sizeof(hd));
+    RAC_ST(enter(h));
+    size_t nb = (size_t)h->n * sizeof(double);
+    // copy through a host staging buffer so `buf` may be pageable host memory
+    RAC_CK(cudaMemcpyAsync(h->x, body, nb, cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(h->z, body + h->n, nb, cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(h->xi, body + 2 * (size_t)h->n, nb, cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(h->mu, body + 3 * (size_t)h->n, sizeof(double), cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+    h->sweep = hd.sweep;
+    RAC_CK(cudaMemcpyAsync(h->sweep_dev, &h->sweep, sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
+    RAC_ST(enqueue_refresh(h));
+    RAC_CK(cudaStreamSynchronize(h->st));
+    return RAC_OK;
+}
+
+extern "C" void rac_admm_destroy(rac_handle *h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    delete h;
+}
+
+// ---------------------------------------------------------------- components
+extern "C" rac_status rac_assembly(int64_t n, int32_t p, uint64_t seed, int64_t sweep0,
+                                   int32_t nsweeps, int32_t *perm_out, int32_t *blk_out,
+                                   void *stream) {
+    if (n <= 0 || n > (int64_t)1 << 30 || p < 1 || p > n || nsweeps <= 0 || !perm_out)
+        return RAC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *tk = nullptr, *ti = nullptr;
+    RAC_CK(cudaMallocAsync(&tk, (size_t)nsweeps * n * sizeof(uint64_t), st));
+    cudaError_t e = cudaMallocAsync(&ti, (size_t)nsweeps * n * sizeof(int), st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(tk, st);
+        return map_cuda(e);
+    }
+    e = launch_assembly((int)n, p, seed, sweep0, nullptr, nsweeps, perm_out, blk_out,
+                        (uint64_t *)tk, (int *)ti, st);
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(ti, st);
+    if (e != cudaSuccess) return map_cuda(e);
+    RAC_CK(cudaStreamSynchronize(st));
+    return RAC_OK;
+}

@@ -1,0 +1,280 @@
+// rac_device.cuh - device helpers shared by the RAC-MBADMM kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "rac_internal.h"
+
+namespace rac {
+
+// ---------------------------------------------------------------- types
+template <class TS> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_f(double v) { return v; }
+
+template <class T> __device__ __forceinline__ T from_d(double v);
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
+    return __float2bfloat16_rn((float)v);
+}
+template <class T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ double from_f<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds of two 64x64->128 multiplies whose halves are mixed
+// with the other counter words and a Weyl-bumped key.
+__device__ __forceinline__ uint64_t philox_key_word0(uint64_t c0, uint64_t c1, uint64_t c2,
+                                                     uint64_t c3, uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; k1 += W1; }
+        uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return c0;
+}
+
+// Block layout of a sweep: the first (n mod p) blocks hold q+1 coordinates.
+struct BlockLayout {
+    int n, p, q, r;
+    __host__ __device__ BlockLayout(int n_, int p_) : n(n_), p(p_), q(n_ / p_), r(n_ % p_) {}
+    __host__ __device__ int size(int i) const { return q + (i < r ? 1 : 0); }
+    __host__ __device__ int offset(int i) const { return i * q + (i < r ? i : r); }
+    __host__ __device__ int block_of(int pos) const {
+        int big = r * (q + 1);
+        return pos < big ? pos / (q + 1) : r + (pos - big) / q;
+    }
+    // offset of block i's s x s factor in the packed factor buffer
+    __host__ __device__ size_t factor_offset(int i) const {
+        size_t b1 = (size_t)(q + 1) * (q + 1), b0 = (size_t)q * q;
+        return i < r ? (size_t)i * b1 : (size_t)r * b1 + (size_t)(i - r) * b0;
+    }
+    __host__ __device__ size_t factor_total() const { return factor_offset(p); }
+    __host__ __device__ int smax() const { return q + (r ? 1 : 0); }
+};
+
+// ---------------------------------------------------------------- errors
+__device__ __forceinline__ void set_err(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------- memory ops
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch.  The barrier word pair must be
+// zero at launch (the host memsets it before every launch); each CTA keeps
+// its own generation count.  The wait is bounded: after kBarrierTimeoutNs the
+// CTA records RAC_ERR_TIMEOUT and the call returns false, so the kernel can
+// return instead of hanging.
+constexpr uint64_t kBarrierTimeoutNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, unsigned nblocks, unsigned &gen,
+                                          int *err, int *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned target = gen + 1;
+        __threadfence();
+        unsigned prev = atomicAdd(&bar->count, 1u);
+        if (prev == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u32(&bar->gen, target);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_u32(&bar->gen) != target) {
+                if (*((volatile int *)err) == RAC_ERR_TIMEOUT ||
+                    globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                    set_err(err, RAC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        gen = target;
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// ---------------------------------------------------------------- reductions
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <class T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum with a fixed order (deterministic); `red` holds >= 32 T.
+template <class T> __device__ T block_sum(T v, T *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T tot = 0;
+    if (warp == 0) {
+        tot = lane < nw ? red[lane] : T(0);
+        tot = warp_sum(tot);
+        if (lane == 0) red[0] = tot;
+    }
+    __syncthreads();
+    tot = red[0];
+    __syncthreads();
+    return tot;
+}
+template <class T> __device__ T block_max(T v, T *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T tot = 0;
+    if (warp == 0) {
+        tot = lane < nw ? red[lane] : T(0);
+        tot = warp_max(tot);
+        if (lane == 0) red[0] = tot;
+    }
+    __syncthreads();
+    tot = red[0];
+    __syncthreads();
+    return tot;
+}
+
+// ---------------------------------------------------------------- prox
+// z-block closed forms (Sec. 3.1): soft-threshold / ridge scaling / box clip.
+__device__ __forceinline__ double prox_z(int phi, double x, double xi, double gamma,
+                                         double lam1, double lam2, double lo, double hi) {
+    if (phi == RAC_PHI_L1L2) {
+        double v = gamma * x - xi;
+        double a = fabs(v) - lam1;
+        return a > 0.0 ? copysign(a, v) / (lam2 + gamma) : 0.0;
+    }
+    double v = x - xi / gamma;
+    if (phi == RAC_PHI_BOX) return fmin(fmax(v, lo), hi);
+    return v;
+}
+
+// Per-coordinate stationarity residual of the KKT measure (see rac_admm.h).
+__device__ __forceinline__ double kkt_coord(int phi, double v, double z, double lam1, double lam2,
+                                            double lo, double hi) {
+    if (phi == RAC_PHI_L1L2) {
+        if (z != 0.0) return fabs(v + lam2 * z + (z > 0.0 ? lam1 : -lam1));
+        return fmax(fabs(v) - lam1, 0.0);
+    }
+    if (phi == RAC_PHI_BOX) {
+        if (z <= lo) return fmax(-v, 0.0);
+        if (z >= hi) return fmax(v, 0.0);
+        return fabs(v);
+    }
+    return fabs(v);
+}
+
+// ---------------------------------------------------------------- dense block factor
+// In-place Cholesky K = L L^T (lower, row-major s x s in M) followed by the
+// in-place triangular inverse W = L^{-1}, so a block solve K^{-1} v becomes
+// W^T (W v).  Executed by one CTA; `diag` is scratch of s entries.
+// A non-positive or non-finite pivot (Assumption 2.1 violated) records
+// RAC_ERR_NOT_PD and is replaced by 1 so the CTA stays well-defined.
+template <class TA>
+__device__ void chol_inverse_inplace(TA *M, int s, TA *diag, TA *tmp, int *err) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int k = 0; k < s; ++k) {
+        TA d = M[k * s + k];
+        bool bad = !(d > TA(0)) || !isfinite((double)d);
+        TA piv = bad ? TA(1) : sqrt(d);
+        if (threadIdx.x == 0) {
+            diag[k] = piv;
+            if (bad) set_err(err, RAC_ERR_NOT_PD);
+        }
+        for (int r = k + 1 + threadIdx.x; r < s; r += blockDim.x) M[r * s + k] /= piv;
+        __syncthreads();
+        for (int r = k + 1 + warp; r < s; r += nw) {
+            const TA lrk = M[r * s + k];
+            for (int c = k + 1 + lane; c <= r; c += 32) M[r * s + c] -= lrk * M[c * s + k];
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < s; k += blockDim.x) M[k * s + k] = diag[k];
+    __syncthreads();
+    // W = L^{-1}, column j from the right: W[j][j] = 1/L[j][j],
+    // W[r][j] = -(sum_{k=j+1..r} W[r][k] L[k][j]) / L[j][j]  for r > j.
+    for (int j = s - 1; j >= 0; --j) {
+        const TA wjj = TA(1) / M[j * s + j];
+        for (int r = j + 1 + warp; r < s; r += nw) {
+            TA acc = 0;
+            for (int k = j + 1 + lane; k <= r; k += 32) acc += M[r * s + k] * M[k * s + j];
+            acc = warp_sum(acc);
+            if (lane == 0) tmp[r] = acc;
+        }
+        __syncthreads();
+        for (int r = j + 1 + threadIdx.x; r < s; r += blockDim.x) M[r * s + j] = -tmp[r] * wjj;
+        if (threadIdx.x == 0) M[j * s + j] = wjj;
+        __syncthreads();
+    }
+    // zero the strict upper triangle so W can be read as a full matrix
+    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+        int r = idx / s, c = idx - r * s;
+        if (c > r) M[idx] = TA(0);
+    }
+    __syncthreads();
+}
+
+// delta = -W^T (W rhs) for one block, by one CTA.  W is s x s lower row-major.
+template <class TA>
+__device__ void block_solve(const TA *__restrict__ W, int s, const TA *rhs, TA *u, TA *delta) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int r = warp; r < s; r += nw) {
+        TA acc = 0;
+        const TA *wr = W + (size_t)r * s;
+        for (int c = lane; c <= r; c += 32) acc += wr[c] * rhs[c];
+        acc = warp_sum(acc);
+        if (lane == 0) u[r] = acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < s; c += blockDim.x) {
+        TA acc = 0;
+        for (int r = c; r < s; ++r) acc += W[(size_t)r * s + c] * u[r];
+        delta[c] = -acc;
+    }
+    __syncthreads();
+}
+
+}  // namespace rac

@@ -1,0 +1,105 @@
+// rac_internal.h - structures shared by the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/rac_admm.h"
+
+namespace rac {
+
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+};
+
+// Device-side statistics written by the refresh / KKT kernel.
+struct DevStats {
+    double stat_max;     // max_j stationarity residual (unscaled)
+    double znorm1;       // ||z||_1
+    double ez_minus_d;   // E z - d
+    double ex_minus_d;   // E x - d (exact, becomes the t anchor)
+    double xz_inf;       // ||x - z||_inf
+    double nonfinite;    // 1 if a non-finite value was seen
+};
+
+enum Store { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2 };
+
+// Arguments of the persistent sweep kernels (one instance, one rhs column).
+struct ChainArgs {
+    int n, p, m;
+    const int *perm;        // this sweep's permutation (n)
+    const int *blk;         // block id of each coordinate (n)
+    const void *W;          // packed L^{-1} factors (compute type)
+    const void *G;          // Gram form: n x n storage-type matrix (row-major = col-major)
+    const void *As;         // residual form: slab-layout copy of A
+    int R;                  // rows per slab
+    int nslab;
+    double *g;              // Gram form: current gradient (n)
+    double *gdef;           // Gram form: deferred own-block gradient increments (n)
+    const double *ga;       // residual form: anchor gradient (n)
+    double *dres;           // residual form: A~ (x - x_anchor) (nslab*R)
+    void *partials;         // residual form: [2][grid][smax] compute type
+    const double *x, *z, *xi;
+    double *dx;             // per-sweep increment of x (n)
+    const double *e;        // coupling row (n) or NULL
+    double *t;              // E x - d (in/out)
+    const double *mu;
+    double beta, gamma;
+    GridBarrier *bar;
+    int *err;
+};
+
+struct ProxArgs {
+    int n;
+    double *x, *z, *xi;
+    const double *dx;
+    double *g;              // Gram form: g += gdef
+    const double *gdef;
+    double *mu;
+    const double *t;
+    int phi;
+    double lam1, lam2, lo, hi, beta, gamma;
+};
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_assembly(int n, int p, uint64_t seed, int64_t sweep0, const int64_t *sweep_dev,
+                            int nsweeps, int *perm, int *blk, uint64_t *tkey, int *tidx,
+                            cudaStream_t st);
+cudaError_t launch_advance(int64_t *sweep_dev, int nb, cudaStream_t st);
+
+cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, const void *srcG,
+                          const void *srcAs, int *err, cudaStream_t st);
+
+cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cudaStream_t st);
+int chain_max_grid(int store, bool gram, int smax, size_t *smem_out);
+
+cudaError_t launch_prox(const ProxArgs &a, cudaStream_t st);
+
+// exact FP64 pieces of the refresh
+cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const double *z,
+                             const double *b, double *r, double *part, int nchunk,
+                             cudaStream_t st);
+cudaError_t launch_gemvt_f64(int m, int n, const double *A, int64_t lda, const double *r,
+                             const double *c, double *g, cudaStream_t st);
+cudaError_t launch_symv_f64(int n, const double *H, const double *z, const double *c, double *g,
+                            cudaStream_t st);
+cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z, const double *e,
+                       double d, const double *mu, int phi, double lam1, double lam2, double lo,
+                       double hi, DevStats *stats, cudaStream_t st);
+// anchor reset in the storage type: g = gz + G~ (x - z)  or  dres = A~ (x - z)
+cudaError_t launch_gram_anchor(int store, int n, const void *G, const double *gz,
+                               const double *x, const double *z, double *g, cudaStream_t st);
+cudaError_t launch_slab_anchor(int store, int n, int nslab, int R, const void *As,
+                               const double *x, const double *z, double *dres, cudaStream_t st);
+
+// setup
+cudaError_t launch_gram_build(int store, int m, int n, const double *A, int64_t lda, void *G,
+                              cudaStream_t st);
+cudaError_t launch_sym_convert(int store, int n, const double *H, void *G, cudaStream_t st);
+cudaError_t launch_to_slab(int store, int m, int n, const double *A, int64_t lda, int R,
+                           int nslab, void *As, cudaStream_t st);
+int slab_rows(int store);
+size_t store_bytes(int store);
+
+}  // namespace rac

@@ -1,0 +1,756 @@
+// rac_kernels.cu - the RAC-MBADMM sweep kernels for sm_103a.
+//
+// One sweep (eq. RAC-ADDM of Sec. 1, split form of Sec. 3.1):
+//   k_assembly   random assembly: Philox4x64-10 keys -> sorted permutation
+//   k_factor     K_S = H_SS + gamma I + beta E_S^T E_S, Cholesky, W_S = L_S^{-1},
+//                for all p blocks in parallel (K_S does not depend on the iterates)
+//   k_chain_*    the p block argmins in cyclic order (persistent cooperative
+//                kernel, one bounded grid barrier per block)
+//   k_prox       z-block closed form and the multiplier ascent
+// plus the exact FP64 refresh (r = A z - b, g = A^T r + c), the KKT reduction
+// and the setup conversions (Gram matrix, slab layout).
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "rac_device.cuh"
+#include "rac_internal.h"
+
+namespace rac {
+
+size_t store_bytes(int store) { return store == ST_F64 ? 8 : (store == ST_F32 ? 4 : 2); }
+int slab_rows(int store) { return 32 / (int)store_bytes(store); }
+
+// ======================================================================
+// Random assembly (Sec. 1 eq. RAC-ADDM, Sec. 2 sigma): one CTA per sweep.
+// Keys are bucketed by their top L bits (counting sort), then each element's
+// rank inside its bucket is counted, which reproduces the exact ascending
+// order of (key, j).
+// ======================================================================
+__device__ void block_exclusive_scan(unsigned *a, int len, unsigned *red) {
+    // each thread scans a contiguous chunk, then the chunk totals are scanned
+    const int T = blockDim.x;
+    const int per = (len + T - 1) / T;
+    const int b0 = threadIdx.x * per;
+    unsigned local = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < len) local += a[b0 + i];
+    // inclusive scan of `local` across the block (warp shuffles + smem)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (T + 31) >> 5;
+        unsigned w = lane < nw ? red[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) red[lane] = w;
+    }
+    __syncthreads();
+    unsigned excl = v - local + (warp ? red[warp - 1] : 0u);
+    __syncthreads();
+    for (int i = 0; i < per; ++i) {
+        if (b0 + i < len) {
+            unsigned c = a[b0 + i];
+            a[b0 + i] = excl;
+            excl += c;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_assembly(int n, int p, uint64_t seed, int64_t sweep0,
+                                                   const int64_t *sweep_dev, int *perm, int *blk,
+                                                   uint64_t *tkey, int *tidx, int L) {
+    if (sweep_dev) sweep0 += *sweep_dev;
+    extern __shared__ unsigned sm_u[];
+    const int nb = 1 << L;
+    unsigned *hist = sm_u, *start = sm_u + nb, *cur = sm_u + 2 * nb, *red = sm_u + 3 * nb;
+    const int slot = blockIdx.x;
+    const uint64_t k = (uint64_t)(sweep0 + slot);
+    int *P = perm + (size_t)slot * n;
+    int *B = blk ? blk + (size_t)slot * n : nullptr;
+    uint64_t *K = tkey + (size_t)slot * n;
+    int *I = tidx + (size_t)slot * n;
+    const int shift = 64 - L;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        uint64_t key = philox_key_word0((uint64_t)j, k, 0, 0, seed, 0);
+        int b = L ? (int)(key >> shift) : 0;
+        atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) start[i] = hist[i];
+    __syncthreads();
+    block_exclusive_scan(start, nb, red);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = start[i];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        uint64_t key = philox_key_word0((uint64_t)j, k, 0, 0, seed, 0);
+        int b = L ? (int)(key >> shift) : 0;
+        unsigned pos = atomicAdd(&cur[b], 1u);
+        K[pos] = key;
+        I[pos] = j;
+    }
+    __syncthreads();
+    BlockLayout lay(n, p);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t key = K[i];
+        const int j = I[i];
+        const int b = L ? (int)(key >> shift) : 0;
+        const unsigned lo = start[b], cnt = hist[b];
+        unsigned rank = 0;
+        for (unsigned q = lo; q < lo + cnt; ++q) {
+            uint64_t kq = K[q];
+            rank += (kq < key) || (kq == key && I[q] < j);
+        }
+        const int pos = (int)(lo + rank);
+        P[pos] = j;
+        if (B) B[j] = lay.block_of(pos);
+    }
+}
+
+cudaError_t launch_assembly(int n, int p, uint64_t seed, int64_t sweep0, const int64_t *sweep_dev,
+                            int nsweeps, int *perm, int *blk, uint64_t *tkey, int *tidx,
+                            cudaStream_t st) {
+    if (n <= 0 || nsweeps <= 0) return cudaSuccess;
+    int L = 0;
+    while (L < 11 && (1 << (L + 1)) * 4 <= n) ++L;  // about 4 keys per bucket, <= 2048 buckets
+    size_t smem = (size_t)(3 * (1 << L) + 32) * sizeof(unsigned);
+    k_assembly<<<nsweeps, 1024, smem, st>>>(n, p, seed, sweep0, sweep_dev, perm, blk, tkey, tidx,
+                                            L);
+    return cudaGetLastError();
+}
+
+__global__ void k_advance(int64_t *sweep_dev, int nb) { *sweep_dev += nb; }
+cudaError_t launch_advance(int64_t *sweep_dev, int nb, cudaStream_t st) {
+    k_advance<<<1, 1, 0, st>>>(sweep_dev, nb);
+    return cudaGetLastError();
+}
+
+// ======================================================================
+// Block factor: K_S = H_SS + gamma I + beta e_S e_S^T -> L_S -> W_S = L_S^{-1}.
+// H_SS is gathered from G (Gram form) or accumulated as A~_S^T A~_S from the
+// slab-layout copy (residual form).  One CTA per block of the sweep.
+// ======================================================================
+template <class TS, class TA, bool GRAM>
+__global__ void __launch_bounds__(256) k_factor(ChainArgs a, TA *Wout, int use_smem) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int i = blockIdx.x;
+    BlockLayout lay(a.n, a.p);
+    const int s = lay.size(i), off = lay.offset(i), smax = lay.smax();
+    int *idx = (int *)sm_raw;
+    TA *es = (TA *)(sm_raw + ((smax * sizeof(int) + 15) & ~15));
+    TA *diag = es + smax;
+    TA *tmp = diag + smax;
+    unsigned char *rest = (unsigned char *)(tmp + smax);
+    rest = (unsigned char *)(((uintptr_t)rest + 15) & ~(uintptr_t)15);
+    TS *tile = (TS *)rest;  // residual form: s x R slab tile
+    TA *M = use_smem ? (TA *)(rest + (GRAM ? 0 : (((size_t)smax * a.R * sizeof(TS) + 15) & ~15)))
+                     : Wout + lay.factor_offset(i);
+    TA *Mg = Wout + lay.factor_offset(i);
+    for (int t = threadIdx.x; t < s; t += blockDim.x) {
+        int j = a.perm[off + t];
+        idx[t] = j;
+        es[t] = a.e ? (TA)a.e[j] : TA(0);
+    }
+    __syncthreads();
+    const TA gam = (TA)a.gamma, bet = (TA)a.beta;
+    if (GRAM) {
+        const TS *G = (const TS *)a.G;
+        for (int ab = threadIdx.x; ab < s * s; ab += blockDim.x) {
+            int r = ab / s, c = ab - r * s;
+            TA v = (TA)to_f(G[(size_t)idx[r] * a.n + idx[c]]);
+            v += bet * es[r] * es[c];
+            if (r == c) v += gam;
+            M[ab] = v;
+        }
+    } else {
+        const TS *As = (const TS *)a.As;
+        const int R = a.R;
+        for (int ab = threadIdx.x; ab < s * s; ab += blockDim.x) M[ab] = TA(0);
+        for (int q = 0; q < a.nslab; ++q) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < s * R; t += blockDim.x) {
+                int aa = t / R, rr = t - aa * R;
+                tile[t] = As[((size_t)q * a.n + idx[aa]) * R + rr];
+            }
+            __syncthreads();
+            for (int ab = threadIdx.x; ab < s * s; ab += blockDim.x) {
+                int r = ab / s, c = ab - r * s;
+                if (c > r) continue;
+                TA acc = 0;
+                for (int rr = 0; rr < R; ++rr)
+                    acc += (TA)to_f(tile[r * R + rr]) * (TA)to_f(tile[c * R + rr]);
+                M[ab] += acc;
+            }
+        }
+        __syncthreads();
+        for (int ab = threadIdx.x; ab < s * s; ab += blockDim.x) {
+            int r = ab / s, c = ab - r * s;
+            if (c > r) continue;
+            TA v = M[ab] + bet * es[r] * es[c];
+            if (r == c) v += gam;
+            M[ab] = v;
+        }
+    }
+    __syncthreads();
+    chol_inverse_inplace<TA>(M, s, diag, tmp, a.err);
+    if (use_smem)
+        for (int ab = threadIdx.x; ab < s * s; ab += blockDim.x) Mg[ab] = M[ab];
+}
+
+template <class TS, class TA, bool GRAM>
+static cudaError_t factor_impl(const ChainArgs &a, void *Wout, cudaStream_t st) {
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    size_t head = ((smax * sizeof(int) + 15) & ~15) + 3 * smax * sizeof(TA) + 16;
+    size_t tileb = GRAM ? 0 : (((size_t)smax * a.R * sizeof(TS) + 15) & ~15);
+    size_t mb = (size_t)smax * smax * sizeof(TA);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int use_smem = (head + tileb + mb) <= (size_t)optin ? 1 : 0;
+    size_t smem = head + tileb + (use_smem ? mb : 0);
+    auto kern = k_factor<TS, TA, GRAM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.p, 256, smem, st>>>(a, (TA *)Wout, use_smem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, const void *,
+                          const void *, int *, cudaStream_t st) {
+    if (store == ST_F64)
+        return gram ? factor_impl<double, double, true>(a, Wout, st)
+                    : factor_impl<double, double, false>(a, Wout, st);
+    if (store == ST_F32)
+        return gram ? factor_impl<float, float, true>(a, Wout, st)
+                    : factor_impl<float, float, false>(a, Wout, st);
+    return gram ? factor_impl<__nv_bfloat16, float, true>(a, Wout, st)
+                : factor_impl<__nv_bfloat16, float, false>(a, Wout, st);
+}
+
+// ======================================================================
+// The block chain of one sweep (eq. RAC-ADDM: x_1 .. x_p in cyclic order).
+// Block i's argmin of the split augmented Lagrangian is
+//   dx_S = -K_S^{-1} (g_S - xi_S + gamma (x_S - z_S) + e_S (beta t - mu)),
+// with g the gradient of the smooth part at the current point and
+// t = E x - d.  Every CTA computes dx_S redundantly from W_S, so one grid
+// barrier per block suffices; the gradient update that block i+1 needs is
+// spread over all CTAs.
+// ======================================================================
+constexpr int kChainThreads = 256;
+
+template <class TA> struct ChainSmem {
+    static size_t bytes(int smax, int nwarps) {
+        return (size_t)smax * sizeof(int) + 3 * (size_t)smax * sizeof(TA) +
+               (size_t)nwarps * 32 * sizeof(TA) + 64 * sizeof(double) + 64;
+    }
+};
+
+// Gram form: g (n) is kept exact up to the storage rounding of G; block i
+// adds G[:, S_i] dx to every coordinate.  Coordinates of block i itself are
+// still being read by slower CTAs for this block's rhs, so their increment is
+// parked in gdef and folded in by k_prox.
+template <class TS, class TA>
+__global__ void __launch_bounds__(kChainThreads) k_chain_gram(ChainArgs a) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int *idx = (int *)sm_raw;
+    TA *rhs = (TA *)(sm_raw + (((size_t)smax * sizeof(int) + 15) & ~15));
+    TA *u = rhs + smax;
+    TA *dl = u + smax;
+    TA *wred = dl + smax;                   // nw x 32
+    double *dred = (double *)(((uintptr_t)(wred + nw * 32) + 15) & ~(uintptr_t)15);
+    __shared__ int s_flag;
+    const TS *G = (const TS *)a.G;
+    const TA *Wall = (const TA *)a.W;
+    const int n = a.n;
+    const double gamma = a.gamma, beta = a.beta;
+    const double mu = a.mu ? *a.mu : 0.0;
+    double t = a.e ? *a.t : 0.0;
+    unsigned gen = 0;
+    const int ntiles = (n + 31) >> 5;
+    for (int i = 0; i < a.p; ++i) {
+        const int s = lay.size(i), off = lay.offset(i);
+        for (int q = threadIdx.x; q < s; q += blockDim.x) {
+            const int j = a.perm[off + q];
+            idx[q] = j;
+            double r = __ldcg(a.g + j) - a.xi[j] + gamma * (a.x[j] - a.z[j]);
+            if (a.e) r += a.e[j] * (beta * t - mu);
+            rhs[q] = (TA)r;
+        }
+        __syncthreads();
+        block_solve<TA>(Wall + lay.factor_offset(i), s, rhs, u, dl);
+        if (a.e) {
+            double loc = 0.0;
+            for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[idx[q]] * (double)dl[q];
+            t += block_sum<double>(loc, dred);
+        }
+        if (blockIdx.x == 0)
+            for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[idx[q]] = (double)dl[q];
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int col = tile * 32 + lane;
+            TA acc = 0;
+            if (col < n) {
+#pragma unroll 4
+                for (int q = warp; q < s; q += nw)
+                    acc += (TA)to_f(G[(size_t)idx[q] * n + col]) * dl[q];
+            }
+            wred[warp * 32 + lane] = acc;
+            __syncthreads();
+            if (warp == 0) {
+                TA tot = 0;
+                for (int w = 0; w < nw; ++w) tot += wred[w * 32 + lane];
+                if (col < n) {
+                    if (a.blk[col] == i)
+                        a.gdef[col] = (double)tot;
+                    else
+                        a.g[col] = __ldcg(a.g + col) + (double)tot;
+                }
+            }
+            __syncthreads();
+        }
+        if (i + 1 < a.p)
+            if (!grid_sync(a.bar, gridDim.x, gen, a.err, &s_flag)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
+}
+
+// Residual form: each CTA owns a set of row slabs of A~ and the matching
+// entries of dres = A~ (x - x_anchor); the block gradient is
+// g_S = g_anchor,S + A~_S^T dres, reduced over CTAs through `partials`
+// (double-buffered by block parity).
+template <class TS, class TA>
+__global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    const int nw = blockDim.x >> 5;
+    int *idx = (int *)sm_raw;
+    TA *rhs = (TA *)(sm_raw + (((size_t)smax * sizeof(int) + 15) & ~15));
+    TA *u = rhs + smax;
+    TA *dl = u + smax;
+    TA *wred = dl + smax;
+    double *dred = (double *)(((uintptr_t)(wred + nw * 32) + 15) & ~(uintptr_t)15);
+    __shared__ int s_flag;
+    const TS *As = (const TS *)a.As;
+    const TA *Wall = (const TA *)a.W;
+    TA *part = (TA *)a.partials;
+    const int n = a.n, R = a.R, G = gridDim.x;
+    const double gamma = a.gamma, beta = a.beta;
+    const double mu = a.mu ? *a.mu : 0.0;
+    double t = a.e ? *a.t : 0.0;
+    unsigned gen = 0;
+    for (int i = 0; i < a.p; ++i) {
+        const int s = lay.size(i), off = lay.offset(i);
+        for (int q = threadIdx.x; q < s; q += blockDim.x) idx[q] = a.perm[off + q];
+        __syncthreads();
+        // partial A~_S^T dres over this CTA's slabs
+        TA *mypart = part + ((size_t)(i & 1) * G + blockIdx.x) * smax;
+        for (int q = threadIdx.x; q < s; q += blockDim.x) {
+            TA acc = 0;
+            const size_t col = (size_t)idx[q];
+            for (int sl = blockIdx.x; sl < a.nslab; sl += G) {
+                const TS *seg = As + ((size_t)sl * n + col) * R;
+                const double *dr = a.dres + (size_t)sl * R;
+                for (int rr = 0; rr < R; ++rr) acc += (TA)to_f(seg[rr]) * (TA)dr[rr];
+            }
+            mypart[q] = acc;
+        }
+        if (!grid_sync(a.bar, G, gen, a.err, &s_flag)) return;
+        const TA *pin = part + (size_t)(i & 1) * G * smax;
+        for (int q = threadIdx.x; q < s; q += blockDim.x) {
+            const int j = idx[q];
+            TA acc = 0;
+            for (int c = 0; c < G; ++c) acc += __ldcg(pin + (size_t)c * smax + q);
+            double r = a.ga[j] + (double)acc - a.xi[j] + gamma * (a.x[j] - a.z[j]);
+            if (a.e) r += a.e[j] * (beta * t - mu);
+            rhs[q] = (TA)r;
+        }
+        __syncthreads();
+        block_solve<TA>(Wall + lay.factor_offset(i), s, rhs, u, dl);
+        if (a.e) {
+            double loc = 0.0;
+            for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[idx[q]] * (double)dl[q];
+            t += block_sum<double>(loc, dred);
+        }
+        if (blockIdx.x == 0)
+            for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[idx[q]] = (double)dl[q];
+        // dres += A~_S dx on this CTA's slabs
+        const int myrows = ((a.nslab - blockIdx.x + G - 1) / G) * R;
+        for (int t2 = threadIdx.x; t2 < myrows; t2 += blockDim.x) {
+            const int sl = blockIdx.x + (t2 / R) * G, rr = t2 % R;
+            if (sl >= a.nslab) continue;
+            TA acc = 0;
+            for (int q = 0; q < s; ++q)
+                acc += (TA)to_f(As[((size_t)sl * n + idx[q]) * R + rr]) * dl[q];
+            a.dres[(size_t)sl * R + rr] += (double)acc;
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
+}
+
+template <class TS, class TA, bool GRAM>
+static cudaError_t chain_impl(const ChainArgs &a, int grid, cudaStream_t st) {
+    BlockLayout lay(a.n, a.p);
+    size_t smem = ChainSmem<TA>::bytes(lay.smax(), kChainThreads / 32);
+    void (*kern)(ChainArgs) = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kChainThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cudaStream_t st) {
+    if (store == ST_F64)
+        return gram ? chain_impl<double, double, true>(a, grid, st)
+                    : chain_impl<double, double, false>(a, grid, st);
+    if (store == ST_F32)
+        return gram ? chain_impl<float, float, true>(a, grid, st)
+                    : chain_impl<float, float, false>(a, grid, st);
+    return gram ? chain_impl<__nv_bfloat16, float, true>(a, grid, st)
+                : chain_impl<__nv_bfloat16, float, false>(a, grid, st);
+}
+
+template <class TS, class TA, bool GRAM>
+static int chain_grid_impl(int smax, size_t *smem_out) {
+    size_t smem = ChainSmem<TA>::bytes(smax, kChainThreads / 32);
+    void (*kern)(ChainArgs) = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChainThreads, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem_out) *smem_out = smem;
+    return per_sm * sms;
+}
+
+int chain_max_grid(int store, bool gram, int smax, size_t *smem_out) {
+    if (store == ST_F64)
+        return gram ? chain_grid_impl<double, double, true>(smax, smem_out)
+                    : chain_grid_impl<double, double, false>(smax, smem_out);
+    if (store == ST_F32)
+        return gram ? chain_grid_impl<float, float, true>(smax, smem_out)
+                    : chain_grid_impl<float, float, false>(smax, smem_out);
+    return gram ? chain_grid_impl<__nv_bfloat16, float, true>(smax, smem_out)
+                : chain_grid_impl<__nv_bfloat16, float, false>(smax, smem_out);
+}
+
+// ======================================================================
+// z-block and multiplier ascent (Sec. 3.1 closed form; eq. RAC-ADDM last line).
+// ======================================================================
+__global__ void k_prox(ProxArgs a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < a.n) {
+        double x = a.x[j] + a.dx[j];
+        if (a.g) a.g[j] += a.gdef[j];
+        double xi = a.xi[j];
+        double z = prox_z(a.phi, x, xi, a.gamma, a.lam1, a.lam2, a.lo, a.hi);
+        a.x[j] = x;
+        a.z[j] = z;
+        a.xi[j] = xi - a.gamma * (x - z);
+    }
+    if (j == 0 && a.mu && a.t) *a.mu = *a.mu - a.beta * (*a.t);
+}
+
+cudaError_t launch_prox(const ProxArgs &a, cudaStream_t st) {
+    k_prox<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ======================================================================
+// Exact FP64 refresh pieces.
+// ======================================================================
+// r = A z - b in two deterministic stages: column chunks -> partial rows.
+__global__ void k_resid_part(int m, int n, const double *__restrict__ A, int64_t lda,
+                             const double *__restrict__ z, double *part, int chunk) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j0 = blockIdx.y * chunk, j1 = min(n, j0 + chunk);
+    if (i >= m) return;
+    double acc = 0.0;
+    for (int j = j0; j < j1; ++j) acc += A[(size_t)j * lda + i] * z[j];
+    part[(size_t)blockIdx.y * m + i] = acc;
+}
+__global__ void k_resid_sum(int m, int nchunk, const double *part, const double *b, double *r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double acc = 0.0;
+    for (int c = 0; c < nchunk; ++c) acc += part[(size_t)c * m + i];
+    r[i] = acc - (b ? b[i] : 0.0);
+}
+cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const double *z,
+                             const double *b, double *r, double *part, int nchunk,
+                             cudaStream_t st) {
+    int chunk = (n + nchunk - 1) / nchunk;
+    int nc = (n + chunk - 1) / chunk;
+    dim3 g1((m + 255) / 256, nc);
+    k_resid_part<<<g1, 256, 0, st>>>(m, n, A, lda, z, part, chunk);
+    k_resid_sum<<<(m + 255) / 256, 256, 0, st>>>(m, nc, part, b, r);
+    return cudaGetLastError();
+}
+
+// g_j = A_j^T r + c_j : one warp per column.
+__global__ void k_gemvt_f64(int m, int n, const double *__restrict__ A, int64_t lda,
+                            const double *__restrict__ r, const double *c, double *g) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const double *aj = A + (size_t)j * lda;
+    double acc = 0.0;
+    for (int i = lane; i < m; i += 32) acc += aj[i] * r[i];
+    acc = warp_sum(acc);
+    if (lane == 0) g[j] = acc + (c ? c[j] : 0.0);
+}
+cudaError_t launch_gemvt_f64(int m, int n, const double *A, int64_t lda, const double *r,
+                             const double *c, double *g, cudaStream_t st) {
+    k_gemvt_f64<<<(n + 7) / 8, 256, 0, st>>>(m, n, A, lda, r, c, g);
+    return cudaGetLastError();
+}
+cudaError_t launch_symv_f64(int n, const double *H, const double *z, const double *c, double *g,
+                            cudaStream_t st) {
+    // symmetric H: row j is column j
+    k_gemvt_f64<<<(n + 7) / 8, 256, 0, st>>>(n, n, H, n, z, c, g);
+    return cudaGetLastError();
+}
+
+// KKT reduction on z (single CTA, fixed order).
+__global__ void __launch_bounds__(1024) k_kkt(int n, const double *gz, const double *x,
+                                              const double *z, const double *e, double d,
+                                              const double *mup, int phi, double lam1,
+                                              double lam2, double lo, double hi, DevStats *out) {
+    __shared__ double red[32];
+    const double mu = mup ? *mup : 0.0;
+    double smax = 0.0, z1 = 0.0, ez = 0.0, ex = 0.0, xz = 0.0, bad = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double zj = z[j], xj = x[j];
+        double v = gz[j] - (e ? e[j] * mu : 0.0);
+        double sj = kkt_coord(phi, v, zj, lam1, lam2, lo, hi);
+        if (!isfinite(sj) || !isfinite(xj)) bad = 1.0;
+        smax = fmax(smax, sj);
+        z1 += fabs(zj);
+        if (e) { ez += e[j] * zj; ex += e[j] * xj; }
+        xz = fmax(xz, fabs(xj - zj));
+    }
+    smax = block_max<double>(smax, red);
+    z1 = block_sum<double>(z1, red);
+    ez = block_sum<double>(ez, red);
+    ex = block_sum<double>(ex, red);
+    xz = block_max<double>(xz, red);
+    bad = block_max<double>(bad, red);
+    if (threadIdx.x == 0) {
+        out->stat_max = smax;
+        out->znorm1 = z1;
+        out->ez_minus_d = ez - d;
+        out->ex_minus_d = ex - d;
+        out->xz_inf = xz;
+        out->nonfinite = bad;
+    }
+}
+cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z, const double *e,
+                       double d, const double *mu, int phi, double lam1, double lam2, double lo,
+                       double hi, DevStats *stats, cudaStream_t st) {
+    k_kkt<<<1, 1024, 0, st>>>(n, gz, x, z, e, d, mu, phi, lam1, lam2, lo, hi, stats);
+    return cudaGetLastError();
+}
+
+// Anchor reset, Gram form: g = gz + G~ (x - z), one warp per row.
+template <class TS, class TA>
+__global__ void k_gram_anchor(int n, const TS *__restrict__ G, const double *gz, const double *x,
+                              const double *z, double *g) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const TS *row = G + (size_t)j * n;
+    TA acc = 0;
+    for (int k = lane; k < n; k += 32) acc += (TA)to_f(row[k]) * (TA)(x[k] - z[k]);
+    acc = warp_sum(acc);
+    if (lane == 0) g[j] = gz[j] + (double)acc;
+}
+cudaError_t launch_gram_anchor(int store, int n, const void *G, const double *gz,
+                               const double *x, const double *z, double *g, cudaStream_t st) {
+    dim3 gr((n + 7) / 8);
+    if (store == ST_F64)
+        k_gram_anchor<double, double><<<gr, 256, 0, st>>>(n, (const double *)G, gz, x, z, g);
+    else if (store == ST_F32)
+        k_gram_anchor<float, float><<<gr, 256, 0, st>>>(n, (const float *)G, gz, x, z, g);
+    else
+        k_gram_anchor<__nv_bfloat16, float>
+            <<<gr, 256, 0, st>>>(n, (const __nv_bfloat16 *)G, gz, x, z, g);
+    return cudaGetLastError();
+}
+
+// Anchor reset, residual form: dres = A~ (x - z) on the slab layout.  One
+// CTA per slab group; threads split the columns and reduce in fixed order.
+template <class TS, class TA>
+__global__ void __launch_bounds__(256) k_slab_anchor(int n, int nslab, int R,
+                                                     const TS *__restrict__ As,
+                                                     const double *x, const double *z,
+                                                     double *dres) {
+    __shared__ TA red[256];
+    const int sl = blockIdx.x;
+    const int per = 256 / R;                 // column lanes per row
+    const int rr = threadIdx.x % R, cl = threadIdx.x / R;
+    TA acc = 0;
+    for (int j = cl; j < n; j += per)
+        acc += (TA)to_f(As[((size_t)sl * n + j) * R + rr]) * (TA)(x[j] - z[j]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < R) {
+        TA tot = 0;
+        for (int c = 0; c < per; ++c) tot += red[c * R + threadIdx.x];
+        dres[(size_t)sl * R + threadIdx.x] = (double)tot;
+    }
+}
+cudaError_t launch_slab_anchor(int store, int n, int nslab, int R, const void *As,
+                               const double *x, const double *z, double *dres, cudaStream_t st) {
+    if (store == ST_F64)
+        k_slab_anchor<double, double><<<nslab, 256, 0, st>>>(n, nslab, R, (const double *)As, x,
+                                                             z, dres);
+    else if (store == ST_F32)
+        k_slab_anchor<float, float><<<nslab, 256, 0, st>>>(n, nslab, R, (const float *)As, x, z,
+                                                           dres);
+    else
+        k_slab_anchor<__nv_bfloat16, float>
+            <<<nslab, 256, 0, st>>>(n, nslab, R, (const __nv_bfloat16 *)As, x, z, dres);
+    return cudaGetLastError();
+}
+
+// ======================================================================
+// Setup conversions.
+// ======================================================================
+// G~ = A~^T A~ (A~ = A rounded to the storage type), 64x64 tiles of the
+// lower triangle, mirrored.  Accumulation in the compute type.
+template <class TS, class TA>
+__global__ void __launch_bounds__(256) k_gram_build(int m, int n, const double *__restrict__ A,
+                                                    int64_t lda, TS *G) {
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj > ti) return;
+    __shared__ TA sa[16][65], sb[16][65];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    TA acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+    const int i0 = ti * 64, j0 = tj * 64;
+    for (int k0 = 0; k0 < m; k0 += 16) {
+        for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+            int kk = t & 15, cc = t >> 4;
+            int row = k0 + kk;
+            double va = (row < m && i0 + cc < n) ? A[(size_t)(i0 + cc) * lda + row] : 0.0;
+            double vb = (row < m && j0 + cc < n) ? A[(size_t)(j0 + cc) * lda + row] : 0.0;
+            sa[kk][cc] = (TA)to_f(from_d<TS>(va));
+            sb[kk][cc] = (TA)to_f(from_d<TS>(vb));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            TA av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = sa[kk][ty + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) bv[v] = sb[kk][tx + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+            if (i < n && j < n) {
+                TS val = from_d<TS>((double)acc[u][v]);
+                G[(size_t)i * n + j] = val;
+                G[(size_t)j * n + i] = val;
+            }
+        }
+}
+cudaError_t launch_gram_build(int store, int m, int n, const double *A, int64_t lda, void *G,
+                              cudaStream_t st) {
+    int t = (n + 63) / 64;
+    dim3 gr(t, t);
+    if (store == ST_F64)
+        k_gram_build<double, double><<<gr, 256, 0, st>>>(m, n, A, lda, (double *)G);
+    else if (store == ST_F32)
+        k_gram_build<float, float><<<gr, 256, 0, st>>>(m, n, A, lda, (float *)G);
+    else
+        k_gram_build<__nv_bfloat16, float><<<gr, 256, 0, st>>>(m, n, A, lda, (__nv_bfloat16 *)G);
+    return cudaGetLastError();
+}
+
+template <class TS>
+__global__ void k_sym_convert(int64_t total, const double *H, TS *G) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < total) G[t] = from_d<TS>(H[t]);
+}
+cudaError_t launch_sym_convert(int store, int n, const double *H, void *G, cudaStream_t st) {
+    int64_t total = (int64_t)n * n;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    if (store == ST_F64)
+        k_sym_convert<double><<<blocks, 256, 0, st>>>(total, H, (double *)G);
+    else if (store == ST_F32)
+        k_sym_convert<float><<<blocks, 256, 0, st>>>(total, H, (float *)G);
+    else
+        k_sym_convert<__nv_bfloat16><<<blocks, 256, 0, st>>>(total, H, (__nv_bfloat16 *)G);
+    return cudaGetLastError();
+}
+
+// Slab layout: As[(q * n + j) * R + rr] = A[q * R + rr, j] (zero past row m),
+// so the R rows of one column inside slab q are one 32-byte sector.
+template <class TS>
+__global__ void k_to_slab(int m, int n, const double *__restrict__ A, int64_t lda, int R,
+                          int64_t total, TS *As) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int rr = (int)(t % R);
+    int64_t qj = t / R;
+    int j = (int)(qj % n);
+    int q = (int)(qj / n);
+    int row = q * R + rr;
+    As[t] = from_d<TS>(row < m ? A[(size_t)j * lda + row] : 0.0);
+}
+cudaError_t launch_to_slab(int store, int m, int n, const double *A, int64_t lda, int R,
+                           int nslab, void *As, cudaStream_t st) {
+    int64_t total = (int64_t)nslab * n * R;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    if (store == ST_F64)
+        k_to_slab<double><<<blocks, 256, 0, st>>>(m, n, A, lda, R, total, (double *)As);
+    else if (store == ST_F32)
+        k_to_slab<float><<<blocks, 256, 0, st>>>(m, n, A, lda, R, total, (float *)As);
+    else
+        k_to_slab<__nv_bfloat16><<<blocks, 256, 0, st>>>(m, n, A, lda, R, total,
+                                                         (__nv_bfloat16 *)As);
+    return cudaGetLastError();
+}
+
+}  // namespace rac

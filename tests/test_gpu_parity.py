@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Integer work (the random assembly) must be bit-exact.  FP64 iterates must
+match the oracle to 1e-10 relative over the first 50 sweeps; converged
+solutions must match the independent oracle solvers within the tolerance of
+their storage precision (FP64 1e-8, FP32 1e-5, BF16 1e-3 plus the support).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import rac_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1907_01995_gb300 import api  # noqa: E402
+from paper_1907_01995_gb300 import _lib  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max()) / max(1.0, float(np.abs(b).max()))
+
+
+# ------------------------------------------------------------------ assembly
+@pytest.mark.parametrize("n,p,seed,sweep0,ns", [
+    (1, 1, 0, 0, 1), (7, 3, 3, 2, 4), (100, 10, 0, 0, 3), (2000, 20, 0, 5, 10),
+    (4097, 13, 9, 1000, 3), (50000, 100, 0, 0, 2), (20000, 313, 77, 3, 2)])
+def test_assembly_bit_exact(n, p, seed, sweep0, ns):
+    perm, blk = api.assembly(n, p, seed, sweep0, ns)
+    perm, blk = perm.cpu().numpy(), blk.cpu().numpy()
+    for s in range(ns):
+        ref = O.random_permutation(n, seed, sweep0 + s)
+        assert np.array_equal(perm[s], ref)
+        bref = np.empty(n, dtype=np.int64)
+        for bi, S in enumerate(O.blocks_from_permutation(ref, p)):
+            bref[S] = bi
+        assert np.array_equal(blk[s], bref)
+
+
+# ------------------------------------------------------- FP64 iterate parity
+CASES = {
+    "lasso_gram": dict(m=57, n=43, p=5, phi="l1l2", form="gram"),
+    "lasso_residual": dict(m=57, n=43, p=5, phi="l1l2", form="residual"),
+    "en_wide_residual": dict(m=31, n=97, p=9, phi="l1l2", lam2=0.1, form="residual"),
+    "en_wide_gram": dict(m=31, n=97, p=9, phi="l1l2", lam2=0.1, form="gram"),
+    "regression_gram": dict(m=80, n=33, p=4, phi="none", form="gram"),
+    "svm_box_residual": dict(m=23, n=71, p=6, phi="box", coupling=True, form="residual",
+                             beta=0.6, gamma=0.6),
+    "svm_box_gram": dict(m=23, n=71, p=6, phi="box", coupling=True, form="gram",
+                         beta=0.6, gamma=0.6),
+    "coupled_l1_gamma_ne_beta": dict(m=40, n=29, p=3, phi="l1l2", coupling=True,
+                                     form="residual", beta=0.5, gamma=1.5),
+    "one_block": dict(m=30, n=12, p=1, phi="l1l2", form="gram"),
+    "singleton_blocks": dict(m=30, n=12, p=12, phi="l1l2", form="residual"),
+}
+
+
+def _instance(c, seed=3):
+    return synth.small_instance(seed, c["m"], c["n"], c["p"], phi=c["phi"],
+                                lam2=c.get("lam2", 0.0), coupling=c.get("coupling", False),
+                                beta=c.get("beta", 1.0), gamma=c.get("gamma", 1.0))
+
+
+def _handle(inst, form, storage="fp64", **kw):
+    return api.Handle(inst.A, inst.b, c=inst.c, E=None if inst.E is None else inst.E[0],
+                      d=inst.d, phi=inst.phi, lambda1=inst.lam1, lambda2=inst.lam2,
+                      lo=inst.lo, hi=inst.hi, num_blocks=inst.num_blocks, beta=inst.beta,
+                      gamma=inst.gamma, storage=storage, form=form, **kw)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_iterates_first_50_sweeps(name):
+    c = CASES[name]
+    inst = _instance(c)
+    P = O.problem_from_instance(inst)
+    ost = O.initial_state(P)
+    with _handle(inst, c["form"], tol=0.0, max_sweeps=1, refresh_every=1, seed=11) as h:
+        for k in range(50):
+            O.sweep(P, ost, inst.num_blocks, 11, inst.beta, inst.gamma)
+            _, info = h.solve()
+            assert info["sweeps"] == 1
+            st = h.state()
+            for key in ("x", "z", "xi"):
+                assert rel(st[key], getattr(ost, key)) <= 1e-10, (k, key)
+            if inst.E is not None:
+                assert abs(st["mu"] - ost.mu[0]) <= 1e-10 * max(1.0, abs(ost.mu[0]))
+
+
+@pytest.mark.parametrize("name", ["lasso_gram", "svm_box_residual", "en_wide_residual"])
+def test_fp64_periods_match_single_sweeps(name):
+    """50 sweeps in periods of 10 (one CUDA graph per period) equal the oracle."""
+    c = CASES[name]
+    inst = _instance(c, seed=5)
+    P = O.problem_from_instance(inst)
+    ost = O.initial_state(P)
+    for _ in range(50):
+        O.sweep(P, ost, inst.num_blocks, 2, inst.beta, inst.gamma)
+    with _handle(inst, c["form"], tol=0.0, max_sweeps=50, refresh_every=10, seed=2) as h:
+        _, info = h.solve()
+        st = h.state()
+    assert info["sweeps"] == 50
+    for key in ("x", "z", "xi"):
+        assert rel(st[key], getattr(ost, key)) <= 1e-10
+
+
+def test_h_form_matches_oracle():
+    rng = np.random.default_rng(0)
+    B = rng.normal(size=(40, 25))
+    H = B.T @ B
+    cvec = rng.normal(size=25)
+    P = O.Problem(H=H, q=cvec, phi="l1l2", lam1=0.5)
+    ost = O.initial_state(P)
+    for _ in range(30):
+        O.sweep(P, ost, 4, 0, 1.0, 1.0)
+    with api.Handle(H=H, c=cvec, phi="l1l2", lambda1=0.5, num_blocks=4, tol=0.0,
+                    max_sweeps=30, refresh_every=7) as h:
+        h.solve()
+        st = h.state()
+    assert rel(st["z"], ost.z) <= 1e-10
+
+
+# ------------------------------------------------------ converged solutions
+def test_regression_config_normal_equations():
+    """Linear regression 500 x 100, p = 10, beta = 1, KKT <= 1e-10 within 300
+    sweeps, equal to the normal-equation solution."""
+    inst = synth.regression_instance(0)
+    ref = O.normal_equations(inst.A, inst.b)
+    with api.Handle(inst.A, inst.b, phi="none", num_blocks=10, beta=1.0, tol=1e-10,
+                    max_sweeps=300, seed=0) as h:
+        z, info = h.solve()
+    assert info["status"] == 0 and info["kkt"] <= 1e-10
+    assert rel(z, ref) <= 1e-8
+    P = O.problem_from_instance(inst)
+    assert O.kkt(P, z)["kkt"] <= 2e-10
+
+
+@pytest.fixture(scope="module")
+def lasso_ref():
+    inst = synth.lasso_instance(0)
+    x = O.cd_enet(inst.A, inst.b, inst.lam1, 0.0, tol=1e-13)
+    return inst, x
+
+
+@pytest.mark.parametrize("storage,form,tol,bound", [
+    ("fp64", "gram", 1e-10, 1e-8), ("fp32", "gram", 1e-9, 1e-5),
+    ("fp64", "residual", 1e-10, 1e-8), ("fp32", "residual", 1e-9, 1e-5),
+    ("bf16", "residual", 1e-7, 1e-3), ("bf16", "gram", 1e-7, 1e-3)])
+def test_lasso_config_converged(lasso_ref, storage, form, tol, bound):
+    """LASSO 10000 x 2000 (lambda1 = 0.1 ||A^T b||_inf, p = 20): every storage
+    precision reaches the FP64 oracle's solution (coordinate descent to
+    1e-13) within its tolerance, with the same support."""
+    inst, ref = lasso_ref
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=inst.lam1, num_blocks=20, beta=1.0,
+                    tol=tol, max_sweeps=3000, refresh_every=10, storage=storage,
+                    form=form) as h:
+        z, info = h.solve()
+    assert info["status"] == 0, info
+    assert rel(z, ref) <= bound, (rel(z, ref), info)
+    assert np.array_equal(z != 0, ref != 0)
+    P = O.problem_from_instance(inst)
+    assert O.kkt(P, z)["kkt"] <= tol * 1.01 + 1e-15
+
+
+def test_svm_small_converged_matches_smo():
+    inst = synth.svm_instance(4, 300, 12, block=64)
+    Q = inst.A.T @ inst.A
+    y = inst.E[0]
+    a_smo = O.smo_svm(Q, y, 1.0, tol=1e-11)
+    with api.Handle(inst.A, inst.b, c=inst.c, E=y, d=inst.d, phi="box", lo=0.0, hi=1.0,
+                    num_blocks=inst.num_blocks, beta=inst.beta, tol=1e-8, max_sweeps=20000,
+                    refresh_every=20) as h:
+        a, info = h.solve()
+    assert info["status"] == 0, info
+    obj = lambda v: 0.5 * v @ Q @ v - v.sum()
+    assert abs(obj(a) - obj(a_smo)) <= 1e-6 * max(1.0, abs(obj(a_smo)))
+    assert rel(inst.A @ a, inst.A @ a_smo) <= 1e-4
+    P = O.problem_from_instance(inst)
+    assert O.kkt(P, a)["kkt"] <= 1e-8 * 1.01
+
+
+# ------------------------------------------------------- state and errors
+def test_checkpoint_restore_bitwise():
+    inst = _instance(CASES["svm_box_residual"], seed=8)
+    with _handle(inst, "residual", tol=0.0, max_sweeps=100, refresh_every=10, seed=4) as h:
+        h.solve()
+        full = h.state()
+    with _handle(inst, "residual", tol=0.0, max_sweeps=50, refresh_every=10, seed=4) as h:
+        h.solve()
+        blob = h.checkpoint()
+    with _handle(inst, "residual", tol=0.0, max_sweeps=50, refresh_every=10, seed=4) as h2:
+        h2.restore(blob)
+        h2.solve()
+        resumed = h2.state()
+    for key in ("x", "z", "xi"):
+        assert np.array_equal(full[key], resumed[key])
+    assert full["mu"] == resumed["mu"]
+
+
+def test_not_positive_definite_is_reported():
+    H = -np.eye(6)
+    with api.Handle(H=H, c=np.ones(6), phi="none", num_blocks=2, beta=0.5, tol=0.0,
+                    max_sweeps=2) as h:
+        with pytest.raises(_lib.RacError) as ei:
+            h.solve()
+    assert ei.value.status == _lib.RAC_ERR_NOT_PD
+
+
+def test_device_inputs_and_outputs():
+    """torch CUDA tensors in and out give the same result as host arrays."""
+    inst = _instance(CASES["lasso_gram"], seed=1)
+    A = torch.tensor(inst.A, device="cuda")
+    b = torch.tensor(inst.b, device="cuda")
+    out = torch.empty(inst.n, dtype=torch.float64, device="cuda")
+    kw = dict(phi="l1l2", lambda1=inst.lam1, num_blocks=inst.num_blocks, tol=0.0,
+              max_sweeps=20)
+    with api.Handle(A, b, **kw) as h:
+        h.solve(out)
+    with api.Handle(inst.A, inst.b, **kw) as h:
+        z, _ = h.solve()
+    assert np.array_equal(out.cpu().numpy(), z)

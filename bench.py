@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: time to KKT <= 1e-6 and block updates/s of RAC-MBADMM.
+
+Workload (one "step"): the LASSO problem A 10000 x 2000 (N(0,1) columns
+scaled to unit norm, x_true 5% nonzero +-U[1,3], noise 0.01, lambda1 =
+0.1 ||A^T b||_inf), p = 20 blocks, beta = gamma = 1, solved from a cold start
+to KKT <= 1e-6 -- setup from the resident FP64 A (storage conversion and the
+Gram matrix) plus every sweep, refresh and check.  The chosen form (picked by
+the autotuner among the mixed-precision forms) is timed, and the plain FP64
+GPU path is timed beside it on the same problem.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to KKT<=1e-6 & block updates/s, chosen form vs plain FP64 GPU path"
+WORKLOAD = dict(name="lasso_10000x2000_p20", m=10000, n=2000, p=20, lam_frac=0.1, tol=1e-6,
+                seed=0, refresh_every=10)
+CPU_SAMPLE_SECONDS = 12.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- CPU oracle leg
+_CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+import synth
+from oracle import rac_oracle as O
+w = %(w)r
+inst = synth.lasso_instance(w["seed"], m=w["m"], n=w["n"], num_blocks=w["p"], lam_frac=w["lam_frac"])
+P = O.problem_from_instance(inst)
+st = O.initial_state(P)
+budget = %(budget)r
+sweeps = 0
+t0 = time.perf_counter()
+while True:
+    O.sweep(P, st, w["p"], w["seed"], 1.0, 1.0)
+    sweeps += 1
+    el = time.perf_counter() - t0
+    if el >= budget or sweeps >= %(max_sweeps)d:
+        break
+print(json.dumps({"sweeps": sweeps, "seconds": el}))
+"""
+
+
+def cpu_oracle_sample(budget=CPU_SAMPLE_SECONDS, max_sweeps=500):
+    """Time the FP64 oracle (as it stands) on a bounded sample: whole sweeps of
+    the same LASSO workload, after its setup, on one host core."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = _CPU_SNIPPET % {"root": ROOT, "w": WORKLOAD, "budget": budget,
+                           "max_sweeps": max_sweeps}
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    bu = r["sweeps"] * WORKLOAD["p"]
+    return {"value": bu / r["seconds"], "unit": "block_updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d whole sweeps (%d block updates) of the LASSO 10000x2000 p=20 workload "
+                      "after setup, FP64 numpy/scipy, 1 thread, %.1f s"
+                      % (r["sweeps"], bu, r["seconds"])}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(max(1, args.warmup)):
+        cpu_oracle_sample(budget=2.0, max_sweeps=20)
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(budget=max(2.0, CPU_SAMPLE_SECONDS / max(1, args.steps)),
+                                      max_sweeps=200))
+    v = statistics.mean(s["value"] for s in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "block_updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * WORKLOAD["p"] / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "m": WORKLOAD["m"], "n": WORKLOAD["n"],
+                       "p": WORKLOAD["p"], "note": "FP64 CPU oracle, bounded sample per step"},
+            "cpu_baseline": {"value": v, "unit": "block_updates/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "block_updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", gpu_index], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.split(",") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def algorithmic_bytes(kclass, m, n, p, sb, ta, gram):
+    """Bytes one launch of a kernel class must move (one sweep / one refresh)."""
+    q, r = divmod(n, p)
+    fac = r * (q + 1) ** 2 + (p - r) * q ** 2           # sum_i s_i^2
+    if kclass == "chain":
+        if gram:   # every row of G once, the p factors, 4 state vectors in, 3 out
+            return n * n * sb + fac * ta + 7 * n * 8
+        return 2 * m * n * sb + fac * ta + 7 * n * 8    # the slab copy of A twice
+    if kclass == "factor":
+        return (fac * sb + fac * ta) if gram else (p * m * (n // p + 1) * sb + fac * ta)
+    if kclass == "refresh":
+        return 2 * m * n * 8 + (n * n * sb if gram else m * n * sb)
+    if kclass == "prox":
+        return 8 * n * 8
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    from paper_1907_01995_gb300 import autotune
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_index = vis.split(",")[local] if vis and vis.split(",")[0].isdigit() else str(local)
+
+    w = WORKLOAD
+    inst = synth.lasso_instance(w["seed"], m=w["m"], n=w["n"], num_blocks=w["p"],
+                                lam_frac=w["lam_frac"])
+    A = torch.tensor(inst.A, device=dev)            # column-major copy below
+    A = A.t().contiguous().t()
+    b = torch.tensor(inst.b, device=dev)
+    common = dict(phi="l1l2", lambda1=inst.lam1, num_blocks=w["p"], beta=1.0, tol=w["tol"],
+                  max_sweeps=5000, refresh_every=w["refresh_every"], seed=w["seed"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run(storage, form, profile=False, **extra):
+        kw = dict(common)
+        kw.update(extra)
+        with api.Handle(A, b, storage=storage, form=form, profile=profile, **kw) as h:
+            z, info = h.solve()
+        return z, info
+
+    # autotuner: the chosen mixed-precision form (cached per workload)
+    choice = autotune.choose(A, b, common, key=w["name"], device=dev)
+    storage, form, grid = choice["storage"], choice["form"], choice["grid"]
+
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        run(storage, form, grid=grid)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(gpu_index)
+    step_ms, infos = [], []
+    for _ in range(args.steps):
+        flush.zero_()                                  # L2 flush between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        _, info = run(storage, form, profile=True, grid=grid)
+        e1.record(st)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    clocks = clk.stop()
+    total_ms = sum(step_ms)
+    bu = sum(i["block_updates"] for i in infos)
+    if world > 1:
+        t = torch.tensor([total_ms, float(bu)], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, bu_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_max, bu_all = total_ms, float(bu)
+    value = bu_all / (total_ms_max / 1000.0)
+
+    # plain FP64 GPU path on the same problem (same solve, FP64 storage, best FP64 form)
+    fp64_ms, fp64_info = [], None
+    run("fp64", "gram")
+    for _ in range(args.fp64_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        _, fp64_info = run("fp64", "gram")
+        e1.record(st)
+        torch.cuda.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+
+    # end to end through the C-ABI with pinned host buffers
+    A_h = torch.empty((w["n"], w["m"]), dtype=torch.float64, pin_memory=True)
+    A_h.copy_(torch.from_numpy(np.ascontiguousarray(inst.A.T)))
+    A_h = A_h.t()                                      # column-major host view
+    b_h = torch.from_numpy(inst.b.copy()).pin_memory()
+    z_h = torch.empty(w["n"], dtype=torch.float64, pin_memory=True)
+    e2e_s, e2e_bu, e2e_info = [], 0, None
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with api.Handle(A_h, b_h, storage=storage, form=form, grid=grid, **common) as h:
+            _, e2e_info = h.solve(z_h)
+        e2e_s.append(time.perf_counter() - t0)
+        e2e_bu += e2e_info["block_updates"]
+    periods = math.ceil(e2e_info["sweeps"] / w["refresh_every"]) + 1
+
+    # roofline of the dominant kernel class, from the live event timings
+    sb = {"fp64": 8, "fp32": 4, "bf16": 2}[storage]
+    ta = 8 if storage == "fp64" else 4
+    gram = infos[-1]["form"].startswith("gram")
+    cls_ms = {c: sum(i["t_%s_ms" % c] for i in infos) for c in
+              ("assembly", "factor", "chain", "prox", "refresh")}
+    launches = {"chain": sum(i["chain_launches"] for i in infos)}
+    launches["factor"] = launches["prox"] = launches["chain"]
+    launches["refresh"] = sum(math.ceil(i["sweeps"] / w["refresh_every"]) for i in infos)
+    dom = max(("factor", "chain", "prox", "refresh"), key=lambda c: cls_ms[c])
+    per_launch_ms = cls_ms[dom] / max(1, launches[dom])
+    abytes = algorithmic_bytes(dom, w["m"], w["n"], w["p"], sb, ta, gram)
+    achieved = abytes / (per_launch_ms / 1000.0) / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tj = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1907_01995_gb300", "csrc", "rac_kernels.cu"),
+                   "rb").read()
+        ent = tj.get("%s/%s/%s" % (dom, storage, "gram" if gram else "residual"))
+        if ent and ent.get("source_sha256") == hashlib.sha256(src).hexdigest():
+            traffic = ent["bytes_per_launch"]
+    except Exception:
+        traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_oracle_sample()
+        except Exception as ex:  # report, never fake
+            cpu = {"value": None, "unit": "block_updates/s", "cores": 1, "kind": "oracle",
+                   "sample": "failed: %s" % str(ex)[:200]}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        ttk = statistics.mean(step_ms)
+        f64 = statistics.mean(fp64_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": "block_updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ttk,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "p": w["p"],
+                       "lambda1": "0.1*||A^T b||_inf", "tol": w["tol"],
+                       "form": infos[-1]["form"], "grid": grid,
+                       "anchor": "FP64 refresh every %d sweeps" % w["refresh_every"],
+                       "l2": "512 MB buffer written between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_kkt_ms": ttk, "sweeps": infos[-1]["sweeps"], "kkt": infos[-1]["kkt"],
+            "fp64_plain": {"time_to_kkt_ms": f64, "sweeps": fp64_info["sweeps"],
+                           "block_updates_per_s": fp64_info["block_updates"] / (f64 / 1000.0),
+                           "form": fp64_info["form"], "kkt": fp64_info["kkt"]},
+            "speedup_vs_fp64_plain": f64 / ttk,
+            "kernel_ms_per_step": {c: v / len(infos) for c, v in cls_ms.items()},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": abytes,
+                         "launch_ms": per_launch_ms, "peak_source": "measured hbm_gbs"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_bu / sum(e2e_s), "unit": "block_updates/s",
+                    "time_to_kkt_ms": 1000.0 * statistics.mean(e2e_s),
+                    "h2d_bytes_per_step": (w["m"] * w["n"] + w["m"]) * 8,
+                    "d2h_bytes_per_step": w["n"] * 8 + periods * 52},
+            "clocks": clocks,
+            "gpu_launches": sum(i["kernel_launches"] + i["setup_launches"] for i in infos),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -109,6 +109,7 @@ typedef struct {
     const double *x0;       /* optional warm start for x = z (n), or NULL */
     const double *xi0;      /* optional warm start for the dual xi (n), or NULL */
     void *stream;           /* cudaStream_t */
+    int32_t profile;        /* 1: time each kernel class with CUDA events (rac_info.t_*) */
 } rac_options;
 
 /* KKT measure used for the stop test, evaluated in FP64 on z with the exact
@@ -126,6 +127,12 @@ typedef struct {
     double seconds;         /* wall time of the call */
     int32_t status;         /* rac_status of this problem */
     char form[32];          /* e.g. "gram/fp32" */
+    int64_t kernel_launches;/* kernels this call launched (graph replays included) */
+    int64_t setup_launches; /* kernels rac_admm_setup launched for this handle */
+    /* with rac_options.profile = 1: device time of each kernel class over the
+     * call, measured by CUDA events on the handle's stream (0 otherwise) */
+    double t_assembly_ms, t_factor_ms, t_chain_ms, t_prox_ms, t_refresh_ms;
+    int64_t chain_launches; /* launches of the sweep-chain kernel in this call */
 } rac_info;
 
 typedef struct rac_handle rac_handle;

@@ -35,13 +35,16 @@ class RacOptions(ctypes.Structure):
     _fields_ = [("num_blocks", c_int32), ("beta", c_double), ("gamma", c_double),
                 ("tol", c_double), ("max_sweeps", c_int32), ("refresh_every", c_int32),
                 ("seed", c_uint64), ("storage", c_int32), ("form", c_int32), ("grid", c_int32),
-                ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p)]
+                ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p), ("profile", c_int32)]
 
 
 class RacInfo(ctypes.Structure):
     _fields_ = [("sweeps", c_int32), ("block_updates", c_int64), ("kkt", c_double),
                 ("primal_res", c_double), ("mu", c_double), ("seconds", c_double),
-                ("status", c_int32), ("form", ctypes.c_char * 32)]
+                ("status", c_int32), ("form", ctypes.c_char * 32),
+                ("kernel_launches", c_int64), ("setup_launches", c_int64),
+                ("t_assembly_ms", c_double), ("t_factor_ms", c_double), ("t_chain_ms", c_double),
+                ("t_prox_ms", c_double), ("t_refresh_ms", c_double), ("chain_launches", c_int64)]
 
 
 P = ctypes.POINTER

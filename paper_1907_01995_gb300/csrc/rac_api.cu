@@ -78,7 +78,15 @@ struct rac_handle {
     int nslots = 0;
     int64_t sweep = 0;
     std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, int64_t> graph_launches;
     bool use_graph = true;
+    // kernel launch accounting and optional per-class event timing
+    int64_t nlaunch = 0, setup_launches = 0;
+    bool profile = false;
+    std::vector<cudaEvent_t> pev;   // 3 + 4 * refresh_every events, reused per period
+    int prof_nb = 0;
+    double t_asm = 0, t_fac = 0, t_chain = 0, t_prox = 0, t_ref = 0;
+    int64_t chain_launches = 0;
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -93,6 +101,7 @@ struct rac_handle {
     }
     ~rac_handle() {
         for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+        for (cudaEvent_t e : pev) cudaEventDestroy(e);
         for (void *q : allocs) cudaFree(q);
         if (h_stats) cudaFreeHost(h_stats);
         if (h_err) cudaFreeHost(h_err);
@@ -147,6 +156,7 @@ static rac_status copy_in(void *dst, const double *src, size_t count, cudaStream
 // t = E x - d.
 static rac_status enqueue_refresh(rac_handle *h) {
     cudaStream_t st = h->st;
+    h->nlaunch += (h->has_A ? 3 : 1) + 2;
     if (h->has_A) {
         RAC_CK(launch_resid_f64(h->m, h->n, h->A64, h->m, h->z, h->b64, h->rbuf, h->rpart,
                                 h->nchunk, st));
@@ -203,13 +213,21 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
 // One period of nb sweeps followed by the refresh (enqueued on h->st).
 static rac_status enqueue_period(rac_handle *h, int nb) {
     cudaStream_t st = h->st;
+    const bool pf = h->profile;
+    if (pf) RAC_CK(cudaEventRecord(h->pev[0], st));
     RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, nb, h->perm, h->blk, h->tkey,
                            h->tidx, st));
+    if (pf) RAC_CK(cudaEventRecord(h->pev[1], st));
+    h->nlaunch += 1 + 3 * (int64_t)nb + 1;
     for (int s = 0; s < nb; ++s) {
         ChainArgs a = chain_args(h, s);
+        cudaEvent_t *ev = pf ? &h->pev[3 + 4 * s] : nullptr;
+        if (pf) RAC_CK(cudaEventRecord(ev[0], st));
         RAC_CK(launch_factor(h->store, h->gram, a, h->W, nullptr, nullptr, h->err, st));
+        if (pf) RAC_CK(cudaEventRecord(ev[1], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
+        if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         ProxArgs pa;
         std::memset(&pa, 0, sizeof(pa));
         pa.n = h->n;
@@ -229,10 +247,32 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         pa.beta = h->beta;
         pa.gamma = h->gamma;
         RAC_CK(launch_prox(pa, st));
+        if (pf) RAC_CK(cudaEventRecord(ev[3], st));
     }
     RAC_ST(enqueue_refresh(h));
     RAC_CK(launch_advance(h->sweep_dev, nb, st));
+    if (pf) RAC_CK(cudaEventRecord(h->pev[2], st));
     return RAC_OK;
+}
+
+// Accumulate the event timings of the period that just completed.
+static void collect_profile(rac_handle *h, int nb) {
+    if (!h->profile) return;
+    auto el = [](cudaEvent_t a, cudaEvent_t b) {
+        float ms = 0.f;
+        return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : 0.0;
+    };
+    h->t_asm += el(h->pev[0], h->pev[1]);
+    cudaEvent_t last = h->pev[1];
+    for (int s = 0; s < nb; ++s) {
+        cudaEvent_t *ev = &h->pev[3 + 4 * s];
+        h->t_fac += el(ev[0], ev[1]);
+        h->t_chain += el(ev[1], ev[2]);
+        h->t_prox += el(ev[2], ev[3]);
+        last = ev[3];
+    }
+    h->t_ref += el(last, h->pev[2]);
+    h->chain_launches += nb;
 }
 
 static rac_status run_period(rac_handle *h, int nb) {
@@ -243,7 +283,10 @@ static rac_status run_period(rac_handle *h, int nb) {
             cudaGraphExec_t exec = nullptr;
             bool ok = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) ==
                       cudaSuccess;
+            int64_t before = h->nlaunch;
             rac_status s = ok ? enqueue_period(h, nb) : RAC_ERR_CUDA;
+            h->graph_launches[nb] = h->nlaunch - before;
+            h->nlaunch = before;
             cudaError_t ce = cudaStreamEndCapture(h->st, &graph);
             if (ok && s == RAC_OK && ce == cudaSuccess &&
                 cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
@@ -253,11 +296,13 @@ static rac_status run_period(rac_handle *h, int nb) {
                 if (graph) cudaGraphDestroy(graph);
                 cudaGetLastError();
                 h->use_graph = false;  // fall back to direct launches
+                h->nlaunch = before;
                 return enqueue_period(h, nb);
             }
             it = h->graphs.find(nb);
         }
         RAC_CK(cudaGraphLaunch(it->second, h->st));
+        h->nlaunch += h->graph_launches[nb];
         return RAC_OK;
     }
     return enqueue_period(h, nb);
@@ -324,9 +369,14 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->seed = o->seed;
     h->store = o->storage;
     h->user = (cudaStream_t)o->stream;
+    h->profile = o->profile != 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     RAC_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
     RAC_CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+    if (h->profile) {
+        h->pev.resize(3 + 4 * (size_t)h->refresh_every, nullptr);
+        for (auto &e : h->pev) RAC_CK(cudaEventCreate(&e));
+    }
     RAC_ST(enter(h));
     cudaStream_t st = h->st;
     const int m = h->m, n = h->n;
@@ -388,6 +438,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         std::vector<double> g0(n);
         if (h->has_A) {
             RAC_CK(cudaMemsetAsync(h->z, 0, n * sizeof(double), st));
+            h->nlaunch += 3;
             RAC_CK(launch_resid_f64(m, n, h->A64, m, h->z, h->b64, h->rbuf, h->rpart, h->nchunk, st));
             RAC_CK(launch_gemvt_f64(m, n, h->A64, m, h->rbuf, h->c64, h->gz, st));
             RAC_CK(cudaMemcpyAsync(g0.data(), h->gz, n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -401,6 +452,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     }
     // storage-precision copy for the sweeps
     const size_t sb = store_bytes(h->store);
+    h->nlaunch += 1;
     if (h->gram) {
         RAC_CK(cudaMalloc(&h->G, (size_t)n * n * sb));
         h->allocs.push_back(h->G);
@@ -448,6 +500,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
                   h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"));
     RAC_ST(set_state(h, o->x0, o->xi0));
     RAC_CK(cudaStreamSynchronize(st));
+    h->setup_launches = h->nlaunch;
     return RAC_OK;
 }
 
@@ -483,6 +536,9 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
     if (!h) return RAC_ERR_ARG;
     auto t0 = std::chrono::steady_clock::now();
     RAC_ST(enter(h));
+    h->nlaunch = 0;
+    h->t_asm = h->t_fac = h->t_chain = h->t_prox = h->t_ref = 0.0;
+    h->chain_launches = 0;
     HostStats hs;
     int dev_err = 0;
     RAC_ST(read_stats(h, &hs, &dev_err));
@@ -495,6 +551,7 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
         h->sweep += nb;
         done += nb;
         RAC_ST(read_stats(h, &hs, &dev_err));
+        collect_profile(h, nb);
         if (dev_err) status = (rac_status)dev_err;
         else if (hs.nonfinite) status = RAC_ERR_NUMERIC;
     }
@@ -515,6 +572,14 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         info->status = status;
         std::memcpy(info->form, h->form, sizeof(info->form));
+        info->kernel_launches = h->nlaunch;
+        info->setup_launches = h->setup_launches;
+        info->t_assembly_ms = h->t_asm;
+        info->t_factor_ms = h->t_fac;
+        info->t_chain_ms = h->t_chain;
+        info->t_prox_ms = h->t_prox;
+        info->t_refresh_ms = h->t_ref;
+        info->chain_launches = h->chain_launches;
     }
     return status;
 }

@@ -140,6 +140,11 @@ typedef struct rac_handle rac_handle;
 /* Human-readable text for a status (static storage). */
 const char *rac_status_string(int32_t status);
 
+/* Text of the most recent CUDA runtime failure seen by the calling thread
+ * inside this library (the CUDA error name and the source line), or "" if
+ * none; valid until the next library call on this thread. */
+const char *rac_last_error(void);
+
 /* Fill *opt with defaults: p = 1, beta = 1, gamma = 0, tol = 1e-6,
  * max_sweeps = 1000, refresh_every = 10, seed = 0, FP64, AUTO form. */
 rac_status rac_options_default(rac_options *opt);

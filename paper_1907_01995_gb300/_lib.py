@@ -51,6 +51,7 @@ P = ctypes.POINTER
 # (name, restype, argtypes) of every exported function
 SIGNATURES = [
     ("rac_status_string", ctypes.c_char_p, [c_int32]),
+    ("rac_last_error", ctypes.c_char_p, []),
     ("rac_options_default", c_int32, [P(RacOptions)]),
     ("rac_admm_setup", c_int32, [P(RacProblem), P(RacOptions), P(c_void_p)]),
     ("rac_admm_solve", c_int32, [c_void_p, c_void_p, P(RacInfo)]),
@@ -80,7 +81,13 @@ _LIB = None
 class RacError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
         self.status = status
-        super().__init__("%s: status %d (%s)" % (where, status, status_string(status)))
+        detail = ""
+        if status == RAC_ERR_CUDA:
+            try:
+                detail = " [%s]" % load().rac_last_error().decode()
+            except Exception:
+                pass
+        super().__init__("%s: status %d (%s)%s" % (where, status, status_string(status), detail))
 
 
 def load() -> ctypes.CDLL:

@@ -24,10 +24,21 @@
 
 using namespace rac;
 
+// The most recent CUDA failure seen by this thread (see rac_last_error()).
+static thread_local char g_last_error[256] = "";
+
+static void note_cuda(cudaError_t e, int line) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at rac_api.cu:%d",
+                  cudaGetErrorName(e), cudaGetErrorString(e), line);
+}
+
 #define RAC_CK(call)                                   \
     do {                                               \
         cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) return map_cuda(e_);    \
+        if (e_ != cudaSuccess) {                       \
+            note_cuda(e_, __LINE__);                   \
+            return map_cuda(e_);                       \
+        }                                              \
     } while (0)
 #define RAC_ST(call)                                   \
     do {                                               \
@@ -110,6 +121,8 @@ struct rac_handle {
     }
 };
 
+extern "C" const char *rac_last_error(void) { return g_last_error; }
+
 extern "C" const char *rac_status_string(int32_t s) {
     switch (s) {
     case RAC_OK: return "ok";
@@ -141,6 +154,7 @@ extern "C" rac_status rac_options_default(rac_options *o) {
 
 // enter: the handle's private stream waits for the caller's stream
 static rac_status enter(rac_handle *h) {
+    (void)cudaGetLastError();  // drop a stale non-sticky error left by another caller
     RAC_CK(cudaEventRecord(h->ev, h->user));
     RAC_CK(cudaStreamWaitEvent(h->st, h->ev, 0));
     return RAC_OK;
@@ -276,7 +290,9 @@ static void collect_profile(rac_handle *h, int nb) {
 }
 
 static rac_status run_period(rac_handle *h, int nb) {
-    if (h->use_graph) {
+    // Profiling brackets every kernel class with events, which is only
+    // reliable for direct launches, so a profiled handle does not use graphs.
+    if (h->use_graph && !h->profile) {
         auto it = h->graphs.find(nb);
         if (it == h->graphs.end()) {
             cudaGraph_t graph = nullptr;
@@ -523,6 +539,7 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
     if (smax > 4096) return RAC_ERR_ARG;
     rac_handle *h = new (std::nothrow) rac_handle();
     if (!h) return RAC_ERR_OOM;
+    (void)cudaGetLastError();
     rac_status s = setup_impl(pr, o, h);
     if (s != RAC_OK) {
         delete h;

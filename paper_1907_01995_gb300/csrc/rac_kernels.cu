@@ -442,7 +442,11 @@ template <class TS, class TA, bool GRAM>
 static int chain_grid_impl(int smax, size_t *smem_out) {
     size_t smem = ChainSmem<TA>::bytes(smax, kChainThreads / 32);
     void (*kern)(ChainArgs) = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
     int per_sm = 0, dev = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChainThreads, smem);
     cudaGetDevice(&dev);

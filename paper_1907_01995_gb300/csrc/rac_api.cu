@@ -68,7 +68,11 @@ struct rac_handle {
     bool gram = true;
     int grid = 0;
     cudaStream_t user = nullptr, st = nullptr;
+    cudaStream_t sf = nullptr;      // factor stream: factors of sweep s+1 overlap chain s
     cudaEvent_t ev = nullptr;
+    std::vector<cudaEvent_t> fev;   // per sweep slot: factor done, chain done (2 each)
+    int kinv = 1, stage = 0;
+    size_t wstride = 0;             // bytes of one factor buffer (two buffers by sweep parity)
     double kkt_scale = 1.0;
     // device buffers
     double *A64 = nullptr, *b64 = nullptr, *c64 = nullptr, *e64 = nullptr, *H64 = nullptr;
@@ -113,6 +117,8 @@ struct rac_handle {
     ~rac_handle() {
         for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
+        for (cudaEvent_t e : fev) cudaEventDestroy(e);
+        if (sf) cudaStreamDestroy(sf);
         for (void *q : allocs) cudaFree(q);
         if (h_stats) cudaFreeHost(h_stats);
         if (h_err) cudaFreeHost(h_err);
@@ -221,27 +227,41 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.gamma = h->gamma;
     a.bar = h->bar;
     a.err = h->err;
+    a.W = (char *)h->W + (size_t)(slot & 1) * h->wstride;
+    a.kinv = h->kinv;
+    a.stage = h->stage;
     return a;
 }
 
 // One period of nb sweeps followed by the refresh (enqueued on h->st).
+// The factors of sweep s run on h->sf and overlap the chain of sweep s-1;
+// factor buffer s & 1 is reused only after chain s-2 has finished with it.
 static rac_status enqueue_period(rac_handle *h, int nb) {
-    cudaStream_t st = h->st;
+    cudaStream_t st = h->st, sf = h->sf;
     const bool pf = h->profile;
     if (pf) RAC_CK(cudaEventRecord(h->pev[0], st));
     RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, nb, h->perm, h->blk, h->tkey,
                            h->tidx, st));
     if (pf) RAC_CK(cudaEventRecord(h->pev[1], st));
+    RAC_CK(cudaEventRecord(h->fev[0], st));      // fork: factors wait for the assembly
+    RAC_CK(cudaStreamWaitEvent(sf, h->fev[0], 0));
     h->nlaunch += 1 + 3 * (int64_t)nb + 1;
     for (int s = 0; s < nb; ++s) {
         ChainArgs a = chain_args(h, s);
-        cudaEvent_t *ev = pf ? &h->pev[3 + 4 * s] : nullptr;
-        if (pf) RAC_CK(cudaEventRecord(ev[0], st));
-        RAC_CK(launch_factor(h->store, h->gram, a, h->W, nullptr, nullptr, h->err, st));
-        if (pf) RAC_CK(cudaEventRecord(ev[1], st));
+        cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
+        cudaEvent_t fdone = h->fev[1 + 2 * s], cdone = h->fev[2 + 2 * s];
+        if (s >= 2) RAC_CK(cudaStreamWaitEvent(sf, h->fev[2 + 2 * (s - 2)], 0));
+        if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
+        int kinv = 1;
+        RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W), &kinv, sf));
+        if (pf) RAC_CK(cudaEventRecord(ev[1], sf));
+        RAC_CK(cudaEventRecord(fdone, sf));
+        RAC_CK(cudaStreamWaitEvent(st, fdone, 0));
+        if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
-        if (pf) RAC_CK(cudaEventRecord(ev[2], st));
+        if (pf) RAC_CK(cudaEventRecord(ev[3], st));
+        RAC_CK(cudaEventRecord(cdone, st));
         ProxArgs pa;
         std::memset(&pa, 0, sizeof(pa));
         pa.n = h->n;
@@ -261,7 +281,7 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         pa.beta = h->beta;
         pa.gamma = h->gamma;
         RAC_CK(launch_prox(pa, st));
-        if (pf) RAC_CK(cudaEventRecord(ev[3], st));
+        if (pf) RAC_CK(cudaEventRecord(ev[4], st));
     }
     RAC_ST(enqueue_refresh(h));
     RAC_CK(launch_advance(h->sweep_dev, nb, st));
@@ -279,11 +299,11 @@ static void collect_profile(rac_handle *h, int nb) {
     h->t_asm += el(h->pev[0], h->pev[1]);
     cudaEvent_t last = h->pev[1];
     for (int s = 0; s < nb; ++s) {
-        cudaEvent_t *ev = &h->pev[3 + 4 * s];
+        cudaEvent_t *ev = &h->pev[3 + 5 * s];
         h->t_fac += el(ev[0], ev[1]);
-        h->t_chain += el(ev[1], ev[2]);
-        h->t_prox += el(ev[2], ev[3]);
-        last = ev[3];
+        h->t_chain += el(ev[2], ev[3]);
+        h->t_prox += el(ev[3], ev[4]);
+        last = ev[4];
     }
     h->t_ref += el(last, h->pev[2]);
     h->chain_launches += nb;
@@ -388,9 +408,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->profile = o->profile != 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     RAC_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    RAC_CK(cudaStreamCreateWithFlags(&h->sf, cudaStreamNonBlocking));
     RAC_CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+    h->fev.resize(1 + 2 * (size_t)h->refresh_every, nullptr);
+    for (auto &e : h->fev) RAC_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (h->profile) {
-        h->pev.resize(3 + 4 * (size_t)h->refresh_every, nullptr);
+        h->pev.resize(3 + 5 * (size_t)h->refresh_every, nullptr);
         for (auto &e : h->pev) RAC_CK(cudaEventCreate(&e));
     }
     RAC_ST(enter(h));
@@ -490,11 +513,14 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     }
     BlockLayout lay(n, h->p);
     const size_t ta = h->store == ST_F64 ? 8 : 4;
-    RAC_CK(cudaMalloc(&h->W, lay.factor_total() * ta));
+    h->wstride = (lay.factor_total() * ta + 255) & ~(size_t)255;
+    RAC_CK(cudaMalloc(&h->W, 2 * h->wstride));
     h->allocs.push_back(h->W);
+    h->kinv = factor_uses_kinv(lay.smax()) ? 1 : 0;
+    h->stage = chain_can_stage(h->store, lay.smax()) ? 1 : 0;
     // chain grid
     size_t smem = 0;
-    int gmax = chain_max_grid(h->store, h->gram, lay.smax(), &smem);
+    int gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, &smem);
     if (gmax <= 0) return RAC_ERR_ARG;
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);

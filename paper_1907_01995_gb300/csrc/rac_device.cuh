@@ -58,9 +58,11 @@ struct BlockLayout {
         int big = r * (q + 1);
         return pos < big ? pos / (q + 1) : r + (pos - big) / q;
     }
-    // offset of block i's s x s factor in the packed factor buffer
+    // offset of block i's s x s factor in the packed factor buffer; every
+    // factor is padded to a multiple of 4 entries so it starts 16-byte aligned
+    __host__ __device__ static size_t pad4(size_t v) { return (v + 3) & ~(size_t)3; }
     __host__ __device__ size_t factor_offset(int i) const {
-        size_t b1 = (size_t)(q + 1) * (q + 1), b0 = (size_t)q * q;
+        size_t b1 = pad4((size_t)(q + 1) * (q + 1)), b0 = pad4((size_t)q * q);
         return i < r ? (size_t)i * b1 : (size_t)r * b1 + (size_t)(i - r) * b0;
     }
     __host__ __device__ size_t factor_total() const { return factor_offset(p); }
@@ -254,6 +256,83 @@ __device__ void chol_inverse_inplace(TA *M, int s, TA *diag, TA *tmp, int *err) 
         if (c > r) M[idx] = TA(0);
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------- sweep operator
+// K^{-1} of a symmetric positive definite s x s matrix by the sweep operator
+// (Goodnight, "A tutorial on the SWEEP operator", Am. Stat. 1979): pivoting on
+// k maps a_ij -> a_ij - a_ik a_kj / a_kk (i, j != k), a_ik -> a_ik / a_kk,
+// a_kk -> -1 / a_kk; after all s pivots the matrix holds -K^{-1}.  The matrix
+// lives in registers: thread t owns entries e = t + T u (u < U) of the
+// row-major s x s array.  Row k is broadcast through a double-buffered shared
+// row written by the owners of row k while they update it, so each pivot costs
+// one barrier.  A pivot that is not positive (Assumption 2.1 violated) records
+// RAC_ERR_NOT_PD and is replaced by 1.
+template <class TA, int U>
+__device__ void sweep_inverse_regs(TA (&a)[U], int s, TA *vbuf /* 2*s */, int *err) {
+    const int T = blockDim.x;
+    const int ss = s * s;
+    for (int u = 0; u < U; ++u) {
+        const int e = threadIdx.x + T * u;
+        if (e < s) vbuf[e] = a[u];          // row 0 lives in entries 0..s-1
+    }
+    __syncthreads();
+    for (int k = 0; k < s; ++k) {
+        const TA *vk = vbuf + (k & 1) * s;
+        TA *vn = vbuf + ((k + 1) & 1) * s;
+        TA d = vk[k];
+        if (!(d > TA(0))) {
+            if (threadIdx.x == 0) set_err(err, RAC_ERR_NOT_PD);
+            d = TA(1);
+        }
+        const TA rd = TA(1) / d;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = threadIdx.x + T * u;
+            if (e < ss) {
+                const int i = e / s, j = e - i * s;
+                TA v;
+                if (i == k && j == k) v = -rd;
+                else if (i == k) v = vk[j] * rd;
+                else if (j == k) v = vk[i] * rd;
+                else v = a[u] - vk[i] * vk[j] * rd;
+                a[u] = v;
+                if (i == k + 1) vn[j] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// delta = -Kinv rhs for one block (Kinv symmetric s x s), one warp per row.
+template <class TA>
+__device__ void block_solve_kinv(const TA *Kinv, int s, const TA *rhs, TA *delta) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int r = warp; r < s; r += nw) {
+        const TA *kr = Kinv + (size_t)r * s;
+        TA acc = 0;
+        for (int c = lane; c < s; c += 32) acc += kr[c] * rhs[c];
+        acc = warp_sum(acc);
+        if (lane == 0) delta[r] = -acc;
+    }
+    __syncthreads();
+}
+
+// 16-byte asynchronous global -> shared copies (sm_80+ cp.async).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// Copy `bytes` (a multiple of 16, both pointers 16-byte aligned) by the CTA.
+__device__ __forceinline__ void cta_copy_async(void *dst, const void *src, size_t bytes) {
+    const size_t nv = bytes >> 4;
+    for (size_t v = threadIdx.x; v < nv; v += blockDim.x)
+        cp_async16((char *)dst + (v << 4), (const char *)src + (v << 4));
 }
 
 // delta = -W^T (W rhs) for one block, by one CTA.  W is s x s lower row-major.

@@ -48,6 +48,8 @@ struct ChainArgs {
     double beta, gamma;
     GridBarrier *bar;
     int *err;
+    int kinv;               // 1: W holds K_S^{-1} (full); 0: W holds L_S^{-1} (lower)
+    int stage;              // 1: stage the next block's K^{-1} in shared memory
 };
 
 struct ProxArgs {
@@ -68,11 +70,15 @@ cudaError_t launch_assembly(int n, int p, uint64_t seed, int64_t sweep0, const i
                             cudaStream_t st);
 cudaError_t launch_advance(int64_t *sweep_dev, int nb, cudaStream_t st);
 
-cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, const void *srcG,
-                          const void *srcAs, int *err, cudaStream_t st);
+// Factor all blocks of a sweep.  Returns through *kinv whether W holds K^{-1}
+// (register sweep operator, s <= 128) or L^{-1} (Cholesky path, larger s).
+cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, int *kinv,
+                          cudaStream_t st);
+bool factor_uses_kinv(int smax);
 
 cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cudaStream_t st);
-int chain_max_grid(int store, bool gram, int smax, size_t *smem_out);
+int chain_max_grid(int store, bool gram, int smax, int stage, size_t *smem_out);
+bool chain_can_stage(int store, int smax);
 
 cudaError_t launch_prox(const ProxArgs &a, cudaStream_t st);
 

@@ -230,16 +230,124 @@ static cudaError_t factor_impl(const ChainArgs &a, void *Wout, cudaStream_t st) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, const void *,
-                          const void *, int *, cudaStream_t st) {
+// Register-resident factor for blocks of at most 128 coordinates: each of
+// the 512 threads holds U entries of K_S, K_S^{-1} is formed by the sweep
+// operator and written out in full (row-major, padded).
+constexpr int kFactorThreads = 512;
+
+template <class TS, class TA, bool GRAM, int U>
+__global__ void __launch_bounds__(kFactorThreads) k_factor_regs(ChainArgs a, TA *Wout) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int i = blockIdx.x;
+    BlockLayout lay(a.n, a.p);
+    const int s = lay.size(i), off = lay.offset(i), smax = lay.smax();
+    int *idx = (int *)sm_raw;
+    TA *es = (TA *)(sm_raw + ((smax * sizeof(int) + 15) & ~15));
+    TA *vbuf = es + smax;                       // 2 * smax
+    TS *tile = (TS *)(((uintptr_t)(vbuf + 2 * smax) + 15) & ~(uintptr_t)15);
+    const int T = blockDim.x, ss = s * s;
+    for (int t = threadIdx.x; t < s; t += T) {
+        const int j = a.perm[off + t];
+        idx[t] = j;
+        es[t] = a.e ? (TA)a.e[j] : TA(0);
+    }
+    __syncthreads();
+    TA acc[U];
+    if (GRAM) {
+        const TS *G = (const TS *)a.G;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = threadIdx.x + T * u;
+            acc[u] = TA(0);
+            if (e < ss) {
+                const int r = e / s, c = e - r * s;
+                acc[u] = (TA)to_f(G[(size_t)idx[r] * a.n + idx[c]]);
+            }
+        }
+    } else {
+        const TS *As = (const TS *)a.As;
+        const int R = a.R;
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = TA(0);
+        for (int q = 0; q < a.nslab; ++q) {
+            for (int t = threadIdx.x; t < s * R; t += T) {
+                const int aa = t / R, rr = t - aa * R;
+                tile[t] = As[((size_t)q * a.n + idx[aa]) * R + rr];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = threadIdx.x + T * u;
+                if (e < ss) {
+                    const int r = e / s, c = e - r * s;
+                    TA sacc = 0;
+                    for (int rr = 0; rr < R; ++rr)
+                        sacc += (TA)to_f(tile[r * R + rr]) * (TA)to_f(tile[c * R + rr]);
+                    acc[u] += sacc;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const TA gam = (TA)a.gamma, bet = (TA)a.beta;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int e = threadIdx.x + T * u;
+        if (e < ss) {
+            const int r = e / s, c = e - r * s;
+            acc[u] += bet * es[r] * es[c] + (r == c ? gam : TA(0));
+        }
+    }
+    sweep_inverse_regs<TA, U>(acc, s, vbuf, a.err);
+    TA *out = Wout + lay.factor_offset(i);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int e = threadIdx.x + T * u;
+        if (e < ss) out[e] = -acc[u];
+    }
+}
+
+template <class TS, class TA, bool GRAM, int U>
+static cudaError_t factor_regs_impl(const ChainArgs &a, void *Wout, cudaStream_t st) {
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    size_t smem = ((smax * sizeof(int) + 15) & ~15) + 3 * smax * sizeof(TA) + 16 +
+                  (GRAM ? 0 : (size_t)smax * a.R * sizeof(TS));
+    auto kern = k_factor_regs<TS, TA, GRAM, U>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.p, kFactorThreads, smem, st>>>(a, (TA *)Wout);
+    return cudaGetLastError();
+}
+
+bool factor_uses_kinv(int smax) { return smax <= 128; }
+
+template <class TS, class TA, bool GRAM>
+static cudaError_t factor_any(const ChainArgs &a, void *Wout, int *kinv, cudaStream_t st) {
+    const int smax = BlockLayout(a.n, a.p).smax();
+    if (smax <= 64) {
+        *kinv = 1;
+        return factor_regs_impl<TS, TA, GRAM, 8>(a, Wout, st);
+    }
+    if (smax <= 128) {
+        *kinv = 1;
+        return factor_regs_impl<TS, TA, GRAM, 32>(a, Wout, st);
+    }
+    *kinv = 0;
+    return factor_impl<TS, TA, GRAM>(a, Wout, st);
+}
+
+cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, int *kinv,
+                          cudaStream_t st) {
     if (store == ST_F64)
-        return gram ? factor_impl<double, double, true>(a, Wout, st)
-                    : factor_impl<double, double, false>(a, Wout, st);
+        return gram ? factor_any<double, double, true>(a, Wout, kinv, st)
+                    : factor_any<double, double, false>(a, Wout, kinv, st);
     if (store == ST_F32)
-        return gram ? factor_impl<float, float, true>(a, Wout, st)
-                    : factor_impl<float, float, false>(a, Wout, st);
-    return gram ? factor_impl<__nv_bfloat16, float, true>(a, Wout, st)
-                : factor_impl<__nv_bfloat16, float, false>(a, Wout, st);
+        return gram ? factor_any<float, float, true>(a, Wout, kinv, st)
+                    : factor_any<float, float, false>(a, Wout, kinv, st);
+    return gram ? factor_any<__nv_bfloat16, float, true>(a, Wout, kinv, st)
+                : factor_any<__nv_bfloat16, float, false>(a, Wout, kinv, st);
 }
 
 // ======================================================================
@@ -253,12 +361,62 @@ cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, 
 // ======================================================================
 constexpr int kChainThreads = 256;
 
+// Shared memory of the chain kernels: indices, rhs, delta, scratch for the
+// two-pass L^{-1} solve, warp partials, and (when staged) two K^{-1} buffers.
 template <class TA> struct ChainSmem {
-    static size_t bytes(int smax, int nwarps) {
-        return (size_t)smax * sizeof(int) + 3 * (size_t)smax * sizeof(TA) +
-               (size_t)nwarps * 32 * sizeof(TA) + 64 * sizeof(double) + 64;
+    static size_t kbytes(int smax) { return BlockLayout::pad4((size_t)smax * smax) * sizeof(TA); }
+    static size_t bytes(int smax, int nwarps, int stage) {
+        return (((size_t)smax * sizeof(int) + 15) & ~(size_t)15) + 3 * (size_t)smax * sizeof(TA) +
+               (size_t)nwarps * 32 * sizeof(TA) + 64 * sizeof(double) + 64 +
+               (stage ? 2 * kbytes(smax) + 16 : 0);
     }
 };
+
+struct ChainLayout {
+    int *idx;
+    void *rhs, *u, *dl, *wred, *kbuf;
+    double *dred;
+};
+template <class TA>
+__device__ __forceinline__ ChainLayout chain_layout(unsigned char *sm_raw, int smax, int nw,
+                                                    int stage) {
+    ChainLayout L;
+    L.idx = (int *)sm_raw;
+    TA *rhs = (TA *)(sm_raw + (((size_t)smax * sizeof(int) + 15) & ~(size_t)15));
+    L.rhs = rhs;
+    L.u = rhs + smax;
+    L.dl = rhs + 2 * smax;
+    TA *wred = rhs + 3 * smax;
+    L.wred = wred;
+    L.dred = (double *)(((uintptr_t)(wred + nw * 32) + 15) & ~(uintptr_t)15);
+    L.kbuf = stage ? (void *)(((uintptr_t)(L.dred + 64) + 15) & ~(uintptr_t)15) : nullptr;
+    return L;
+}
+
+// dx_S = -K_S^{-1} rhs (staged or from global) or -W^T (W rhs).
+template <class TA>
+__device__ __forceinline__ void chain_block_solve(const ChainArgs &a, const BlockLayout &lay,
+                                                  int i, int s, const TA *kst, TA *rhs, TA *u,
+                                                  TA *dl) {
+    const TA *Wall = (const TA *)a.W;
+    if (a.kinv)
+        block_solve_kinv<TA>(kst ? kst : Wall + lay.factor_offset(i), s, rhs, dl);
+    else
+        block_solve<TA>(Wall + lay.factor_offset(i), s, rhs, u, dl);
+}
+
+// Issue the asynchronous copy of block i's K^{-1} into buffer i & 1.
+template <class TA>
+__device__ __forceinline__ void chain_prefetch(const ChainArgs &a, const BlockLayout &lay, int i,
+                                               TA *kbuf, int smax) {
+    if (i < a.p) {
+        const int si = lay.size(i);
+        const size_t bytes = BlockLayout::pad4((size_t)si * si) * sizeof(TA);
+        cta_copy_async(kbuf + (size_t)(i & 1) * BlockLayout::pad4((size_t)smax * smax),
+                       (const TA *)a.W + lay.factor_offset(i), bytes);
+    }
+    cp_async_commit();
+}
 
 // Gram form: g (n) is kept exact up to the storage rounding of G; block i
 // adds G[:, S_i] dx to every coordinate.  Coordinates of block i itself are
@@ -270,23 +428,26 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram(ChainArgs a) {
     BlockLayout lay(a.n, a.p);
     const int smax = lay.smax();
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int *idx = (int *)sm_raw;
-    TA *rhs = (TA *)(sm_raw + (((size_t)smax * sizeof(int) + 15) & ~15));
-    TA *u = rhs + smax;
-    TA *dl = u + smax;
-    TA *wred = dl + smax;                   // nw x 32
-    double *dred = (double *)(((uintptr_t)(wred + nw * 32) + 15) & ~(uintptr_t)15);
+    ChainLayout Ly = chain_layout<TA>(sm_raw, smax, nw, a.stage);
+    int *idx = Ly.idx;
+    TA *rhs = (TA *)Ly.rhs, *u = (TA *)Ly.u, *dl = (TA *)Ly.dl, *wred = (TA *)Ly.wred;
+    TA *kbuf = (TA *)Ly.kbuf;
+    const size_t kstride = BlockLayout::pad4((size_t)smax * smax);
     __shared__ int s_flag;
     const TS *G = (const TS *)a.G;
-    const TA *Wall = (const TA *)a.W;
     const int n = a.n;
     const double gamma = a.gamma, beta = a.beta;
     const double mu = a.mu ? *a.mu : 0.0;
     double t = a.e ? *a.t : 0.0;
     unsigned gen = 0;
     const int ntiles = (n + 31) >> 5;
+    if (a.stage) chain_prefetch<TA>(a, lay, 0, kbuf, smax);
     for (int i = 0; i < a.p; ++i) {
         const int s = lay.size(i), off = lay.offset(i);
+        if (a.stage) {
+            chain_prefetch<TA>(a, lay, i + 1, kbuf, smax);
+            cp_async_wait<1>();
+        }
         for (int q = threadIdx.x; q < s; q += blockDim.x) {
             const int j = a.perm[off + q];
             idx[q] = j;
@@ -295,11 +456,12 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram(ChainArgs a) {
             rhs[q] = (TA)r;
         }
         __syncthreads();
-        block_solve<TA>(Wall + lay.factor_offset(i), s, rhs, u, dl);
+        chain_block_solve<TA>(a, lay, i, s, a.stage ? kbuf + (size_t)(i & 1) * kstride : nullptr,
+                              rhs, u, dl);
         if (a.e) {
             double loc = 0.0;
             for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[idx[q]] * (double)dl[q];
-            t += block_sum<double>(loc, dred);
+            t += block_sum<double>(loc, Ly.dred);
         }
         if (blockIdx.x == 0)
             for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[idx[q]] = (double)dl[q];
@@ -307,9 +469,15 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram(ChainArgs a) {
             const int col = tile * 32 + lane;
             TA acc = 0;
             if (col < n) {
-#pragma unroll 4
-                for (int q = warp; q < s; q += nw)
-                    acc += (TA)to_f(G[(size_t)idx[q] * n + col]) * dl[q];
+                int q = warp;
+                for (; q + 7 * nw < s; q += 8 * nw) {   // 8 independent row loads in flight
+                    TA v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = (TA)to_f(G[(size_t)idx[q + k * nw] * n + col]);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc += v[k] * dl[q + k * nw];
+                }
+                for (; q < s; q += nw) acc += (TA)to_f(G[(size_t)idx[q] * n + col]) * dl[q];
             }
             wred[warp * 32 + lane] = acc;
             __syncthreads();
@@ -326,8 +494,12 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram(ChainArgs a) {
             __syncthreads();
         }
         if (i + 1 < a.p)
-            if (!grid_sync(a.bar, gridDim.x, gen, a.err, &s_flag)) return;
+            if (!grid_sync(a.bar, gridDim.x, gen, a.err, &s_flag)) {
+                cp_async_wait<0>();
+                return;
+            }
     }
+    if (a.stage) cp_async_wait<0>();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
 }
 
@@ -341,23 +513,23 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
     BlockLayout lay(a.n, a.p);
     const int smax = lay.smax();
     const int nw = blockDim.x >> 5;
-    int *idx = (int *)sm_raw;
-    TA *rhs = (TA *)(sm_raw + (((size_t)smax * sizeof(int) + 15) & ~15));
-    TA *u = rhs + smax;
-    TA *dl = u + smax;
-    TA *wred = dl + smax;
-    double *dred = (double *)(((uintptr_t)(wred + nw * 32) + 15) & ~(uintptr_t)15);
+    ChainLayout Ly = chain_layout<TA>(sm_raw, smax, nw, a.stage);
+    int *idx = Ly.idx;
+    TA *rhs = (TA *)Ly.rhs, *u = (TA *)Ly.u, *dl = (TA *)Ly.dl;
+    TA *kbuf = (TA *)Ly.kbuf;
+    const size_t kstride = BlockLayout::pad4((size_t)smax * smax);
     __shared__ int s_flag;
     const TS *As = (const TS *)a.As;
-    const TA *Wall = (const TA *)a.W;
     TA *part = (TA *)a.partials;
     const int n = a.n, R = a.R, G = gridDim.x;
     const double gamma = a.gamma, beta = a.beta;
     const double mu = a.mu ? *a.mu : 0.0;
     double t = a.e ? *a.t : 0.0;
     unsigned gen = 0;
+    if (a.stage) chain_prefetch<TA>(a, lay, 0, kbuf, smax);
     for (int i = 0; i < a.p; ++i) {
         const int s = lay.size(i), off = lay.offset(i);
+        if (a.stage) chain_prefetch<TA>(a, lay, i + 1, kbuf, smax);
         for (int q = threadIdx.x; q < s; q += blockDim.x) idx[q] = a.perm[off + q];
         __syncthreads();
         // partial A~_S^T dres over this CTA's slabs
@@ -372,7 +544,11 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
             }
             mypart[q] = acc;
         }
-        if (!grid_sync(a.bar, G, gen, a.err, &s_flag)) return;
+        if (!grid_sync(a.bar, G, gen, a.err, &s_flag)) {
+            cp_async_wait<0>();
+            return;
+        }
+        if (a.stage) cp_async_wait<1>();
         const TA *pin = part + (size_t)(i & 1) * G * smax;
         for (int q = threadIdx.x; q < s; q += blockDim.x) {
             const int j = idx[q];
@@ -383,11 +559,12 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
             rhs[q] = (TA)r;
         }
         __syncthreads();
-        block_solve<TA>(Wall + lay.factor_offset(i), s, rhs, u, dl);
+        chain_block_solve<TA>(a, lay, i, s, a.stage ? kbuf + (size_t)(i & 1) * kstride : nullptr,
+                              rhs, u, dl);
         if (a.e) {
             double loc = 0.0;
             for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[idx[q]] * (double)dl[q];
-            t += block_sum<double>(loc, dred);
+            t += block_sum<double>(loc, Ly.dred);
         }
         if (blockIdx.x == 0)
             for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[idx[q]] = (double)dl[q];
@@ -403,13 +580,14 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
         }
         __syncthreads();
     }
+    if (a.stage) cp_async_wait<0>();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
 }
 
 template <class TS, class TA, bool GRAM>
 static cudaError_t chain_impl(const ChainArgs &a, int grid, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
-    size_t smem = ChainSmem<TA>::bytes(lay.smax(), kChainThreads / 32);
+    size_t smem = ChainSmem<TA>::bytes(lay.smax(), kChainThreads / 32, a.stage);
     void (*kern)(ChainArgs) = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -439,8 +617,8 @@ cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cud
 }
 
 template <class TS, class TA, bool GRAM>
-static int chain_grid_impl(int smax, size_t *smem_out) {
-    size_t smem = ChainSmem<TA>::bytes(smax, kChainThreads / 32);
+static int chain_grid_impl(int smax, int stage, size_t *smem_out) {
+    size_t smem = ChainSmem<TA>::bytes(smax, kChainThreads / 32, stage);
     void (*kern)(ChainArgs) = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
@@ -455,15 +633,27 @@ static int chain_grid_impl(int smax, size_t *smem_out) {
     return per_sm * sms;
 }
 
-int chain_max_grid(int store, bool gram, int smax, size_t *smem_out) {
+int chain_max_grid(int store, bool gram, int smax, int stage, size_t *smem_out) {
     if (store == ST_F64)
-        return gram ? chain_grid_impl<double, double, true>(smax, smem_out)
-                    : chain_grid_impl<double, double, false>(smax, smem_out);
+        return gram ? chain_grid_impl<double, double, true>(smax, stage, smem_out)
+                    : chain_grid_impl<double, double, false>(smax, stage, smem_out);
     if (store == ST_F32)
-        return gram ? chain_grid_impl<float, float, true>(smax, smem_out)
-                    : chain_grid_impl<float, float, false>(smax, smem_out);
-    return gram ? chain_grid_impl<__nv_bfloat16, float, true>(smax, smem_out)
-                : chain_grid_impl<__nv_bfloat16, float, false>(smax, smem_out);
+        return gram ? chain_grid_impl<float, float, true>(smax, stage, smem_out)
+                    : chain_grid_impl<float, float, false>(smax, stage, smem_out);
+    return gram ? chain_grid_impl<__nv_bfloat16, float, true>(smax, stage, smem_out)
+                : chain_grid_impl<__nv_bfloat16, float, false>(smax, stage, smem_out);
+}
+
+// Staging K^{-1} needs two buffers in shared memory next to the rest.
+bool chain_can_stage(int store, int smax) {
+    if (!factor_uses_kinv(smax)) return false;
+    size_t ta = store == ST_F64 ? 8 : 4;
+    size_t need = (ta == 8 ? ChainSmem<double>::bytes(smax, kChainThreads / 32, 1)
+                           : ChainSmem<float>::bytes(smax, kChainThreads / 32, 1));
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return need <= (size_t)optin;
 }
 
 // ======================================================================

@@ -71,8 +71,11 @@ struct rac_handle {
     cudaStream_t sf = nullptr;      // factor stream: factors of sweep s+1 overlap chain s
     cudaEvent_t ev = nullptr;
     std::vector<cudaEvent_t> fev;   // per sweep slot: factor done, chain done (2 each)
-    int kinv = 1, stage = 0;
+    int kinv = 1, stage = 0, stage_p = 0, lookahead = 0;
     size_t wstride = 0;             // bytes of one factor buffer (two buffers by sweep parity)
+    void *Pbuf = nullptr;           // lookahead matrices P_i (two buffers by sweep parity)
+    size_t pstride = 0;
+    double *gnext = nullptr;
     double kkt_scale = 1.0;
     // device buffers
     double *A64 = nullptr, *b64 = nullptr, *c64 = nullptr, *e64 = nullptr, *H64 = nullptr;
@@ -230,6 +233,10 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.W = (char *)h->W + (size_t)(slot & 1) * h->wstride;
     a.kinv = h->kinv;
     a.stage = h->stage;
+    a.stage_p = h->stage_p;
+    a.lookahead = h->lookahead;
+    a.P = h->lookahead ? (const void *)((char *)h->Pbuf + (size_t)(slot & 1) * h->pstride) : nullptr;
+    a.gnext = h->gnext;
     return a;
 }
 
@@ -253,7 +260,8 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         if (s >= 2) RAC_CK(cudaStreamWaitEvent(sf, h->fev[2 + 2 * (s - 2)], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
         int kinv = 1;
-        RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W), &kinv, sf));
+        RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W),
+                             const_cast<void *>(a.P), &kinv, sf));
         if (pf) RAC_CK(cudaEventRecord(ev[1], sf));
         RAC_CK(cudaEventRecord(fdone, sf));
         RAC_CK(cudaStreamWaitEvent(st, fdone, 0));
@@ -271,6 +279,7 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         pa.dx = h->dx;
         pa.g = h->gram ? h->g : nullptr;
         pa.gdef = h->gdef;
+        pa.gnext = h->gram ? h->gnext : nullptr;
         pa.mu = h->k ? h->mu : nullptr;
         pa.t = h->k ? h->t : nullptr;
         pa.phi = h->phi;
@@ -502,6 +511,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         }
         RAC_ST(h->alloc(&h->g, n));
         RAC_ST(h->alloc(&h->gdef, n));
+        RAC_ST(h->alloc(&h->gnext, n));
+        RAC_CK(cudaMemsetAsync(h->gnext, 0, (size_t)n * sizeof(double), st));
     } else {
         h->R = slab_rows(h->store);
         h->nslab = (m + h->R - 1) / h->R;
@@ -517,17 +528,38 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_CK(cudaMalloc(&h->W, 2 * h->wstride));
     h->allocs.push_back(h->W);
     h->kinv = factor_uses_kinv(lay.smax()) ? 1 : 0;
-    h->stage = chain_can_stage(h->store, lay.smax()) ? 1 : 0;
-    // chain grid
-    size_t smem = 0;
-    int gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, &smem);
-    if (gmax <= 0) return RAC_ERR_ARG;
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // Gram form with register factors: lookahead chain (P_i precomputed)
+    h->lookahead = (h->gram && h->kinv && factor_can_make_p(h->store, lay.smax())) ? 1 : 0;
+    if (h->lookahead) {
+        h->stage = chain_can_stage(h->store, lay.smax(), 1) ? 1 : 0;
+        h->stage_p = h->stage;
+        if (!h->stage) h->stage = chain_can_stage(h->store, lay.smax(), 0) ? 1 : 0;
+    } else {
+        h->stage = chain_can_stage(h->store, lay.smax(), 0) ? 1 : 0;
+    }
+    size_t smem = 0;
+    int gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, h->stage_p, h->lookahead,
+                              &smem);
+    if (h->lookahead && gmax < lookahead_min_grid(n)) {
+        h->lookahead = 0;
+        h->stage_p = 0;
+        h->stage = chain_can_stage(h->store, lay.smax(), 0) ? 1 : 0;
+        gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, 0, 0, &smem);
+    }
+    if (gmax <= 0) return RAC_ERR_ARG;
     int want = h->gram ? std::min(sms, (n + 31) / 32) : std::min(sms, h->nslab);
     if (o->grid > 0) want = o->grid;
+    if (h->lookahead) want = std::max(want, lookahead_min_grid(n));
     h->grid = std::max(1, std::min(want, gmax));
+    if (h->lookahead) {
+        h->pstride = ((size_t)h->p * BlockLayout::pad4((size_t)lay.smax() * lay.smax()) * ta + 255) &
+                     ~(size_t)255;
+        RAC_CK(cudaMalloc(&h->Pbuf, 2 * h->pstride));
+        h->allocs.push_back(h->Pbuf);
+    }
     if (!h->gram) {
         RAC_CK(cudaMalloc(&h->cpart, (size_t)2 * h->grid * lay.smax() * ta));
         h->allocs.push_back(h->cpart);

@@ -50,14 +50,20 @@ struct ChainArgs {
     int *err;
     int kinv;               // 1: W holds K_S^{-1} (full); 0: W holds L_S^{-1} (lower)
     int stage;              // 1: stage the next block's K^{-1} in shared memory
+    // Gram-form lookahead (see k_chain_gram_la)
+    const void *P;          // P_i = K_i^{-1} G[S_i, S_{i-1}], stride pad4(smax^2) per block
+    double *gnext;          // increments of the next block's coordinates, folded in by k_prox
+    int stage_p;            // 1: stage P_i in shared memory too
+    int lookahead;          // 1: run k_chain_gram_la
 };
 
 struct ProxArgs {
     int n;
     double *x, *z, *xi;
     const double *dx;
-    double *g;              // Gram form: g += gdef
+    double *g;              // Gram form: g += gdef + gnext, gnext = 0
     const double *gdef;
+    double *gnext;
     double *mu;
     const double *t;
     int phi;
@@ -72,13 +78,16 @@ cudaError_t launch_advance(int64_t *sweep_dev, int nb, cudaStream_t st);
 
 // Factor all blocks of a sweep.  Returns through *kinv whether W holds K^{-1}
 // (register sweep operator, s <= 128) or L^{-1} (Cholesky path, larger s).
-cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, int *kinv,
-                          cudaStream_t st);
+cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, void *Pout,
+                          int *kinv, cudaStream_t st);
+bool factor_can_make_p(int store, int smax);
+int lookahead_min_grid(int n);
 bool factor_uses_kinv(int smax);
 
 cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cudaStream_t st);
-int chain_max_grid(int store, bool gram, int smax, int stage, size_t *smem_out);
-bool chain_can_stage(int store, int smax);
+int chain_max_grid(int store, bool gram, int smax, int stage, int stage_p, int lookahead,
+                   size_t *smem_out);
+bool chain_can_stage(int store, int smax, int with_p);
 
 cudaError_t launch_prox(const ProxArgs &a, cudaStream_t st);
 

@@ -230,124 +230,232 @@ static cudaError_t factor_impl(const ChainArgs &a, void *Wout, cudaStream_t st) 
     return cudaGetLastError();
 }
 
-// Register-resident factor for blocks of at most 128 coordinates: each of
-// the 512 threads holds U entries of K_S, K_S^{-1} is formed by the sweep
-// operator and written out in full (row-major, padded).
+// Register-resident factor for blocks of at most 128 coordinates.  The 512
+// threads own whole row pieces: thread t holds row r = t / NP, columns
+// c0 + NP u (c0 = t % NP, u < U) of K_S.  K_S^{-1} is formed by the sweep
+// operator and written out in full (row-major, padded).  In the Gram form the
+// kernel also forms the lookahead matrix P_i = K_i^{-1} G[S_i, S_{i-1}]
+// (i >= 1) used by the chain kernel.
 constexpr int kFactorThreads = 512;
 
-template <class TS, class TA, bool GRAM, int U>
-__global__ void __launch_bounds__(kFactorThreads) k_factor_regs(ChainArgs a, TA *Wout) {
+template <class TS, class TA, bool GRAM, int NP, int U>
+__global__ void __launch_bounds__(kFactorThreads) k_factor_rows(ChainArgs a, TA *Wout, TA *Pout) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int i = blockIdx.x;
     BlockLayout lay(a.n, a.p);
     const int s = lay.size(i), off = lay.offset(i), smax = lay.smax();
     int *idx = (int *)sm_raw;
-    TA *es = (TA *)(sm_raw + ((smax * sizeof(int) + 15) & ~15));
-    TA *vbuf = es + smax;                       // 2 * smax
-    TS *tile = (TS *)(((uintptr_t)(vbuf + 2 * smax) + 15) & ~(uintptr_t)15);
-    const int T = blockDim.x, ss = s * s;
+    int *idxp = idx + smax;
+    TA *es = (TA *)(sm_raw + ((2 * smax * sizeof(int) + 15) & ~15));
+    TA *vbuf = es + smax;                                   // 2 * smax
+    unsigned char *big = (unsigned char *)(((uintptr_t)(vbuf + 2 * smax) + 15) & ~(uintptr_t)15);
+    const int T = blockDim.x;
+    const int r = threadIdx.x / NP, c0 = threadIdx.x % NP;
+    const bool rv = r < s;
+    const bool want_p = GRAM && Pout != nullptr && i > 0;
+    const int sp = i > 0 ? lay.size(i - 1) : 0, offp = i > 0 ? lay.offset(i - 1) : 0;
     for (int t = threadIdx.x; t < s; t += T) {
         const int j = a.perm[off + t];
         idx[t] = j;
         es[t] = a.e ? (TA)a.e[j] : TA(0);
     }
+    if (want_p)
+        for (int t = threadIdx.x; t < sp; t += T) idxp[t] = a.perm[offp + t];
     __syncthreads();
     TA acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = TA(0);
     if (GRAM) {
         const TS *G = (const TS *)a.G;
+        if (rv) {
+            const size_t rowoff = (size_t)idx[r] * a.n;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = threadIdx.x + T * u;
-            acc[u] = TA(0);
-            if (e < ss) {
-                const int r = e / s, c = e - r * s;
-                acc[u] = (TA)to_f(G[(size_t)idx[r] * a.n + idx[c]]);
+            for (int u = 0; u < U; ++u) {
+                const int j = c0 + NP * u;
+                if (j < s) acc[u] = (TA)to_f(G[rowoff + idx[j]]);
             }
         }
     } else {
         const TS *As = (const TS *)a.As;
+        TS *tile = (TS *)big;
         const int R = a.R;
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc[u] = TA(0);
         for (int q = 0; q < a.nslab; ++q) {
             for (int t = threadIdx.x; t < s * R; t += T) {
                 const int aa = t / R, rr = t - aa * R;
                 tile[t] = As[((size_t)q * a.n + idx[aa]) * R + rr];
             }
             __syncthreads();
+            if (rv) {
+                TA tr[16];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = threadIdx.x + T * u;
-                if (e < ss) {
-                    const int r = e / s, c = e - r * s;
-                    TA sacc = 0;
-                    for (int rr = 0; rr < R; ++rr)
-                        sacc += (TA)to_f(tile[r * R + rr]) * (TA)to_f(tile[c * R + rr]);
-                    acc[u] += sacc;
+                for (int rr = 0; rr < 16; ++rr) tr[rr] = rr < R ? (TA)to_f(tile[r * R + rr]) : TA(0);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = c0 + NP * u;
+                    if (j < s) {
+                        TA sacc = 0;
+#pragma unroll
+                        for (int rr = 0; rr < 16; ++rr)
+                            if (rr < R) sacc += tr[rr] * (TA)to_f(tile[j * R + rr]);
+                        acc[u] += sacc;
+                    }
                 }
             }
             __syncthreads();
         }
     }
     const TA gam = (TA)a.gamma, bet = (TA)a.beta;
+    if (rv) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int e = threadIdx.x + T * u;
-        if (e < ss) {
-            const int r = e / s, c = e - r * s;
-            acc[u] += bet * es[r] * es[c] + (r == c ? gam : TA(0));
+        for (int u = 0; u < U; ++u) {
+            const int j = c0 + NP * u;
+            if (j < s) acc[u] += bet * es[r] * es[j] + (r == j ? gam : TA(0));
+        }
+        if (r == 0) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = c0 + NP * u;
+                if (j < s) vbuf[j] = acc[u];
+            }
         }
     }
-    sweep_inverse_regs<TA, U>(acc, s, vbuf, a.err);
-    TA *out = Wout + lay.factor_offset(i);
+    __syncthreads();
+    // sweep operator, one pivot per step (see sweep_inverse_regs)
+    for (int k = 0; k < s; ++k) {
+        const TA *vk = vbuf + (k & 1) * smax;
+        TA *vn = vbuf + ((k + 1) & 1) * smax;
+        TA d = vk[k];
+        if (!(d > TA(0))) {
+            if (threadIdx.x == 0) set_err(a.err, RAC_ERR_NOT_PD);
+            d = TA(1);
+        }
+        const TA rd = TA(1) / d;
+        if (rv) {
+            if (r == k) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int e = threadIdx.x + T * u;
-        if (e < ss) out[e] = -acc[u];
+                for (int u = 0; u < U; ++u) {
+                    const int j = c0 + NP * u;
+                    if (j < s) acc[u] = (j == k) ? -rd : vk[j] * rd;
+                }
+            } else {
+                const TA vir = vk[r] * rd;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = c0 + NP * u;
+                    if (j < s) acc[u] = (j == k) ? vir : acc[u] - vir * vk[j];
+                }
+            }
+            if (r == k + 1) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int j = c0 + NP * u;
+                    if (j < s) vn[j] = acc[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    TA *out = Wout + lay.factor_offset(i);
+    if (rv) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = c0 + NP * u;
+            if (j < s) out[(size_t)r * s + j] = -acc[u];
+        }
+    }
+    if (!want_p) return;
+    // P_i = K_i^{-1} G[S_i, S_{i-1}]  (s x sp), staged through shared memory
+    TA *Ks = (TA *)big;
+    TA *Gp = Ks + (size_t)smax * smax;
+    if (rv) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = c0 + NP * u;
+            if (j < s) Ks[(size_t)r * s + j] = -acc[u];
+        }
+    }
+    const TS *G = (const TS *)a.G;
+    for (int t = threadIdx.x; t < s * sp; t += T) {
+        const int kk = t / sp, cc = t - kk * sp;
+        Gp[t] = (TA)to_f(G[(size_t)idx[kk] * a.n + idxp[cc]]);
+    }
+    __syncthreads();
+    if (rv) {
+        TA pacc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) pacc[u] = TA(0);
+        for (int kk = 0; kk < s; ++kk) {
+            const TA kv = Ks[(size_t)r * s + kk];
+            const TA *gr = Gp + (size_t)kk * sp;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int c = c0 + NP * u;
+                if (c < sp) pacc[u] += kv * gr[c];
+            }
+        }
+        TA *po = Pout + (size_t)i * BlockLayout::pad4((size_t)smax * smax);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = c0 + NP * u;
+            if (c < sp) po[(size_t)r * sp + c] = pacc[u];
+        }
     }
 }
 
-template <class TS, class TA, bool GRAM, int U>
-static cudaError_t factor_regs_impl(const ChainArgs &a, void *Wout, cudaStream_t st) {
+template <class TS, class TA, bool GRAM, int NP, int U>
+static cudaError_t factor_rows_impl(const ChainArgs &a, void *Wout, void *Pout, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
     const int smax = lay.smax();
-    size_t smem = ((smax * sizeof(int) + 15) & ~15) + 3 * smax * sizeof(TA) + 16 +
-                  (GRAM ? 0 : (size_t)smax * a.R * sizeof(TS));
-    auto kern = k_factor_regs<TS, TA, GRAM, U>;
+    size_t big = GRAM ? (Pout ? 2 * (size_t)smax * smax * sizeof(TA) : 0)
+                      : (size_t)smax * a.R * sizeof(TS);
+    size_t smem = ((2 * smax * sizeof(int) + 15) & ~15) + 3 * smax * sizeof(TA) + 16 + big;
+    auto kern = k_factor_rows<TS, TA, GRAM, NP, U>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<a.p, kFactorThreads, smem, st>>>(a, (TA *)Wout);
+    kern<<<a.p, kFactorThreads, smem, st>>>(a, (TA *)Wout, (TA *)Pout);
     return cudaGetLastError();
 }
 
 bool factor_uses_kinv(int smax) { return smax <= 128; }
 
+bool factor_can_make_p(int store, int smax) {
+    if (!factor_uses_kinv(smax)) return false;
+    size_t ta = store == ST_F64 ? 8 : 4;
+    size_t smem = ((2 * smax * sizeof(int) + 15) & ~15) + 3 * smax * ta + 16 +
+                  2 * (size_t)smax * smax * ta;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return smem <= (size_t)optin;
+}
+
 template <class TS, class TA, bool GRAM>
-static cudaError_t factor_any(const ChainArgs &a, void *Wout, int *kinv, cudaStream_t st) {
+static cudaError_t factor_any(const ChainArgs &a, void *Wout, void *Pout, int *kinv,
+                              cudaStream_t st) {
     const int smax = BlockLayout(a.n, a.p).smax();
     if (smax <= 64) {
         *kinv = 1;
-        return factor_regs_impl<TS, TA, GRAM, 8>(a, Wout, st);
+        return factor_rows_impl<TS, TA, GRAM, 8, 8>(a, Wout, Pout, st);
     }
     if (smax <= 128) {
         *kinv = 1;
-        return factor_regs_impl<TS, TA, GRAM, 32>(a, Wout, st);
+        return factor_rows_impl<TS, TA, GRAM, 4, 32>(a, Wout, Pout, st);
     }
     *kinv = 0;
     return factor_impl<TS, TA, GRAM>(a, Wout, st);
 }
 
-cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, int *kinv,
-                          cudaStream_t st) {
+cudaError_t launch_factor(int store, bool gram, const ChainArgs &a, void *Wout, void *Pout,
+                          int *kinv, cudaStream_t st) {
     if (store == ST_F64)
-        return gram ? factor_any<double, double, true>(a, Wout, kinv, st)
-                    : factor_any<double, double, false>(a, Wout, kinv, st);
+        return gram ? factor_any<double, double, true>(a, Wout, Pout, kinv, st)
+                    : factor_any<double, double, false>(a, Wout, Pout, kinv, st);
     if (store == ST_F32)
-        return gram ? factor_any<float, float, true>(a, Wout, kinv, st)
-                    : factor_any<float, float, false>(a, Wout, kinv, st);
-    return gram ? factor_any<__nv_bfloat16, float, true>(a, Wout, kinv, st)
-                : factor_any<__nv_bfloat16, float, false>(a, Wout, kinv, st);
+        return gram ? factor_any<float, float, true>(a, Wout, Pout, kinv, st)
+                    : factor_any<float, float, false>(a, Wout, Pout, kinv, st);
+    return gram ? factor_any<__nv_bfloat16, float, true>(a, Wout, Pout, kinv, st)
+                : factor_any<__nv_bfloat16, float, false>(a, Wout, Pout, kinv, st);
 }
 
 // ======================================================================
@@ -503,6 +611,227 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram(ChainArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
 }
 
+// Gram form with lookahead (block factors from the register sweep, P_i
+// available).  Writing rhs'_i for the block-i right-hand side evaluated with
+// the gradient as it stood before step i-1, the block step is
+//   dx_i = -K_i^{-1} (rhs'_i + G[S_i, S_{i-1}] dx_{i-1}) = -K_i^{-1} rhs'_i - P_i dx_{i-1},
+// so the next block needs only the bulk gradient updates of steps <= i-1.  The
+// grid barrier is split: a CTA arrives after its step-i update and waits for
+// step i-1 only right before it gathers rhs'_{i+1}, which hides the barrier
+// behind one step of work.  Step i's increments to block i+1's coordinates
+// are parked in gnext (they are in P_{i+1} dx_i instead), block i's own in
+// gdef; k_prox folds both in.  Each CTA owns up to kMaxTiles 32-column tiles
+// of g and keeps them in registers of warp 0.
+constexpr int kMaxTiles = 8;
+
+template <class TA>
+__device__ __forceinline__ void gemv_rows(const TA *M, int rows, int cols, const TA *v, TA *out,
+                                          bool negate_add) {
+    // out[r] (+)= M[r, :] v, one warp per row
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < rows; r += nw) {
+        const TA *mr = M + (size_t)r * cols;
+        TA acc = 0;
+        for (int c = lane; c < cols; c += 32) acc += mr[c] * v[c];
+        acc = warp_sum(acc);
+        if (lane == 0) out[r] = negate_add ? -acc - out[r] : acc;
+    }
+}
+
+__device__ __forceinline__ bool grid_wait_count(GridBarrier *bar, unsigned target, int *err,
+                                                int *s_flag) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint64_t t0 = 0;
+        bool timed = false;
+        while (ld_acquire_u32(&bar->count) < target) {
+            if (!timed) { t0 = globaltimer_ns(); timed = true; }
+            if (*((volatile int *)err) == RAC_ERR_TIMEOUT ||
+                globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                set_err(err, RAC_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__device__ __forceinline__ void grid_arrive(GridBarrier *bar) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&bar->count, 1u);
+    }
+}
+
+template <class TA> struct LaSmem {
+    __host__ __device__ static size_t kst(int smax) { return BlockLayout::pad4((size_t)smax * smax); }
+    static size_t bytes(int smax, int nw, int stage, int stage_p) {
+        return 2 * (((size_t)smax * sizeof(int) + 15) & ~(size_t)15) + 3 * (size_t)smax * sizeof(TA) +
+               (size_t)nw * 32 * sizeof(TA) + 64 * sizeof(double) + 64 +
+               (stage ? 2 * kst(smax) * sizeof(TA) : 0) + (stage_p ? 2 * kst(smax) * sizeof(TA) : 0);
+    }
+};
+
+template <class TS, class TA>
+__global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t ib = ((size_t)smax * sizeof(int) + 15) & ~(size_t)15;
+    int *idxb = (int *)sm_raw;                           // 2 index buffers
+    TA *rhs = (TA *)(sm_raw + 2 * ib);
+    TA *dl = rhs + smax;
+    TA *dn = dl + smax;
+    TA *wred = dn + smax;
+    double *dred = (double *)(((uintptr_t)(wred + nw * 32) + 15) & ~(uintptr_t)15);
+    const size_t kst = LaSmem<TA>::kst(smax);
+    TA *kbuf = (TA *)(((uintptr_t)(dred + 64) + 15) & ~(uintptr_t)15);
+    TA *pbuf = a.stage ? kbuf + 2 * kst : kbuf;
+    __shared__ int s_flag;
+    const TS *G = (const TS *)a.G;
+    const TA *Wall = (const TA *)a.W;
+    const TA *Pall = (const TA *)a.P;
+    const int n = a.n, grid = gridDim.x;
+    const double gamma = a.gamma, beta = a.beta;
+    const double mu = a.mu ? *a.mu : 0.0;
+    double t = a.e ? *a.t : 0.0;
+    const int ntiles = (n + 31) >> 5;
+
+    auto prefetch = [&](int b) {
+        if (b < a.p) {
+            const int sb = lay.size(b);
+            if (a.stage)
+                cta_copy_async(kbuf + (size_t)(b & 1) * kst, Wall + lay.factor_offset(b),
+                               BlockLayout::pad4((size_t)sb * sb) * sizeof(TA));
+            if (a.stage_p && b > 0)
+                cta_copy_async(pbuf + (size_t)(b & 1) * kst, Pall + (size_t)b * kst,
+                               BlockLayout::pad4((size_t)sb * lay.size(b - 1)) * sizeof(TA));
+        }
+        cp_async_commit();
+    };
+    auto kptr = [&](int b) -> const TA * {
+        return a.stage ? kbuf + (size_t)(b & 1) * kst : Wall + lay.factor_offset(b);
+    };
+    auto pptr = [&](int b) -> const TA * {
+        return a.stage_p ? pbuf + (size_t)(b & 1) * kst : Pall + (size_t)b * kst;
+    };
+
+    // this CTA's tiles of g, cached in warp 0
+    double greg[kMaxTiles];
+    int breg[kMaxTiles];
+#pragma unroll
+    for (int k = 0; k < kMaxTiles; ++k) {
+        const int col = (blockIdx.x + k * grid) * 32 + lane;
+        greg[k] = 0.0;
+        breg[k] = -1;
+        if (warp == 0 && col < n) {
+            greg[k] = a.g[col];
+            breg[k] = a.blk[col];
+        }
+    }
+    prefetch(0);
+    prefetch(1);
+    // prologue: rhs of block 0 from the gradient at kernel start
+    {
+        const int s0 = lay.size(0);
+        int *cur = idxb;
+        for (int q = threadIdx.x; q < s0; q += blockDim.x) {
+            const int j = a.perm[q];
+            cur[q] = j;
+            double r = a.g[j] - a.xi[j] + gamma * (a.x[j] - a.z[j]);
+            if (a.e) r += a.e[j] * (beta * t - mu);
+            rhs[q] = (TA)r;
+        }
+    }
+    cp_async_wait<1>();
+    __syncthreads();
+    for (int i = 0; i < a.p; ++i) {
+        const int s = lay.size(i);
+        const int *cur = (const int *)((unsigned char *)idxb + (i & 1) * ib);
+        // dx_i = -K_i^{-1} rhs - dn  (dn = P_i dx_{i-1}, zero for block 0)
+        if (i == 0)
+            for (int q = threadIdx.x; q < s; q += blockDim.x) dl[q] = TA(0);
+        else
+            for (int q = threadIdx.x; q < s; q += blockDim.x) dl[q] = dn[q];
+        __syncthreads();
+        gemv_rows<TA>(kptr(i), s, s, rhs, dl, true);
+        __syncthreads();
+        if (a.e) {
+            double loc = 0.0;
+            for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[cur[q]] * (double)dl[q];
+            t += block_sum<double>(loc, dred);
+        }
+        if (blockIdx.x == 0)
+            for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[cur[q]] = (double)dl[q];
+        if (i + 1 < a.p) {
+            const int sn = lay.size(i + 1), offn = lay.offset(i + 1);
+            int *nxt = (int *)((unsigned char *)idxb + ((i + 1) & 1) * ib);
+            prefetch(i + 2);            // buffers (i+2)&1 = i&1 are free: block i is solved
+            cp_async_wait<1>();         // block i+1's K^{-1} and P have landed
+            for (int q = threadIdx.x; q < sn; q += blockDim.x) nxt[q] = a.perm[offn + q];
+            __syncthreads();
+            gemv_rows<TA>(pptr(i + 1), sn, s, dl, dn, false);   // dn = P_{i+1} dx_i
+            if (i >= 1)
+                if (!grid_wait_count(a.bar, (unsigned)i * grid, a.err, &s_flag)) {
+                    cp_async_wait<0>();
+                    return;
+                }
+            for (int q = threadIdx.x; q < sn; q += blockDim.x) {
+                const int j = nxt[q];
+                double r = __ldcg(a.g + j) - a.xi[j] + gamma * (a.x[j] - a.z[j]);
+                if (a.e) r += a.e[j] * (beta * t - mu);
+                rhs[q] = (TA)r;
+            }
+        }
+        // bulk update of this CTA's tiles: g += G[:, S_i] dx_i
+#pragma unroll
+        for (int k = 0; k < kMaxTiles; ++k) {
+            const int tile = blockIdx.x + k * grid;
+            if (tile >= ntiles) break;
+            const int col = tile * 32 + lane;
+            TA acc = 0;
+            if (col < n) {
+                int q = warp;
+                for (; q + 7 * nw < s; q += 8 * nw) {
+                    TA v[8];
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk)
+                        v[kk] = (TA)to_f(G[(size_t)cur[q + kk * nw] * n + col]);
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) acc += v[kk] * dl[q + kk * nw];
+                }
+                for (; q < s; q += nw) acc += (TA)to_f(G[(size_t)cur[q] * n + col]) * dl[q];
+            }
+            wred[warp * 32 + lane] = acc;
+            __syncthreads();
+            if (warp == 0 && col < n) {
+                TA tot = 0;
+                for (int w = 0; w < nw; ++w) tot += wred[w * 32 + lane];
+                if (breg[k] == i)
+                    a.gdef[col] = (double)tot;
+                else if (breg[k] == i + 1)
+                    a.gnext[col] = (double)tot;
+                else {
+                    greg[k] += (double)tot;
+                    a.g[col] = greg[k];
+                }
+            }
+            __syncthreads();
+        }
+        grid_arrive(a.bar);
+    }
+    cp_async_wait<0>();
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
+}
+
+int lookahead_min_grid(int n) { return ((n + 31) / 32 + kMaxTiles - 1) / kMaxTiles; }
+
 // Residual form: each CTA owns a set of row slabs of A~ and the matching
 // entries of dres = A~ (x - x_anchor); the block gradient is
 // g_S = g_anchor,S + A~_S^T dres, reduced over CTAs through `partials`
@@ -585,10 +914,23 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
 }
 
 template <class TS, class TA, bool GRAM>
+static void chain_pick(int smax, int stage, int stage_p, int lookahead, size_t *smem,
+                       void (**kern)(ChainArgs)) {
+    if (GRAM && lookahead) {
+        *kern = k_chain_gram_la<TS, TA>;
+        *smem = LaSmem<TA>::bytes(smax, kChainThreads / 32, stage, stage_p);
+    } else {
+        *kern = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
+        *smem = ChainSmem<TA>::bytes(smax, kChainThreads / 32, stage);
+    }
+}
+
+template <class TS, class TA, bool GRAM>
 static cudaError_t chain_impl(const ChainArgs &a, int grid, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
-    size_t smem = ChainSmem<TA>::bytes(lay.smax(), kChainThreads / 32, a.stage);
-    void (*kern)(ChainArgs) = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
+    size_t smem = 0;
+    void (*kern)(ChainArgs) = nullptr;
+    chain_pick<TS, TA, GRAM>(lay.smax(), a.stage, a.stage_p, a.lookahead, &smem, &kern);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -617,9 +959,10 @@ cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cud
 }
 
 template <class TS, class TA, bool GRAM>
-static int chain_grid_impl(int smax, int stage, size_t *smem_out) {
-    size_t smem = ChainSmem<TA>::bytes(smax, kChainThreads / 32, stage);
-    void (*kern)(ChainArgs) = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
+static int chain_grid_impl(int smax, int stage, int stage_p, int lookahead, size_t *smem_out) {
+    size_t smem = 0;
+    void (*kern)(ChainArgs) = nullptr;
+    chain_pick<TS, TA, GRAM>(smax, stage, stage_p, lookahead, &smem, &kern);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         (void)cudaGetLastError();
@@ -633,23 +976,26 @@ static int chain_grid_impl(int smax, int stage, size_t *smem_out) {
     return per_sm * sms;
 }
 
-int chain_max_grid(int store, bool gram, int smax, int stage, size_t *smem_out) {
+int chain_max_grid(int store, bool gram, int smax, int stage, int stage_p, int lookahead,
+                   size_t *smem_out) {
     if (store == ST_F64)
-        return gram ? chain_grid_impl<double, double, true>(smax, stage, smem_out)
-                    : chain_grid_impl<double, double, false>(smax, stage, smem_out);
+        return gram ? chain_grid_impl<double, double, true>(smax, stage, stage_p, lookahead, smem_out)
+                    : chain_grid_impl<double, double, false>(smax, stage, stage_p, lookahead, smem_out);
     if (store == ST_F32)
-        return gram ? chain_grid_impl<float, float, true>(smax, stage, smem_out)
-                    : chain_grid_impl<float, float, false>(smax, stage, smem_out);
-    return gram ? chain_grid_impl<__nv_bfloat16, float, true>(smax, stage, smem_out)
-                : chain_grid_impl<__nv_bfloat16, float, false>(smax, stage, smem_out);
+        return gram ? chain_grid_impl<float, float, true>(smax, stage, stage_p, lookahead, smem_out)
+                    : chain_grid_impl<float, float, false>(smax, stage, stage_p, lookahead, smem_out);
+    return gram ? chain_grid_impl<__nv_bfloat16, float, true>(smax, stage, stage_p, lookahead, smem_out)
+                : chain_grid_impl<__nv_bfloat16, float, false>(smax, stage, stage_p, lookahead, smem_out);
 }
 
-// Staging K^{-1} needs two buffers in shared memory next to the rest.
-bool chain_can_stage(int store, int smax) {
+// Staging K^{-1} (and P) needs two buffers each in shared memory.
+bool chain_can_stage(int store, int smax, int with_p) {
     if (!factor_uses_kinv(smax)) return false;
     size_t ta = store == ST_F64 ? 8 : 4;
-    size_t need = (ta == 8 ? ChainSmem<double>::bytes(smax, kChainThreads / 32, 1)
-                           : ChainSmem<float>::bytes(smax, kChainThreads / 32, 1));
+    size_t need = with_p ? (ta == 8 ? LaSmem<double>::bytes(smax, kChainThreads / 32, 1, 1)
+                                    : LaSmem<float>::bytes(smax, kChainThreads / 32, 1, 1))
+                         : (ta == 8 ? ChainSmem<double>::bytes(smax, kChainThreads / 32, 1)
+                                    : ChainSmem<float>::bytes(smax, kChainThreads / 32, 1));
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -663,7 +1009,10 @@ __global__ void k_prox(ProxArgs a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < a.n) {
         double x = a.x[j] + a.dx[j];
-        if (a.g) a.g[j] += a.gdef[j];
+        if (a.g) {
+            a.g[j] += a.gdef[j] + (a.gnext ? a.gnext[j] : 0.0);
+            if (a.gnext) a.gnext[j] = 0.0;
+        }
         double xi = a.xi[j];
         double z = prox_z(a.phi, x, xi, a.gamma, a.lam1, a.lam2, a.lo, a.hi);
         a.x[j] = x;

@@ -68,14 +68,16 @@ struct rac_handle {
     bool gram = true;
     int grid = 0;
     cudaStream_t user = nullptr, st = nullptr;
-    cudaStream_t sf = nullptr;      // factor stream: factors of sweep s+1 overlap chain s
+    static constexpr int kFactorStreams = 3;
+    cudaStream_t sfs[kFactorStreams] = {nullptr, nullptr, nullptr};  // factors run ahead of the chain
     cudaEvent_t ev = nullptr;
     std::vector<cudaEvent_t> fev;   // per sweep slot: factor done, chain done (2 each)
     int kinv = 1, stage = 0, stage_p = 0, lookahead = 0;
-    size_t wstride = 0;             // bytes of one factor buffer (two buffers by sweep parity)
-    void *Pbuf = nullptr;           // lookahead matrices P_i (two buffers by sweep parity)
+    size_t wstride = 0;             // bytes of one sweep's factors (one buffer per period slot)
+    void *Pbuf = nullptr;           // lookahead matrices P_i^T (one buffer per period slot)
     size_t pstride = 0;
-    double *gnext = nullptr;
+    double *gnext = nullptr, *sperm = nullptr, *eperm = nullptr;
+    int perm_in_smem = 0;
     double kkt_scale = 1.0;
     // device buffers
     double *A64 = nullptr, *b64 = nullptr, *c64 = nullptr, *e64 = nullptr, *H64 = nullptr;
@@ -121,7 +123,8 @@ struct rac_handle {
         for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
         for (cudaEvent_t e : fev) cudaEventDestroy(e);
-        if (sf) cudaStreamDestroy(sf);
+        for (cudaStream_t q : sfs)
+            if (q) cudaStreamDestroy(q);
         for (void *q : allocs) cudaFree(q);
         if (h_stats) cudaFreeHost(h_stats);
         if (h_err) cudaFreeHost(h_err);
@@ -230,46 +233,57 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.gamma = h->gamma;
     a.bar = h->bar;
     a.err = h->err;
-    a.W = (char *)h->W + (size_t)(slot & 1) * h->wstride;
+    a.W = (char *)h->W + (size_t)slot * h->wstride;
     a.kinv = h->kinv;
     a.stage = h->stage;
     a.stage_p = h->stage_p;
     a.lookahead = h->lookahead;
-    a.P = h->lookahead ? (const void *)((char *)h->Pbuf + (size_t)(slot & 1) * h->pstride) : nullptr;
+    a.P = h->lookahead ? (const void *)((char *)h->Pbuf + (size_t)slot * h->pstride) : nullptr;
     a.gnext = h->gnext;
+    a.sperm = h->sperm;
+    a.eperm = h->k ? h->eperm : nullptr;
+    a.perm_in_smem = h->perm_in_smem;
     return a;
 }
 
 // One period of nb sweeps followed by the refresh (enqueued on h->st).
-// The factors of sweep s run on h->sf and overlap the chain of sweep s-1;
-// factor buffer s & 1 is reused only after chain s-2 has finished with it.
+// Block factors depend only on the assembly, so the factors of every sweep of
+// the period are launched up front on kFactorStreams streams (one buffer per
+// sweep slot) and run ahead of the chain; chain s waits only for factor s.
 static rac_status enqueue_period(rac_handle *h, int nb) {
-    cudaStream_t st = h->st, sf = h->sf;
+    cudaStream_t st = h->st;
     const bool pf = h->profile;
     if (pf) RAC_CK(cudaEventRecord(h->pev[0], st));
     RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, nb, h->perm, h->blk, h->tkey,
                            h->tidx, st));
     if (pf) RAC_CK(cudaEventRecord(h->pev[1], st));
     RAC_CK(cudaEventRecord(h->fev[0], st));      // fork: factors wait for the assembly
-    RAC_CK(cudaStreamWaitEvent(sf, h->fev[0], 0));
-    h->nlaunch += 1 + 3 * (int64_t)nb + 1;
+    // fork only the streams that receive work, so every forked stream rejoins
+    for (int q = 0; q < std::min(nb, (int)rac_handle::kFactorStreams); ++q)
+        RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[0], 0));
+    h->nlaunch += 1 + (3 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;
     for (int s = 0; s < nb; ++s) {
         ChainArgs a = chain_args(h, s);
+        cudaStream_t sf = h->sfs[s % rac_handle::kFactorStreams];
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
-        cudaEvent_t fdone = h->fev[1 + 2 * s], cdone = h->fev[2 + 2 * s];
-        if (s >= 2) RAC_CK(cudaStreamWaitEvent(sf, h->fev[2 + 2 * (s - 2)], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
         int kinv = 1;
         RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W),
                              const_cast<void *>(a.P), &kinv, sf));
         if (pf) RAC_CK(cudaEventRecord(ev[1], sf));
-        RAC_CK(cudaEventRecord(fdone, sf));
-        RAC_CK(cudaStreamWaitEvent(st, fdone, 0));
+        RAC_CK(cudaEventRecord(h->fev[1 + s], sf));
+    }
+    for (int s = 0; s < nb; ++s) {
+        ChainArgs a = chain_args(h, s);
+        cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
+        if (h->lookahead)
+            RAC_CK(launch_prepare(h->n, a.perm, h->x, h->z, h->xi, h->k ? h->e64 : nullptr,
+                                  h->gamma, h->sperm, h->eperm, st));
+        RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
         if (pf) RAC_CK(cudaEventRecord(ev[3], st));
-        RAC_CK(cudaEventRecord(cdone, st));
         ProxArgs pa;
         std::memset(&pa, 0, sizeof(pa));
         pa.n = h->n;
@@ -417,9 +431,9 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->profile = o->profile != 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     RAC_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
-    RAC_CK(cudaStreamCreateWithFlags(&h->sf, cudaStreamNonBlocking));
+    for (auto &q : h->sfs) RAC_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
     RAC_CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
-    h->fev.resize(1 + 2 * (size_t)h->refresh_every, nullptr);
+    h->fev.resize(1 + (size_t)h->refresh_every, nullptr);
     for (auto &e : h->fev) RAC_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     if (h->profile) {
         h->pev.resize(3 + 5 * (size_t)h->refresh_every, nullptr);
@@ -525,7 +539,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     BlockLayout lay(n, h->p);
     const size_t ta = h->store == ST_F64 ? 8 : 4;
     h->wstride = (lay.factor_total() * ta + 255) & ~(size_t)255;
-    RAC_CK(cudaMalloc(&h->W, 2 * h->wstride));
+    RAC_CK(cudaMalloc(&h->W, (size_t)h->refresh_every * h->wstride));
     h->allocs.push_back(h->W);
     h->kinv = factor_uses_kinv(lay.smax()) ? 1 : 0;
     int sms = 148, dev = 0;
@@ -533,21 +547,24 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // Gram form with register factors: lookahead chain (P_i precomputed)
     h->lookahead = (h->gram && h->kinv && factor_can_make_p(h->store, lay.smax())) ? 1 : 0;
+    h->perm_in_smem = (h->lookahead && n <= lookahead_perm_smem_max()) ? 1 : 0;
+    const int nperm = h->perm_in_smem ? n : 0;
     if (h->lookahead) {
-        h->stage = chain_can_stage(h->store, lay.smax(), 1) ? 1 : 0;
+        h->stage = chain_can_stage(h->store, lay.smax(), 1, nperm) ? 1 : 0;
         h->stage_p = h->stage;
-        if (!h->stage) h->stage = chain_can_stage(h->store, lay.smax(), 0) ? 1 : 0;
+        if (!h->stage) h->stage = chain_can_stage(h->store, lay.smax(), 0, 0) ? 1 : 0;
     } else {
-        h->stage = chain_can_stage(h->store, lay.smax(), 0) ? 1 : 0;
+        h->stage = chain_can_stage(h->store, lay.smax(), 0, 0) ? 1 : 0;
     }
     size_t smem = 0;
     int gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, h->stage_p, h->lookahead,
-                              &smem);
+                              nperm, &smem);
     if (h->lookahead && gmax < lookahead_min_grid(n)) {
         h->lookahead = 0;
         h->stage_p = 0;
-        h->stage = chain_can_stage(h->store, lay.smax(), 0) ? 1 : 0;
-        gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, 0, 0, &smem);
+        h->perm_in_smem = 0;
+        h->stage = chain_can_stage(h->store, lay.smax(), 0, 0) ? 1 : 0;
+        gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, 0, 0, 0, &smem);
     }
     if (gmax <= 0) return RAC_ERR_ARG;
     int want = h->gram ? std::min(sms, (n + 31) / 32) : std::min(sms, h->nslab);
@@ -557,8 +574,10 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     if (h->lookahead) {
         h->pstride = ((size_t)h->p * BlockLayout::pad4((size_t)lay.smax() * lay.smax()) * ta + 255) &
                      ~(size_t)255;
-        RAC_CK(cudaMalloc(&h->Pbuf, 2 * h->pstride));
+        RAC_CK(cudaMalloc(&h->Pbuf, (size_t)h->refresh_every * h->pstride));
         h->allocs.push_back(h->Pbuf);
+        RAC_ST(h->alloc(&h->sperm, n));
+        if (h->k) RAC_ST(h->alloc(&h->eperm, n));
     }
     if (!h->gram) {
         RAC_CK(cudaMalloc(&h->cpart, (size_t)2 * h->grid * lay.smax() * ta));

@@ -55,6 +55,9 @@ struct ChainArgs {
     double *gnext;          // increments of the next block's coordinates, folded in by k_prox
     int stage_p;            // 1: stage P_i in shared memory too
     int lookahead;          // 1: run k_chain_gram_la
+    const double *sperm;    // lookahead: -xi + gamma (x - z) in permuted order (n)
+    const double *eperm;    // lookahead: e in permuted order (n) or NULL
+    int perm_in_smem;       // lookahead: the whole permutation fits in shared memory
 };
 
 struct ProxArgs {
@@ -85,11 +88,17 @@ int lookahead_min_grid(int n);
 bool factor_uses_kinv(int smax);
 
 cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cudaStream_t st);
+// nperm: n when the lookahead kernel holds the whole permutation in shared memory, else 0
 int chain_max_grid(int store, bool gram, int smax, int stage, int stage_p, int lookahead,
-                   size_t *smem_out);
-bool chain_can_stage(int store, int smax, int with_p);
+                   int nperm, size_t *smem_out);
+bool chain_can_stage(int store, int smax, int with_p, int nperm);
 
 cudaError_t launch_prox(const ProxArgs &a, cudaStream_t st);
+// static part of the block right-hand sides, in the sweep's permuted order
+cudaError_t launch_prepare(int n, const int *perm, const double *x, const double *z,
+                           const double *xi, const double *e, double gamma, double *sperm,
+                           double *eperm, cudaStream_t st);
+int lookahead_perm_smem_max();
 
 // exact FP64 pieces of the refresh
 cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const double *z,

@@ -320,11 +320,16 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_rows(ChainArgs a, TA 
         }
     }
     __syncthreads();
-    // sweep operator, one pivot per step (see sweep_inverse_regs)
+    // Sweep operator, one pivot per step.  The broadcast row k holds d - 1 at
+    // position k (d = a_kk), so the single update a_ij -= (a_ik / d) v_j also
+    // produces a_ik / d in the pivot column; the pivot row itself is scaled
+    // by 1/d and its diagonal set to -1/d.
+    if (threadIdx.x == 0) vbuf[0] -= TA(1);
+    __syncthreads();
     for (int k = 0; k < s; ++k) {
         const TA *vk = vbuf + (k & 1) * smax;
         TA *vn = vbuf + ((k + 1) & 1) * smax;
-        TA d = vk[k];
+        TA d = vk[k] + TA(1);
         if (!(d > TA(0))) {
             if (threadIdx.x == 0) set_err(a.err, RAC_ERR_NOT_PD);
             d = TA(1);
@@ -335,21 +340,21 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_rows(ChainArgs a, TA 
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int j = c0 + NP * u;
-                    if (j < s) acc[u] = (j == k) ? -rd : vk[j] * rd;
+                    if (j < s) acc[u] = (j == k) ? -rd : acc[u] * rd;
                 }
             } else {
                 const TA vir = vk[r] * rd;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int j = c0 + NP * u;
-                    if (j < s) acc[u] = (j == k) ? vir : acc[u] - vir * vk[j];
+                    if (j < s) acc[u] = fma(-vir, vk[j], acc[u]);
                 }
             }
             if (r == k + 1) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int j = c0 + NP * u;
-                    if (j < s) vn[j] = acc[u];
+                    if (j < s) vn[j] = (j == k + 1) ? acc[u] - TA(1) : acc[u];
                 }
             }
         }
@@ -364,7 +369,8 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_rows(ChainArgs a, TA 
         }
     }
     if (!want_p) return;
-    // P_i = K_i^{-1} G[S_i, S_{i-1}]  (s x sp), staged through shared memory
+    // P_i = K_i^{-1} G[S_i, S_{i-1}]  (s x sp), stored transposed (sp x s) so
+    // the chain reads it column-wise without bank conflicts.
     TA *Ks = (TA *)big;
     TA *Gp = Ks + (size_t)smax * smax;
     if (rv) {
@@ -390,14 +396,14 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_rows(ChainArgs a, TA 
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int c = c0 + NP * u;
-                if (c < sp) pacc[u] += kv * gr[c];
+                if (c < sp) pacc[u] = fma(kv, gr[c], pacc[u]);
             }
         }
         TA *po = Pout + (size_t)i * BlockLayout::pad4((size_t)smax * smax);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int c = c0 + NP * u;
-            if (c < sp) po[(size_t)r * sp + c] = pacc[u];
+            if (c < sp) po[(size_t)c * s + r] = pacc[u];
         }
     }
 }
@@ -668,12 +674,17 @@ __device__ __forceinline__ void grid_arrive(GridBarrier *bar) {
     }
 }
 
+constexpr int kPermSmemMax = 8192;   // whole-sweep permutation in shared memory up to this n
+int lookahead_perm_smem_max() { return kPermSmemMax; }
+
 template <class TA> struct LaSmem {
     __host__ __device__ static size_t kst(int smax) { return BlockLayout::pad4((size_t)smax * smax); }
-    static size_t bytes(int smax, int nw, int stage, int stage_p) {
-        return 2 * (((size_t)smax * sizeof(int) + 15) & ~(size_t)15) + 3 * (size_t)smax * sizeof(TA) +
-               (size_t)nw * 32 * sizeof(TA) + 64 * sizeof(double) + 64 +
-               (stage ? 2 * kst(smax) * sizeof(TA) : 0) + (stage_p ? 2 * kst(smax) * sizeof(TA) : 0);
+    static size_t bytes(int smax, int nw, int stage, int stage_p, int n = 0) {
+        size_t permb = n > 0 && n <= kPermSmemMax ? (((size_t)n * sizeof(int) + 15) & ~(size_t)15)
+                                                  : 3 * (((size_t)smax * sizeof(int) + 15) & ~(size_t)15);
+        return permb + 3 * (size_t)smax * sizeof(TA) + (size_t)nw * 32 * sizeof(TA) +
+               64 * sizeof(double) + 64 + (stage ? 2 * kst(smax) * sizeof(TA) : 0) +
+               (stage_p ? 2 * kst(smax) * sizeof(TA) : 0);
     }
 };
 
@@ -683,9 +694,12 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
     BlockLayout lay(a.n, a.p);
     const int smax = lay.smax();
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = a.n, grid = gridDim.x;
+    const bool pin = a.perm_in_smem != 0;
     const size_t ib = ((size_t)smax * sizeof(int) + 15) & ~(size_t)15;
-    int *idxb = (int *)sm_raw;                           // 2 index buffers
-    TA *rhs = (TA *)(sm_raw + 2 * ib);
+    const size_t permb = pin ? (((size_t)n * sizeof(int) + 15) & ~(size_t)15) : 3 * ib;
+    int *permsm = (int *)sm_raw;
+    TA *rhs = (TA *)(sm_raw + permb);
     TA *dl = rhs + smax;
     TA *dn = dl + smax;
     TA *wred = dn + smax;
@@ -697,12 +711,23 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
     const TS *G = (const TS *)a.G;
     const TA *Wall = (const TA *)a.W;
     const TA *Pall = (const TA *)a.P;
-    const int n = a.n, grid = gridDim.x;
-    const double gamma = a.gamma, beta = a.beta;
+    const double beta = a.beta;
     const double mu = a.mu ? *a.mu : 0.0;
     double t = a.e ? *a.t : 0.0;
     const int ntiles = (n + 31) >> 5;
 
+    // indices of block b: whole permutation in smem, or a ring of three
+    // per-block buffers filled one block ahead
+    auto bidx = [&](int b) -> int * {
+        return pin ? permsm + lay.offset(b) : (int *)((unsigned char *)sm_raw + (b % 3) * ib);
+    };
+    auto load_idx = [&](int b) {
+        if (!pin && b < a.p) {
+            int *d = bidx(b);
+            const int sb = lay.size(b), ob = lay.offset(b);
+            for (int q = threadIdx.x; q < sb; q += blockDim.x) d[q] = a.perm[ob + q];
+        }
+    };
     auto prefetch = [&](int b) {
         if (b < a.p) {
             const int sb = lay.size(b);
@@ -722,7 +747,6 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
         return a.stage_p ? pbuf + (size_t)(b & 1) * kst : Pall + (size_t)b * kst;
     };
 
-    // this CTA's tiles of g, cached in warp 0
     double greg[kMaxTiles];
     int breg[kMaxTiles];
 #pragma unroll
@@ -737,15 +761,19 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
     }
     prefetch(0);
     prefetch(1);
-    // prologue: rhs of block 0 from the gradient at kernel start
-    {
+    if (pin) {
+        for (int q = threadIdx.x; q < n; q += blockDim.x) permsm[q] = a.perm[q];
+    } else {
+        load_idx(0);
+        load_idx(1);
+    }
+    __syncthreads();
+    {   // rhs of block 0 from the gradient at kernel start
         const int s0 = lay.size(0);
-        int *cur = idxb;
+        const int *cur = bidx(0);
         for (int q = threadIdx.x; q < s0; q += blockDim.x) {
-            const int j = a.perm[q];
-            cur[q] = j;
-            double r = a.g[j] - a.xi[j] + gamma * (a.x[j] - a.z[j]);
-            if (a.e) r += a.e[j] * (beta * t - mu);
+            double r = a.g[cur[q]] + a.sperm[q];
+            if (a.e) r += a.eperm[q] * (beta * t - mu);
             rhs[q] = (TA)r;
         }
     }
@@ -753,14 +781,37 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
     __syncthreads();
     for (int i = 0; i < a.p; ++i) {
         const int s = lay.size(i);
-        const int *cur = (const int *)((unsigned char *)idxb + (i & 1) * ib);
-        // dx_i = -K_i^{-1} rhs - dn  (dn = P_i dx_{i-1}, zero for block 0)
-        if (i == 0)
-            for (int q = threadIdx.x; q < s; q += blockDim.x) dl[q] = TA(0);
-        else
-            for (int q = threadIdx.x; q < s; q += blockDim.x) dl[q] = dn[q];
-        __syncthreads();
-        gemv_rows<TA>(kptr(i), s, s, rhs, dl, true);
+        const int *cur = bidx(i);
+        const bool has_next = i + 1 < a.p;
+        const int sn = has_next ? lay.size(i + 1) : 0, offn = has_next ? lay.offset(i + 1) : 0;
+        // loads that do not depend on dx_i, issued early: the static rhs part
+        // of block i+1 and this CTA's first gradient tile of G[S_i, :]
+        double snext = 0.0, enext = 0.0;
+        if (has_next && threadIdx.x < sn) {
+            snext = a.sperm[offn + threadIdx.x];
+            if (a.e) enext = a.eperm[offn + threadIdx.x];
+        }
+        const int col0 = blockIdx.x * 32 + lane;
+        constexpr int GV = 16;
+        TA gv[GV];
+#pragma unroll
+        for (int k = 0; k < GV; ++k) {
+            const int q = warp + k * nw;
+            gv[k] = (col0 < n && q < s) ? (TA)to_f(G[(size_t)cur[q] * n + col0]) : TA(0);
+        }
+        // dx_i = -K_i^{-1} rhs - P_i dx_{i-1}; K^{-1} symmetric, one thread per row
+        for (int r = threadIdx.x; r < s; r += blockDim.x) {
+            const TA *kc = kptr(i) + r;
+            TA acc = i ? dn[r] : TA(0);
+            TA acc2 = 0;
+            int c = 0;
+            for (; c + 1 < s; c += 2) {
+                acc = fma(kc[(size_t)c * s], rhs[c], acc);
+                acc2 = fma(kc[(size_t)(c + 1) * s], rhs[c + 1], acc2);
+            }
+            if (c < s) acc = fma(kc[(size_t)c * s], rhs[c], acc);
+            dl[r] = -(acc + acc2);
+        }
         __syncthreads();
         if (a.e) {
             double loc = 0.0;
@@ -769,24 +820,28 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
         }
         if (blockIdx.x == 0)
             for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[cur[q]] = (double)dl[q];
-        if (i + 1 < a.p) {
-            const int sn = lay.size(i + 1), offn = lay.offset(i + 1);
-            int *nxt = (int *)((unsigned char *)idxb + ((i + 1) & 1) * ib);
+        if (has_next) {
             prefetch(i + 2);            // buffers (i+2)&1 = i&1 are free: block i is solved
-            cp_async_wait<1>();         // block i+1's K^{-1} and P have landed
-            for (int q = threadIdx.x; q < sn; q += blockDim.x) nxt[q] = a.perm[offn + q];
+            load_idx(i + 2);
+            cp_async_wait<1>();         // block i+1's K^{-1} and P^T have landed
             __syncthreads();
-            gemv_rows<TA>(pptr(i + 1), sn, s, dl, dn, false);   // dn = P_{i+1} dx_i
+            // dn = P_{i+1} dx_i from P^T (s_i x s_{i+1}), one thread per row
+            const TA *pt = pptr(i + 1);
+            for (int q = threadIdx.x; q < sn; q += blockDim.x) {
+                TA acc = 0;
+                for (int c = 0; c < s; ++c) acc = fma(pt[(size_t)c * sn + q], dl[c], acc);
+                dn[q] = acc;
+            }
             if (i >= 1)
                 if (!grid_wait_count(a.bar, (unsigned)i * grid, a.err, &s_flag)) {
                     cp_async_wait<0>();
                     return;
                 }
-            for (int q = threadIdx.x; q < sn; q += blockDim.x) {
-                const int j = nxt[q];
-                double r = __ldcg(a.g + j) - a.xi[j] + gamma * (a.x[j] - a.z[j]);
-                if (a.e) r += a.e[j] * (beta * t - mu);
-                rhs[q] = (TA)r;
+            const int *nxt = bidx(i + 1);
+            if (threadIdx.x < sn) {
+                double r = __ldcg(a.g + nxt[threadIdx.x]) + snext;
+                if (a.e) r += enext * (beta * t - mu);
+                rhs[threadIdx.x] = (TA)r;
             }
         }
         // bulk update of this CTA's tiles: g += G[:, S_i] dx_i
@@ -796,7 +851,15 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
             if (tile >= ntiles) break;
             const int col = tile * 32 + lane;
             TA acc = 0;
-            if (col < n) {
+            if (k == 0) {
+#pragma unroll
+                for (int kk = 0; kk < GV; ++kk) {
+                    const int q = warp + kk * nw;
+                    if (q < s) acc = fma(gv[kk], dl[q], acc);
+                }
+                for (int q = warp + GV * nw; q < s; q += nw)
+                    if (col < n) acc += (TA)to_f(G[(size_t)cur[q] * n + col]) * dl[q];
+            } else if (col < n) {
                 int q = warp;
                 for (; q + 7 * nw < s; q += 8 * nw) {
                     TA v[8];
@@ -828,6 +891,22 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
     }
     cp_async_wait<0>();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
+}
+
+__global__ void k_prepare(int n, const int *perm, const double *x, const double *z,
+                          const double *xi, const double *e, double gamma, double *sperm,
+                          double *eperm) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int j = perm[q];
+    sperm[q] = -xi[j] + gamma * (x[j] - z[j]);
+    if (e) eperm[q] = e[j];
+}
+cudaError_t launch_prepare(int n, const int *perm, const double *x, const double *z,
+                           const double *xi, const double *e, double gamma, double *sperm,
+                           double *eperm, cudaStream_t st) {
+    k_prepare<<<(n + 255) / 256, 256, 0, st>>>(n, perm, x, z, xi, e, gamma, sperm, eperm);
+    return cudaGetLastError();
 }
 
 int lookahead_min_grid(int n) { return ((n + 31) / 32 + kMaxTiles - 1) / kMaxTiles; }
@@ -914,11 +993,11 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
 }
 
 template <class TS, class TA, bool GRAM>
-static void chain_pick(int smax, int stage, int stage_p, int lookahead, size_t *smem,
+static void chain_pick(int smax, int stage, int stage_p, int lookahead, int nperm, size_t *smem,
                        void (**kern)(ChainArgs)) {
     if (GRAM && lookahead) {
         *kern = k_chain_gram_la<TS, TA>;
-        *smem = LaSmem<TA>::bytes(smax, kChainThreads / 32, stage, stage_p);
+        *smem = LaSmem<TA>::bytes(smax, kChainThreads / 32, stage, stage_p, nperm);
     } else {
         *kern = GRAM ? k_chain_gram<TS, TA> : k_chain_res<TS, TA>;
         *smem = ChainSmem<TA>::bytes(smax, kChainThreads / 32, stage);
@@ -930,7 +1009,8 @@ static cudaError_t chain_impl(const ChainArgs &a, int grid, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
     size_t smem = 0;
     void (*kern)(ChainArgs) = nullptr;
-    chain_pick<TS, TA, GRAM>(lay.smax(), a.stage, a.stage_p, a.lookahead, &smem, &kern);
+    chain_pick<TS, TA, GRAM>(lay.smax(), a.stage, a.stage_p, a.lookahead,
+                             a.perm_in_smem ? a.n : 0, &smem, &kern);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -959,10 +1039,11 @@ cudaError_t launch_chain(int store, bool gram, const ChainArgs &a, int grid, cud
 }
 
 template <class TS, class TA, bool GRAM>
-static int chain_grid_impl(int smax, int stage, int stage_p, int lookahead, size_t *smem_out) {
+static int chain_grid_impl(int smax, int stage, int stage_p, int lookahead, int nperm,
+                           size_t *smem_out) {
     size_t smem = 0;
     void (*kern)(ChainArgs) = nullptr;
-    chain_pick<TS, TA, GRAM>(smax, stage, stage_p, lookahead, &smem, &kern);
+    chain_pick<TS, TA, GRAM>(smax, stage, stage_p, lookahead, nperm, &smem, &kern);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         (void)cudaGetLastError();
@@ -977,23 +1058,20 @@ static int chain_grid_impl(int smax, int stage, int stage_p, int lookahead, size
 }
 
 int chain_max_grid(int store, bool gram, int smax, int stage, int stage_p, int lookahead,
-                   size_t *smem_out) {
-    if (store == ST_F64)
-        return gram ? chain_grid_impl<double, double, true>(smax, stage, stage_p, lookahead, smem_out)
-                    : chain_grid_impl<double, double, false>(smax, stage, stage_p, lookahead, smem_out);
-    if (store == ST_F32)
-        return gram ? chain_grid_impl<float, float, true>(smax, stage, stage_p, lookahead, smem_out)
-                    : chain_grid_impl<float, float, false>(smax, stage, stage_p, lookahead, smem_out);
-    return gram ? chain_grid_impl<__nv_bfloat16, float, true>(smax, stage, stage_p, lookahead, smem_out)
-                : chain_grid_impl<__nv_bfloat16, float, false>(smax, stage, stage_p, lookahead, smem_out);
+                   int nperm, size_t *smem_out) {
+#define RAC_CG(TS, TA, GR) chain_grid_impl<TS, TA, GR>(smax, stage, stage_p, lookahead, nperm, smem_out)
+    if (store == ST_F64) return gram ? RAC_CG(double, double, true) : RAC_CG(double, double, false);
+    if (store == ST_F32) return gram ? RAC_CG(float, float, true) : RAC_CG(float, float, false);
+    return gram ? RAC_CG(__nv_bfloat16, float, true) : RAC_CG(__nv_bfloat16, float, false);
+#undef RAC_CG
 }
 
 // Staging K^{-1} (and P) needs two buffers each in shared memory.
-bool chain_can_stage(int store, int smax, int with_p) {
+bool chain_can_stage(int store, int smax, int with_p, int nperm) {
     if (!factor_uses_kinv(smax)) return false;
     size_t ta = store == ST_F64 ? 8 : 4;
-    size_t need = with_p ? (ta == 8 ? LaSmem<double>::bytes(smax, kChainThreads / 32, 1, 1)
-                                    : LaSmem<float>::bytes(smax, kChainThreads / 32, 1, 1))
+    size_t need = with_p ? (ta == 8 ? LaSmem<double>::bytes(smax, kChainThreads / 32, 1, 1, nperm)
+                                    : LaSmem<float>::bytes(smax, kChainThreads / 32, 1, 1, nperm))
                          : (ta == 8 ? ChainSmem<double>::bytes(smax, kChainThreads / 32, 1)
                                     : ChainSmem<float>::bytes(smax, kChainThreads / 32, 1));
     int dev = 0, optin = 0;

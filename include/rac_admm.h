@@ -110,6 +110,10 @@ typedef struct {
     const double *xi0;      /* optional warm start for the dual xi (n), or NULL */
     void *stream;           /* cudaStream_t */
     int32_t profile;        /* 1: time each kernel class with CUDA events (rac_info.t_*) */
+    int32_t xi0_from_grad;  /* 1 (with x0): start xi at grad f(x0), the value xi takes at a
+                               fixed point (block stationarity with x = z); overrides xi0 */
+    int32_t ws_fallback;    /* 1 (with x0): if the KKT after the first refresh period exceeds
+                               the KKT of the cold start z = 0, restart from zero */
 } rac_options;
 
 /* KKT measure used for the stop test, evaluated in FP64 on z with the exact
@@ -133,6 +137,7 @@ typedef struct {
      * call, measured by CUDA events on the handle's stream (0 otherwise) */
     double t_assembly_ms, t_factor_ms, t_chain_ms, t_prox_ms, t_refresh_ms;
     int64_t chain_launches; /* launches of the sweep-chain kernel in this call */
+    int32_t warm_start_rejected; /* 1 if ws_fallback restarted this solve from zero */
 } rac_info;
 
 typedef struct rac_handle rac_handle;
@@ -208,41 +213,56 @@ void rac_admm_destroy(rac_handle *h);
 rac_status rac_assembly(int64_t n, int32_t num_blocks, uint64_t seed, int64_t sweep0,
                         int32_t nsweeps, int32_t *perm_out, int32_t *blk_out, void *stream);
 
-/* Learned warm start (per-coordinate MLP, 6 -> 128 -> 128 -> 2). */
+/* ---- learned warm start (no counterpart in the paper) -----------------
+ * A per-coordinate MLP (6 -> 128 -> 128 -> 2, ReLU) predicts, from features
+ * of column j of a data-form LASSO / Elastic-Net problem, the scale-free
+ * solution u_j = x*_j ||A_j|| / lambda_max and the logit of x*_j != 0
+ * (lambda_max = ||A^T b||_inf).  It only chooses the starting point: the
+ * solver still runs to the same KKT tolerance (rac_options.x0 with
+ * xi0_from_grad = 1, optionally ws_fallback = 1).  All pointers here are
+ * device pointers unless stated; parameters are float, laid out W1[128][6],
+ * b1[128], W2[128][128], b2[128], W3[2][128], b3[2]. */
 #define RAC_WS_FEATURES 6
 #define RAC_WS_HIDDEN 128
 #define RAC_WS_OUT 2
-/* Number of float parameters of the network (W1,b1,W2,b2,W3,b3). */
+
+/* Number of float parameters of the network. */
 int64_t rac_ws_num_params(void);
 
-/* Per-coordinate features of a data-form problem (device pointers):
- * F (n x 6 row-major, float) = [A_j^T b / ||A_j||, ||A_j||, lambda1/lambda_max,
- * lambda2, |A_j^T b| / lambda1, log(n/m)], lambda_max = ||A^T b||_inf.
- * Also writes lambda_max to *lam_max_out (host). */
-rac_status rac_ws_features(int64_t m, int64_t n, const double *A, int64_t lda,
-                           const double *b, double lambda1, double lambda2,
-                           float *F, double *lam_max_out, void *stream);
+/* Features F (n x 6 row-major): [A_j^T b / (||A_j|| lambda_max), ||A_j||,
+ * lambda1 / lambda_max, lambda2, |A_j^T b| / lambda1, log(n / m)];
+ * *lam_max_out (host) receives lambda_max.  A (m x n, lda) and b on the device. */
+rac_status rac_ws_features(int64_t m, int64_t n, const double *A, int64_t lda, const double *b,
+                           double lambda1, double lambda2, float *F, double *lam_max_out,
+                           void *stream);
 
-/* Forward pass for N rows of features (device): out (N x 2 row-major) =
- * [predicted x_j / (|A_j^T b| / ||A_j||^2 + eps) scale-free target, logit of
- * p(active)].  params has rac_ws_num_params() floats (device). */
+/* Same, plus training targets T (n x 2 row-major) = [x*_j ||A_j|| / lambda_max,
+ * 1 if x*_j != 0 else 0] from a solution xstar (n, device). */
+rac_status rac_ws_features_targets(int64_t m, int64_t n, const double *A, int64_t lda,
+                                   const double *b, double lambda1, double lambda2, float *F,
+                                   const double *xstar, float *T, double *lam_max_out,
+                                   void *stream);
+
+/* Network outputs for N feature rows: out (N x 2 row-major) = [u, logit]. */
 rac_status rac_ws_forward(int64_t N, const float *F, const float *params, float *out,
                           void *stream);
 
-/* One training step on N samples: loss = mean((out0 - t0)^2 * mask)
- * + mean(BCE(out1, t1)); grads accumulated into grad (zeroed first), then one
- * Adam step (lr, beta1, beta2, eps) at step count `step` (>= 1) updating
- * params, m1, m2 (device, rac_ws_num_params() floats each).  *loss_out
- * receives the loss (host). */
-rac_status rac_ws_train_step(int64_t N, const float *F, const float *T, float *params,
-                             float *grad, float *m1, float *m2, int32_t step, float lr,
-                             float beta1, float beta2, float eps, float *loss_out,
-                             void *stream);
-
-/* Gradient only (no Adam step): grad (device) receives d loss / d params and
- * *loss_out the loss; used to check the backward kernels. */
+/* Mean loss over N samples, (u - t0)^2 + BCE-with-logits(logit, t1), and its
+ * gradient: grad (rac_ws_num_params() floats) is overwritten; *loss_out (host). */
 rac_status rac_ws_loss_grad(int64_t N, const float *F, const float *T, const float *params,
                             float *grad, float *loss_out, void *stream);
+
+/* rac_ws_loss_grad followed by one Adam step (lr, beta1, beta2, eps; bias
+ * correction for step >= 1) on params with moment buffers m1, m2. */
+rac_status rac_ws_train_step(int64_t N, const float *F, const float *T, float *params,
+                             float *grad, float *m1, float *m2, int32_t step, float lr,
+                             float beta1, float beta2, float eps, float *loss_out, void *stream);
+
+/* Warm start for a problem: x0_out (n, host or device) = u_j lambda_max /
+ * ||A_j|| where the predicted probability exceeds 1/2, else 0. */
+rac_status rac_ws_predict(int64_t m, int64_t n, const double *A, int64_t lda, const double *b,
+                          double lambda1, double lambda2, const float *params, double *x0_out,
+                          void *stream);
 
 #ifdef __cplusplus
 }

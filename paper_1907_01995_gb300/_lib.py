@@ -35,7 +35,8 @@ class RacOptions(ctypes.Structure):
     _fields_ = [("num_blocks", c_int32), ("beta", c_double), ("gamma", c_double),
                 ("tol", c_double), ("max_sweeps", c_int32), ("refresh_every", c_int32),
                 ("seed", c_uint64), ("storage", c_int32), ("form", c_int32), ("grid", c_int32),
-                ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p), ("profile", c_int32)]
+                ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p), ("profile", c_int32),
+                ("xi0_from_grad", c_int32), ("ws_fallback", c_int32)]
 
 
 class RacInfo(ctypes.Structure):
@@ -44,7 +45,8 @@ class RacInfo(ctypes.Structure):
                 ("status", c_int32), ("form", ctypes.c_char * 32),
                 ("kernel_launches", c_int64), ("setup_launches", c_int64),
                 ("t_assembly_ms", c_double), ("t_factor_ms", c_double), ("t_chain_ms", c_double),
-                ("t_prox_ms", c_double), ("t_refresh_ms", c_double), ("chain_launches", c_int64)]
+                ("t_prox_ms", c_double), ("t_refresh_ms", c_double), ("chain_launches", c_int64),
+                ("warm_start_rejected", c_int32)]
 
 
 P = ctypes.POINTER
@@ -67,7 +69,12 @@ SIGNATURES = [
     ("rac_ws_num_params", c_int64, []),
     ("rac_ws_features", c_int32, [c_int64, c_int64, c_void_p, c_int64, c_void_p, c_double,
                                   c_double, c_void_p, P(c_double), c_void_p]),
+    ("rac_ws_features_targets", c_int32, [c_int64, c_int64, c_void_p, c_int64, c_void_p, c_double,
+                                          c_double, c_void_p, c_void_p, c_void_p, P(c_double),
+                                          c_void_p]),
     ("rac_ws_forward", c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("rac_ws_predict", c_int32, [c_int64, c_int64, c_void_p, c_int64, c_void_p, c_double, c_double,
+                                 c_void_p, c_void_p, c_void_p]),
     ("rac_ws_train_step", c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_int32, c_float, c_float, c_float, c_float,
                                     P(c_float), c_void_p]),

@@ -92,7 +92,8 @@ def make_problem(keep: _Keep, A=None, b=None, *, H=None, c=None, E=None, d=None,
 
 def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=1e-6,
                  max_sweeps=1000, refresh_every=10, seed=0, storage="fp64", form="auto",
-                 grid=0, x0=None, xi0=None, stream=None, profile=False) -> L.RacOptions:
+                 grid=0, x0=None, xi0=None, stream=None, profile=False, xi0_from_grad=False,
+                 ws_fallback=False) -> L.RacOptions:
     o = L.RacOptions()
     L.load().rac_options_default(ctypes.byref(o))
     o.num_blocks = int(num_blocks)
@@ -106,6 +107,8 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
     o.xi0 = keep.vec(xi0, n)
     o.stream = _stream_handle(stream)
     o.profile = 1 if profile else 0
+    o.xi0_from_grad = 1 if xi0_from_grad else 0
+    o.ws_fallback = 1 if ws_fallback else 0
     return o
 
 
@@ -116,7 +119,8 @@ def _info_dict(info: L.RacInfo) -> dict:
             "kernel_launches": info.kernel_launches, "setup_launches": info.setup_launches,
             "t_assembly_ms": info.t_assembly_ms, "t_factor_ms": info.t_factor_ms,
             "t_chain_ms": info.t_chain_ms, "t_prox_ms": info.t_prox_ms,
-            "t_refresh_ms": info.t_refresh_ms, "chain_launches": info.chain_launches}
+            "t_refresh_ms": info.t_refresh_ms, "chain_launches": info.chain_launches,
+            "warm_start_rejected": info.warm_start_rejected}
 
 
 class Handle:

@@ -77,8 +77,12 @@ struct rac_handle {
     void *Pbuf = nullptr;           // lookahead matrices P_i^T (one buffer per period slot)
     size_t pstride = 0;
     double *gnext = nullptr, *sperm = nullptr, *eperm = nullptr;
+    double *lam_dev = nullptr;      // (lambda1, lambda2) read by the prox and KKT kernels
     int perm_in_smem = 0;
     double kkt_scale = 1.0;
+    double kkt_cold0 = 0.0;         // KKT of z = 0 (for the warm-start fallback)
+    bool xi_from_grad = false, ws_fallback = false, warm = false;
+    int solves = 0;
     // device buffers
     double *A64 = nullptr, *b64 = nullptr, *c64 = nullptr, *e64 = nullptr, *H64 = nullptr;
     void *G = nullptr, *As = nullptr;
@@ -191,7 +195,7 @@ static rac_status enqueue_refresh(rac_handle *h) {
         RAC_CK(launch_symv_f64(h->n, h->H64, h->z, h->c64, h->gz, st));
     }
     RAC_CK(launch_kkt(h->n, h->gz, h->x, h->z, h->e64, h->d, h->k ? h->mu : nullptr, h->phi,
-                      h->lam1, h->lam2, h->lo, h->hi, h->stats, st));
+                      h->lam1, h->lam2, h->lo, h->hi, h->stats, st, h->lam_dev));
     if (h->gram) {
         RAC_CK(launch_gram_anchor(h->store, h->n, h->G, h->gz, h->x, h->z, h->g, st));
     } else {
@@ -303,6 +307,7 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         pa.hi = h->hi;
         pa.beta = h->beta;
         pa.gamma = h->gamma;
+        pa.lam_dev = h->lam_dev;
         RAC_CK(launch_prox(pa, st));
         if (pf) RAC_CK(cudaEventRecord(ev[4], st));
     }
@@ -406,7 +411,29 @@ static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) 
     h->sweep = 0;
     RAC_CK(cudaMemsetAsync(h->sweep_dev, 0, sizeof(int64_t), st));
     RAC_ST(enqueue_refresh(h));
+    if (x0 && h->xi_from_grad) {
+        // xi = grad f(x0): the refresh just evaluated the exact gradient at z = x0
+        RAC_CK(cudaMemcpyAsync(h->xi, h->gz, nb, cudaMemcpyDeviceToDevice, st));
+        RAC_ST(enqueue_refresh(h));
+    }
+    h->warm = x0 != nullptr;
     return RAC_OK;
+}
+
+// KKT of the cold start z = 0 from the gradient at zero (host mirror of kkt_coord).
+static double kkt_at_zero(const rac_handle *h, const std::vector<double> &g0) {
+    double worst = 0.0;
+    for (double v : g0) {
+        double s;
+        if (h->phi == RAC_PHI_L1L2) s = std::max(std::fabs(v) - h->lam1, 0.0);
+        else if (h->phi == RAC_PHI_BOX) {
+            if (0.0 <= h->lo) s = std::max(-v, 0.0);
+            else if (0.0 >= h->hi) s = std::max(v, 0.0);
+            else s = std::fabs(v);
+        } else s = std::fabs(v);
+        worst = std::max(worst, s);
+    }
+    return worst / h->kkt_scale;
 }
 
 static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_handle *h) {
@@ -429,6 +456,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->store = o->storage;
     h->user = (cudaStream_t)o->stream;
     h->profile = o->profile != 0;
+    h->xi_from_grad = o->xi0_from_grad != 0;
+    h->ws_fallback = o->ws_fallback != 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     RAC_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
     for (auto &q : h->sfs) RAC_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
@@ -483,6 +512,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(h->alloc(&h->stats, 1));
     RAC_ST(h->alloc(&h->bar, 1));
     RAC_ST(h->alloc(&h->sweep_dev, 1));
+    RAC_ST(h->alloc(&h->lam_dev, 2));
+    {
+        double lam[2] = {h->lam1, h->lam2};
+        RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, st));
+        RAC_CK(cudaStreamSynchronize(st));
+    }
     RAC_CK(cudaMallocHost(&h->h_stats, sizeof(DevStats)));
     RAC_CK(cudaMallocHost(&h->h_err, sizeof(int)));
     if (h->has_A) {
@@ -511,6 +546,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         double mx = 0.0;
         for (double v : g0) mx = std::max(mx, std::fabs(v));
         h->kkt_scale = std::max(1.0, mx);
+        h->kkt_cold0 = kkt_at_zero(h, g0);
     }
     // storage-precision copy for the sweeps
     const size_t sb = store_bytes(h->store);
@@ -637,8 +673,10 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
     int dev_err = 0;
     RAC_ST(read_stats(h, &hs, &dev_err));
     int done = 0;
+    int rejected = 0;
     rac_status status = RAC_OK;
     if (dev_err) status = (rac_status)dev_err;
+    const bool check_ws = h->ws_fallback && h->warm && h->solves == 0;
     while (status == RAC_OK && hs.kkt > h->tol && done < h->max_sweeps) {
         int nb = std::min(h->refresh_every, h->max_sweeps - done);
         RAC_ST(run_period(h, nb));
@@ -648,7 +686,14 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
         collect_profile(h, nb);
         if (dev_err) status = (rac_status)dev_err;
         else if (hs.nonfinite) status = RAC_ERR_NUMERIC;
+        if (check_ws && done == nb && status == RAC_OK && hs.kkt > h->kkt_cold0) {
+            // the warm start is worse than starting from zero: restart cold
+            RAC_ST(set_state(h, nullptr, nullptr));
+            RAC_ST(read_stats(h, &hs, &dev_err));
+            rejected = 1;
+        }
     }
+    h->solves += 1;
     if (status == RAC_OK && hs.kkt > h->tol) status = RAC_ERR_NOT_CONVERGED;
     if (x_out) {
         RAC_CK(cudaMemcpyAsync(x_out, h->z, (size_t)h->n * sizeof(double), cudaMemcpyDefault, h->st));
@@ -674,6 +719,7 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
         info->t_prox_ms = h->t_prox;
         info->t_refresh_ms = h->t_ref;
         info->chain_launches = h->chain_launches;
+        info->warm_start_rejected = rejected;
     }
     return status;
 }
@@ -696,6 +742,42 @@ extern "C" rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, do
     if (mu) RAC_CK(cudaMemcpyAsync(mu, h->mu, sizeof(double), cudaMemcpyDefault, h->st));
     RAC_CK(cudaStreamSynchronize(h->st));
     return RAC_OK;
+}
+
+// ---------------------------------------------------------------- path
+// Regularisation path: the points are solved in the given order, each warm
+// started from the previous point's iterates (x, z, xi); only the prox and
+// the KKT measure depend on (lambda1, lambda2), so the block factors, the
+// Gram matrix and the captured period graphs are shared by all points.
+extern "C" rac_status rac_admm_path(rac_handle *h, int32_t nlambda, const double *lambda1,
+                                    const double *lambda2, double *X_out, rac_info *infos) {
+    if (!h || nlambda <= 0 || !lambda1 || !X_out || h->phi != RAC_PHI_L1L2) return RAC_ERR_ARG;
+    std::vector<double> l1(nlambda), l2(nlambda, h->lam2);
+    {
+        RAC_ST(enter(h));
+        RAC_CK(cudaMemcpyAsync(l1.data(), lambda1, nlambda * sizeof(double), cudaMemcpyDefault,
+                               h->st));
+        if (lambda2)
+            RAC_CK(cudaMemcpyAsync(l2.data(), lambda2, nlambda * sizeof(double), cudaMemcpyDefault,
+                                   h->st));
+        RAC_CK(cudaStreamSynchronize(h->st));
+    }
+    for (int l = 0; l < nlambda; ++l)
+        if (!(l1[l] >= 0) || !(l2[l] >= 0)) return RAC_ERR_ARG;
+    rac_status worst = RAC_OK;
+    for (int l = 0; l < nlambda; ++l) {
+        h->lam1 = l1[l];
+        h->lam2 = l2[l];
+        double lam[2] = {h->lam1, h->lam2};
+        RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, h->st));
+        RAC_ST(enqueue_refresh(h));
+        rac_info info;
+        rac_status s = rac_admm_solve(h, X_out + (size_t)l * h->n, &info);
+        if (s != RAC_OK && s != RAC_ERR_NOT_CONVERGED) return s;
+        if (s != RAC_OK && worst == RAC_OK) worst = s;
+        if (infos) infos[l] = info;
+    }
+    return worst;
 }
 
 // ---------------------------------------------------------------- checkpoint

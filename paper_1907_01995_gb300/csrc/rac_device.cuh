@@ -356,4 +356,100 @@ __device__ void block_solve(const TA *__restrict__ W, int s, const TA *rhs, TA *
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- random assembly
+// Random assembly (Sec. 1 eq. RAC-ADDM, Sec. 2 sigma).
+__device__ inline void block_exclusive_scan(unsigned *a, int len, unsigned *red) {
+    // each thread scans a contiguous chunk, then the chunk totals are scanned
+    const int T = blockDim.x;
+    const int per = (len + T - 1) / T;
+    const int b0 = threadIdx.x * per;
+    unsigned local = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < len) local += a[b0 + i];
+    // inclusive scan of `local` across the block (warp shuffles + smem)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (T + 31) >> 5;
+        unsigned w = lane < nw ? red[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) red[lane] = w;
+    }
+    __syncthreads();
+    unsigned excl = v - local + (warp ? red[warp - 1] : 0u);
+    __syncthreads();
+    for (int i = 0; i < per; ++i) {
+        if (b0 + i < len) {
+            unsigned c = a[b0 + i];
+            a[b0 + i] = excl;
+            excl += c;
+        }
+    }
+    __syncthreads();
+}
+
+// One sweep's assembly by one CTA: keys of coordinates 0..n-1 for sweep k,
+// bucketed by their top L bits (counting sort into K/I), then ranked inside
+// their bucket.  smem holds 3 * 2^L + 32 words.
+__device__ inline void assemble_one(int n, int p, uint64_t seed, uint64_t k, int *P, int *B,
+                             uint64_t *K, int *I, int L, unsigned *sm_u) {
+    const int nb = 1 << L;
+    unsigned *hist = sm_u, *start = sm_u + nb, *cur = sm_u + 2 * nb, *red = sm_u + 3 * nb;
+    const int shift = 64 - L;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        uint64_t key = philox_key_word0((uint64_t)j, k, 0, 0, seed, 0);
+        int b = L ? (int)(key >> shift) : 0;
+        atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) start[i] = hist[i];
+    __syncthreads();
+    block_exclusive_scan(start, nb, red);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = start[i];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        uint64_t key = philox_key_word0((uint64_t)j, k, 0, 0, seed, 0);
+        int b = L ? (int)(key >> shift) : 0;
+        unsigned pos = atomicAdd(&cur[b], 1u);
+        K[pos] = key;
+        I[pos] = j;
+    }
+    __syncthreads();
+    BlockLayout lay(n, p);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint64_t key = K[i];
+        const int j = I[i];
+        const int b = L ? (int)(key >> shift) : 0;
+        const unsigned lo = start[b], cnt = hist[b];
+        unsigned rank = 0;
+        for (unsigned q = lo; q < lo + cnt; ++q) {
+            uint64_t kq = K[q];
+            rank += (kq < key) || (kq == key && I[q] < j);
+        }
+        const int pos = (int)(lo + rank);
+        P[pos] = j;
+        if (B) B[j] = lay.block_of(pos);
+    }
+    __syncthreads();
+}
+
+__host__ __device__ inline int assembly_log2_buckets(int n) {
+    int L = 0;
+    while (L < 11 && (1 << (L + 1)) * 4 <= n) ++L;  // about 4 keys per bucket, <= 2048 buckets
+    return L;
+}
+
 }  // namespace rac

@@ -71,6 +71,7 @@ struct ProxArgs {
     const double *t;
     int phi;
     double lam1, lam2, lo, hi, beta, gamma;
+    const double *lam_dev;  // if set: (lambda1, lambda2) read from device memory
 };
 
 // ------------------------------------------------------------------ launchers
@@ -110,7 +111,7 @@ cudaError_t launch_symv_f64(int n, const double *H, const double *z, const doubl
                             cudaStream_t st);
 cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z, const double *e,
                        double d, const double *mu, int phi, double lam1, double lam2, double lo,
-                       double hi, DevStats *stats, cudaStream_t st);
+                       double hi, DevStats *stats, cudaStream_t st, const double *lam_dev = nullptr);
 // anchor reset in the storage type: g = gz + G~ (x - z)  or  dres = A~ (x - z)
 cudaError_t launch_gram_anchor(int store, int n, const void *G, const double *gz,
                                const double *x, const double *z, double *g, cudaStream_t st);

@@ -27,105 +27,22 @@ int slab_rows(int store) { return 32 / (int)store_bytes(store); }
 // rank inside its bucket is counted, which reproduces the exact ascending
 // order of (key, j).
 // ======================================================================
-__device__ void block_exclusive_scan(unsigned *a, int len, unsigned *red) {
-    // each thread scans a contiguous chunk, then the chunk totals are scanned
-    const int T = blockDim.x;
-    const int per = (len + T - 1) / T;
-    const int b0 = threadIdx.x * per;
-    unsigned local = 0;
-    for (int i = 0; i < per; ++i)
-        if (b0 + i < len) local += a[b0 + i];
-    // inclusive scan of `local` across the block (warp shuffles + smem)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned v = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = (T + 31) >> 5;
-        unsigned w = lane < nw ? red[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < nw) red[lane] = w;
-    }
-    __syncthreads();
-    unsigned excl = v - local + (warp ? red[warp - 1] : 0u);
-    __syncthreads();
-    for (int i = 0; i < per; ++i) {
-        if (b0 + i < len) {
-            unsigned c = a[b0 + i];
-            a[b0 + i] = excl;
-            excl += c;
-        }
-    }
-    __syncthreads();
-}
-
 __global__ void __launch_bounds__(1024) k_assembly(int n, int p, uint64_t seed, int64_t sweep0,
                                                    const int64_t *sweep_dev, int *perm, int *blk,
                                                    uint64_t *tkey, int *tidx, int L) {
     if (sweep_dev) sweep0 += *sweep_dev;
     extern __shared__ unsigned sm_u[];
-    const int nb = 1 << L;
-    unsigned *hist = sm_u, *start = sm_u + nb, *cur = sm_u + 2 * nb, *red = sm_u + 3 * nb;
     const int slot = blockIdx.x;
-    const uint64_t k = (uint64_t)(sweep0 + slot);
-    int *P = perm + (size_t)slot * n;
-    int *B = blk ? blk + (size_t)slot * n : nullptr;
-    uint64_t *K = tkey + (size_t)slot * n;
-    int *I = tidx + (size_t)slot * n;
-    const int shift = 64 - L;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        uint64_t key = philox_key_word0((uint64_t)j, k, 0, 0, seed, 0);
-        int b = L ? (int)(key >> shift) : 0;
-        atomicAdd(&hist[b], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) start[i] = hist[i];
-    __syncthreads();
-    block_exclusive_scan(start, nb, red);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) cur[i] = start[i];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        uint64_t key = philox_key_word0((uint64_t)j, k, 0, 0, seed, 0);
-        int b = L ? (int)(key >> shift) : 0;
-        unsigned pos = atomicAdd(&cur[b], 1u);
-        K[pos] = key;
-        I[pos] = j;
-    }
-    __syncthreads();
-    BlockLayout lay(n, p);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint64_t key = K[i];
-        const int j = I[i];
-        const int b = L ? (int)(key >> shift) : 0;
-        const unsigned lo = start[b], cnt = hist[b];
-        unsigned rank = 0;
-        for (unsigned q = lo; q < lo + cnt; ++q) {
-            uint64_t kq = K[q];
-            rank += (kq < key) || (kq == key && I[q] < j);
-        }
-        const int pos = (int)(lo + rank);
-        P[pos] = j;
-        if (B) B[j] = lay.block_of(pos);
-    }
+    assemble_one(n, p, seed, (uint64_t)(sweep0 + slot), perm + (size_t)slot * n,
+                 blk ? blk + (size_t)slot * n : nullptr, tkey + (size_t)slot * n,
+                 tidx + (size_t)slot * n, L, sm_u);
 }
 
 cudaError_t launch_assembly(int n, int p, uint64_t seed, int64_t sweep0, const int64_t *sweep_dev,
                             int nsweeps, int *perm, int *blk, uint64_t *tkey, int *tidx,
                             cudaStream_t st) {
     if (n <= 0 || nsweeps <= 0) return cudaSuccess;
-    int L = 0;
-    while (L < 11 && (1 << (L + 1)) * 4 <= n) ++L;  // about 4 keys per bucket, <= 2048 buckets
+    const int L = assembly_log2_buckets(n);
     size_t smem = (size_t)(3 * (1 << L) + 32) * sizeof(unsigned);
     k_assembly<<<nsweeps, 1024, smem, st>>>(n, p, seed, sweep0, sweep_dev, perm, blk, tkey, tidx,
                                             L);
@@ -1085,6 +1002,10 @@ bool chain_can_stage(int store, int smax, int with_p, int nperm) {
 // ======================================================================
 __global__ void k_prox(ProxArgs a) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a.lam_dev) {
+        a.lam1 = a.lam_dev[0];
+        a.lam2 = a.lam_dev[1];
+    }
     if (j < a.n) {
         double x = a.x[j] + a.dx[j];
         if (a.g) {
@@ -1164,9 +1085,14 @@ cudaError_t launch_symv_f64(int n, const double *H, const double *z, const doubl
 __global__ void __launch_bounds__(1024) k_kkt(int n, const double *gz, const double *x,
                                               const double *z, const double *e, double d,
                                               const double *mup, int phi, double lam1,
-                                              double lam2, double lo, double hi, DevStats *out) {
+                                              double lam2, double lo, double hi, DevStats *out,
+                                              const double *lam_dev) {
     __shared__ double red[32];
     const double mu = mup ? *mup : 0.0;
+    if (lam_dev) {
+        lam1 = lam_dev[0];
+        lam2 = lam_dev[1];
+    }
     double smax = 0.0, z1 = 0.0, ez = 0.0, ex = 0.0, xz = 0.0, bad = 0.0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         double zj = z[j], xj = x[j];
@@ -1195,8 +1121,8 @@ __global__ void __launch_bounds__(1024) k_kkt(int n, const double *gz, const dou
 }
 cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z, const double *e,
                        double d, const double *mu, int phi, double lam1, double lam2, double lo,
-                       double hi, DevStats *stats, cudaStream_t st) {
-    k_kkt<<<1, 1024, 0, st>>>(n, gz, x, z, e, d, mu, phi, lam1, lam2, lo, hi, stats);
+                       double hi, DevStats *stats, cudaStream_t st, const double *lam_dev) {
+    k_kkt<<<1, 1024, 0, st>>>(n, gz, x, z, e, d, mu, phi, lam1, lam2, lo, hi, stats, lam_dev);
     return cudaGetLastError();
 }
 

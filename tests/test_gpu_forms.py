@@ -1,0 +1,198 @@
+"""GPU parity of the batched form, the regularisation path and the learned
+warm start (all through the C-ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import rac_oracle as O
+from oracle import ws_mlp as WO
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1907_01995_gb300 import api  # noqa: E402
+from paper_1907_01995_gb300 import warmstart as ws  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max()) / max(1.0, float(np.abs(b).max()))
+
+
+def _svm_set(seed=0, count=5):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = int(rng.integers(70, 400))
+        d = int(rng.integers(3, 60))
+        out.append(synth.svm_instance(seed * 100 + i, N, d, block=64))
+    return out
+
+
+def _probs(insts):
+    return [dict(A=s.A, b=s.b, c=s.c, E=s.E[0], d=s.d, phi="box", lo=0.0, hi=1.0) for s in insts]
+
+
+def test_batch_fp64_iterates_match_oracle():
+    insts = _svm_set(1)
+    zs, infos = api.batch(_probs(insts), num_blocks=-64, beta=0.0, tol=0.0, max_sweeps=12,
+                          refresh_every=5, seed=7, storage="fp64")
+    for i, s in enumerate(insts):
+        P = O.problem_from_instance(s)
+        st = O.initial_state(P)
+        for _ in range(12):
+            O.sweep(P, st, s.num_blocks, 7 + i, s.beta, s.gamma)
+        assert infos[i]["sweeps"] == 12
+        assert rel(zs[i], st.z) <= 1e-10, i
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-8), ("fp32", 1e-7), ("bf16", 1e-6)])
+def test_batch_converged_matches_smo(storage, tol):
+    insts = _svm_set(2, count=6)
+    zs, infos = api.batch(_probs(insts), num_blocks=-64, beta=0.0, tol=tol, max_sweeps=40000,
+                          refresh_every=20, seed=0, storage=storage)
+    for i, s in enumerate(insts):
+        assert infos[i]["status"] == 0, infos[i]
+        Q = s.A.T @ s.A
+        a_smo = O.smo_svm(Q, s.E[0], 1.0, tol=1e-11)
+        obj = lambda v: 0.5 * v @ Q @ v - v.sum()
+        assert abs(obj(zs[i]) - obj(a_smo)) <= 1e-5 * max(1.0, abs(obj(a_smo)))
+        P = O.problem_from_instance(s)
+        assert O.kkt(P, zs[i])["kkt"] <= tol * 1.01
+
+
+def test_batch_mixed_lasso_and_regression():
+    """The batch is not SVM-only: uneven LASSO / regression instances."""
+    insts = [synth.small_instance(i, 40 + 13 * i, 20 + 7 * i, 3 + i,
+                                  phi=("l1l2" if i % 2 else "none")) for i in range(4)]
+    probs = [dict(A=s.A, b=s.b, phi=s.phi, lambda1=s.lam1) for s in insts]
+    zs, infos = api.batch(probs, num_blocks=-8, beta=1.0, tol=1e-9, max_sweeps=5000,
+                          refresh_every=10, storage="fp64")
+    for i, s in enumerate(insts):
+        assert infos[i]["status"] == 0
+        ref = O.cd_enet(s.A, s.b, s.lam1, 0.0) if s.phi == "l1l2" else O.normal_equations(s.A, s.b)
+        assert rel(zs[i], ref) <= 1e-6
+
+
+def test_path_points_match_coordinate_descent():
+    inst = synth.small_instance(9, 150, 60, 6, lam2=0.05)
+    lmax = float(np.abs(inst.A.T @ inst.b).max())
+    lams = lmax * np.geomspace(0.9, 0.05, 6)
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=lams[0], lambda2=0.05, num_blocks=6,
+                    tol=1e-10, max_sweeps=4000) as h:
+        X, infos = h.path(lams, np.full(6, 0.05))
+    for l, lam in enumerate(lams):
+        ref = O.cd_enet(inst.A, inst.b, lam, 0.05)
+        assert infos[l]["status"] == 0
+        assert rel(X[:, l], ref) <= 1e-8
+        assert np.array_equal(X[:, l] != 0, ref != 0)
+    # warm starting along the path needs fewer sweeps than the first point
+    assert sum(i["sweeps"] for i in infos[1:]) / 5 <= infos[0]["sweeps"] * 1.5
+
+
+# ------------------------------------------------------------ warm start
+def _ws_params():
+    rng = np.random.default_rng(3)
+    d = {}
+    for name, shp in WO.SHAPES:
+        d[name] = rng.normal(size=shp) * (0.3 if name.startswith("W") else 0.05)
+    return WO.pack(d)
+
+
+def test_ws_forward_and_gradient_match_oracle():
+    rng = np.random.default_rng(0)
+    N = 777                                  # several tiles and a ragged tail
+    X = rng.normal(size=(N, 6))
+    T = np.stack([rng.normal(size=N), (rng.random(N) < 0.3).astype(float)], axis=1)
+    p = _ws_params()
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Tt = torch.tensor(T, dtype=torch.float32, device="cuda")
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    out = ws.forward(Xt, pt).cpu().numpy()
+    ref, _ = WO.forward(X.astype(np.float32).astype(np.float64), p.astype(np.float32).astype(np.float64))
+    assert np.abs(out - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    loss, g = ws.loss_grad(Xt, Tt, pt)
+    lref, gref = WO.loss_grad(X.astype(np.float32).astype(np.float64), T,
+                              p.astype(np.float32).astype(np.float64))
+    assert abs(loss - lref) <= 1e-4 * max(1.0, abs(lref))
+    assert np.abs(g.cpu().numpy() - gref).max() <= 1e-4 * max(1e-3, np.abs(gref).max())
+
+
+def test_ws_adam_step_matches_oracle():
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(300, 6))
+    T = np.stack([rng.normal(size=300), (rng.random(300) < 0.5).astype(float)], axis=1)
+    p = _ws_params()
+    pt = torch.tensor(p, dtype=torch.float32, device="cuda")
+    tr = ws.Trainer(pt, lr=1e-2)
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Tt = torch.tensor(T, dtype=torch.float32, device="cuda")
+    tr.train_step(Xt, Tt)
+    _, g = WO.loss_grad(X.astype(np.float32).astype(np.float64), T,
+                        p.astype(np.float32).astype(np.float64))
+    p1, _, _ = WO.adam_step(p.astype(np.float32).astype(np.float64), g, 0 * p, 0 * p, 1, 1e-2,
+                            0.9, 0.999, 1e-8)
+    got = pt.cpu().numpy()
+    # the first Adam step is ~ -lr sign(g): compare where |g| is not tiny
+    big = np.abs(g) > 1e-4
+    assert np.abs(got[big] - p1[big]).max() <= 2e-4
+
+
+def test_ws_features_targets_and_decode():
+    inst = synth.warmstart_instance(4, 200, 90, 0.4, 0.05, 0.2, 0.1)
+    A = torch.tensor(inst.A, device="cuda")
+    b = torch.tensor(inst.b, device="cuda")
+    xs = O.cd_enet(inst.A, inst.b, inst.lam1, inst.lam2)
+    Fx, T, lmax = ws.features(A, b, inst.lam1, inst.lam2, torch.tensor(xs, device="cuda"))
+    Fr, Tr, lr_ = WO.features_targets(inst.A, inst.b, inst.lam1, inst.lam2, xs)
+    assert abs(lmax - lr_) <= 1e-12 * lr_
+    assert np.abs(Fx.cpu().numpy() - Fr).max() <= 1e-5 * max(1.0, np.abs(Fr).max())
+    assert np.abs(T.cpu().numpy() - Tr).max() <= 1e-5 * max(1.0, np.abs(Tr).max())
+    p = torch.tensor(_ws_params(), dtype=torch.float32, device="cuda")
+    x0 = ws.predict(A, b, inst.lam1, inst.lam2, p).cpu().numpy()
+    out = ws.forward(Fx, p).cpu().numpy()
+    nrm = np.sqrt((inst.A ** 2).sum(0))
+    dec = np.where(out[:, 1] > 0, out[:, 0] * lmax / nrm, 0.0)
+    assert np.abs(x0 - dec).max() <= 1e-6 * max(1.0, np.abs(dec).max())
+
+
+def _family(seed, count, scale):
+    return [synth.warmstart_instance(s, **kw, block=50)
+            for s, kw in synth.warmstart_family(seed, count, scale=scale)]
+
+
+def test_ws_training_gains_over_cold_start():
+    """Trained on the solver's own solutions, the network's warm start needs
+    fewer sweeps to the same KKT tolerance than the cold start on held-out
+    instances; every held-out solve still meets the tolerance."""
+    train = _family(0, 24, 0.08)
+    test = _family(5000, 8, 0.08)
+    Fs, Ts = [], []
+    for inst in train:
+        A = torch.tensor(inst.A, device="cuda")
+        b = torch.tensor(inst.b, device="cuda")
+        with api.Handle(A, b, phi="l1l2", lambda1=inst.lam1, lambda2=inst.lam2,
+                        num_blocks=inst.num_blocks, tol=1e-9, max_sweeps=20000) as h:
+            x, info = h.solve()
+        Fx, T, _ = ws.features(A, b, inst.lam1, inst.lam2, torch.tensor(x, device="cuda"))
+        Fs.append(Fx)
+        Ts.append(T)
+    Fx, T = torch.cat(Fs), torch.cat(Ts)
+    params = ws.init_params(0)
+    tr = ws.Trainer(params, lr=2e-3)
+    hist = tr.fit(Fx, T, epochs=60, batch=1024)
+    assert hist[-1] < 0.5 * hist[0]
+    cold, warm = [], []
+    for inst in test:
+        A = torch.tensor(inst.A, device="cuda")
+        b = torch.tensor(inst.b, device="cuda")
+        kw = dict(phi="l1l2", lambda1=inst.lam1, lambda2=inst.lam2, num_blocks=inst.num_blocks,
+                  tol=1e-6, max_sweeps=20000, refresh_every=5)
+        with api.Handle(A, b, **kw) as h:
+            _, ic = h.solve()
+        x0 = ws.predict(A, b, inst.lam1, inst.lam2, params)
+        with api.Handle(A, b, x0=x0, xi0_from_grad=True, ws_fallback=True, **kw) as h:
+            _, iw = h.solve()
+        assert ic["status"] == 0 and iw["status"] == 0
+        cold.append(ic["sweeps"])
+        warm.append(iw["sweeps"])
+    assert np.mean(warm) < np.mean(cold), (cold, warm)

@@ -98,7 +98,9 @@ typedef struct {
 typedef struct {
     int32_t num_blocks;     /* p, 1 <= p <= n; the first (n mod p) blocks get ceil(n/p) coordinates */
     double beta;            /* penalty of E x = d (eq. lagrangian), > 0 */
-    double gamma;           /* penalty of x - z = 0 (Sec. 3.1); 0 means gamma = beta */
+    double gamma;           /* penalty of x - z = 0 (Sec. 3.1); 0 means gamma = beta; a
+                               negative value means gamma = |gamma| * mean_j ||A_j||^2
+                               (= |gamma| * trace(H) / n), a curvature-scaled penalty */
     double tol;             /* stop when KKT(z) <= tol (KKT defined in rac_info) */
     int32_t max_sweeps;     /* sweep cap per solve call */
     int32_t refresh_every;  /* sweeps between exact FP64 refreshes + KKT checks (>= 1) */
@@ -178,7 +180,9 @@ rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, double *xi, d
  * SVM duals are the intended use).  All problems share opt except that
  * problem i uses seed opt->seed + i and, when opt->num_blocks <= 0, blocks of
  * at most -opt->num_blocks coordinates (p_i = ceil(n_i / -num_blocks)) with
- * beta_i = gamma_i = 0.1 p_i (the paper's SVM rule) when opt->beta <= 0.
+ * beta_i = 0.1 p_i (the paper's SVM rule) when opt->beta <= 0; gamma follows
+ * rac_options.gamma per problem (0: gamma_i = beta_i; < 0: scaled by the
+ * problem's own mean ||A_j||^2).
  * Each problem must be in data form with m <= 4096.  x_out[i] receives z_i;
  * infos[i] its info.  Returns the first non-OK per-problem status (or OK). */
 rac_status rac_admm_batch(int32_t count, const rac_problem *probs, const rac_options *opt,

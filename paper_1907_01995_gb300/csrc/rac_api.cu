@@ -547,6 +547,25 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         for (double v : g0) mx = std::max(mx, std::fabs(v));
         h->kkt_scale = std::max(1.0, mx);
         h->kkt_cold0 = kkt_at_zero(h, g0);
+        if (o->gamma < 0) {
+            // curvature-scaled split penalty |gamma| * trace(H) / n
+            double tr = 0.0;
+            if (h->has_A) {
+                std::vector<double> nrm(n);
+                RAC_CK(launch_colsq_f64(m, n, h->A64, m, h->gz, st));
+                RAC_CK(cudaMemcpyAsync(nrm.data(), h->gz, n * sizeof(double),
+                                       cudaMemcpyDeviceToHost, st));
+                RAC_CK(cudaStreamSynchronize(st));
+                for (double v : nrm) tr += v;
+            } else {
+                std::vector<double> Hh((size_t)n * n);
+                RAC_CK(cudaMemcpyAsync(Hh.data(), h->H64, Hh.size() * sizeof(double),
+                                       cudaMemcpyDeviceToHost, st));
+                RAC_CK(cudaStreamSynchronize(st));
+                for (int j = 0; j < n; ++j) tr += Hh[(size_t)j * n + j];
+            }
+            h->gamma = -o->gamma * std::max(tr / n, 1e-300);
+        }
     }
     // storage-precision copy for the sweeps
     const size_t sb = store_bytes(h->store);
@@ -645,7 +664,8 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
     if (pr->phi == RAC_PHI_L1L2 && (pr->lambda1 < 0 || pr->lambda2 < 0)) return RAC_ERR_ARG;
     if (pr->phi == RAC_PHI_BOX && !(pr->lo < pr->hi)) return RAC_ERR_ARG;
     if (o->num_blocks < 1 || o->num_blocks > pr->n) return RAC_ERR_ARG;
-    if (!(o->beta > 0) || o->gamma < 0 || !(o->tol >= 0) || o->max_sweeps < 0) return RAC_ERR_ARG;
+    if (!(o->beta > 0) || !std::isfinite(o->gamma) || !(o->tol >= 0) || o->max_sweeps < 0)
+        return RAC_ERR_ARG;
     if (o->storage < RAC_FP64 || o->storage > RAC_BF16) return RAC_ERR_ARG;
     if (o->form == RAC_FORM_RESIDUAL && !pr->A) return RAC_ERR_ARG;
     int64_t smax = (pr->n + o->num_blocks - 1) / o->num_blocks;

@@ -39,6 +39,7 @@ struct BatchDesc {
     double stat, gmax, znorm1, ez, ex, xz;
     int nonfinite;
     double mu, t;
+    double fro2;                  // ||A||_F^2 (for the curvature-scaled gamma)
 };
 
 struct BatchPools {
@@ -311,14 +312,20 @@ __global__ void __launch_bounds__(256) k_batch_refresh(BatchDesc *D, BatchPools 
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double fro = 0.0;
     for (int j = warp; j < n; j += nw) {
         const double *aj = A + (size_t)j * m;
-        double acc = 0.0;
-        for (int i = lane; i < m; i += 32) acc += aj[i] * r[i];
+        double acc = 0.0, sq = 0.0;
+        for (int i = lane; i < m; i += 32) {
+            acc += aj[i] * r[i];
+            sq += aj[i] * aj[i];
+        }
         acc = warp_sum(acc);
+        fro += warp_sum(sq);
         if (lane == 0) ga[j] = acc + c[j];
     }
     __syncthreads();
+    fro = block_sum<double>(lane == 0 ? fro : 0.0, red);
     double smax = 0.0, gmax = 0.0, z1 = 0.0, ez = 0.0, ex = 0.0, xz = 0.0, bad = 0.0;
     const double mu = d.mu;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -356,6 +363,7 @@ __global__ void __launch_bounds__(256) k_batch_refresh(BatchDesc *D, BatchPools 
         d.xz = xz;
         d.nonfinite = bad != 0.0;
         d.t = ex - d.d;
+        d.fro2 = fro;
     }
 }
 
@@ -506,7 +514,7 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         d.phi = pr.phi;
         d.k = pr.k;
         d.beta = o->beta > 0 ? o->beta : 0.1 * d.p;
-        d.gamma = o->gamma > 0 ? o->gamma : d.beta;
+        d.gamma = o->gamma > 0 ? o->gamma : d.beta;   // o->gamma < 0: set after the first refresh
         d.lam1 = pr.lambda1;
         d.lam2 = pr.lambda2;
         d.lo = pr.lo;
@@ -637,6 +645,12 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         double feas = d.k ? std::fabs(d.ez) / std::max(1.0, d.znorm1) : 0.0;
         return std::max(stat, feas);
     };
+    if (o->gamma < 0) {
+        // curvature-scaled split penalty: |gamma| * ||A_i||_F^2 / n_i; the anchor
+        // reset (dres) does not depend on gamma, so only the descriptors change
+        for (int i = 0; i < count; ++i)
+            B.hd[i].gamma = -o->gamma * std::max(B.hd[i].fro2 / B.hd[i].n, 1e-300);
+    }
     int active = 0;
     for (int i = 0; i < count; ++i) {
         scale[i] = std::max(1.0, B.hd[i].gmax);

@@ -1074,6 +1074,21 @@ cudaError_t launch_gemvt_f64(int m, int n, const double *A, int64_t lda, const d
     k_gemvt_f64<<<(n + 7) / 8, 256, 0, st>>>(m, n, A, lda, r, c, g);
     return cudaGetLastError();
 }
+__global__ void k_colsq_f64(int m, int n, const double *__restrict__ A, int64_t lda, double *out) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const double *aj = A + (size_t)j * lda;
+    double acc = 0.0;
+    for (int i = lane; i < m; i += 32) acc += aj[i] * aj[i];
+    acc = warp_sum(acc);
+    if (lane == 0) out[j] = acc;
+}
+cudaError_t launch_colsq_f64(int m, int n, const double *A, int64_t lda, double *out,
+                             cudaStream_t st) {
+    k_colsq_f64<<<(n + 7) / 8, 256, 0, st>>>(m, n, A, lda, out);
+    return cudaGetLastError();
+}
 cudaError_t launch_symv_f64(int n, const double *H, const double *z, const double *c, double *g,
                             cudaStream_t st) {
     // symmetric H: row j is column j

@@ -123,7 +123,9 @@ def svm_instance(seed: int, N: int, d: int, C: float = 1.0, mu_norm: float = 1.5
     Samples x_i ~ N(y_i mu, I_d) with ||mu|| = 1.5, 5% of labels flipped.
     With Z = diag(y) X the dual is min 1/2 a^T Z Z^T a - e^T a s.t. y^T a = 0,
     0 <= a <= C, i.e. A = Z^T (d x N), b = 0, c = -e, E = y^T, box [0, C].
-    Blocks hold at most `block` dual variables; beta = gamma = 0.1 p (Sec. 3.2).
+    Blocks hold at most `block` dual variables; beta = 0.1 p (Sec. 3.2) for
+    the coupling row, and the split penalty gamma = 0.3 mean_j ||A_j||^2 (the
+    split x - z = 0 has no counterpart in the paper's SVM runs).
     """
     rng = np.random.default_rng(seed)
     u = rng.standard_normal(d)
@@ -136,9 +138,10 @@ def svm_instance(seed: int, N: int, d: int, C: float = 1.0, mu_norm: float = 1.5
     A = np.asfortranarray(Z.T)                  # d x N, column i = y_i x_i
     p = (N + block - 1) // block
     pen = 0.1 * p
+    gam = 0.3 * float((A * A).sum()) / N
     return Instance("svm", A, np.zeros(d), "box", lo=0.0, hi=C,
                     c=-np.ones(N), E=y.reshape(1, N).copy(), d=np.zeros(1),
-                    num_blocks=p, beta=pen, gamma=pen, seed=seed,
+                    num_blocks=p, beta=pen, gamma=gam, seed=seed,
                     meta={"X": X, "y": y, "C": C, "block": block})
 
 

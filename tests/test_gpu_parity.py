@@ -168,8 +168,8 @@ def test_svm_small_converged_matches_smo():
     y = inst.E[0]
     a_smo = O.smo_svm(Q, y, 1.0, tol=1e-11)
     with api.Handle(inst.A, inst.b, c=inst.c, E=y, d=inst.d, phi="box", lo=0.0, hi=1.0,
-                    num_blocks=inst.num_blocks, beta=inst.beta, tol=1e-8, max_sweeps=20000,
-                    refresh_every=20) as h:
+                    num_blocks=inst.num_blocks, beta=inst.beta, gamma=-0.3, tol=1e-8,
+                    max_sweeps=40000, refresh_every=20) as h:
         a, info = h.solve()
     assert info["status"] == 0, info
     obj = lambda v: 0.5 * v @ Q @ v - v.sum()

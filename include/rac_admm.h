@@ -112,8 +112,11 @@ typedef struct {
     const double *xi0;      /* optional warm start for the dual xi (n), or NULL */
     void *stream;           /* cudaStream_t */
     int32_t profile;        /* 1: time each kernel class with CUDA events (rac_info.t_*) */
-    int32_t xi0_from_grad;  /* 1 (with x0): start xi at grad f(x0), the value xi takes at a
-                               fixed point (block stationarity with x = z); overrides xi0 */
+    int32_t xi0_from_grad;  /* (with x0) 1: start xi at grad f(x0), the value xi takes at a
+                               fixed point (block stationarity with x = z); 2: l1l2 only,
+                               xi_j = -(lambda1 sign(x0_j) + lambda2 x0_j) where x0_j != 0
+                               and clip(grad_j f(x0), -lambda1, lambda1) elsewhere, the
+                               dual a KKT point with x0's signs would have; overrides xi0 */
     int32_t ws_fallback;    /* 1 (with x0): if the KKT after the first refresh period exceeds
                                the KKT of the cold start z = 0, restart from zero */
 } rac_options;

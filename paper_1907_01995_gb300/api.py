@@ -107,7 +107,7 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
     o.xi0 = keep.vec(xi0, n)
     o.stream = _stream_handle(stream)
     o.profile = 1 if profile else 0
-    o.xi0_from_grad = 1 if xi0_from_grad else 0
+    o.xi0_from_grad = int(xi0_from_grad)
     o.ws_fallback = 1 if ws_fallback else 0
     return o
 

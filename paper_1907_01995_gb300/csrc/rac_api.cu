@@ -81,7 +81,8 @@ struct rac_handle {
     int perm_in_smem = 0;
     double kkt_scale = 1.0;
     double kkt_cold0 = 0.0;         // KKT of z = 0 (for the warm-start fallback)
-    bool xi_from_grad = false, ws_fallback = false, warm = false;
+    int xi_from_grad = 0;
+    bool ws_fallback = false, warm = false;
     int solves = 0;
     // device buffers
     double *A64 = nullptr, *b64 = nullptr, *c64 = nullptr, *e64 = nullptr, *H64 = nullptr;
@@ -412,8 +413,12 @@ static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) 
     RAC_CK(cudaMemsetAsync(h->sweep_dev, 0, sizeof(int64_t), st));
     RAC_ST(enqueue_refresh(h));
     if (x0 && h->xi_from_grad) {
-        // xi = grad f(x0): the refresh just evaluated the exact gradient at z = x0
-        RAC_CK(cudaMemcpyAsync(h->xi, h->gz, nb, cudaMemcpyDeviceToDevice, st));
+        // the refresh just evaluated the exact gradient at z = x0
+        if (h->xi_from_grad == 2 && h->phi == RAC_PHI_L1L2) {
+            RAC_CK(launch_xi_project(h->n, h->x, h->gz, h->lam1, h->lam2, h->xi, st));
+        } else {
+            RAC_CK(cudaMemcpyAsync(h->xi, h->gz, nb, cudaMemcpyDeviceToDevice, st));
+        }
         RAC_ST(enqueue_refresh(h));
     }
     h->warm = x0 != nullptr;
@@ -456,7 +461,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->store = o->storage;
     h->user = (cudaStream_t)o->stream;
     h->profile = o->profile != 0;
-    h->xi_from_grad = o->xi0_from_grad != 0;
+    h->xi_from_grad = o->xi0_from_grad;
     h->ws_fallback = o->ws_fallback != 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     RAC_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));

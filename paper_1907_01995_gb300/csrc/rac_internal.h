@@ -109,6 +109,8 @@ cudaError_t launch_gemvt_f64(int m, int n, const double *A, int64_t lda, const d
                              const double *c, double *g, cudaStream_t st);
 cudaError_t launch_symv_f64(int n, const double *H, const double *z, const double *c, double *g,
                             cudaStream_t st);
+cudaError_t launch_xi_project(int n, const double *x0, const double *g, double lam1, double lam2,
+                              double *xi, cudaStream_t st);
 // out_j = ||A_j||^2
 cudaError_t launch_colsq_f64(int m, int n, const double *A, int64_t lda, double *out,
                              cudaStream_t st);

@@ -1074,6 +1074,20 @@ cudaError_t launch_gemvt_f64(int m, int n, const double *A, int64_t lda, const d
     k_gemvt_f64<<<(n + 7) / 8, 256, 0, st>>>(m, n, A, lda, r, c, g);
     return cudaGetLastError();
 }
+// Dual start consistent with the signs of x0 (see rac_options.xi0_from_grad = 2).
+__global__ void k_xi_project(int n, const double *x0, const double *g, double lam1, double lam2,
+                             double *xi) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double x = x0[j];
+    xi[j] = x != 0.0 ? -(copysign(lam1, x) + lam2 * x) : fmin(fmax(g[j], -lam1), lam1);
+}
+cudaError_t launch_xi_project(int n, const double *x0, const double *g, double lam1, double lam2,
+                              double *xi, cudaStream_t st) {
+    k_xi_project<<<(n + 255) / 256, 256, 0, st>>>(n, x0, g, lam1, lam2, xi);
+    return cudaGetLastError();
+}
+
 __global__ void k_colsq_f64(int m, int n, const double *__restrict__ A, int64_t lda, double *out) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);

@@ -220,6 +220,30 @@ void rac_admm_destroy(rac_handle *h);
 rac_status rac_assembly(int64_t n, int32_t num_blocks, uint64_t seed, int64_t sweep0,
                         int32_t nsweeps, int32_t *perm_out, int32_t *blk_out, void *stream);
 
+/* Random assembly that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * such as programs whose device memory is wholly owned by their own
+ * allocator, or latency-critical loops where an allocation could
+ * synchronise with other work.  It computes exactly what rac_assembly()
+ * computes (same arguments and outputs), but its scratch lives in one
+ * file-scope device array sized for RAC_ASSEMBLY_NOALLOC_MAX
+ * (coordinate, sweep) pairs (3 MiB), which every GPU that loads the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   - n * nsweeps > RAC_ASSEMBLY_NOALLOC_MAX returns RAC_ERR_ARG (use
+ *     rac_assembly() for larger requests).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents;
+ *     nothing in it needs to start at zero, but calls that overlap on the GPU
+ *     (on different streams) race and must not be issued concurrently.
+ * perm_out / blk_out are device pointers; the call returns after the work on
+ * `stream` has finished. */
+#define RAC_ASSEMBLY_NOALLOC_MAX 262144
+rac_status rac_assembly_noalloc(int64_t n, int32_t num_blocks, uint64_t seed, int64_t sweep0,
+                                int32_t nsweeps, int32_t *perm_out, int32_t *blk_out,
+                                void *stream);
+
 /* ---- learned warm start (no counterpart in the paper) -----------------
  * A per-coordinate MLP (6 -> 128 -> 128 -> 2, ReLU) predicts, from features
  * of column j of a data-form LASSO / Elastic-Net problem, the scale-free

@@ -220,6 +220,15 @@ void rac_admm_destroy(rac_handle *h);
 rac_status rac_assembly(int64_t n, int32_t num_blocks, uint64_t seed, int64_t sweep0,
                         int32_t nsweeps, int32_t *perm_out, int32_t *blk_out, void *stream);
 
+/* G_out (n x n, row-major = column-major, device) = A~^T A~ in the storage
+ * precision `storage` (rac_precision): the Gram matrix H = A^T A of the
+ * general model (Sec. 1) that the Gram form keeps.  FP64: FP64 FMA tiles;
+ * FP32: tensor cores with the three-term TF32 split (FP32-level accuracy);
+ * BF16: the Gram matrix of the BF16-rounded A with FP32 accumulation, stored
+ * as BF16.  A (m x n, lda) on the device. */
+rac_status rac_gram(int64_t m, int64_t n, const double *A, int64_t lda, int32_t storage,
+                    void *G_out, void *stream);
+
 /* Random assembly that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory,
  * such as programs whose device memory is wholly owned by their own

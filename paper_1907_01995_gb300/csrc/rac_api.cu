@@ -579,7 +579,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_CK(cudaMalloc(&h->G, (size_t)n * n * sb));
         h->allocs.push_back(h->G);
         if (h->has_A) {
-            RAC_CK(launch_gram_build(h->store, m, n, h->A64, m, h->G, st));
+            if (h->store == ST_F64) {
+                RAC_CK(launch_gram_build(h->store, m, n, h->A64, m, h->G, st));
+            } else {
+                h->nlaunch += 1;  // conversion + tensor-core tiles
+                RAC_CK(launch_gram_build_mma(h->store, m, n, h->A64, m, h->G, st));
+            }
         } else {
             RAC_CK(launch_sym_convert(h->store, n, h->H64, h->G, st));
         }

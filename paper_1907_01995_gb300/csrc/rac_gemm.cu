@@ -1,0 +1,222 @@
+// rac_gemm.cu - G~ = A~^T A~ on the tensor cores (the Gram form's setup).
+//
+// The Gram form keeps G = A^T A (Sec. 1 eq. general_model with H = A^T A) in
+// the storage precision.  For BF16 storage G~ is the Gram matrix of the
+// BF16-rounded A with FP32 accumulation (mma m16n8k16 bf16); for FP32 storage
+// it is computed from the FP32-rounded A with the three-term TF32 split
+// a = a_hi + a_lo, a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (mma m16n8k8 tf32),
+// which keeps FP32-level accuracy.  A is first converted once into a
+// column-major copy padded to the tile sizes, then each CTA computes one
+// 128 x 128 tile of the lower triangle and mirrors it.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "rac_device.cuh"
+#include "rac_internal.h"
+
+namespace rac {
+
+constexpr int GT = 128;   // output tile
+constexpr int KC = 32;    // reduction chunk (rows of A) per stage
+
+template <class TS>
+__global__ void k_pad_convert(int m, int n, int mp, int np, const double *__restrict__ A,
+                              int64_t lda, TS *Ac) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)mp * np) return;
+    const int r = (int)(t % mp), c = (int)(t / mp);
+    Ac[t] = from_d<TS>(r < m && c < n ? A[(size_t)c * lda + r] : 0.0);
+}
+
+__device__ __forceinline__ uint32_t f2tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One 128 x 128 tile of C = Ac^T Ac (Ac: mp x np column-major, ld = mp).
+// 8 warps as 2 (rows) x 4 (cols), 64 x 32 per warp: 4 m16 x 4 n8 fragments.
+// Shared tiles are stored [column][k] with a padded row so that fragment
+// loads are conflict-free.
+template <class TE, bool TF32X3>
+__global__ void __launch_bounds__(256) k_gram_mma(int n, int mp, const TE *__restrict__ Ac,
+                                                  void *Gout, int out_bf16) {
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj > ti) return;
+    constexpr int LD = TF32X3 ? KC + 4 : KC + 8;          // elements per smem row
+    __shared__ __align__(16) TE As[GT * LD];
+    __shared__ __align__(16) TE Bs[GT * LD];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int i0 = ti * GT, j0 = tj * GT;
+    float acc[4][4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    constexpr int VEC = 16 / sizeof(TE);                  // elements per 16-byte load
+    constexpr int PER_COL = KC / VEC;
+    for (int k0 = 0; k0 < mp; k0 += KC) {
+        for (int v = threadIdx.x; v < GT * PER_COL; v += blockDim.x) {
+            const int col = v / PER_COL, part = v % PER_COL;
+            const uint4 va = *(const uint4 *)(Ac + (size_t)(i0 + col) * mp + k0 + part * VEC);
+            const uint4 vb = *(const uint4 *)(Ac + (size_t)(j0 + col) * mp + k0 + part * VEC);
+            *(uint2 *)(&As[col * LD + part * VEC]) = make_uint2(va.x, va.y);
+            *(uint2 *)(&As[col * LD + part * VEC + VEC / 2]) = make_uint2(va.z, va.w);
+            *(uint2 *)(&Bs[col * LD + part * VEC]) = make_uint2(vb.x, vb.y);
+            *(uint2 *)(&Bs[col * LD + part * VEC + VEC / 2]) = make_uint2(vb.z, vb.w);
+        }
+        __syncthreads();
+        if constexpr (!TF32X3) {
+#pragma unroll
+            for (int kb = 0; kb < KC; kb += 16) {
+                uint32_t af[4][4], bfr[4][2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int rb = wm * 64 + a * 16;
+                    const TE *p0 = &As[(rb + g) * LD + kb + 2 * t];
+                    const TE *p1 = &As[(rb + g + 8) * LD + kb + 2 * t];
+                    af[a][0] = *(const uint32_t *)p0;
+                    af[a][1] = *(const uint32_t *)p1;
+                    af[a][2] = *(const uint32_t *)(p0 + 8);
+                    af[a][3] = *(const uint32_t *)(p1 + 8);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int cb = wn * 32 + b * 8;
+                    const TE *q = &Bs[(cb + g) * LD + kb + 2 * t];
+                    bfr[b][0] = *(const uint32_t *)q;
+                    bfr[b][1] = *(const uint32_t *)(q + 8);
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) mma_bf16(acc[a][b], af[a], bfr[b]);
+            }
+        } else {
+#pragma unroll
+            for (int kb = 0; kb < KC; kb += 8) {
+                uint32_t ahi[4][4], alo[4][4], bhi[4][2], blo[4][2];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int rb = wm * 64 + a * 16;
+                    const float v[4] = {(float)As[(rb + g) * LD + kb + t],
+                                        (float)As[(rb + g + 8) * LD + kb + t],
+                                        (float)As[(rb + g) * LD + kb + t + 4],
+                                        (float)As[(rb + g + 8) * LD + kb + t + 4]};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        ahi[a][e] = f2tf32(v[e]);
+                        alo[a][e] = f2tf32(v[e] - __uint_as_float(ahi[a][e]));
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int cb = wn * 32 + b * 8;
+                    const float v[2] = {(float)Bs[(cb + g) * LD + kb + t],
+                                        (float)Bs[(cb + g) * LD + kb + t + 4]};
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        bhi[b][e] = f2tf32(v[e]);
+                        blo[b][e] = f2tf32(v[e] - __uint_as_float(bhi[b][e]));
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        mma_tf32(acc[a][b], alo[a], bhi[b]);
+                        mma_tf32(acc[a][b], ahi[a], blo[b]);
+                        mma_tf32(acc[a][b], ahi[a], bhi[b]);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    // store the tile and its mirror image
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = i0 + wm * 64 + a * 16 + g + (e >= 2 ? 8 : 0);
+                const int j = j0 + wn * 32 + b * 8 + 2 * t + (e & 1);
+                if (i < n && j < n) {
+                    const float v = acc[a][b][e];
+                    if (out_bf16) {
+                        __nv_bfloat16 *G = (__nv_bfloat16 *)Gout;
+                        G[(size_t)i * n + j] = __float2bfloat16_rn(v);
+                        if (ti != tj) G[(size_t)j * n + i] = __float2bfloat16_rn(v);
+                    } else {
+                        float *G = (float *)Gout;
+                        G[(size_t)i * n + j] = v;
+                        if (ti != tj) G[(size_t)j * n + i] = v;
+                    }
+                }
+            }
+}
+
+// G (storage type, n x n) = A~^T A~ on the tensor cores; store is ST_F32 or ST_BF16.
+cudaError_t launch_gram_build_mma(int store, int m, int n, const double *A, int64_t lda, void *G,
+                                  cudaStream_t st) {
+    const int mp = (m + KC - 1) / KC * KC, np = (n + GT - 1) / GT * GT;
+    const size_t es = store == ST_BF16 ? 2 : 4;
+    void *Ac = nullptr;
+    cudaError_t e = cudaMallocAsync(&Ac, (size_t)mp * np * es, st);
+    if (e != cudaSuccess) return e;
+    const int64_t tot = (int64_t)mp * np;
+    const unsigned cb = (unsigned)((tot + 255) / 256);
+    const dim3 grid(np / GT, np / GT);
+    if (store == ST_BF16) {
+        k_pad_convert<__nv_bfloat16><<<cb, 256, 0, st>>>(m, n, mp, np, A, lda, (__nv_bfloat16 *)Ac);
+        k_gram_mma<__nv_bfloat16, false><<<grid, 256, 0, st>>>(n, mp, (const __nv_bfloat16 *)Ac, G, 1);
+    } else {
+        k_pad_convert<float><<<cb, 256, 0, st>>>(m, n, mp, np, A, lda, (float *)Ac);
+        k_gram_mma<float, true><<<grid, 256, 0, st>>>(n, mp, (const float *)Ac, G, 0);
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(Ac, st);
+    return e;
+}
+
+}  // namespace rac
+
+using namespace rac;
+
+extern "C" rac_status rac_gram(int64_t m, int64_t n, const double *A, int64_t lda, int32_t storage,
+                               void *G_out, void *stream) {
+    if (m <= 0 || n <= 0 || lda < m || !A || !G_out || storage < RAC_FP64 || storage > RAC_BF16 ||
+        m > ((int64_t)1 << 30) || n > ((int64_t)1 << 20))
+        return RAC_ERR_ARG;
+    (void)cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = storage == RAC_FP64
+                        ? launch_gram_build(ST_F64, (int)m, (int)n, A, lda, G_out, st)
+                        : launch_gram_build_mma(storage, (int)m, (int)n, A, lda, G_out, st);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? RAC_ERR_OOM : RAC_ERR_CUDA;
+    }
+    return cudaStreamSynchronize(st) == cudaSuccess ? RAC_OK : RAC_ERR_CUDA;
+}

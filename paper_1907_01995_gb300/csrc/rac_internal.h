@@ -127,6 +127,9 @@ cudaError_t launch_slab_anchor(int store, int n, int nslab, int R, const void *A
 cudaError_t launch_gram_build(int store, int m, int n, const double *A, int64_t lda, void *G,
                               cudaStream_t st);
 cudaError_t launch_sym_convert(int store, int n, const double *H, void *G, cudaStream_t st);
+// tensor-core Gram build for FP32 (three-term TF32) and BF16 storage
+cudaError_t launch_gram_build_mma(int store, int m, int n, const double *A, int64_t lda, void *G,
+                                  cudaStream_t st);
 cudaError_t launch_to_slab(int store, int m, int n, const double *A, int64_t lda, int R,
                            int nslab, void *As, cudaStream_t st);
 int slab_rows(int store);

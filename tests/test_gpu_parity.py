@@ -219,3 +219,29 @@ def test_device_inputs_and_outputs():
     with api.Handle(inst.A, inst.b, **kw) as h:
         z, _ = h.solve()
     assert np.array_equal(out.cpu().numpy(), z)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16"])
+def test_gram_build_matches_fp64(storage):
+    """G~ = A~^T A~ (rac_gram) on ragged sizes against the FP64 Gram matrix of
+    the storage-rounded A: FP64 to 1e-12, FP32 (three-term TF32 split) to
+    1e-6, BF16 (stored as BF16) to one BF16 rounding of each entry."""
+    rng = np.random.default_rng(7)
+    m, n = 333, 301
+    A = np.asfortranarray(rng.normal(size=(m, n)))
+    At = torch.tensor(A, device="cuda").t().contiguous().t()
+    dt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}[storage]
+    G = torch.empty((n, n), dtype=dt, device="cuda")
+    code = _lib.STORAGE[storage]
+    assert _lib.load().rac_gram(m, n, At.data_ptr(), m, code, G.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream) == 0
+    Ar = torch.tensor(A).to(dt).double().numpy()
+    ref = Ar.T @ Ar
+    got = G.double().cpu().numpy()
+    scale = np.abs(ref).max()
+    if storage == "bf16":
+        assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6 * scale)
+    else:
+        tol = 1e-12 if storage == "fp64" else 1e-6
+        assert np.abs(got - ref).max() <= tol * scale
+    assert np.array_equal(got, got.T)

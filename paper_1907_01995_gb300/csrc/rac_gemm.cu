@@ -162,16 +162,18 @@ __global__ void __launch_bounds__(256) k_gram_mma(int n, int mp, const TE *__res
             for (int e = 0; e < 4; ++e) {
                 const int i = i0 + wm * 64 + a * 16 + g + (e >= 2 ? 8 : 0);
                 const int j = j0 + wn * 32 + b * 8 + 2 * t + (e & 1);
-                if (i < n && j < n) {
+                // diagonal tiles: only the lower triangle, mirrored, so G is
+                // exactly symmetric
+                if (i < n && j < n && (ti != tj || i >= j)) {
                     const float v = acc[a][b][e];
                     if (out_bf16) {
                         __nv_bfloat16 *G = (__nv_bfloat16 *)Gout;
                         G[(size_t)i * n + j] = __float2bfloat16_rn(v);
-                        if (ti != tj) G[(size_t)j * n + i] = __float2bfloat16_rn(v);
+                        G[(size_t)j * n + i] = __float2bfloat16_rn(v);
                     } else {
                         float *G = (float *)Gout;
                         G[(size_t)i * n + j] = v;
-                        if (ti != tj) G[(size_t)j * n + i] = v;
+                        G[(size_t)j * n + i] = v;
                     }
                 }
             }

@@ -230,12 +230,25 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(st)
-        _, info = run(storage, form, profile=True, grid=grid)
+        _, info = run(storage, form, grid=grid)       # the product path (CUDA graphs)
         e1.record(st)
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         infos.append(info)
     clocks = clk.stop()
+    # the same steps again with every kernel class bracketed by CUDA events on
+    # the library's stream (direct launches): per-kernel device times
+    prof_infos, prof_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        _, info = run(storage, form, profile=True, grid=grid)
+        e1.record(st)
+        torch.cuda.synchronize()
+        prof_ms.append(e0.elapsed_time(e1))
+        prof_infos.append(info)
     total_ms = sum(step_ms)
     bu = sum(i["block_updates"] for i in infos)
     if world > 1:
@@ -281,11 +294,11 @@ def main():
     sb = {"fp64": 8, "fp32": 4, "bf16": 2}[storage]
     ta = 8 if storage == "fp64" else 4
     gram = infos[-1]["form"].startswith("gram")
-    cls_ms = {c: sum(i["t_%s_ms" % c] for i in infos) for c in
+    cls_ms = {c: sum(i["t_%s_ms" % c] for i in prof_infos) for c in
               ("assembly", "factor", "chain", "prox", "refresh")}
-    launches = {"chain": sum(i["chain_launches"] for i in infos)}
+    launches = {"chain": sum(i["chain_launches"] for i in prof_infos)}
     launches["factor"] = launches["prox"] = launches["chain"]
-    launches["refresh"] = sum(math.ceil(i["sweeps"] / w["refresh_every"]) for i in infos)
+    launches["refresh"] = sum(math.ceil(i["sweeps"] / w["refresh_every"]) for i in prof_infos)
     dom = max(("factor", "chain", "prox", "refresh"), key=lambda c: cls_ms[c])
     per_launch_ms = cls_ms[dom] / max(1, launches[dom])
     abytes = algorithmic_bytes(dom, w["m"], w["n"], w["p"], sb, ta, gram)
@@ -338,7 +351,8 @@ def main():
                            "block_updates_per_s": fp64_info["block_updates"] / (f64 / 1000.0),
                            "form": fp64_info["form"], "kkt": fp64_info["kkt"]},
             "speedup_vs_fp64_plain": f64 / ttk,
-            "kernel_ms_per_step": {c: v / len(infos) for c, v in cls_ms.items()},
+            "kernel_ms_per_step": {c: v / len(prof_infos) for c, v in cls_ms.items()},
+            "profiled_ms_per_step": statistics.mean(prof_ms),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": abytes,

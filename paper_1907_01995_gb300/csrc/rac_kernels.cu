@@ -583,12 +583,12 @@ __device__ __forceinline__ bool grid_wait_count(GridBarrier *bar, unsigned targe
     return *s_flag != 0;
 }
 
+// Arrival: after the CTA barrier, thread 0 adds with release semantics at GPU
+// scope, which publishes every write the CTA made before the barrier.
 __device__ __forceinline__ void grid_arrive(GridBarrier *bar) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&bar->count, 1u);
-    }
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
 }
 
 constexpr int kPermSmemMax = 8192;   // whole-sweep permutation in shared memory up to this n
@@ -1036,7 +1036,10 @@ __global__ void k_resid_part(int m, int n, const double *__restrict__ A, int64_t
     const int j0 = blockIdx.y * chunk, j1 = min(n, j0 + chunk);
     if (i >= m) return;
     double acc = 0.0;
-    for (int j = j0; j < j1; ++j) acc += A[(size_t)j * lda + i] * z[j];
+    for (int j = j0; j < j1; ++j) {
+        const double zj = z[j];
+        if (zj != 0.0) acc += A[(size_t)j * lda + i] * zj;   // z is sparse for l1 problems
+    }
     part[(size_t)blockIdx.y * m + i] = acc;
 }
 __global__ void k_resid_sum(int m, int nchunk, const double *part, const double *b, double *r) {

@@ -54,15 +54,25 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
 // One 128 x 128 tile of C = Ac^T Ac (Ac: mp x np column-major, ld = mp).
 // 8 warps as 2 (rows) x 4 (cols), 64 x 32 per warp: 4 m16 x 4 n8 fragments.
 // Shared tiles are stored [column][k] with a padded row so that fragment
-// loads are conflict-free.
+// loads are conflict-free; a 3-stage cp.async ring of 32-row chunks overlaps
+// the loads of chunk k+2 with the mma work on chunk k.
+constexpr int GSTAGES = 3;
+
+template <class TE, bool TF32X3> struct GramTile {
+    static constexpr int LD = TF32X3 ? KC + 4 : KC + 8;    // elements per smem row
+    static constexpr int STAGE = 2 * GT * LD;                // As + Bs elements per stage
+    static size_t bytes() { return (size_t)GSTAGES * STAGE * sizeof(TE); }
+};
+
 template <class TE, bool TF32X3>
 __global__ void __launch_bounds__(256) k_gram_mma(int n, int mp, const TE *__restrict__ Ac,
                                                   void *Gout, int out_bf16) {
     const int ti = blockIdx.y, tj = blockIdx.x;
     if (tj > ti) return;
-    constexpr int LD = TF32X3 ? KC + 4 : KC + 8;          // elements per smem row
-    __shared__ __align__(16) TE As[GT * LD];
-    __shared__ __align__(16) TE Bs[GT * LD];
+    constexpr int LD = GramTile<TE, TF32X3>::LD;
+    constexpr int STAGE = GramTile<TE, TF32X3>::STAGE;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    TE *ring = (TE *)gsm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int wm = warp & 1, wn = warp >> 1;
@@ -74,19 +84,29 @@ __global__ void __launch_bounds__(256) k_gram_mma(int n, int mp, const TE *__res
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-    constexpr int VEC = 16 / sizeof(TE);                  // elements per 16-byte load
+    constexpr int VEC = 16 / sizeof(TE);                  // elements per 16-byte copy
     constexpr int PER_COL = KC / VEC;
-    for (int k0 = 0; k0 < mp; k0 += KC) {
-        for (int v = threadIdx.x; v < GT * PER_COL; v += blockDim.x) {
-            const int col = v / PER_COL, part = v % PER_COL;
-            const uint4 va = *(const uint4 *)(Ac + (size_t)(i0 + col) * mp + k0 + part * VEC);
-            const uint4 vb = *(const uint4 *)(Ac + (size_t)(j0 + col) * mp + k0 + part * VEC);
-            *(uint2 *)(&As[col * LD + part * VEC]) = make_uint2(va.x, va.y);
-            *(uint2 *)(&As[col * LD + part * VEC + VEC / 2]) = make_uint2(va.z, va.w);
-            *(uint2 *)(&Bs[col * LD + part * VEC]) = make_uint2(vb.x, vb.y);
-            *(uint2 *)(&Bs[col * LD + part * VEC + VEC / 2]) = make_uint2(vb.z, vb.w);
+    const int nk = mp / KC;
+    auto load = [&](int kc) {
+        if (kc < nk) {
+            TE *As = ring + (size_t)(kc % GSTAGES) * STAGE;
+            TE *Bs = As + GT * LD;
+            const int k0 = kc * KC;
+            for (int v = threadIdx.x; v < GT * PER_COL; v += blockDim.x) {
+                const int col = v / PER_COL, part = v % PER_COL;
+                cp_async16(&As[col * LD + part * VEC], Ac + (size_t)(i0 + col) * mp + k0 + part * VEC);
+                cp_async16(&Bs[col * LD + part * VEC], Ac + (size_t)(j0 + col) * mp + k0 + part * VEC);
+            }
         }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int s = 0; s < GSTAGES - 1; ++s) load(s);
+    for (int kc = 0; kc < nk; ++kc) {
+        cp_async_wait<GSTAGES - 2>();
         __syncthreads();
+        const TE *As = ring + (size_t)(kc % GSTAGES) * STAGE;
+        const TE *Bs = As + GT * LD;
         if constexpr (!TF32X3) {
 #pragma unroll
             for (int kb = 0; kb < KC; kb += 16) {
@@ -151,8 +171,11 @@ __global__ void __launch_bounds__(256) k_gram_mma(int n, int mp, const TE *__res
                     }
             }
         }
-        __syncthreads();
+        // the slot of chunk kc - 1 is free: every thread passed this
+        // iteration's barrier after finishing its mma work on it
+        load(kc + GSTAGES - 1);
     }
+    cp_async_wait<0>();
     // store the tile and its mirror image
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -191,11 +214,17 @@ cudaError_t launch_gram_build_mma(int store, int m, int n, const double *A, int6
     const unsigned cb = (unsigned)((tot + 255) / 256);
     const dim3 grid(np / GT, np / GT);
     if (store == ST_BF16) {
+        const size_t sm = GramTile<__nv_bfloat16, false>::bytes();
+        cudaFuncSetAttribute(k_gram_mma<__nv_bfloat16, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_pad_convert<__nv_bfloat16><<<cb, 256, 0, st>>>(m, n, mp, np, A, lda, (__nv_bfloat16 *)Ac);
-        k_gram_mma<__nv_bfloat16, false><<<grid, 256, 0, st>>>(n, mp, (const __nv_bfloat16 *)Ac, G, 1);
+        k_gram_mma<__nv_bfloat16, false><<<grid, 256, sm, st>>>(n, mp, (const __nv_bfloat16 *)Ac, G, 1);
     } else {
+        const size_t sm = GramTile<float, true>::bytes();
+        cudaFuncSetAttribute(k_gram_mma<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
         k_pad_convert<float><<<cb, 256, 0, st>>>(m, n, mp, np, A, lda, (float *)Ac);
-        k_gram_mma<float, true><<<grid, 256, 0, st>>>(n, mp, (const float *)Ac, G, 0);
+        k_gram_mma<float, true><<<grid, 256, sm, st>>>(n, mp, (const float *)Ac, G, 0);
     }
     e = cudaGetLastError();
     cudaFreeAsync(Ac, st);

@@ -73,6 +73,8 @@ struct rac_handle {
     cudaEvent_t ev = nullptr;
     std::vector<cudaEvent_t> fev;   // per sweep slot: factor done, chain done (2 each)
     int kinv = 1, stage = 0, stage_p = 0, lookahead = 0;
+    int big = 0;                    // residual form with 128 < s: large-block factor + chain
+    void *rhs_big = nullptr, *dx_big = nullptr;
     size_t wstride = 0;             // bytes of one sweep's factors (one buffer per period slot)
     void *Pbuf = nullptr;           // lookahead matrices P_i^T (one buffer per period slot)
     size_t pstride = 0;
@@ -273,8 +275,12 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
         if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
         int kinv = 1;
-        RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W),
-                             const_cast<void *>(a.P), &kinv, sf));
+        if (h->big) {
+            RAC_CK(launch_big_factor(h->store, a, const_cast<void *>(a.W), sf));
+        } else {
+            RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W),
+                                 const_cast<void *>(a.P), &kinv, sf));
+        }
         if (pf) RAC_CK(cudaEventRecord(ev[1], sf));
         RAC_CK(cudaEventRecord(h->fev[1 + s], sf));
     }
@@ -287,7 +293,11 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
-        RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
+        if (h->big) {
+            RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
+        } else {
+            RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
+        }
         if (pf) RAC_CK(cudaEventRecord(ev[3], st));
         ProxArgs pa;
         std::memset(&pa, 0, sizeof(pa));
@@ -607,6 +617,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_CK(cudaMalloc(&h->W, (size_t)h->refresh_every * h->wstride));
     h->allocs.push_back(h->W);
     h->kinv = factor_uses_kinv(lay.smax()) ? 1 : 0;
+    h->big = (!h->gram && !h->kinv && big_factor_fits(h->store, lay.smax())) ? 1 : 0;
+    if (h->big) h->kinv = 1;
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -630,6 +642,14 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         h->perm_in_smem = 0;
         h->stage = chain_can_stage(h->store, lay.smax(), 0, 0) ? 1 : 0;
         gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, 0, 0, 0, &smem);
+    }
+    if (h->big) {
+        h->stage = 0;
+        gmax = big_chain_max_grid(h->store);
+        RAC_CK(cudaMalloc(&h->rhs_big, (size_t)lay.smax() * ta));
+        h->allocs.push_back(h->rhs_big);
+        RAC_CK(cudaMalloc(&h->dx_big, (size_t)lay.smax() * ta));
+        h->allocs.push_back(h->dx_big);
     }
     if (gmax <= 0) return RAC_ERR_ARG;
     int want = h->gram ? std::min(sms, (n + 31) / 32) : std::min(sms, h->nslab);

@@ -101,6 +101,14 @@ cudaError_t launch_prepare(int n, const int *perm, const double *x, const double
                            double *eperm, cudaStream_t st);
 int lookahead_perm_smem_max();
 
+// large blocks (residual form, 128 < s): gathered Gram + blocked sweep inverse
+// into Wout (K^{-1}), and the chain with a distributed block solve
+cudaError_t launch_big_factor(int store, const ChainArgs &a, void *Wout, cudaStream_t st);
+bool big_factor_fits(int store, int smax);
+cudaError_t launch_big_chain(int store, const ChainArgs &a, int grid, void *rhs, void *dxs,
+                             cudaStream_t st);
+int big_chain_max_grid(int store);
+
 // exact FP64 pieces of the refresh
 cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const double *z,
                              const double *b, double *r, double *part, int nchunk,

@@ -53,6 +53,11 @@ CASES = {
                                      form="residual", beta=0.5, gamma=1.5),
     "one_block": dict(m=30, n=12, p=1, phi="l1l2", form="gram"),
     "singleton_blocks": dict(m=30, n=12, p=12, phi="l1l2", form="residual"),
+    # blocks of more than 128 coordinates: gathered Gram + blocked inverse +
+    # distributed-solve chain (ragged: 602 = 201 + 201 + 200)
+    "big_blocks_residual": dict(m=150, n=602, p=3, phi="l1l2", lam2=0.1, form="residual"),
+    "big_blocks_coupled": dict(m=90, n=451, p=2, phi="box", coupling=True, form="residual",
+                               beta=0.7, gamma=0.9),
 }
 
 
@@ -140,6 +145,20 @@ def lasso_ref():
     inst = synth.lasso_instance(0)
     x = O.cd_enet(inst.A, inst.b, inst.lam1, 0.0, tol=1e-13)
     return inst, x
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_big_blocks_converged(storage):
+    """Elastic-Net with n > m and 3 blocks of ~300 coordinates in FP32 / BF16
+    storage reaches the coordinate-descent solution."""
+    inst = synth.small_instance(21, 200, 900, 3, lam2=0.1, lam_frac=0.1)
+    ref = O.cd_enet(inst.A, inst.b, inst.lam1, 0.1, tol=1e-13)
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=inst.lam1, lambda2=0.1, num_blocks=3,
+                    tol=1e-9, max_sweeps=20000, storage=storage, form="residual") as h:
+        z, info = h.solve()
+    assert info["status"] == 0, info
+    assert rel(z, ref) <= (1e-5 if storage == "fp32" else 1e-3)
+    assert np.array_equal(z != 0, ref != 0)
 
 
 @pytest.mark.parametrize("storage,form,tol,bound", [

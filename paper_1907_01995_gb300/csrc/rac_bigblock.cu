@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, T
     const int smax = lay.smax();
     int *idx = (int *)sm_raw;
     TA *dl = (TA *)(sm_raw + (((size_t)smax * sizeof(int) + 15) & ~(size_t)15));
-    double *dred = (double *)(((uintptr_t)(dl + smax) + 15) & ~(uintptr_t)15);
+    double *dred = (double *)(((uintptr_t)(dl + smax + 256) + 15) & ~(uintptr_t)15);
     __shared__ int s_flag;
     const TS *As = (const TS *)a.As;
     const TA *Wall = (const TA *)a.W;
@@ -402,17 +402,17 @@ __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, T
         const int s = lay.size(i), off = lay.offset(i);
         for (int q = threadIdx.x; q < s; q += blockDim.x) idx[q] = a.perm[off + q];
         __syncthreads();
-        // (1) partial A~_S^T dres over this CTA's slabs: warp per column
-        for (int q = warp; q < s; q += nw) {
+        // (1) partial A~_S^T dres over this CTA's slabs: one thread per column,
+        // each streaming the column's 32-byte sectors of its slabs
+        for (int q = threadIdx.x; q < s; q += blockDim.x) {
             TA acc = 0;
             const size_t col = (size_t)idx[q];
-            for (int e2 = lane; e2 < ((a.nslab - c + G - 1) / G) * R; e2 += 32) {
-                const int sl = c + (e2 / R) * G, rr = e2 % R;
-                if (sl < a.nslab)
-                    acc += (TA)to_f(As[((size_t)sl * n + col) * R + rr]) * (TA)a.dres[(size_t)sl * R + rr];
+            for (int sl = c; sl < a.nslab; sl += G) {
+                const TS *seg = As + ((size_t)sl * n + col) * R;
+                const double *dr = a.dres + (size_t)sl * R;
+                for (int rr = 0; rr < R; ++rr) acc += (TA)to_f(seg[rr]) * (TA)dr[rr];
             }
-            acc = warp_sum(acc);
-            if (lane == 0) part[(size_t)c * smax + q] = acc;
+            part[(size_t)c * smax + q] = acc;
         }
         if (!grid_sync(a.bar, G, gen, a.err, &s_flag)) return;
         // (2) rhs for this CTA's columns (all threads of the CTA reduce one
@@ -455,16 +455,28 @@ __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, T
             for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[idx[q]] * (double)dl[q];
             t += block_sum<double>(loc, dred);
         }
-        const int myrows = ((a.nslab - c + G - 1) / G) * R;
-        for (int t2 = threadIdx.x; t2 < myrows; t2 += blockDim.x) {
-            const int sl = c + (t2 / R) * G, rr = t2 % R;
-            if (sl >= a.nslab) continue;
-            TA acc = 0;
-            for (int q = 0; q < s; ++q)
-                acc += (TA)to_f(As[((size_t)sl * n + idx[q]) * R + rr]) * dl[q];
-            a.dres[(size_t)sl * R + rr] += (double)acc;
+        // dres += A~_S dx on this CTA's slabs: thread (chunk, row) sums one
+        // chunk of the columns for one row; chunks are reduced in order
+        {
+            const int nch = blockDim.x / R;                    // column chunks
+            const int ch = threadIdx.x / R, rr = threadIdx.x % R;
+            const int per = (s + nch - 1) / nch;
+            TA *red = (TA *)(dl + smax);
+            for (int sl = c; sl < a.nslab; sl += G) {
+                TA acc = 0;
+                const int q0 = ch * per, q1 = min(s, q0 + per);
+                for (int q = q0; q < q1; ++q)
+                    acc += (TA)to_f(As[((size_t)sl * n + idx[q]) * R + rr]) * dl[q];
+                red[threadIdx.x] = acc;
+                __syncthreads();
+                if (threadIdx.x < R) {
+                    TA tot = 0;
+                    for (int k2 = 0; k2 < nch; ++k2) tot += red[k2 * R + threadIdx.x];
+                    a.dres[(size_t)sl * R + threadIdx.x] += (double)tot;
+                }
+                __syncthreads();
+            }
         }
-        __syncthreads();
     }
     if (c == 0 && threadIdx.x == 0 && a.e) *a.t = t;
 }
@@ -528,7 +540,7 @@ static cudaError_t big_chain_impl(const ChainArgs &a, int grid, void *rhs, void 
                                   cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
     const size_t smem = (((size_t)lay.smax() * sizeof(int) + 15) & ~(size_t)15) +
-                        lay.smax() * sizeof(TA) + 16 + 64 * sizeof(double);
+                        (lay.smax() + 256) * sizeof(TA) + 16 + 64 * sizeof(double);
     auto kern = k_chain_res_big<TS, TA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -155,6 +155,14 @@ const char *rac_status_string(int32_t status);
  * none; valid until the next library call on this thread. */
 const char *rac_last_error(void);
 
+/* Device memory of solver handles comes from one stream-ordered pool per
+ * GPU that keeps freed memory cached, so that setting up the next handle
+ * allocates nothing from the driver; streams, events and pinned status words
+ * are likewise reused.  rac_trim_pool() synchronises the current device and
+ * returns the pool's unused memory to the driver.  Memory of live handles is
+ * not affected.  Returns RAC_ERR_CUDA if the device call fails. */
+rac_status rac_trim_pool(void);
+
 /* Fill *opt with defaults: p = 1, beta = 1, gamma = 0, tol = 1e-6,
  * max_sweeps = 1000, refresh_every = 10, seed = 0, FP64, AUTO form. */
 rac_status rac_options_default(rac_options *opt);

@@ -54,6 +54,7 @@ P = ctypes.POINTER
 SIGNATURES = [
     ("rac_status_string", ctypes.c_char_p, [c_int32]),
     ("rac_last_error", ctypes.c_char_p, []),
+    ("rac_trim_pool", c_int32, []),
     ("rac_options_default", c_int32, [P(RacOptions)]),
     ("rac_admm_setup", c_int32, [P(RacProblem), P(RacOptions), P(c_void_p)]),
     ("rac_admm_solve", c_int32, [c_void_p, c_void_p, P(RacInfo)]),

@@ -250,3 +250,8 @@ def assembly(n: int, num_blocks: int, seed: int, sweep0: int, nsweeps: int, stre
     L.check(lib.rac_assembly(n, num_blocks, seed, sweep0, nsweeps, perm.data_ptr(),
                              blk.data_ptr(), _stream_handle(stream)), "rac_assembly")
     return perm, blk
+
+
+def trim_pool():
+    """Return the cached, unused device memory of closed handles to the driver."""
+    L.check(L.load().rac_trim_pool(), "rac_trim_pool")

@@ -117,26 +117,31 @@ struct rac_handle {
     std::vector<void *> allocs;
     char form[32] = {0};
 
-    template <class T> rac_status alloc(T **p_, size_t count) {
+    StreamSet *ss = nullptr;        // borrowed streams / events / pinned words
+    cudaMemPool_t pool = nullptr;   // the device's cached pool
+
+    // device memory, stream-ordered on st from the device's pool
+    rac_status alloc_bytes(void **p_, size_t bytes) {
         void *q = nullptr;
-        if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        cudaError_t e = cudaMallocFromPoolAsync(&q, std::max<size_t>(bytes, 16), pool, st);
         if (e != cudaSuccess) return map_cuda(e);
         allocs.push_back(q);
-        *p_ = (T *)q;
+        *p_ = q;
         return RAC_OK;
+    }
+    template <class T> rac_status alloc(T **p_, size_t count) {
+        void *q = nullptr;
+        rac_status r = alloc_bytes(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (r == RAC_OK) *p_ = (T *)q;
+        return r;
     }
     ~rac_handle() {
         for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
-        for (cudaEvent_t e : pev) cudaEventDestroy(e);
-        for (cudaEvent_t e : fev) cudaEventDestroy(e);
-        for (cudaStream_t q : sfs)
-            if (q) cudaStreamDestroy(q);
-        for (void *q : allocs) cudaFree(q);
-        if (h_stats) cudaFreeHost(h_stats);
-        if (h_err) cudaFreeHost(h_err);
-        if (ev) cudaEventDestroy(ev);
-        if (st) cudaStreamDestroy(st);
+        if (st) {
+            for (void *q : allocs) cudaFreeAsync(q, st);
+            cudaStreamSynchronize(st);
+        }
+        runtime_give_streams(ss);
     }
 };
 
@@ -269,6 +274,7 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
     for (int q = 0; q < std::min(nb, (int)rac_handle::kFactorStreams); ++q)
         RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[0], 0));
     h->nlaunch += 1 + (3 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;
+    if (h->big) h->nlaunch += (int64_t)(big_factor_launches(BlockLayout(h->n, h->p).smax(), h->store) - 1) * nb;
     for (int s = 0; s < nb; ++s) {
         ChainArgs a = chain_args(h, s);
         cudaStream_t sf = h->sfs[s % rac_handle::kFactorStreams];
@@ -276,7 +282,8 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
         int kinv = 1;
         if (h->big) {
-            RAC_CK(launch_big_factor(h->store, a, const_cast<void *>(a.W), sf));
+            RAC_CK(launch_big_factor(h->store, a, const_cast<void *>(a.W),
+                                     (char *)h->Pbuf + (size_t)s * h->pstride, sf));
         } else {
             RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W),
                                  const_cast<void *>(a.P), &kinv, sf));
@@ -474,14 +481,18 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->xi_from_grad = o->xi0_from_grad;
     h->ws_fallback = o->ws_fallback != 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
-    RAC_CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
-    for (auto &q : h->sfs) RAC_CK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
-    RAC_CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
-    h->fev.resize(1 + (size_t)h->refresh_every, nullptr);
-    for (auto &e : h->fev) RAC_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    if (h->profile) {
-        h->pev.resize(3 + 5 * (size_t)h->refresh_every, nullptr);
-        for (auto &e : h->pev) RAC_CK(cudaEventCreate(&e));
+    {
+        const size_t nfev = 1 + (size_t)h->refresh_every;
+        const size_t npev = h->profile ? 3 + 5 * (size_t)h->refresh_every : 0;
+        RAC_CK(runtime_take_streams(&h->ss, nfev, npev));
+        RAC_CK(runtime_pool(&h->pool));
+        h->st = h->ss->st;
+        for (int q = 0; q < rac_handle::kFactorStreams; ++q) h->sfs[q] = h->ss->sfs[q];
+        h->ev = h->ss->ev;
+        h->fev.assign(h->ss->fev.begin(), h->ss->fev.begin() + nfev);
+        h->pev.assign(h->ss->pev.begin(), h->ss->pev.begin() + npev);
+        h->h_stats = h->ss->h_stats;
+        h->h_err = h->ss->h_err;
     }
     RAC_ST(enter(h));
     cudaStream_t st = h->st;
@@ -533,8 +544,6 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, st));
         RAC_CK(cudaStreamSynchronize(st));
     }
-    RAC_CK(cudaMallocHost(&h->h_stats, sizeof(DevStats)));
-    RAC_CK(cudaMallocHost(&h->h_err, sizeof(int)));
     if (h->has_A) {
         RAC_ST(h->alloc(&h->rbuf, m));
         int sms = 148;
@@ -586,8 +595,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     const size_t sb = store_bytes(h->store);
     h->nlaunch += 1;
     if (h->gram) {
-        RAC_CK(cudaMalloc(&h->G, (size_t)n * n * sb));
-        h->allocs.push_back(h->G);
+        RAC_ST(h->alloc_bytes((void **)&h->G, (size_t)n * n * sb));
         if (h->has_A) {
             if (h->store == ST_F64) {
                 RAC_CK(launch_gram_build(h->store, m, n, h->A64, m, h->G, st));
@@ -605,8 +613,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     } else {
         h->R = slab_rows(h->store);
         h->nslab = (m + h->R - 1) / h->R;
-        RAC_CK(cudaMalloc(&h->As, (size_t)h->nslab * n * h->R * sb));
-        h->allocs.push_back(h->As);
+        RAC_ST(h->alloc_bytes((void **)&h->As, (size_t)h->nslab * n * h->R * sb));
         RAC_CK(launch_to_slab(h->store, m, n, h->A64, m, h->R, h->nslab, h->As, st));
         RAC_ST(h->alloc(&h->ga, n));
         RAC_ST(h->alloc(&h->dres, (size_t)h->nslab * h->R));
@@ -614,10 +621,9 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     BlockLayout lay(n, h->p);
     const size_t ta = h->store == ST_F64 ? 8 : 4;
     h->wstride = (lay.factor_total() * ta + 255) & ~(size_t)255;
-    RAC_CK(cudaMalloc(&h->W, (size_t)h->refresh_every * h->wstride));
-    h->allocs.push_back(h->W);
+    RAC_ST(h->alloc_bytes((void **)&h->W, (size_t)h->refresh_every * h->wstride));
     h->kinv = factor_uses_kinv(lay.smax()) ? 1 : 0;
-    h->big = (!h->gram && !h->kinv && big_factor_fits(h->store, lay.smax())) ? 1 : 0;
+    h->big = (!h->gram && !h->kinv) ? 1 : 0;
     if (h->big) h->kinv = 1;
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
@@ -646,10 +652,11 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     if (h->big) {
         h->stage = 0;
         gmax = big_chain_max_grid(h->store);
-        RAC_CK(cudaMalloc(&h->rhs_big, (size_t)lay.smax() * ta));
-        h->allocs.push_back(h->rhs_big);
-        RAC_CK(cudaMalloc(&h->dx_big, (size_t)lay.smax() * ta));
-        h->allocs.push_back(h->dx_big);
+        RAC_ST(h->alloc_bytes((void **)&h->rhs_big, (size_t)lay.smax() * ta));
+        RAC_ST(h->alloc_bytes((void **)&h->dx_big, (size_t)lay.smax() * ta));
+        // per period slot: the pivot panels of the blocked inverse
+        h->pstride = (big_panel_bytes(h->store, h->p, lay.smax()) + 255) & ~(size_t)255;
+        RAC_ST(h->alloc_bytes((void **)&h->Pbuf, (size_t)h->refresh_every * h->pstride));
     }
     if (gmax <= 0) return RAC_ERR_ARG;
     int want = h->gram ? std::min(sms, (n + 31) / 32) : std::min(sms, h->nslab);
@@ -659,14 +666,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     if (h->lookahead) {
         h->pstride = ((size_t)h->p * BlockLayout::pad4((size_t)lay.smax() * lay.smax()) * ta + 255) &
                      ~(size_t)255;
-        RAC_CK(cudaMalloc(&h->Pbuf, (size_t)h->refresh_every * h->pstride));
-        h->allocs.push_back(h->Pbuf);
+        RAC_ST(h->alloc_bytes((void **)&h->Pbuf, (size_t)h->refresh_every * h->pstride));
         RAC_ST(h->alloc(&h->sperm, n));
         if (h->k) RAC_ST(h->alloc(&h->eperm, n));
     }
     if (!h->gram) {
-        RAC_CK(cudaMalloc(&h->cpart, (size_t)2 * h->grid * lay.smax() * ta));
-        h->allocs.push_back(h->cpart);
+        RAC_ST(h->alloc_bytes((void **)&h->cpart, (size_t)2 * h->grid * lay.smax() * ta));
     }
     // assembly slots
     h->nslots = h->refresh_every;

@@ -6,8 +6,10 @@
 // inverse, and a chain whose block solve is too large for one CTA to redo.
 //   k_gather_gram   K_S tiles from the slab copy of A, 64 x 64 per CTA, all
 //                   blocks at once (mma bf16 / three-term tf32; FP64 SIMT)
-//   k_big_inverse   K_S^{-1} by the blocked sweep operator (pivot blocks of
-//                   32) in global memory, one CTA per block
+//   k_big_panel     one pivot step of the blocked sweep operator for K_S^{-1}:
+//                   D^{-1} and the pivot panels, one CTA per block
+//   k_big_update    the rank-32 update of that step, 64 x 64 tiles of every
+//                   block's matrix on their own CTAs
 //   k_chain_res_big the residual-form chain with the reduction of A_S^T d and
 //                   the product K_S^{-1} rhs spread over the CTAs
 #include <cuda_runtime.h>
@@ -261,117 +263,189 @@ __global__ void __launch_bounds__(256) k_gather_gram_f64(ChainArgs a, double *Kw
 
 // ---------------------------------------------------------------- inverse
 // K_S^{-1} by the blocked sweep operator (Goodnight 1979, applied to pivot
-// blocks): with D = M_kk for pivot block k and T = D^{-1} M_k., every other
-// entry becomes M_ij - M_ik T_kj, the pivot rows become T, the pivot
-// columns T^T, and M_kk becomes -D^{-1}.  After all blocks M = -K^{-1}.
-// M (s x s, row-major) lives in global memory (L2) and is updated in place;
-// the pivot rows R = M_k. and T are staged in shared memory.  The CTA first
-// adds gamma I + beta e e^T.  The rank-PB update uses 4 x 4 register tiles.
+// blocks of PB rows): with D = M_kk for pivot block k and T = D^{-1} M_k.,
+// every other entry becomes M_ij - M_ik T_kj, the pivot rows become T, the
+// pivot columns T^T, and M_kk becomes -D^{-1}.  After all pivot blocks
+// M = -K^{-1}; the last step stores the negation, so M ends as K^{-1}.
+// M (s x s, row-major) stays in global memory and is updated in place.  One
+// pivot step is two launches over every block of the sweep: k_big_panel (one
+// CTA per block: D^{-1}, the pivot rows R and T into a panel buffer) and
+// k_big_update (64 x 64 tiles of every block's M on their own CTAs, so the
+// rank-PB update spreads over the whole GPU).  The first step adds
+// gamma I + beta e e^T to the gathered Gram as it reads it.
 template <class TA> struct BigPB { static constexpr int v = 32; };
 template <> struct BigPB<double> { static constexpr int v = 16; };
+constexpr int IT = 64;          // rank-update tile
+
+// Panel buffer of one block: R (PB x smax), T (PB x smax), -D^{-1} (PB x PB).
+template <class TA> __host__ __device__ inline size_t big_panel_stride(int smax) {
+    constexpr int PB = BigPB<TA>::v;
+    return 2 * (size_t)PB * smax + PB * PB;
+}
 
 template <class TA>
-__global__ void __launch_bounds__(256) k_big_inverse(ChainArgs a, TA *Mall) {
+__global__ void __launch_bounds__(256) k_big_panel(ChainArgs a, TA *Mall, TA *Pan, int k0) {
     constexpr int PB = BigPB<TA>::v;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ TA D[PB * PB];
+    __shared__ TA vb[PB];
+    __shared__ TA ek[PB];
     const int b = blockIdx.x;
     BlockLayout lay(a.n, a.p);
     const int s = lay.size(b), off = lay.offset(b);
-    TA *M = Mall + lay.factor_offset(b);
-    TA *Rk = (TA *)sm_raw;                     // PB x s: pivot rows (original)
-    TA *Tk = Rk + PB * s;                      // PB x s: D^{-1} M_k.
-    TA *D = Tk + PB * s;                       // PB x PB, inverted in place
-    TA *es = D + PB * PB;                      // s
-    TA *vb = es + s;                           // PB
-    for (int q = threadIdx.x; q < s; q += blockDim.x)
-        es[q] = a.e ? (TA)a.e[a.perm[off + q]] : TA(0);
-    __syncthreads();
+    if (k0 >= s) return;
+    const int bk = min(PB, s - k0);
+    const bool first = k0 == 0;
     const TA gam = (TA)a.gamma, bet = (TA)a.beta;
-    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
-        const int i = idx / s, j = idx - i * s;
-        M[idx] += bet * es[i] * es[j] + (i == j ? gam : TA(0));
+    const TA *M = Mall + lay.factor_offset(b);
+    TA *Rg = Pan + (size_t)b * big_panel_stride<TA>(lay.smax());
+    TA *Tg = Rg + (size_t)PB * s;
+    TA *Dg = Rg + 2 * (size_t)PB * lay.smax();
+    if (threadIdx.x < PB)
+        ek[threadIdx.x] = (first && a.e && (int)threadIdx.x < bk)
+                              ? (TA)a.e[a.perm[off + k0 + threadIdx.x]] : TA(0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+        const int l = idx / PB, c = idx - l * PB;
+        TA v = 0;
+        if (l < bk && c < bk) {
+            v = M[(size_t)(k0 + l) * s + k0 + c];
+            if (first) v += bet * ek[l] * ek[c] + (l == c ? gam : TA(0));
+        }
+        D[idx] = v;
     }
     __syncthreads();
-    const int s4 = (s + 3) / 4;
-    for (int k0 = 0; k0 < s; k0 += PB) {
-        const int bk = min(PB, s - k0);
-        for (int idx = threadIdx.x; idx < bk * s; idx += blockDim.x) {
-            const int l = idx / s, j = idx - l * s;
-            Rk[l * s + j] = M[(size_t)(k0 + l) * s + j];
+    // D <- -D^{-1} by the scalar sweep operator (bk pivots)
+    for (int k = 0; k < bk; ++k) {
+        TA d = D[k * PB + k];
+        if (!(d > TA(0))) {
+            if (threadIdx.x == 0) set_err(a.err, RAC_ERR_NOT_PD);
+            d = TA(1);
         }
+        for (int c = threadIdx.x; c < bk; c += blockDim.x) vb[c] = D[k * PB + c];
         __syncthreads();
+        const TA rd = TA(1) / d;
         for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) {
             const int l = idx / bk, c = idx - l * bk;
-            D[l * PB + c] = Rk[l * s + k0 + c];
-        }
-        __syncthreads();
-        // D <- -D^{-1} by the scalar sweep operator (bk pivots)
-        for (int k = 0; k < bk; ++k) {
-            TA d = D[k * PB + k];
-            if (!(d > TA(0))) {
-                if (threadIdx.x == 0) set_err(a.err, RAC_ERR_NOT_PD);
-                d = TA(1);
-            }
-            for (int c = threadIdx.x; c < bk; c += blockDim.x) vb[c] = D[k * PB + c];
-            __syncthreads();
-            const TA rd = TA(1) / d;
-            for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) {
-                const int l = idx / bk, c = idx - l * bk;
-                TA v = D[l * PB + c];
-                if (l == k && c == k) v = -rd;
-                else if (l == k) v = vb[c] * rd;
-                else if (c == k) v = vb[l] * rd;
-                else v = v - vb[l] * vb[c] * rd;
-                D[l * PB + c] = v;
-            }
-            __syncthreads();
-        }
-        // D holds -D^{-1}.  T = D^{-1} R (bk x s)
-        for (int idx = threadIdx.x; idx < bk * s; idx += blockDim.x) {
-            const int l = idx / s, j = idx - l * s;
-            TA acc = 0;
-            for (int c = 0; c < bk; ++c) acc += D[l * PB + c] * Rk[c * s + j];
-            Tk[l * s + j] = -acc;
-        }
-        __syncthreads();
-        // M_ij -= sum_l R_li T_lj on 4 x 4 register tiles (pivot rows and
-        // columns are overwritten below)
-        for (int tile = threadIdx.x; tile < s4 * s4; tile += blockDim.x) {
-            const int i0 = (tile / s4) * 4, j0 = (tile % s4) * 4;
-            TA acc[4][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = 0;
-            for (int l = 0; l < bk; ++l) {
-                TA rv[4], tv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    rv[u] = i0 + u < s ? Rk[l * s + i0 + u] : TA(0);
-                    tv[u] = j0 + u < s ? Tk[l * s + j0 + u] : TA(0);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] += rv[u] * tv[v];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (i0 + u < s && j0 + v < s) M[(size_t)(i0 + u) * s + j0 + v] -= acc[u][v];
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < bk * s; idx += blockDim.x) {
-            const int l = idx / s, j = idx - l * s;
-            const bool pj = j >= k0 && j < k0 + bk;
-            const TA v = pj ? D[l * PB + (j - k0)] : Tk[l * s + j];
-            M[(size_t)(k0 + l) * s + j] = v;                  // pivot row
-            if (!pj) M[(size_t)j * s + k0 + l] = v;           // pivot column (symmetric)
+            TA v = D[l * PB + c];
+            if (l == k && c == k) v = -rd;
+            else if (l == k) v = vb[c] * rd;
+            else if (c == k) v = vb[l] * rd;
+            else v = v - vb[l] * vb[c] * rd;
+            D[l * PB + c] = v;
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) M[idx] = -M[idx];
+    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) Dg[idx] = D[idx];
+    // thread per column j: R_.j (shifted on the first step) and T_.j = D^{-1} R_.j
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        const TA ej = (first && a.e) ? (TA)a.e[a.perm[off + j]] : TA(0);
+        TA r[PB];
+#pragma unroll
+        for (int l = 0; l < PB; ++l) {
+            TA v = 0;
+            if (l < bk) {
+                v = M[(size_t)(k0 + l) * s + j];
+                if (first) v += bet * ek[l] * ej + (k0 + l == j ? gam : TA(0));
+                Rg[(size_t)l * s + j] = v;
+            }
+            r[l] = v;
+        }
+#pragma unroll 4
+        for (int l = 0; l < bk; ++l) {
+            TA acc = 0;
+#pragma unroll
+            for (int c = 0; c < PB; ++c) acc += D[l * PB + c] * r[c];
+            Tg[(size_t)l * s + j] = -acc;
+        }
+    }
+}
+
+template <class TA> __device__ __forceinline__ void lds4(const TA *p, TA (&o)[4]) {
+    if constexpr (sizeof(TA) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        const double2 v0 = reinterpret_cast<const double2 *>(p)[0];
+        const double2 v1 = reinterpret_cast<const double2 *>(p)[1];
+        o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+    }
+}
+
+// Tile (ti, tj) of block blockIdx.y: thread (tx, ty) owns rows i0 + 4 ty + u
+// and columns j0 + 4 tx + v (u, v < 4).
+template <class TA>
+__global__ void __launch_bounds__(256) k_big_update(ChainArgs a, TA *Mall, const TA *Pan, int k0) {
+    constexpr int PB = BigPB<TA>::v;
+    __shared__ __align__(16) TA Rs[PB][IT];
+    __shared__ __align__(16) TA Ts[PB][IT];
+    __shared__ TA ei[IT], ej[IT];
+    const int b = blockIdx.y;
+    BlockLayout lay(a.n, a.p);
+    const int s = lay.size(b), off = lay.offset(b);
+    const int ntm = (lay.smax() + IT - 1) / IT;
+    const int i0 = (blockIdx.x / ntm) * IT, j0 = (blockIdx.x % ntm) * IT;
+    if (k0 >= s || i0 >= s || j0 >= s) return;
+    const int bk = min(PB, s - k0);
+    const bool first = k0 == 0, last = k0 + bk == s;
+    TA *M = Mall + lay.factor_offset(b);
+    const TA *Rg = Pan + (size_t)b * big_panel_stride<TA>(lay.smax());
+    const TA *Tg = Rg + (size_t)PB * s;
+    const TA *Dg = Rg + 2 * (size_t)PB * lay.smax();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // read this thread's 16 entries of M first; the loads overlap the staging
+    TA mv[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + 4 * ty + u, j = j0 + 4 * tx + v;
+            mv[u][v] = (i < s && j < s) ? M[(size_t)i * s + j] : TA(0);
+        }
+    for (int idx = threadIdx.x; idx < PB * IT; idx += blockDim.x) {
+        const int l = idx / IT, q = idx - l * IT;
+        Rs[l][q] = (l < bk && i0 + q < s) ? Rg[(size_t)l * s + i0 + q] : TA(0);
+        Ts[l][q] = (l < bk && j0 + q < s) ? Tg[(size_t)l * s + j0 + q] : TA(0);
+    }
+    if (first && threadIdx.x < IT) {
+        const int q = threadIdx.x;
+        ei[q] = (a.e && i0 + q < s) ? (TA)a.e[a.perm[off + i0 + q]] : TA(0);
+        ej[q] = (a.e && j0 + q < s) ? (TA)a.e[a.perm[off + j0 + q]] : TA(0);
+    }
+    __syncthreads();
+    TA acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+#pragma unroll 8
+    for (int l = 0; l < PB; ++l) {
+        TA r[4], t[4];
+        lds4(&Rs[l][4 * ty], r);
+        lds4(&Ts[l][4 * tx], t);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += r[u] * t[v];
+    }
+    const TA gam = (TA)a.gamma, bet = (TA)a.beta;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + 4 * ty + u, j = j0 + 4 * tx + v;
+            if (i >= s || j >= s) continue;
+            const bool pi = i >= k0 && i < k0 + bk, pj = j >= k0 && j < k0 + bk;
+            TA val;
+            if (pi && pj) val = Dg[(i - k0) * PB + (j - k0)];
+            else if (pi) val = Ts[i - k0][4 * tx + v];
+            else if (pj) val = Tg[(size_t)(j - k0) * s + i];
+            else {
+                TA m = mv[u][v];
+                if (first) m += bet * ei[4 * ty + u] * ej[4 * tx + v] + (i == j ? gam : TA(0));
+                val = m - acc[u][v];
+            }
+            M[(size_t)i * s + j] = last ? -val : val;
+        }
 }
 
 // ---------------------------------------------------------------- chain
@@ -482,15 +556,10 @@ __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, T
 }
 
 // ---------------------------------------------------------------- launchers
-template <class TA> static size_t big_inverse_smem(int smax) {
-    constexpr int PB = BigPB<TA>::v;
-    return (2 * (size_t)PB * smax + PB * PB + smax + PB) * sizeof(TA);
-}
-
 // K_S for every block is gathered straight into the factor buffer W and
 // inverted there in place.
 template <class TS, class TA>
-static cudaError_t big_factor_impl(const ChainArgs &a, void *Wout, cudaStream_t st) {
+static cudaError_t big_factor_impl(const ChainArgs &a, void *Wout, void *Pan, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
     const int smax = lay.smax();
     const int nt = (smax + BT - 1) / BT;
@@ -513,26 +582,29 @@ static cudaError_t big_factor_impl(const ChainArgs &a, void *Wout, cudaStream_t 
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = big_inverse_smem<TA>(smax);
-    e = cudaFuncSetAttribute(k_big_inverse<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_big_inverse<TA><<<a.p, 256, smem, st>>>(a, (TA *)Wout);
+    const int ntm = (smax + IT - 1) / IT;
+    for (int k0 = 0; k0 < smax; k0 += BigPB<TA>::v) {
+        k_big_panel<TA><<<a.p, 256, 0, st>>>(a, (TA *)Wout, (TA *)Pan, k0);
+        k_big_update<TA><<<dim3(ntm * ntm, a.p), 256, 0, st>>>(a, (TA *)Wout, (const TA *)Pan, k0);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_big_factor(int store, const ChainArgs &a, void *Wout, cudaStream_t st) {
-    if (store == ST_F64) return big_factor_impl<double, double>(a, Wout, st);
-    if (store == ST_F32) return big_factor_impl<float, float>(a, Wout, st);
-    return big_factor_impl<__nv_bfloat16, float>(a, Wout, st);
+cudaError_t launch_big_factor(int store, const ChainArgs &a, void *Wout, void *Pan,
+                              cudaStream_t st) {
+    if (store == ST_F64) return big_factor_impl<double, double>(a, Wout, Pan, st);
+    if (store == ST_F32) return big_factor_impl<float, float>(a, Wout, Pan, st);
+    return big_factor_impl<__nv_bfloat16, float>(a, Wout, Pan, st);
 }
 
-bool big_factor_fits(int store, int smax) {
-    const size_t smem = store == ST_F64 ? big_inverse_smem<double>(smax) : big_inverse_smem<float>(smax);
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return smem <= (size_t)optin;
+size_t big_panel_bytes(int store, int p, int smax) {
+    return store == ST_F64 ? (size_t)p * big_panel_stride<double>(smax) * sizeof(double)
+                           : (size_t)p * big_panel_stride<float>(smax) * sizeof(float);
+}
+
+int big_factor_launches(int smax, int store) {
+    const int pb = store == ST_F64 ? BigPB<double>::v : BigPB<float>::v;
+    return 1 + 2 * ((smax + pb - 1) / pb);
 }
 
 template <class TS, class TA>

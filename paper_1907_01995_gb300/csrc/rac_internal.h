@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/rac_admm.h"
 
 namespace rac {
@@ -24,6 +26,24 @@ struct DevStats {
 };
 
 enum Store { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2 };
+
+// Streams, events and pinned status words of one handle, borrowed from a
+// per-device free list (rac_runtime.cu) and returned idle.
+struct StreamSet {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    cudaStream_t sfs[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev = nullptr;
+    std::vector<cudaEvent_t> fev;   // no timing
+    std::vector<cudaEvent_t> pev;   // timing
+    DevStats *h_stats = nullptr;
+    int *h_err = nullptr;
+};
+// the current device's memory pool (freed memory stays cached for reuse)
+cudaError_t runtime_pool(cudaMemPool_t *pool);
+// a stream set with at least nfev plain and npev timing events
+cudaError_t runtime_take_streams(StreamSet **out, size_t nfev, size_t npev);
+void runtime_give_streams(StreamSet *ss);
 
 // Arguments of the persistent sweep kernels (one instance, one rhs column).
 struct ChainArgs {
@@ -102,9 +122,12 @@ cudaError_t launch_prepare(int n, const int *perm, const double *x, const double
 int lookahead_perm_smem_max();
 
 // large blocks (residual form, 128 < s): gathered Gram + blocked sweep inverse
-// into Wout (K^{-1}), and the chain with a distributed block solve
-cudaError_t launch_big_factor(int store, const ChainArgs &a, void *Wout, cudaStream_t st);
-bool big_factor_fits(int store, int smax);
+// into Wout (K^{-1}) with a panel scratch Pan of big_panel_bytes(), and the
+// chain with a distributed block solve
+cudaError_t launch_big_factor(int store, const ChainArgs &a, void *Wout, void *Pan,
+                              cudaStream_t st);
+size_t big_panel_bytes(int store, int p, int smax);
+int big_factor_launches(int smax, int store);
 cudaError_t launch_big_chain(int store, const ChainArgs &a, int grid, void *rhs, void *dxs,
                              cudaStream_t st);
 int big_chain_max_grid(int store);

@@ -325,6 +325,155 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_rows(ChainArgs a, TA 
     }
 }
 
+// Gram-form factor for s <= SP (SP = 64 or 128), FP32 arithmetic.  The sweep
+// operator runs on the augmented s x (s + s') matrix [K_S | G[S_i, S_{i-1}]]:
+// sweeping K_S's s pivots turns the left part into -K_S^{-1} and the right
+// part into K_S^{-1} G[S_i, S_{i-1}] = P_i (Goodnight 1979), so the lookahead
+// matrix needs no separate product.  The matrix is padded to SP x 2SP (an
+// identity on the padding) and held in registers: thread (tr, tc) of
+// 16 x NT/16 owns rows 64 q + 4 tr + u (q < SP/64) and columns 4 tc + v
+// (left part) and SP + 4 tc + v (right part), so the pivot-row values it
+// needs come in float4 loads from shared memory.  The owners of the row after
+// the pivot publish it into the other half of a double buffer, with its
+// diagonal entry as d - 1 and the reciprocal of d beside it: one barrier per
+// pivot.  With that diagonal entry the single update
+// a_ij -= (a_ik / d) v_j yields a_ik / d in the pivot column and a_kj / d in
+// the pivot row; only the pivot itself, -1/d, is set apart.
+template <class TS, int SP, int NT, bool WITH_P>
+__global__ void __launch_bounds__(NT) k_factor_sq(ChainArgs a, float *Wout, float *Pout) {
+    constexpr int TC = NT / 16;
+    static_assert(4 * TC == SP, "one float4 column chunk per part");
+    constexpr int NR = SP / 16;                 // rows per thread (SP/64 chunks of 4)
+    constexpr int NC = WITH_P ? 8 : 4;          // columns per thread
+    __shared__ __align__(16) float vbuf[2][2 * SP + 4];
+    __shared__ int idx[SP], idxp[SP];
+    __shared__ float es[SP];
+    const int i = blockIdx.x;
+    BlockLayout lay(a.n, a.p);
+    const int s = lay.size(i), off = lay.offset(i);
+    const int sp = (WITH_P && i > 0) ? lay.size(i - 1) : 0, offp = i > 0 ? lay.offset(i - 1) : 0;
+    const int tr = threadIdx.x / TC, tc = threadIdx.x % TC;
+    for (int t = threadIdx.x; t < SP; t += NT) {
+        const int j = t < s ? a.perm[off + t] : 0;
+        idx[t] = j;
+        es[t] = (t < s && a.e) ? (float)a.e[j] : 0.f;
+        idxp[t] = t < sp ? a.perm[offp + t] : 0;
+    }
+    __syncthreads();
+    const TS *G = (const TS *)a.G;
+    const float gam = (float)a.gamma, bet = (float)a.beta;
+    float acc[NR][NC];
+#pragma unroll
+    for (int ru = 0; ru < NR; ++ru) {
+        const int row = 64 * (ru >> 2) + 4 * tr + (ru & 3);
+        const size_t rowoff = (size_t)idx[row] * a.n;
+#pragma unroll
+        for (int cu = 0; cu < NC; ++cu) {
+            const int c = 4 * tc + (cu & 3);
+            float v;
+            if (cu < 4) {
+                if (row < s && c < s)
+                    v = to_f(G[rowoff + idx[c]]) + bet * es[row] * es[c] + (row == c ? gam : 0.f);
+                else
+                    v = row == c ? 1.f : 0.f;
+            } else {
+                v = (row < s && c < sp) ? to_f(G[rowoff + idxp[c]]) : 0.f;
+            }
+            acc[ru][cu] = v;
+        }
+        if (ru & 1) asm volatile("" ::: "memory");   // bound the gathers in flight
+    }
+    // publish row 0 (tr = 0, slot 0) with d - 1 on its diagonal and 1/d after the row
+    bool bad = false;
+    if (tr == 0) {
+        float4 w = make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+        if (tc == 0) {
+            bad = !(acc[0][0] > 0.f);
+            vbuf[0][2 * SP] = __frcp_rn(bad ? 1.f : acc[0][0]);
+            w.x -= 1.f;
+        }
+        *reinterpret_cast<float4 *>(&vbuf[0][4 * tc]) = w;
+        if (WITH_P)
+            *reinterpret_cast<float4 *>(&vbuf[0][SP + 4 * tc]) =
+                make_float4(acc[0][4], acc[0][5], acc[0][6], acc[0][7]);
+    }
+    __syncthreads();
+    for (int k = 0; k < s; ++k) {
+        const float *vk = vbuf[k & 1];
+        float *vn = vbuf[(k + 1) & 1];
+        const float rd = vk[2 * SP];
+        float f[NR], cv[NC];
+#pragma unroll
+        for (int q = 0; q < NR / 4; ++q) {
+            const float4 w = *reinterpret_cast<const float4 *>(&vk[64 * q + 4 * tr]);
+            f[4 * q] = w.x * rd; f[4 * q + 1] = w.y * rd; f[4 * q + 2] = w.z * rd; f[4 * q + 3] = w.w * rd;
+        }
+#pragma unroll
+        for (int q = 0; q < NC / 4; ++q) {
+            const float4 w = *reinterpret_cast<const float4 *>(&vk[SP * q + 4 * tc]);
+            cv[4 * q] = w.x; cv[4 * q + 1] = w.y; cv[4 * q + 2] = w.z; cv[4 * q + 3] = w.w;
+        }
+#pragma unroll
+        for (int ru = 0; ru < NR; ++ru)
+#pragma unroll
+            for (int cu = 0; cu < NC; ++cu) acc[ru][cu] = fmaf(-f[ru], cv[cu], acc[ru][cu]);
+        // the pivot: row k lives in threads tr == (k % 64) / 4 (row slot
+        // 4 (k / 64) + k % 4), column k in threads tc == k / 4 (slot k % 4)
+        const int kk = k & 63;
+        if (tr == (kk >> 2) && tc == (k >> 2)) {
+            const int slot = 4 * (k >> 6) + (k & 3), kv = k & 3;
+#pragma unroll
+            for (int ru = 0; ru < NR; ++ru)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[ru][v] = (ru == slot && v == kv) ? -rd : acc[ru][v];
+        }
+        // publish row k + 1
+        const int k1 = k + 1, kk1 = k1 & 63;
+        if (k1 < s && tr == (kk1 >> 2)) {
+            const int slot = 4 * (k1 >> 6) + (k1 & 3), kv = k1 & 3;
+            float rowv[NC];
+#pragma unroll
+            for (int cu = 0; cu < NC; ++cu) rowv[cu] = acc[0][cu];
+#pragma unroll
+            for (int ru = 1; ru < NR; ++ru)
+#pragma unroll
+                for (int cu = 0; cu < NC; ++cu) rowv[cu] = ru == slot ? acc[ru][cu] : rowv[cu];
+            if (tc == (k1 >> 2)) {
+                float d1 = rowv[0];
+#pragma unroll
+                for (int v = 1; v < 4; ++v) d1 = v == kv ? rowv[v] : d1;
+                if (!(d1 > 0.f)) bad = true;
+                vn[2 * SP] = __frcp_rn(d1 > 0.f ? d1 : 1.f);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) rowv[v] -= v == kv ? 1.f : 0.f;
+            }
+            *reinterpret_cast<float4 *>(&vn[4 * tc]) = make_float4(rowv[0], rowv[1], rowv[2], rowv[3]);
+            if (WITH_P)
+                *reinterpret_cast<float4 *>(&vn[SP + 4 * tc]) =
+                    make_float4(rowv[NC - 4], rowv[NC - 3], rowv[NC - 2], rowv[NC - 1]);
+        }
+        __syncthreads();
+    }
+    if (bad) set_err(a.err, RAC_ERR_NOT_PD);
+    float *out = Wout + lay.factor_offset(i);
+    float *po = (WITH_P && sp > 0) ? Pout + (size_t)i * BlockLayout::pad4((size_t)lay.smax() * lay.smax())
+                                   : nullptr;
+#pragma unroll
+    for (int ru = 0; ru < NR; ++ru) {
+        const int row = 64 * (ru >> 2) + 4 * tr + (ru & 3);
+        if (row >= s) continue;
+#pragma unroll
+        for (int cu = 0; cu < NC; ++cu) {
+            const int c = 4 * tc + (cu & 3);
+            if (cu < 4) {
+                if (c < s) out[(size_t)row * s + c] = -acc[ru][cu];
+            } else if (po && c < sp) {
+                po[(size_t)c * s + row] = acc[ru][cu];
+            }
+        }
+    }
+}
+
 template <class TS, class TA, bool GRAM, int NP, int U>
 static cudaError_t factor_rows_impl(const ChainArgs &a, void *Wout, void *Pout, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
@@ -357,6 +506,20 @@ template <class TS, class TA, bool GRAM>
 static cudaError_t factor_any(const ChainArgs &a, void *Wout, void *Pout, int *kinv,
                               cudaStream_t st) {
     const int smax = BlockLayout(a.n, a.p).smax();
+    if constexpr (GRAM && sizeof(TA) == 4) {
+        if (smax <= 128) {
+            *kinv = 1;
+            float *W = (float *)Wout, *P = (float *)Pout;
+            if (smax <= 64) {
+                if (P) k_factor_sq<TS, 64, 256, true><<<a.p, 256, 0, st>>>(a, W, P);
+                else k_factor_sq<TS, 64, 256, false><<<a.p, 256, 0, st>>>(a, W, P);
+            } else {
+                if (P) k_factor_sq<TS, 128, 512, true><<<a.p, 512, 0, st>>>(a, W, P);
+                else k_factor_sq<TS, 128, 512, false><<<a.p, 512, 0, st>>>(a, W, P);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (smax <= 64) {
         *kinv = 1;
         return factor_rows_impl<TS, TA, GRAM, 8, 8>(a, Wout, Pout, st);

@@ -216,10 +216,11 @@ def test_checkpoint_restore_bitwise():
     assert full["mu"] == resumed["mu"]
 
 
-def test_not_positive_definite_is_reported():
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_not_positive_definite_is_reported(storage):
     H = -np.eye(6)
     with api.Handle(H=H, c=np.ones(6), phi="none", num_blocks=2, beta=0.5, tol=0.0,
-                    max_sweeps=2) as h:
+                    max_sweeps=2, storage=storage) as h:
         with pytest.raises(_lib.RacError) as ei:
             h.solve()
     assert ei.value.status == _lib.RAC_ERR_NOT_PD
@@ -266,3 +267,21 @@ def test_gram_build_matches_fp64(storage):
         tol = 1e-12 if storage == "fp64" else m * 2.0 ** -23
         assert np.abs(got - ref).max() <= tol * scale
     assert np.array_equal(got, got.T)
+
+
+@pytest.mark.parametrize("storage,form", [("fp64", "gram"), ("bf16", "gram"), ("fp32", "residual")])
+def test_pooled_handles_repeat_bitwise(storage, form):
+    """Handles draw memory, streams and events from per-device caches: a
+    handle set up on reused (not re-zeroed) memory, or after the cache was
+    trimmed, gives bit-identical iterates."""
+    inst = _instance(CASES["lasso_gram"], seed=2)
+    runs = []
+    for rep in range(3):
+        if rep == 2:
+            api.trim_pool()
+        with _handle(inst, form, storage=storage, tol=0.0, max_sweeps=25, refresh_every=5) as h:
+            h.solve()
+            runs.append(h.state())
+    for r in runs[1:]:
+        for key in ("x", "z", "xi"):
+            assert np.array_equal(runs[0][key], r[key])

@@ -329,6 +329,72 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 // Copy `bytes` (a multiple of 16, both pointers 16-byte aligned) by the CTA.
+// ---- bulk (TMA) copies global -> shared that complete on an mbarrier ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+// make initialised mbarriers visible to the async proxy (then __syncthreads)
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses before later async-proxy
+// (bulk copy) writes to the same memory
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity to complete, at most limit_ns; on
+// timeout record RAC_ERR_TIMEOUT and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          uint64_t limit_ns) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_test(bar, parity)) {
+        if (globaltimer_ns() - t0 > limit_ns) {
+            set_err(err, RAC_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+// One thread: copy bytes (a multiple of 16) in chunks of at most 32 KiB,
+// all completing on bar.
+__device__ __forceinline__ void bulk_g2s_chunks(void *dst, const void *src, size_t bytes,
+                                                uint64_t *bar) {
+    constexpr size_t kChunk = 32768;
+    for (size_t o = 0; o < bytes; o += kChunk) {
+        const uint32_t nb = (uint32_t)(bytes - o < kChunk ? bytes - o : kChunk);
+        bulk_g2s((char *)dst + o, (const char *)src + o, nb, bar);
+    }
+}
+
 __device__ __forceinline__ void cta_copy_async(void *dst, const void *src, size_t bytes) {
     const size_t nv = bytes >> 4;
     for (size_t v = threadIdx.x; v < nv; v += blockDim.x)

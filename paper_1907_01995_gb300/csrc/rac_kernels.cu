@@ -724,6 +724,74 @@ __device__ __forceinline__ void gemv_rows(const TA *M, int rows, int cols, const
     }
 }
 
+// y[r] = scale (sum_c M[c ld + r] x[c] + add[r]) for r < rows <= 128 and
+// c < cols, by a CTA of 256 threads: warp w takes the columns w, w + 8, ...
+// and lane l the row quad 4l..4l+3, so each step is one float4 (two double2)
+// load of M that the warp reads as 512 contiguous bytes and a broadcast of
+// x[c]; the 8 column-slice partials are summed in a fixed tree order.  The
+// vector path needs ld and rows multiples of 4 and a 16-byte aligned M.
+// Ends with a barrier (y ready); x and add must be ready on entry.
+template <class TA> __device__ __forceinline__ void ld4(const TA *p, bool vec, TA (&o)[4], int lim) {
+    if (vec) {
+        if constexpr (sizeof(TA) == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p);
+            o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+        } else {
+            const double2 v0 = reinterpret_cast<const double2 *>(p)[0];
+            const double2 v1 = reinterpret_cast<const double2 *>(p)[1];
+            o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = u < lim ? p[u] : TA(0);
+    }
+}
+
+constexpr int kGemvRows = 128;   // gemv_cm: rows per call at most (lanes x 4)
+
+template <class TA>
+__device__ __forceinline__ void gemv_cm(const TA *M, int ld, int rows, int cols, const TA *x,
+                                        const TA *add, TA scale, TA *y, TA *red) {
+    const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5, ns = blockDim.x >> 5;
+    const int r0 = 4 * lane;
+    const bool vec = ((ld | rows) & 3) == 0 && (((uintptr_t)M) & 15) == 0;
+    TA acc[4] = {0, 0, 0, 0};
+    if (r0 < rows) {
+        const TA *mp = M + r0;
+        if (vec) {
+#pragma unroll 4
+            for (int c = sl; c < cols; c += ns) {
+                TA m[4];
+                ld4<TA>(mp + (size_t)c * ld, true, m, 4);
+                const TA xc = x[c];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma(m[u], xc, acc[u]);
+            }
+        } else {
+            const int lim = rows - r0;
+            for (int c = sl; c < cols; c += ns) {
+                TA m[4];
+                ld4<TA>(mp + (size_t)c * ld, false, m, lim);
+                const TA xc = x[c];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma(m[u], xc, acc[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) red[sl * kGemvRows + r0 + u] = acc[u];
+    __syncthreads();
+    if ((int)threadIdx.x < rows) {
+        const int r = threadIdx.x;
+        TA v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = k < ns ? red[k * kGemvRows + r] : TA(0);
+        const TA tot = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        y[r] = scale * (tot + (add ? add[r] : TA(0)));
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ bool grid_wait_count(GridBarrier *bar, unsigned target, int *err,
                                                 int *s_flag) {
     if (threadIdx.x == 0) {
@@ -759,12 +827,14 @@ int lookahead_perm_smem_max() { return kPermSmemMax; }
 
 template <class TA> struct LaSmem {
     __host__ __device__ static size_t kst(int smax) { return BlockLayout::pad4((size_t)smax * smax); }
+    // partials of gemv_cm: 8 column slices x 128 rows
+    __host__ __device__ static size_t gemv_red(int) { return 8 * (size_t)kGemvRows; }
     static size_t bytes(int smax, int nw, int stage, int stage_p, int n = 0) {
         size_t permb = n > 0 && n <= kPermSmemMax ? (((size_t)n * sizeof(int) + 15) & ~(size_t)15)
                                                   : 3 * (((size_t)smax * sizeof(int) + 15) & ~(size_t)15);
         return permb + 3 * (size_t)smax * sizeof(TA) + (size_t)nw * 32 * sizeof(TA) +
                64 * sizeof(double) + 64 + (stage ? 2 * kst(smax) * sizeof(TA) : 0) +
-               (stage_p ? 2 * kst(smax) * sizeof(TA) : 0);
+               (stage_p ? 2 * kst(smax) * sizeof(TA) : 0) + gemv_red(smax) * sizeof(TA) + 16;
     }
 };
 
@@ -787,7 +857,10 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
     const size_t kst = LaSmem<TA>::kst(smax);
     TA *kbuf = (TA *)(((uintptr_t)(dred + 64) + 15) & ~(uintptr_t)15);
     TA *pbuf = a.stage ? kbuf + 2 * kst : kbuf;
+    TA *gred = (a.stage_p ? pbuf + 2 * kst : pbuf) ;
+    gred = (TA *)(((uintptr_t)gred + 15) & ~(uintptr_t)15);
     __shared__ int s_flag;
+    __shared__ __align__(8) uint64_t s_mbar[2];   // one per staging slot (block parity)
     const TS *G = (const TS *)a.G;
     const TA *Wall = (const TA *)a.W;
     const TA *Pall = (const TA *)a.P;
@@ -808,17 +881,31 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
             for (int q = threadIdx.x; q < sb; q += blockDim.x) d[q] = a.perm[ob + q];
         }
     };
+    // K_b^{-1} and P_b^T are staged by bulk copies that thread 0 issues and
+    // that complete on the mbarrier of slot b & 1 (its (b >> 1)-th phase)
+    auto pf_bytes = [&](int b, size_t *kb, size_t *pb) {
+        const int sb = lay.size(b);
+        *kb = a.stage ? BlockLayout::pad4((size_t)sb * sb) * sizeof(TA) : 0;
+        *pb = (a.stage_p && b > 0) ? BlockLayout::pad4((size_t)sb * lay.size(b - 1)) * sizeof(TA) : 0;
+    };
     auto prefetch = [&](int b) {
-        if (b < a.p) {
-            const int sb = lay.size(b);
-            if (a.stage)
-                cta_copy_async(kbuf + (size_t)(b & 1) * kst, Wall + lay.factor_offset(b),
-                               BlockLayout::pad4((size_t)sb * sb) * sizeof(TA));
-            if (a.stage_p && b > 0)
-                cta_copy_async(pbuf + (size_t)(b & 1) * kst, Pall + (size_t)b * kst,
-                               BlockLayout::pad4((size_t)sb * lay.size(b - 1)) * sizeof(TA));
-        }
-        cp_async_commit();
+        if (b >= a.p || threadIdx.x != 0) return;
+        size_t kb, pb;
+        pf_bytes(b, &kb, &pb);
+        if (kb + pb == 0) return;
+        // the slot's last readers finished before the CTA barrier that precedes
+        // every call, which orders their reads before these copies
+        uint64_t *bar = &s_mbar[b & 1];
+        mbar_expect_tx(bar, (uint32_t)(kb + pb));
+        if (kb) bulk_g2s_chunks(kbuf + (size_t)(b & 1) * kst, Wall + lay.factor_offset(b), kb, bar);
+        if (pb) bulk_g2s_chunks(pbuf + (size_t)(b & 1) * kst, Pall + (size_t)b * kst, pb, bar);
+    };
+    auto landed = [&](int b) -> bool {
+        if (b >= a.p) return true;
+        size_t kb, pb;
+        pf_bytes(b, &kb, &pb);
+        if (kb + pb == 0) return true;
+        return mbar_wait(&s_mbar[b & 1], (uint32_t)((b >> 1) & 1), a.err, kBarrierTimeoutNs);
     };
     auto kptr = [&](int b) -> const TA * {
         return a.stage ? kbuf + (size_t)(b & 1) * kst : Wall + lay.factor_offset(b);
@@ -839,6 +926,12 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
             breg[k] = a.blk[col];
         }
     }
+    if (threadIdx.x == 0) {
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
     prefetch(0);
     prefetch(1);
     if (pin) {
@@ -857,42 +950,24 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
             rhs[q] = (TA)r;
         }
     }
-    cp_async_wait<1>();
+    if (!landed(0)) {
+        landed(1);
+        return;
+    }
     __syncthreads();
     for (int i = 0; i < a.p; ++i) {
         const int s = lay.size(i);
         const int *cur = bidx(i);
         const bool has_next = i + 1 < a.p;
         const int sn = has_next ? lay.size(i + 1) : 0, offn = has_next ? lay.offset(i + 1) : 0;
-        // loads that do not depend on dx_i, issued early: the static rhs part
-        // of block i+1 and this CTA's first gradient tile of G[S_i, :]
+        // the static rhs part of block i+1 does not depend on dx_i: load early
         double snext = 0.0, enext = 0.0;
         if (has_next && threadIdx.x < sn) {
             snext = a.sperm[offn + threadIdx.x];
             if (a.e) enext = a.eperm[offn + threadIdx.x];
         }
-        const int col0 = blockIdx.x * 32 + lane;
-        constexpr int GV = 16;
-        TA gv[GV];
-#pragma unroll
-        for (int k = 0; k < GV; ++k) {
-            const int q = warp + k * nw;
-            gv[k] = (col0 < n && q < s) ? (TA)to_f(G[(size_t)cur[q] * n + col0]) : TA(0);
-        }
-        // dx_i = -K_i^{-1} rhs - P_i dx_{i-1}; K^{-1} symmetric, one thread per row
-        for (int r = threadIdx.x; r < s; r += blockDim.x) {
-            const TA *kc = kptr(i) + r;
-            TA acc = i ? dn[r] : TA(0);
-            TA acc2 = 0;
-            int c = 0;
-            for (; c + 1 < s; c += 2) {
-                acc = fma(kc[(size_t)c * s], rhs[c], acc);
-                acc2 = fma(kc[(size_t)(c + 1) * s], rhs[c + 1], acc2);
-            }
-            if (c < s) acc = fma(kc[(size_t)c * s], rhs[c], acc);
-            dl[r] = -(acc + acc2);
-        }
-        __syncthreads();
+        // dx_i = -K_i^{-1} rhs - P_i dx_{i-1} (K^{-1} symmetric: columns = rows)
+        gemv_cm<TA>(kptr(i), s, s, s, rhs, i ? dn : nullptr, TA(-1), dl, gred);
         if (a.e) {
             double loc = 0.0;
             for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[cur[q]] * (double)dl[q];
@@ -900,29 +975,34 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
         }
         if (blockIdx.x == 0)
             for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[cur[q]] = (double)dl[q];
+        // this CTA's first gradient tile of G[S_i, :], raw (converted where
+        // used), so the loads stay in flight through the P product and the wait
+        const int col0 = blockIdx.x * 32 + lane;
+        constexpr int GV = 16;
+        TS gv[GV];
+#pragma unroll
+        for (int k = 0; k < GV; ++k) {
+            const int q = warp + k * nw;
+            gv[k] = TS(0);
+            if (col0 < n && q < s) gv[k] = G[(size_t)cur[q] * n + col0];
+        }
+        double gval = 0.0;   // g at block i+1's coordinates (final: block i parks in gnext)
         if (has_next) {
             prefetch(i + 2);            // buffers (i+2)&1 = i&1 are free: block i is solved
             load_idx(i + 2);
-            cp_async_wait<1>();         // block i+1's K^{-1} and P^T have landed
-            __syncthreads();
-            // dn = P_{i+1} dx_i from P^T (s_i x s_{i+1}), one thread per row
-            const TA *pt = pptr(i + 1);
-            for (int q = threadIdx.x; q < sn; q += blockDim.x) {
-                TA acc = 0;
-                for (int c = 0; c < s; ++c) acc = fma(pt[(size_t)c * sn + q], dl[c], acc);
-                dn[q] = acc;
+            if (!landed(i + 1)) {       // block i+1's K^{-1} and P^T have landed
+                landed(i + 2);
+                return;
             }
+            __syncthreads();
+            // dn = P_{i+1} dx_i from P^T (s_i x s_{i+1}): column c of P is row c of P^T
+            gemv_cm<TA>(pptr(i + 1), sn, sn, s, dl, nullptr, TA(1), dn, gred);
             if (i >= 1)
                 if (!grid_wait_count(a.bar, (unsigned)i * grid, a.err, &s_flag)) {
-                    cp_async_wait<0>();
+                    landed(i + 2);      // no copy may still target shared memory
                     return;
                 }
-            const int *nxt = bidx(i + 1);
-            if (threadIdx.x < sn) {
-                double r = __ldcg(a.g + nxt[threadIdx.x]) + snext;
-                if (a.e) r += enext * (beta * t - mu);
-                rhs[threadIdx.x] = (TA)r;
-            }
+            if (threadIdx.x < sn) gval = __ldcg(a.g + bidx(i + 1)[threadIdx.x]);
         }
         // bulk update of this CTA's tiles: g += G[:, S_i] dx_i
 #pragma unroll
@@ -935,7 +1015,7 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
 #pragma unroll
                 for (int kk = 0; kk < GV; ++kk) {
                     const int q = warp + kk * nw;
-                    if (q < s) acc = fma(gv[kk], dl[q], acc);
+                    if (q < s) acc = fma((TA)to_f(gv[kk]), dl[q], acc);
                 }
                 for (int q = warp + GV * nw; q < s; q += nw)
                     if (col < n) acc += (TA)to_f(G[(size_t)cur[q] * n + col]) * dl[q];
@@ -967,9 +1047,15 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_gram_la(ChainArgs a) {
             }
             __syncthreads();
         }
+        // rhs of block i+1, written after the tile work so that the load of g
+        // overlaps it; the barrier in grid_arrive publishes it to the CTA
+        if (has_next && threadIdx.x < sn) {
+            double r = gval + snext;
+            if (a.e) r += enext * (beta * t - mu);
+            rhs[threadIdx.x] = (TA)r;
+        }
         grid_arrive(a.bar);
     }
-    cp_async_wait<0>();
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.e) *a.t = t;
 }
 

@@ -119,6 +119,11 @@ typedef struct {
                                dual a KKT point with x0's signs would have; overrides xi0 */
     int32_t ws_fallback;    /* 1 (with x0): if the KKT after the first refresh period exceeds
                                the KKT of the cold start z = 0, restart from zero */
+    int32_t chain;          /* block-chain kernel of the Gram form: 0 = automatic, 1 = grid of
+                               CTAs with a global-memory barrier, 2 = one thread-block cluster
+                               (FP32/BF16 storage, block size <= 128, n even and at most 4096;
+                               falls back to 1 where it does not apply).  Same iterates up to
+                               floating-point summation order. */
 } rac_options;
 
 /* KKT measure used for the stop test, evaluated in FP64 on z with the exact

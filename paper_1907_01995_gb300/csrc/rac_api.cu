@@ -74,6 +74,7 @@ struct rac_handle {
     std::vector<cudaEvent_t> fev;   // per sweep slot: factor done, chain done (2 each)
     int kinv = 1, stage = 0, stage_p = 0, lookahead = 0;
     int big = 0;                    // residual form with 128 < s: large-block factor + chain
+    int cluster = 0;                // > 0: Gram-form chain on one cluster of this many CTAs
     void *rhs_big = nullptr, *dx_big = nullptr;
     size_t wstride = 0;             // bytes of one sweep's factors (one buffer per period slot)
     void *Pbuf = nullptr;           // lookahead matrices P_i^T (one buffer per period slot)
@@ -255,6 +256,7 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.sperm = h->sperm;
     a.eperm = h->k ? h->eperm : nullptr;
     a.perm_in_smem = h->perm_in_smem;
+    a.p_rows = h->cluster ? 1 : 0;
     return a;
 }
 
@@ -302,6 +304,8 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         if (h->big) {
             RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
+        } else if (h->cluster) {
+            RAC_CK(launch_cluster_chain(h->store, a, h->cluster, st));
         } else {
             RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
         }
@@ -630,6 +634,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // Gram form with register factors: lookahead chain (P_i precomputed)
     h->lookahead = (h->gram && h->kinv && factor_can_make_p(h->store, lay.smax())) ? 1 : 0;
+    if (h->lookahead && o->chain != 1) h->cluster = cluster_chain_size(h->store, n, lay.smax());
     h->perm_in_smem = (h->lookahead && n <= lookahead_perm_smem_max()) ? 1 : 0;
     const int nperm = h->perm_in_smem ? n : 0;
     if (h->lookahead) {
@@ -642,7 +647,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     size_t smem = 0;
     int gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, h->stage_p, h->lookahead,
                               nperm, &smem);
-    if (h->lookahead && gmax < lookahead_min_grid(n)) {
+    if (h->lookahead && !h->cluster && gmax < lookahead_min_grid(n)) {
         h->lookahead = 0;
         h->stage_p = 0;
         h->perm_in_smem = 0;
@@ -679,8 +684,9 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(h->alloc(&h->blk, (size_t)h->nslots * n));
     RAC_ST(h->alloc(&h->tidx, (size_t)h->nslots * n));
     RAC_ST(h->alloc(&h->tkey, (size_t)h->nslots * n));
-    std::snprintf(h->form, sizeof(h->form), "%s/%s", h->gram ? "gram" : "residual",
-                  h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"));
+    std::snprintf(h->form, sizeof(h->form), "%s/%s%s", h->gram ? "gram" : "residual",
+                  h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
+                  h->cluster ? (h->cluster == 16 ? "/cluster16" : "/cluster8") : "");
     RAC_ST(set_state(h, o->x0, o->xi0));
     RAC_CK(cudaStreamSynchronize(st));
     h->setup_launches = h->nlaunch;

@@ -78,6 +78,7 @@ struct ChainArgs {
     const double *sperm;    // lookahead: -xi + gamma (x - z) in permuted order (n)
     const double *eperm;    // lookahead: e in permuted order (n) or NULL
     int perm_in_smem;       // lookahead: the whole permutation fits in shared memory
+    int p_rows;             // factor writes P_i row-major (s_i x s_{i-1}) instead of P_i^T
 };
 
 struct ProxArgs {
@@ -131,6 +132,11 @@ int big_factor_launches(int smax, int store);
 cudaError_t launch_big_chain(int store, const ChainArgs &a, int grid, void *rhs, void *dxs,
                              cudaStream_t st);
 int big_chain_max_grid(int store);
+
+// Gram-form lookahead chain on one thread-block cluster: the cluster size
+// usable for this problem (0: not applicable), and its launch
+int cluster_chain_size(int store, int n, int smax);
+cudaError_t launch_cluster_chain(int store, const ChainArgs &a, int C, cudaStream_t st);
 
 // exact FP64 pieces of the refresh
 cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const double *z,

@@ -468,7 +468,8 @@ __global__ void __launch_bounds__(NT) k_factor_sq(ChainArgs a, float *Wout, floa
             if (cu < 4) {
                 if (c < s) out[(size_t)row * s + c] = -acc[ru][cu];
             } else if (po && c < sp) {
-                po[(size_t)c * s + row] = acc[ru][cu];
+                if (a.p_rows) po[(size_t)row * sp + c] = acc[ru][cu];
+                else po[(size_t)c * s + row] = acc[ru][cu];
             }
         }
     }

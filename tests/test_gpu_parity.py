@@ -285,3 +285,47 @@ def test_pooled_handles_repeat_bitwise(storage, form):
     for r in runs[1:]:
         for key in ("x", "z", "xi"):
             assert np.array_equal(runs[0][key], r[key])
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape", [
+    dict(m=70, n=96, p=7, phi="l1l2"),                          # few owning CTAs, ragged blocks
+    dict(m=90, n=104, p=8, phi="box", coupling=True),           # coupling row (t, mu terms)
+    dict(m=400, n=2048, p=17, phi="l1l2", lam2=0.05),            # s = 121 / 120
+])
+def test_cluster_chain_matches_grid_chain(storage, shape):
+    """The Gram-form chain on one thread-block cluster and the grid-barrier
+    chain compute the same iterates up to FP32 summation order."""
+    inst = synth.small_instance(5, shape["m"], shape["n"], shape["p"], phi=shape["phi"],
+                                lam2=shape.get("lam2", 0.0), coupling=shape.get("coupling", False))
+    out = {}
+    for chain in ("grid", "cluster"):
+        with _handle(inst, "gram", storage=storage, tol=0.0, max_sweeps=20, refresh_every=5,
+                     chain=chain) as h:
+            _, info = h.solve()
+            out[chain] = (h.state(), info)
+    assert "cluster" in out["cluster"][1]["form"], out["cluster"][1]["form"]
+    assert "cluster" not in out["grid"][1]["form"]
+    for key in ("x", "z", "xi"):
+        a, b = out["grid"][0][key], out["cluster"][0][key]
+        assert np.linalg.norm(a - b) <= 1e-4 * max(1.0, np.linalg.norm(a)), key
+
+
+def test_cluster_chain_svm_converged():
+    """Soft-margin SVM dual (box + equality row) in FP32 Gram storage on the
+    cluster chain reaches the SMO solution."""
+    inst = synth.svm_instance(4, 300, 12, block=64)
+    Q = inst.A.T @ inst.A
+    y = inst.E[0]
+    a_smo = O.smo_svm(Q, y, 1.0, tol=1e-11)
+    with api.Handle(inst.A, inst.b, c=inst.c, E=y, d=inst.d, phi="box", lo=0.0, hi=1.0,
+                    num_blocks=inst.num_blocks, beta=inst.beta, gamma=-0.3, tol=1e-8,
+                    max_sweeps=40000, refresh_every=20, storage="fp32", form="gram",
+                    chain="cluster") as h:
+        a, info = h.solve()
+    assert "cluster" in info["form"], info["form"]
+    assert info["status"] == 0, info
+    obj = lambda v: 0.5 * v @ Q @ v - v.sum()
+    assert abs(obj(a) - obj(a_smo)) <= 1e-6 * max(1.0, abs(obj(a_smo)))
+    P = O.problem_from_instance(inst)
+    assert O.kkt(P, a)["kkt"] <= 1e-8 * 1.01

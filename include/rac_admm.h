@@ -121,7 +121,8 @@ typedef struct {
                                the KKT of the cold start z = 0, restart from zero */
     int32_t chain;          /* block-chain kernel of the Gram form: 0 = automatic, 1 = grid of
                                CTAs with a global-memory barrier, 2 = one thread-block cluster
-                               (FP32/BF16 storage, block size <= 128, n even and at most 4096;
+                               (FP32/BF16 storage, block size <= 128, n <= 4096 and a multiple
+                               of 2, 4 or 8 as n grows past 1024, 2048;
                                falls back to 1 where it does not apply).  Same iterates up to
                                floating-point summation order. */
 } rac_options;

@@ -74,19 +74,33 @@ struct ClLayout {
     }
 };
 
-template <class TS> struct GPair;
-template <> struct GPair<float> {
-    using R = float2;
-    __device__ static R ld(const float *p) { return __ldcg(reinterpret_cast<const float2 *>(p)); }
-    __device__ static float2 f(R v) { return v; }
-};
-template <> struct GPair<__nv_bfloat16> {
-    using R = unsigned;
-    __device__ static R ld(const __nv_bfloat16 *p) { return __ldcg(reinterpret_cast<const unsigned *>(p)); }
-    __device__ static float2 f(R v) {
-        __nv_bfloat162 h;
-        *reinterpret_cast<unsigned *>(&h) = v;
-        return __bfloat1622float2(h);
+// G values of one lane for one row: VEC = 2 NK contiguous columns held as
+// 32-bit words (one vector load of 4, 8 or 16 bytes; two for 32)
+template <class TS, int NK> struct GVec {
+    static constexpr int VEC = 2 * NK;
+    static constexpr int WORDS = VEC * (int)sizeof(TS) / 4;
+    __device__ static void ld(const TS *p, unsigned (&w)[WORDS]) {
+        const unsigned *q = reinterpret_cast<const unsigned *>(p);
+        if constexpr (WORDS == 1) {
+            w[0] = __ldcg(q);
+        } else if constexpr (WORDS == 2) {
+            const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(q));
+            w[0] = v.x; w[1] = v.y;
+        } else {
+#pragma unroll
+            for (int h = 0; h < WORDS / 4; ++h) {
+                const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(q) + h);
+                w[4 * h] = v.x; w[4 * h + 1] = v.y; w[4 * h + 2] = v.z; w[4 * h + 3] = v.w;
+            }
+        }
+    }
+    __device__ static float at(const unsigned (&w)[WORDS], int v) {   // v compile-time
+        if constexpr (sizeof(TS) == 4) {
+            return __uint_as_float(w[v]);
+        } else {
+            const unsigned x = w[v >> 1];
+            return __uint_as_float((v & 1) ? (x & 0xffff0000u) : (x << 16));
+        }
     }
 };
 
@@ -147,7 +161,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     // lane l columns 4l..4l+3 of each
     float kv[kClRowSlots][4], pv[kClRowSlots][4];
     double spv = 0.0, epv = 0.0;                  // static rhs of entry q = threadIdx.x
-    typename GPair<TS>::R gv[kClRows][NK];        // G[S_b[w + 8 j], c0 + 2l + 64k .. +1]
+    using GV = GVec<TS, NK>;
+    unsigned gv[kClRows][GV::WORDS];              // G[S_b[w + 8 j], c0 + VEC l .. + VEC - 1]
     auto fetch_kp = [&](int b) {
         if (b >= p) return;
         const int sb = lay.size(b), ob = lay.offset(b);
@@ -173,14 +188,15 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     auto fetch_g = [&](int b) {
         if (b >= p) return;
         const int sb = lay.size(b), ob = lay.offset(b);
+        const int col = c0 + GV::VEC * lane;    // n % VEC == 0: the vector is all in or out
 #pragma unroll
         for (int j = 0; j < kClRows; ++j) {
             const int q = warp + kClWarps * j;
-            const TS *row = G + (size_t)perm[ob + (q < sb ? q : 0)] * n;
+            if (q < sb && col < n) {
+                GV::ld(G + (size_t)perm[ob + q] * n + col, gv[j]);
+            } else {
 #pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                const int col = c0 + 64 * k + 2 * lane;
-                gv[j][k] = (q < sb && col < n) ? GPair<TS>::ld(row + col) : typename GPair<TS>::R();
+                for (int w = 0; w < GV::WORDS; ++w) gv[j][w] = 0u;
             }
         }
     };
@@ -237,28 +253,23 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
             t += block_sum<double>(loc, dred);
         }
         // G[own, S_i] dx_i from the prefetched registers: warp w rows
-        // q = w + 8 j, lane l the column pairs 2l + 64k
+        // q = w + 8 j, lane l the columns VEC l .. VEC l + VEC - 1
         {
-            float acc[NK][2];
+            float acc[GV::VEC];
 #pragma unroll
-            for (int k = 0; k < NK; ++k) acc[k][0] = acc[k][1] = 0.f;
+            for (int v = 0; v < GV::VEC; ++v) acc[v] = 0.f;
 #pragma unroll
             for (int j = 0; j < kClRows; ++j) {
                 const int q = warp + kClWarps * j;
                 if (q < s) {
                     const float dq = dxi[q];
 #pragma unroll
-                    for (int k = 0; k < NK; ++k) {
-                        const float2 v = GPair<TS>::f(gv[j][k]);
-                        acc[k][0] = fmaf(v.x, dq, acc[k][0]);
-                        acc[k][1] = fmaf(v.y, dq, acc[k][1]);
-                    }
+                    for (int v = 0; v < GV::VEC; ++v) acc[v] = fmaf(GV::at(gv[j], v), dq, acc[v]);
                 }
             }
+            float *rw = red + warp * ncp + GV::VEC * lane;
 #pragma unroll
-            for (int k = 0; k < NK; ++k)
-                *reinterpret_cast<float2 *>(red + warp * ncp + 64 * k + 2 * lane) =
-                    make_float2(acc[k][0], acc[k][1]);
+            for (int v = 0; v < GV::VEC; v += 2) *reinterpret_cast<float2 *>(rw + v) = make_float2(acc[v], acc[v + 1]);
         }
         fetch_g(i + 1);         // this step's G values are consumed
         __syncthreads();
@@ -355,9 +366,10 @@ static_assert(kClRows * kClWarps == kClSmax, "G rows per warp cover a block");
 
 template <class TS>
 static int cluster_pick(int n, int smax) {
-    if (smax > kClSmax || (n % 2) != 0) return 0;   // 4-byte G pairs need n even
+    if (smax > kClSmax) return 0;
     for (int C : {16, 8}) {
         const int nk = chunks_for(n, C);
+        if (n % (2 * nk) != 0) continue;   // a lane's vector of 2 nk columns must be aligned
         size_t smem = 0;
         bool ok = false;
         if (nk == 1) ok = cluster_fits<TS, 1>(n, smax, C, &smem);

@@ -94,6 +94,8 @@ struct rac_handle {
     double *x = nullptr, *z = nullptr, *xi = nullptr, *mu = nullptr, *t = nullptr;
     double *g = nullptr, *gdef = nullptr, *ga = nullptr, *dres = nullptr, *dx = nullptr;
     double *gz = nullptr, *rbuf = nullptr, *rpart = nullptr;
+    double *kpart = nullptr;        // KKT partials
+    float *dxz = nullptr;           // x - z in FP32 for the anchor reset
     void *W = nullptr, *cpart = nullptr;
     GridBarrier *bar = nullptr;
     int *err = nullptr;
@@ -195,7 +197,7 @@ static rac_status copy_in(void *dst, const double *src, size_t count, cudaStream
 // t = E x - d.
 static rac_status enqueue_refresh(rac_handle *h) {
     cudaStream_t st = h->st;
-    h->nlaunch += (h->has_A ? 3 : 1) + 2;
+    h->nlaunch += (h->has_A ? 3 : 1) + 3 + ((h->gram && h->store != ST_F64) ? 1 : 0);
     if (h->has_A) {
         RAC_CK(launch_resid_f64(h->m, h->n, h->A64, h->m, h->z, h->b64, h->rbuf, h->rpart,
                                 h->nchunk, st));
@@ -204,9 +206,9 @@ static rac_status enqueue_refresh(rac_handle *h) {
         RAC_CK(launch_symv_f64(h->n, h->H64, h->z, h->c64, h->gz, st));
     }
     RAC_CK(launch_kkt(h->n, h->gz, h->x, h->z, h->e64, h->d, h->k ? h->mu : nullptr, h->phi,
-                      h->lam1, h->lam2, h->lo, h->hi, h->stats, st, h->lam_dev));
+                      h->lam1, h->lam2, h->lo, h->hi, h->stats, h->kpart, st, h->lam_dev));
     if (h->gram) {
-        RAC_CK(launch_gram_anchor(h->store, h->n, h->G, h->gz, h->x, h->z, h->g, st));
+        RAC_CK(launch_gram_anchor(h->store, h->n, h->G, h->gz, h->x, h->z, h->dxz, h->g, st));
     } else {
         RAC_CK(cudaMemcpyAsync(h->ga, h->gz, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RAC_CK(launch_slab_anchor(h->store, h->n, h->nslab, h->R, h->As, h->x, h->z, h->dres, st));
@@ -543,6 +545,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(h->alloc(&h->bar, 1));
     RAC_ST(h->alloc(&h->sweep_dev, 1));
     RAC_ST(h->alloc(&h->lam_dev, 2));
+    RAC_ST(h->alloc(&h->kpart, (size_t)kkt_part_doubles()));
+    RAC_ST(h->alloc(&h->dxz, n));
     {
         double lam[2] = {h->lam1, h->lam2};
         RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, st));
@@ -556,6 +560,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         int rowblocks = (m + 255) / 256;
         h->nchunk = std::max(1, std::min(n, (4 * sms + rowblocks - 1) / rowblocks));
+        h->nchunk = std::max(h->nchunk, resid_min_chunks(n));
         RAC_ST(h->alloc(&h->rpart, (size_t)h->nchunk * m));
     }
     // the scale of the KKT measure: max(1, ||grad at 0||_inf)

@@ -139,6 +139,8 @@ int cluster_chain_size(int store, int n, int smax);
 cudaError_t launch_cluster_chain(int store, const ChainArgs &a, int C, cudaStream_t st);
 
 // exact FP64 pieces of the refresh
+// column chunks the residual needs at least (nchunk >= this)
+int resid_min_chunks(int n);
 cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const double *z,
                              const double *b, double *r, double *part, int nchunk,
                              cudaStream_t st);
@@ -151,12 +153,17 @@ cudaError_t launch_xi_project(int n, const double *x0, const double *g, double l
 // out_j = ||A_j||^2
 cudaError_t launch_colsq_f64(int m, int n, const double *A, int64_t lda, double *out,
                              cudaStream_t st);
+// part: kkt_part_doubles() of scratch
 cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z, const double *e,
                        double d, const double *mu, int phi, double lam1, double lam2, double lo,
-                       double hi, DevStats *stats, cudaStream_t st, const double *lam_dev = nullptr);
-// anchor reset in the storage type: g = gz + G~ (x - z)  or  dres = A~ (x - z)
+                       double hi, DevStats *stats, double *part, cudaStream_t st,
+                       const double *lam_dev = nullptr);
+int kkt_part_doubles();
+// anchor reset in the storage type: g = gz + G~ (x - z)  or  dres = A~ (x - z);
+// dxz: n floats of scratch (FP32/BF16 storage)
 cudaError_t launch_gram_anchor(int store, int n, const void *G, const double *gz,
-                               const double *x, const double *z, double *g, cudaStream_t st);
+                               const double *x, const double *z, float *dxz, double *g,
+                               cudaStream_t st);
 cudaError_t launch_slab_anchor(int store, int n, int nslab, int R, const void *As,
                                const double *x, const double *z, double *dres, cudaStream_t st);
 

@@ -10,6 +10,8 @@
 // plus the exact FP64 refresh (r = A z - b, g = A^T r + c), the KKT reduction
 // and the setup conversions (Gram matrix, slab layout).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -1280,16 +1282,59 @@ cudaError_t launch_prox(const ProxArgs &a, cudaStream_t st) {
 // Exact FP64 refresh pieces.
 // ======================================================================
 // r = A z - b in two deterministic stages: column chunks -> partial rows.
-__global__ void k_resid_part(int m, int n, const double *__restrict__ A, int64_t lda,
-                             const double *__restrict__ z, double *part, int chunk) {
+// A CTA first lists the nonzero z_j of its column chunk in shared memory
+// (increasing j), so that a sparse z costs neither loads nor FP64 work for
+// its zeros: on this part even a predicated-off FP64 instruction occupies the
+// slow FP64 pipe.  A thread then owns one row and takes the listed columns in
+// batches of 8 independent loads, summing in the listed order.
+constexpr int kResidBatch = 8;
+constexpr int kResidMaxChunk = 1024;
+int resid_min_chunks(int n) { return (n + kResidMaxChunk - 1) / kResidMaxChunk; }
+__global__ void __launch_bounds__(256) k_resid_part(int m, int n, const double *__restrict__ A,
+                                                    int64_t lda, const double *__restrict__ z,
+                                                    double *part, int chunk) {
+    __shared__ int js[kResidMaxChunk];
+    __shared__ double zs[kResidMaxChunk];
+    __shared__ int wcount[8];
+    __shared__ int s_total;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j0 = blockIdx.y * chunk, j1 = min(n, j0 + chunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int total = 0;
+    for (int base = j0; base < j1; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        const double zj = j < j1 ? z[j] : 0.0;
+        const bool nz = (__double_as_longlong(zj) << 1) != 0;
+        const unsigned mask = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) wcount[warp] = __popc(mask);
+        __syncthreads();
+        int before = total;
+        for (int w = 0; w < warp; ++w) before += wcount[w];
+        if (nz) {
+            const int at = before + __popc(mask & ((1u << lane) - 1u));
+            js[at] = j;
+            zs[at] = zj;
+        }
+        if (threadIdx.x == 0) {
+            int t = total;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wcount[w];
+            s_total = t;
+        }
+        __syncthreads();
+        total = s_total;
+        __syncthreads();   // wcount is rewritten next round
+    }
     if (i >= m) return;
     double acc = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        const double zj = z[j];
-        if (zj != 0.0) acc += A[(size_t)j * lda + i] * zj;   // z is sparse for l1 problems
+    int k = 0;
+    for (; k + kResidBatch <= total; k += kResidBatch) {
+        double av[kResidBatch];
+#pragma unroll
+        for (int u = 0; u < kResidBatch; ++u) av[u] = __ldcs(A + (size_t)js[k + u] * lda + i);
+#pragma unroll
+        for (int u = 0; u < kResidBatch; ++u) acc = fma(av[u], zs[k + u], acc);
     }
+    for (; k < total; ++k) acc = fma(__ldcs(A + (size_t)js[k] * lda + i), zs[k], acc);
     part[(size_t)blockIdx.y * m + i] = acc;
 }
 __global__ void k_resid_sum(int m, int nchunk, const double *part, const double *b, double *r) {
@@ -1303,6 +1348,7 @@ cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const d
                              const double *b, double *r, double *part, int nchunk,
                              cudaStream_t st) {
     int chunk = (n + nchunk - 1) / nchunk;
+    if (chunk > kResidMaxChunk) return cudaErrorInvalidValue;   // nchunk >= n / 1024 required
     int nc = (n + chunk - 1) / chunk;
     dim3 g1((m + 255) / 256, nc);
     k_resid_part<<<g1, 256, 0, st>>>(m, n, A, lda, z, part, chunk);
@@ -1310,17 +1356,53 @@ cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const d
     return cudaGetLastError();
 }
 
-// g_j = A_j^T r + c_j : one warp per column.
-__global__ void k_gemvt_f64(int m, int n, const double *__restrict__ A, int64_t lda,
-                            const double *__restrict__ r, const double *c, double *g) {
+// g_j = A_j^T r + c_j : one warp per column.  With an even leading dimension
+// each lane reads 16-byte pairs of rows, 8 pairs per step into independent
+// accumulators (summed in a fixed order), so a warp keeps 4 KB of its column
+// in flight; r is read through the read-only cache.
+constexpr int kGemvtUnroll = 8;
+__global__ void __launch_bounds__(256) k_gemvt_f64(int m, int n, const double *__restrict__ A,
+                                                   int64_t lda, const double *__restrict__ r,
+                                                   const double *c, double *g) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= n) return;
     const double *aj = A + (size_t)j * lda;
-    double acc = 0.0;
-    for (int i = lane; i < m; i += 32) acc += aj[i] * r[i];
-    acc = warp_sum(acc);
-    if (lane == 0) g[j] = acc + (c ? c[j] : 0.0);
+    double acc[kGemvtUnroll];
+#pragma unroll
+    for (int u = 0; u < kGemvtUnroll; ++u) acc[u] = 0.0;
+    int i0 = 0;
+    if ((lda & 1) == 0 && (((uintptr_t)A) & 15) == 0) {
+        // pairs of rows: pair k covers rows 2k, 2k + 1; lane takes pairs lane + 32 t
+        const int npair = m >> 1;
+        const double2 *a2 = reinterpret_cast<const double2 *>(aj);
+        const double2 *r2 = reinterpret_cast<const double2 *>(r);
+        const bool r_al = (((uintptr_t)r) & 15) == 0;
+        int k = lane;
+        for (; k + 32 * (kGemvtUnroll - 1) < npair; k += 32 * kGemvtUnroll) {
+            double2 av[kGemvtUnroll], rv[kGemvtUnroll];
+#pragma unroll
+            for (int u = 0; u < kGemvtUnroll; ++u) av[u] = __ldcs(a2 + k + 32 * u);
+#pragma unroll
+            for (int u = 0; u < kGemvtUnroll; ++u)
+                rv[u] = r_al ? __ldg(r2 + k + 32 * u)
+                             : make_double2(__ldg(r + 2 * (k + 32 * u)), __ldg(r + 2 * (k + 32 * u) + 1));
+#pragma unroll
+            for (int u = 0; u < kGemvtUnroll; ++u)
+                acc[u] = fma(av[u].y, rv[u].y, fma(av[u].x, rv[u].x, acc[u]));
+        }
+        for (; k < npair; k += 32) {
+            const double2 av = __ldcs(a2 + k);
+            acc[0] = fma(av.y, __ldg(r + 2 * k + 1), fma(av.x, __ldg(r + 2 * k), acc[0]));
+        }
+        i0 = 2 * npair;   // an odd last row is taken below
+    }
+    for (int i = i0 + lane; i < m; i += 32) acc[1] = fma(aj[i], __ldg(r + i), acc[1]);
+    double tot = 0.0;
+#pragma unroll
+    for (int u = 0; u < kGemvtUnroll; ++u) tot += acc[u];
+    tot = warp_sum(tot);
+    if (lane == 0) g[j] = tot + (c ? c[j] : 0.0);
 }
 cudaError_t launch_gemvt_f64(int m, int n, const double *A, int64_t lda, const double *r,
                              const double *c, double *g, cudaStream_t st) {
@@ -1363,12 +1445,15 @@ cudaError_t launch_symv_f64(int n, const double *H, const double *z, const doubl
     return cudaGetLastError();
 }
 
-// KKT reduction on z (single CTA, fixed order).
-__global__ void __launch_bounds__(1024) k_kkt(int n, const double *gz, const double *x,
-                                              const double *z, const double *e, double d,
-                                              const double *mup, int phi, double lam1,
-                                              double lam2, double lo, double hi, DevStats *out,
-                                              const double *lam_dev) {
+// KKT reduction on z in two fixed-order stages: kKktParts CTAs reduce
+// strided slices to 6 partials each, one CTA combines them.  (One CTA alone
+// would be bound by this part's FP64 pipe on a single SM.)
+constexpr int kKktParts = 32;
+__global__ void __launch_bounds__(256) k_kkt_part(int n, const double *gz, const double *x,
+                                                  const double *z, const double *e,
+                                                  const double *mup, int phi, double lam1,
+                                                  double lam2, double lo, double hi,
+                                                  const double *lam_dev, double *part) {
     __shared__ double red[32];
     const double mu = mup ? *mup : 0.0;
     if (lam_dev) {
@@ -1376,10 +1461,10 @@ __global__ void __launch_bounds__(1024) k_kkt(int n, const double *gz, const dou
         lam2 = lam_dev[1];
     }
     double smax = 0.0, z1 = 0.0, ez = 0.0, ex = 0.0, xz = 0.0, bad = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double zj = z[j], xj = x[j];
-        double v = gz[j] - (e ? e[j] * mu : 0.0);
-        double sj = kkt_coord(phi, v, zj, lam1, lam2, lo, hi);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double zj = z[j], xj = x[j];
+        const double v = gz[j] - (e ? e[j] * mu : 0.0);
+        const double sj = kkt_coord(phi, v, zj, lam1, lam2, lo, hi);
         if (!isfinite(sj) || !isfinite(xj)) bad = 1.0;
         smax = fmax(smax, sj);
         z1 += fabs(zj);
@@ -1393,44 +1478,79 @@ __global__ void __launch_bounds__(1024) k_kkt(int n, const double *gz, const dou
     xz = block_max<double>(xz, red);
     bad = block_max<double>(bad, red);
     if (threadIdx.x == 0) {
-        out->stat_max = smax;
-        out->znorm1 = z1;
-        out->ez_minus_d = ez - d;
-        out->ex_minus_d = ex - d;
-        out->xz_inf = xz;
-        out->nonfinite = bad;
+        double *o = part + 6 * blockIdx.x;
+        o[0] = smax; o[1] = z1; o[2] = ez; o[3] = ex; o[4] = xz; o[5] = bad;
     }
+}
+__global__ void k_kkt_final(int nparts, const double *part, double d, DevStats *out) {
+    if (threadIdx.x != 0) return;
+    double smax = 0.0, z1 = 0.0, ez = 0.0, ex = 0.0, xz = 0.0, bad = 0.0;
+    for (int b = 0; b < nparts; ++b) {
+        const double *o = part + 6 * b;
+        smax = fmax(smax, o[0]);
+        z1 += o[1];
+        ez += o[2];
+        ex += o[3];
+        xz = fmax(xz, o[4]);
+        bad = fmax(bad, o[5]);
+    }
+    out->stat_max = smax;
+    out->znorm1 = z1;
+    out->ez_minus_d = ez - d;
+    out->ex_minus_d = ex - d;
+    out->xz_inf = xz;
+    out->nonfinite = bad;
 }
 cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z, const double *e,
                        double d, const double *mu, int phi, double lam1, double lam2, double lo,
-                       double hi, DevStats *stats, cudaStream_t st, const double *lam_dev) {
-    k_kkt<<<1, 1024, 0, st>>>(n, gz, x, z, e, d, mu, phi, lam1, lam2, lo, hi, stats, lam_dev);
+                       double hi, DevStats *stats, double *part, cudaStream_t st,
+                       const double *lam_dev) {
+    const int nb = std::max(1, std::min(kKktParts, (n + 255) / 256));
+    k_kkt_part<<<nb, 256, 0, st>>>(n, gz, x, z, e, mu, phi, lam1, lam2, lo, hi, lam_dev, part);
+    k_kkt_final<<<1, 32, 0, st>>>(nb, part, d, stats);
     return cudaGetLastError();
 }
+int kkt_part_doubles() { return 6 * kKktParts; }
 
 // Anchor reset, Gram form: g = gz + G~ (x - z), one warp per row.
+// (The FP32/BF16 forms take x - z, formed once in FP64 and rounded, from
+// dxz: an FP64 subtraction per matrix element would bind this part's FP64
+// pipe.)
 template <class TS, class TA>
 __global__ void k_gram_anchor(int n, const TS *__restrict__ G, const double *gz, const double *x,
-                              const double *z, double *g) {
+                              const double *z, const TA *dxz, double *g) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= n) return;
     const TS *row = G + (size_t)j * n;
     TA acc = 0;
-    for (int k = lane; k < n; k += 32) acc += (TA)to_f(row[k]) * (TA)(x[k] - z[k]);
+    if (dxz) {
+        for (int k = lane; k < n; k += 32) acc += (TA)to_f(row[k]) * __ldg(dxz + k);
+    } else {
+        for (int k = lane; k < n; k += 32) acc += (TA)to_f(row[k]) * (TA)(x[k] - z[k]);
+    }
     acc = warp_sum(acc);
     if (lane == 0) g[j] = gz[j] + (double)acc;
 }
+__global__ void k_diff_f32(int n, const double *x, const double *z, float *d) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) d[j] = (float)(x[j] - z[j]);
+}
 cudaError_t launch_gram_anchor(int store, int n, const void *G, const double *gz,
-                               const double *x, const double *z, double *g, cudaStream_t st) {
+                               const double *x, const double *z, float *dxz, double *g,
+                               cudaStream_t st) {
     dim3 gr((n + 7) / 8);
-    if (store == ST_F64)
-        k_gram_anchor<double, double><<<gr, 256, 0, st>>>(n, (const double *)G, gz, x, z, g);
-    else if (store == ST_F32)
-        k_gram_anchor<float, float><<<gr, 256, 0, st>>>(n, (const float *)G, gz, x, z, g);
+    if (store == ST_F64) {
+        k_gram_anchor<double, double>
+            <<<gr, 256, 0, st>>>(n, (const double *)G, gz, x, z, (const double *)nullptr, g);
+        return cudaGetLastError();
+    }
+    k_diff_f32<<<(n + 255) / 256, 256, 0, st>>>(n, x, z, dxz);
+    if (store == ST_F32)
+        k_gram_anchor<float, float><<<gr, 256, 0, st>>>(n, (const float *)G, gz, x, z, dxz, g);
     else
         k_gram_anchor<__nv_bfloat16, float>
-            <<<gr, 256, 0, st>>>(n, (const __nv_bfloat16 *)G, gz, x, z, g);
+            <<<gr, 256, 0, st>>>(n, (const __nv_bfloat16 *)G, gz, x, z, dxz, g);
     return cudaGetLastError();
 }
 

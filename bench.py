@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--solve-once", type=int, default=0, metavar="K",
+                    help="run K plain solves of the workload in the default mixed-precision "
+                         "form and exit (no timing; a fixed command to profile)")
     return ap.parse_args()
 
 
@@ -157,10 +160,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
+def block_sizes(n, p):
+    q, r = divmod(n, p)
+    return [q + 1] * r + [q] * (p - r)
+
+
 def algorithmic_bytes(kclass, m, n, p, sb, ta, gram):
     """Bytes one launch of a kernel class must move (one sweep / one refresh)."""
-    q, r = divmod(n, p)
-    fac = r * (q + 1) ** 2 + (p - r) * q ** 2           # sum_i s_i^2
+    fac = sum(s * s for s in block_sizes(n, p))          # sum_i s_i^2
     if kclass == "chain":
         if gram:   # every row of G once, the p factors, 4 state vectors in, 3 out
             return n * n * sb + fac * ta + 7 * n * 8
@@ -172,6 +179,50 @@ def algorithmic_bytes(kclass, m, n, p, sb, ta, gram):
     if kclass == "prox":
         return 8 * n * 8
     return 0
+
+
+def algorithmic_flops(kclass, m, n, p, gram):
+    """Floating-point operations one launch must do: the Gram-form factor
+    sweeps the augmented s_i x (s_i + s_{i-1}) matrix over s_i pivots (one
+    multiply-add per entry and pivot); the refresh is two FP64 GEMVs."""
+    ss = block_sizes(n, p)
+    if kclass == "factor" and gram:
+        return sum(2 * s * s * (s + (ss[i - 1] if i else 0)) for i, s in enumerate(ss))
+    if kclass == "refresh":
+        return 4 * m * n
+    return 0
+
+
+def roofline_for(kclass, ms_per_launch, w, sb, ta, gram, peaks, sms):
+    """Roofline entry of one kernel class.  The Gram-form factor is FP32
+    multiply-add work (bound "alu", peak = SMs x 128 FP32 lanes x 2 flop x the
+    maximum SM clock); the chain is bound by the bytes it must read ("hbm",
+    the measured copy bandwidth); the refresh by this part's FP64 pipe
+    (nominal 1.25 TFLOP/s)."""
+    m, n, p = w["m"], w["n"], w["p"]
+    sec = ms_per_launch / 1000.0
+    if kclass == "factor" and gram:
+        fl = algorithmic_flops("factor", m, n, p, gram)
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = fl / sec / 1e12
+        return {"bound": "alu", "kernel": kclass, "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "flops_per_launch": fl,
+                "launch_ms": ms_per_launch,
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
+                    sms, peaks.get("sm_max_mhz", 2070.0)),
+                "note": "one CTA per block: a launch keeps p = %d of %d SMs busy" % (p, sms)}
+    if kclass == "refresh":
+        fl = algorithmic_flops("refresh", m, n, p, gram)
+        ach = fl / sec / 1e12
+        return {"bound": "alu", "kernel": kclass, "achieved": ach, "peak": 1.25,
+                "unit": "TFLOP/s", "frac": ach / 1.25, "flops_per_launch": fl,
+                "launch_ms": ms_per_launch, "peak_source": "nominal FP64 1.25 TFLOP/s"}
+    ab = algorithmic_bytes(kclass, m, n, p, sb, ta, gram)
+    peak = peaks.get("hbm_gbs", 6800.0)
+    ach = ab / sec / 1e9
+    return {"bound": "hbm", "kernel": kclass, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "algorithmic_bytes_per_launch": ab, "launch_ms": ms_per_launch,
+            "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
 
 
 def main():
@@ -213,6 +264,13 @@ def main():
             z, info = h.solve()
         return z, info
 
+    if args.solve_once:
+        for _ in range(args.solve_once):
+            _, info = run("bf16", "gram")
+        torch.cuda.synchronize()
+        print(json.dumps({"solve_once": args.solve_once, "form": info["form"],
+                          "sweeps": info["sweeps"], "kkt": info["kkt"]}), flush=True)
+        return 0
     # autotuner: the chosen mixed-precision form (cached per workload)
     choice = autotune.choose(A, b, common, key=w["name"], device=dev)
     storage, form, grid = choice["storage"], choice["form"], choice["grid"]
@@ -300,27 +358,30 @@ def main():
     launches["factor"] = launches["prox"] = launches["chain"]
     launches["refresh"] = sum(math.ceil(i["sweeps"] / w["refresh_every"]) for i in prof_infos)
     dom = max(("factor", "chain", "prox", "refresh"), key=lambda c: cls_ms[c])
-    per_launch_ms = cls_ms[dom] / max(1, launches[dom])
-    abytes = algorithmic_bytes(dom, w["m"], w["n"], w["p"], sb, ta, gram)
-    achieved = abytes / (per_launch_ms / 1000.0) / 1e9
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peaks = json.load(f)
     except Exception:
         pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = {c: roofline_for(c, cls_ms[c] / max(1, launches[c]), w, sb, ta, gram, peaks, sms)
+            for c in ("factor", "chain", "refresh")}
+    # DRAM traffic per launch from the committed ncu capture, if it was taken
+    # on the kernels as they are now (source hash)
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tj = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1907_01995_gb300", "csrc", "rac_kernels.cu"),
-                   "rb").read()
-        ent = tj.get("%s/%s/%s" % (dom, storage, "gram" if gram else "residual"))
-        if ent and ent.get("source_sha256") == hashlib.sha256(src).hexdigest():
-            traffic = ent["bytes_per_launch"]
+        for c, ent in roof.items():
+            t = tj.get("%s/%s/%s" % (c, storage, "gram" if gram else "residual"))
+            ent["traffic"] = None
+            if t:
+                src = open(os.path.join(ROOT, t["source"]), "rb").read()
+                if t.get("source_sha256") == hashlib.sha256(src).hexdigest():
+                    ent["traffic"] = t["bytes_per_launch"]
     except Exception:
-        traffic = None
+        for ent in roof.values():
+            ent.setdefault("traffic", None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -353,10 +414,8 @@ def main():
             "speedup_vs_fp64_plain": f64 / ttk,
             "kernel_ms_per_step": {c: v / len(prof_infos) for c, v in cls_ms.items()},
             "profiled_ms_per_step": statistics.mean(prof_ms),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": abytes,
-                         "launch_ms": per_launch_ms, "peak_source": "measured hbm_gbs"},
+            "roofline": roof.get(dom, roof["chain"]),
+            "roofline_chain": roof["chain"],
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_bu / sum(e2e_s), "unit": "block_updates/s",
                     "time_to_kkt_ms": 1000.0 * statistics.mean(e2e_s),

@@ -55,7 +55,8 @@ typedef enum {
     RAC_ERR_ARG = 1,            /* invalid argument (sizes, pointers, options) */
     RAC_ERR_CUDA = 2,           /* a CUDA runtime call failed */
     RAC_ERR_OOM = 3,            /* device allocation failed */
-    RAC_ERR_NOT_PD = 4,         /* a block matrix failed Cholesky (Assumption 2.1 violated) */
+    RAC_ERR_NOT_PD = 4,         /* a block matrix had a non-positive pivot (Assumption 2.1
+                                   violated) */
     RAC_ERR_NUMERIC = 5,        /* a non-finite value appeared in the iterates */
     RAC_ERR_TIMEOUT = 6,        /* a bounded in-kernel wait gave up (grid barrier) */
     RAC_ERR_NOT_CONVERGED = 7,  /* max_sweeps reached before KKT <= tol */

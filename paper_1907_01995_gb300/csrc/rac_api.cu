@@ -449,21 +449,6 @@ static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) 
 }
 
 // KKT of the cold start z = 0 from the gradient at zero (host mirror of kkt_coord).
-static double kkt_at_zero(const rac_handle *h, const std::vector<double> &g0) {
-    double worst = 0.0;
-    for (double v : g0) {
-        double s;
-        if (h->phi == RAC_PHI_L1L2) s = std::max(std::fabs(v) - h->lam1, 0.0);
-        else if (h->phi == RAC_PHI_BOX) {
-            if (0.0 <= h->lo) s = std::max(-v, 0.0);
-            else if (0.0 >= h->hi) s = std::max(v, 0.0);
-            else s = std::fabs(v);
-        } else s = std::fabs(v);
-        worst = std::max(worst, s);
-    }
-    return worst / h->kkt_scale;
-}
-
 static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_handle *h) {
     h->m = (int)pr->m;
     h->n = (int)pr->n;
@@ -547,10 +532,9 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(h->alloc(&h->lam_dev, 2));
     RAC_ST(h->alloc(&h->kpart, (size_t)kkt_part_doubles()));
     RAC_ST(h->alloc(&h->dxz, n));
-    {
+    {   // pageable source: the copy has consumed it when the call returns
         double lam[2] = {h->lam1, h->lam2};
         RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, st));
-        RAC_CK(cudaStreamSynchronize(st));
     }
     if (h->has_A) {
         RAC_ST(h->alloc(&h->rbuf, m));
@@ -565,21 +549,24 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     }
     // the scale of the KKT measure: max(1, ||grad at 0||_inf)
     {
-        std::vector<double> g0(n);
+        // gradient at z = 0 and its statistics, read back after the final sync
+        h->ss->h_aux[0] = h->ss->h_aux[1] = 0.0;
+        const double *g0 = nullptr;
         if (h->has_A) {
             RAC_CK(cudaMemsetAsync(h->z, 0, n * sizeof(double), st));
             h->nlaunch += 3;
             RAC_CK(launch_resid_f64(m, n, h->A64, m, h->z, h->b64, h->rbuf, h->rpart, h->nchunk, st));
             RAC_CK(launch_gemvt_f64(m, n, h->A64, m, h->rbuf, h->c64, h->gz, st));
-            RAC_CK(cudaMemcpyAsync(g0.data(), h->gz, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+            g0 = h->gz;
         } else if (h->c64) {
-            RAC_CK(cudaMemcpyAsync(g0.data(), h->c64, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+            g0 = h->c64;
         }
-        RAC_CK(cudaStreamSynchronize(st));
-        double mx = 0.0;
-        for (double v : g0) mx = std::max(mx, std::fabs(v));
-        h->kkt_scale = std::max(1.0, mx);
-        h->kkt_cold0 = kkt_at_zero(h, g0);
+        if (g0) {
+            h->nlaunch += 1;
+            RAC_CK(launch_kkt_zero(n, g0, h->phi, h->lam1, h->lo, h->hi, h->kpart, st));
+            RAC_CK(cudaMemcpyAsync(h->ss->h_aux, h->kpart, 2 * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+        }
         if (o->gamma < 0) {
             // curvature-scaled split penalty |gamma| * trace(H) / n
             double tr = 0.0;
@@ -694,6 +681,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
                   h->cluster ? (h->cluster == 16 ? "/cluster16" : "/cluster8") : "");
     RAC_ST(set_state(h, o->x0, o->xi0));
     RAC_CK(cudaStreamSynchronize(st));
+    h->kkt_scale = std::max(1.0, h->ss->h_aux[0]);
+    h->kkt_cold0 = h->ss->h_aux[1] / h->kkt_scale;
     h->setup_launches = h->nlaunch;
     return RAC_OK;
 }

@@ -208,7 +208,10 @@ cudaError_t launch_gram_build_mma(int store, int m, int n, const double *A, int6
     const int mp = (m + KC - 1) / KC * KC, np = (n + GT - 1) / GT * GT;
     const size_t es = store == ST_BF16 ? 2 : 4;
     void *Ac = nullptr;
-    cudaError_t e = cudaMallocAsync(&Ac, (size_t)mp * np * es, st);
+    cudaMemPool_t pool = nullptr;   // the device's cached pool: no driver call per build
+    cudaError_t e = runtime_pool(&pool);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocFromPoolAsync(&Ac, (size_t)mp * np * es, pool, st);
     if (e != cudaSuccess) return e;
     const int64_t tot = (int64_t)mp * np;
     const unsigned cb = (unsigned)((tot + 255) / 256);

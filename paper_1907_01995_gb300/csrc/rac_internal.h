@@ -38,6 +38,7 @@ struct StreamSet {
     std::vector<cudaEvent_t> pev;   // timing
     DevStats *h_stats = nullptr;
     int *h_err = nullptr;
+    double *h_aux = nullptr;        // 4 pinned words for small setup results
 };
 // the current device's memory pool (freed memory stays cached for reuse)
 cudaError_t runtime_pool(cudaMemPool_t *pool);
@@ -137,6 +138,10 @@ int big_chain_max_grid(int store);
 // usable for this problem (0: not applicable), and its launch
 int cluster_chain_size(int store, int n, int smax);
 cudaError_t launch_cluster_chain(int store, const ChainArgs &a, int C, cudaStream_t st);
+
+// setup: out[0] = max_j |g0_j|, out[1] = max_j (stationarity of z = 0), one CTA
+cudaError_t launch_kkt_zero(int n, const double *g0, int phi, double lam1, double lo, double hi,
+                            double *out, cudaStream_t st);
 
 // exact FP64 pieces of the refresh
 // column chunks the residual needs at least (nchunk >= this)

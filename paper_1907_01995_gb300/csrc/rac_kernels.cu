@@ -1512,6 +1512,34 @@ cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z
 }
 int kkt_part_doubles() { return 6 * kKktParts; }
 
+// Statistics of the gradient at z = 0 for setup: the KKT scale max|g0| and
+// the unscaled stationarity of z = 0 (the cold start a warm start must beat).
+__global__ void __launch_bounds__(1024) k_kkt_zero(int n, const double *g0, int phi, double lam1,
+                                                   double lo, double hi, double *out) {
+    __shared__ double red[32];
+    double mx = 0.0, cold = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double v = g0[j];
+        mx = fmax(mx, fabs(v));
+        double s;
+        if (phi == RAC_PHI_L1L2) s = fmax(fabs(v) - lam1, 0.0);
+        else if (phi == RAC_PHI_BOX) s = (0.0 <= lo) ? fmax(-v, 0.0) : ((0.0 >= hi) ? fmax(v, 0.0) : fabs(v));
+        else s = fabs(v);
+        cold = fmax(cold, s);
+    }
+    mx = block_max<double>(mx, red);
+    cold = block_max<double>(cold, red);
+    if (threadIdx.x == 0) {
+        out[0] = mx;
+        out[1] = cold;
+    }
+}
+cudaError_t launch_kkt_zero(int n, const double *g0, int phi, double lam1, double lo, double hi,
+                            double *out, cudaStream_t st) {
+    k_kkt_zero<<<1, 1024, 0, st>>>(n, g0, phi, lam1, lo, hi, out);
+    return cudaGetLastError();
+}
+
 // Anchor reset, Gram form: g = gz + G~ (x - z), one warp per row.
 // (The FP32/BF16 forms take x - z, formed once in FP64 and rounded, from
 // dxz: an FP64 subtraction per matrix element would bind this part's FP64

@@ -85,6 +85,7 @@ cudaError_t runtime_take_streams(StreamSet **out, size_t nfev, size_t npev) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ss->ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(&ss->h_stats, sizeof(DevStats));
         if (e == cudaSuccess) e = cudaMallocHost(&ss->h_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMallocHost(&ss->h_aux, 4 * sizeof(double));
         if (e != cudaSuccess) {
             runtime_give_streams(ss);   // keeps what was made for a later handle
             return e;
@@ -102,7 +103,7 @@ cudaError_t runtime_take_streams(StreamSet **out, size_t nfev, size_t npev) {
 
 void runtime_give_streams(StreamSet *ss) {
     if (!ss) return;
-    if (!ss->st || !ss->ev || !ss->h_stats || !ss->h_err) {
+    if (!ss->st || !ss->ev || !ss->h_stats || !ss->h_err || !ss->h_aux) {
         // incomplete set (creation failed part-way): release what it holds
         for (auto q : ss->sfs)
             if (q) cudaStreamDestroy(q);
@@ -112,6 +113,7 @@ void runtime_give_streams(StreamSet *ss) {
         for (auto e : ss->pev) cudaEventDestroy(e);
         if (ss->h_stats) cudaFreeHost(ss->h_stats);
         if (ss->h_err) cudaFreeHost(ss->h_err);
+        if (ss->h_aux) cudaFreeHost(ss->h_aux);
         delete ss;
         return;
     }

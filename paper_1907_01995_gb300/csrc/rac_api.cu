@@ -597,7 +597,10 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
                 RAC_CK(launch_gram_build(h->store, m, n, h->A64, m, h->G, st));
             } else {
                 h->nlaunch += 1;  // conversion + tensor-core tiles
-                RAC_CK(launch_gram_build_mma(h->store, m, n, h->A64, m, h->G, st));
+                if (h->store == ST_BF16)
+                    RAC_CK(launch_gram_build_tc(m, n, h->A64, m, h->G, h->err, st));
+                else
+                    RAC_CK(launch_gram_build_mma(h->store, m, n, h->A64, m, h->G, st));
             }
         } else {
             RAC_CK(launch_sym_convert(h->store, n, h->H64, h->G, st));

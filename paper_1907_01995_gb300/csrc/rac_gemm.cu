@@ -8,9 +8,19 @@
 // which keeps FP32-level accuracy.  A is first converted once into a
 // column-major copy padded to the tile sizes, then each CTA computes one
 // 128 x 128 tile of the lower triangle and mirrors it.
+//
+// BF16 storage runs on the 5th-generation tensor cores (k_gram_tc): TMA
+// loads 128 x 64 K-major tiles with the 128-byte swizzle into a 4-stage ring,
+// one thread issues tcgen05.mma (M = N = 128, K = 16, FP32 accumulator in
+// tensor memory), and the tile is read back with tcgen05.ld.  FP32 storage
+// (three-term TF32) keeps the mma.sync kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "rac_device.cuh"
 #include "rac_internal.h"
@@ -234,6 +244,259 @@ cudaError_t launch_gram_build_mma(int store, int m, int n, const double *A, int6
     return e;
 }
 
+// ======================================================================
+// tcgen05 Gram (BF16 storage)
+// ======================================================================
+constexpr int TC_T = 128;                         // output tile (M = N)
+constexpr int TC_K = 64;                          // K per stage: one 128-byte swizzle row of bf16
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_TILE_BYTES = TC_T * TC_K * 2;          // 16 KB
+constexpr int TC_LD = TC_T + 8;                   // staged output row (bf16), padded
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * 2 * TC_TILE_BYTES + 1024;
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: 8-row groups of 1 KB (stride byte offset 1024), leading
+// byte offset unused for this layout, descriptor version 1, swizzle mode 2.
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+// Instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One CTA per 128 x 128 tile (ti, tj), tj <= ti, of G = Ac^T Ac.  Warp 0
+// lane 0 produces the TMA stages, warp 1 lane 0 issues the MMAs, all four
+// warps run the epilogue (warp w owns accumulator lanes 32w .. 32w + 31).
+// Every wait is bounded (kBarrierTimeoutNs): on expiry the error flag is set
+// and the CTA finishes the tile with whatever it holds.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap tmap, int n, int nkb, __nv_bfloat16 *G,
+              int *err) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *ring = (unsigned char *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    __shared__ uint32_t tmem_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // lower-triangle tile index -> (ti, tj)
+    const int t = blockIdx.x;
+    int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TC_T)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        mbar_init_fence();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    auto stageA = [&](int s) { return ring + (size_t)s * 2 * TC_TILE_BYTES; };
+    auto stageB = [&](int s) { return ring + (size_t)s * 2 * TC_TILE_BYTES + TC_TILE_BYTES; };
+    if (warp == 0) {
+        if (lane == 0) {   // producer
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % TC_STAGES;
+                const uint32_t it = (uint32_t)(kb / TC_STAGES);
+                if (kb >= TC_STAGES && !mbar_wait(&empty[s], (it - 1) & 1u, err, kBarrierTimeoutNs))
+                    break;
+                mbar_expect_tx(&full[s], 2 * TC_TILE_BYTES);
+                tma_load_2d(stageA(s), &tmap, kb * TC_K, ti * TC_T, &full[s]);
+                tma_load_2d(stageB(s), &tmap, kb * TC_K, tj * TC_T, &full[s]);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = tc_idesc(TC_T, TC_T);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % TC_STAGES;
+                if (!mbar_wait(&full[s], (uint32_t)(kb / TC_STAGES) & 1u, err, kBarrierTimeoutNs))
+                    break;
+                tc_fence_after();
+                const uint64_t ad = tc_desc_sw128(smem_u32(stageA(s)));
+                const uint64_t bd = tc_desc_sw128(smem_u32(stageB(s)));
+#pragma unroll
+                for (int k = 0; k < TC_K / 16; ++k) {
+                    const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                    // K advances 16 bf16 = 32 bytes inside the swizzle row: +2 in address units
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad + 2u * k), "l"(bd + 2u * k), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&empty[s]))
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&done))
+                : "memory");
+        }
+        __syncwarp();
+    }
+    // epilogue: accumulator -> bf16 tile in shared memory (the ring is free once
+    // every MMA has completed) -> coalesced stores of the tile and its mirror
+    mbar_wait(&done, 0u, err, kBarrierTimeoutNs);
+    tc_fence_after();
+    __nv_bfloat16 *tile = (__nv_bfloat16 *)ring;
+    const int r = 32 * warp + lane;
+#pragma unroll 1
+    for (int c = 0; c < TC_T / 32; ++c) {
+        uint32_t v[32];
+        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);
+#pragma unroll
+        for (int k = 0; k < 32; k += 2) {
+            const __nv_bfloat162 h =
+                __floats2bfloat162_rn(__uint_as_float(v[k]), __uint_as_float(v[k + 1]));
+            *reinterpret_cast<__nv_bfloat162 *>(tile + r * TC_LD + 32 * c + k) = h;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    const int i0 = ti * TC_T, j0 = tj * TC_T;
+    const bool pairs = (n & 1) == 0;
+    for (int idx = threadIdx.x; idx < TC_T * (TC_T / 2); idx += TC_THREADS) {
+        const int rr = idx / (TC_T / 2), cp = idx - rr * (TC_T / 2);
+        const int i = i0 + rr, j = j0 + 2 * cp;
+        if (i >= n || j >= n) continue;
+        const __nv_bfloat16 *src = tile + rr * TC_LD + 2 * cp;
+        if (pairs) {
+            *reinterpret_cast<__nv_bfloat162 *>(G + (size_t)i * n + j) =
+                *reinterpret_cast<const __nv_bfloat162 *>(src);
+        } else {
+            G[(size_t)i * n + j] = src[0];
+            if (j + 1 < n) G[(size_t)i * n + j + 1] = src[1];
+        }
+    }
+    if (ti != tj) {   // mirror: G[j][i] = tile[i][j]
+        for (int idx = threadIdx.x; idx < TC_T * (TC_T / 2); idx += TC_THREADS) {
+            const int cc = idx / (TC_T / 2), rp = idx - cc * (TC_T / 2);
+            const int j = j0 + cc, i = i0 + 2 * rp;
+            if (j >= n || i >= n) continue;
+            const __nv_bfloat16 a = tile[(2 * rp) * TC_LD + cc];
+            const __nv_bfloat16 b = tile[(2 * rp + 1) * TC_LD + cc];
+            if (pairs) {
+                __nv_bfloat162 h;
+                h.x = a;
+                h.y = b;
+                *reinterpret_cast<__nv_bfloat162 *>(G + (size_t)j * n + i) = h;
+            } else {
+                G[(size_t)j * n + i] = a;
+                if (i + 1 < n) G[(size_t)j * n + i + 1] = b;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TC_T)
+                     : "memory");
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+cudaError_t launch_gram_build_tc(int m, int n, const double *A, int64_t lda, void *G, int *err,
+                                 cudaStream_t st) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    const int mp = (m + TC_K - 1) / TC_K * TC_K, np = (n + TC_T - 1) / TC_T * TC_T;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = runtime_pool(&pool);
+    if (e != cudaSuccess) return e;
+    void *Ac = nullptr;
+    e = cudaMallocFromPoolAsync(&Ac, (size_t)mp * np * 2, pool, st);
+    if (e != cudaSuccess) return e;
+    const int64_t tot = (int64_t)mp * np;
+    k_pad_convert<__nv_bfloat16><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+        m, n, mp, np, A, lda, (__nv_bfloat16 *)Ac);
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)mp, (cuuint64_t)np};
+    const cuuint64_t strides[1] = {(cuuint64_t)mp * 2};
+    const cuuint32_t box[2] = {TC_K, TC_T};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Ac, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        cudaFreeAsync(Ac, st);
+        return cudaErrorInvalidValue;
+    }
+    e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    if (e == cudaSuccess) {
+        const int nt = np / TC_T;
+        k_gram_tc<<<nt * (nt + 1) / 2, TC_THREADS, TC_SMEM, st>>>(map, n, mp / TC_K,
+                                                                (__nv_bfloat16 *)G, err);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(Ac, st);
+    return e;
+}
+
 }  // namespace rac
 
 using namespace rac;
@@ -245,12 +508,29 @@ extern "C" rac_status rac_gram(int64_t m, int64_t n, const double *A, int64_t ld
         return RAC_ERR_ARG;
     (void)cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = storage == RAC_FP64
-                        ? launch_gram_build(ST_F64, (int)m, (int)n, A, lda, G_out, st)
-                        : launch_gram_build_mma(storage, (int)m, (int)n, A, lda, G_out, st);
+    cudaError_t e;
+    int *err = nullptr;
+    if (storage == RAC_BF16) {
+        cudaMemPool_t pool = nullptr;
+        e = runtime_pool(&pool);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void **)&err, sizeof(int), pool, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = launch_gram_build_tc((int)m, (int)n, A, lda, G_out, err, st);
+    } else {
+        e = storage == RAC_FP64 ? launch_gram_build(ST_F64, (int)m, (int)n, A, lda, G_out, st)
+                                : launch_gram_build_mma(storage, (int)m, (int)n, A, lda, G_out, st);
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
+        if (err) cudaFreeAsync(err, st);
         return e == cudaErrorMemoryAllocation ? RAC_ERR_OOM : RAC_ERR_CUDA;
     }
-    return cudaStreamSynchronize(st) == cudaSuccess ? RAC_OK : RAC_ERR_CUDA;
+    int herr = 0;
+    if (err) {
+        if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            herr = RAC_ERR_CUDA;
+        cudaFreeAsync(err, st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RAC_ERR_CUDA;
+    return herr ? (rac_status)herr : RAC_OK;
 }

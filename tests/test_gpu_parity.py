@@ -241,15 +241,15 @@ def test_device_inputs_and_outputs():
     assert np.array_equal(out.cpu().numpy(), z)
 
 
-@pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16"])
-def test_gram_build_matches_fp64(storage):
+@pytest.mark.parametrize("storage,m,n", [("fp64", 333, 301), ("fp32", 333, 301),
+                                         ("bf16", 333, 301), ("bf16", 1000, 520)])
+def test_gram_build_matches_fp64(storage, m, n):
     """G~ = A~^T A~ (rac_gram) on ragged sizes against the FP64 Gram matrix of
     the storage-rounded A: FP64 to 1e-12; FP32 (three-term TF32 split, FP32
     tensor-core accumulation, whose additions are not round-to-nearest) within
     the worst-case bound of a length-m FP32 reduction, m 2^-23 max|G|; BF16
     (stored as BF16) to one BF16 rounding of each entry."""
     rng = np.random.default_rng(7)
-    m, n = 333, 301
     A = np.asfortranarray(rng.normal(size=(m, n)))
     At = torch.tensor(A, device="cuda").t().contiguous().t()
     dt = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}[storage]

@@ -4,30 +4,34 @@
 // The block chain (the cyclic pass over the blocks S_1 .. S_p of a sweep,
 // Sec. 2) is a sequence of small dependent steps; on this form each step is a
 // K_S^{-1} product of a few hundred thousand flops plus the gradient update
-// g += G[:, S_i] dx_i.  Its cost is latency, and a grid-wide barrier through
-// global memory per step dominates it.  Here the whole chain runs on C CTAs
-// of one cluster (C = 16, else 8), synchronised by the hardware cluster
-// barrier and exchanging data through distributed shared memory:
+// g += G[:, S_i] dx_i.  Its cost is latency.  Here the whole chain runs on C
+// CTAs of one cluster (C = 16, else 8) that exchange data through distributed
+// shared memory:
 //   * CTA c owns the gradient columns [c ncp, (c + 1) ncp) in shared memory;
-//   * step i: every CTA computes a slice of the rows of
-//         dx_i = -K_i^{-1} rhs'_i - P_i dx_{i-1}
-//     (the lookahead form: rhs'_i holds the gradient as it stood before step
-//     i-1, P_i = K_i^{-1} G[S_i, S_{i-1}]) and stores it into every CTA's
-//     copy of dx_i; one cluster barrier; every CTA then adds G[own, S_i] dx_i
-//     to its columns, parking the increments of S_i (gdef) and S_{i+1}
-//     (gnext) as the grid-barrier chain does;
-//   * a column's value is final for rhs'_{i+2} once step i has updated it,
-//     so its owner pushes it into every CTA's rhs buffer of block i+2 right
-//     away: the gather leaves the critical path;
-//   * what step i+1 reads from global memory (its rows of K^{-1} and P, the
+//   * the lookahead form dx_i = -K_i^{-1} rhs'_i - P_i dx_{i-1} (rhs'_i holds
+//     the gradient as it stood before step i-1, P_i = K_i^{-1} G[S_i, S_{i-1}])
+//     makes dx_{i+1} independent of step i's gradient update, so each CTA
+//     runs two warp groups that overlap:
+//       - the solve warps compute this CTA's rows of dx_i, store them into
+//         every CTA's copy, and arrive on every CTA's "dx ready" mbarrier;
+//       - the update warps wait for dx_i, add G[own, S_i] dx_i to their
+//         columns (parking the increments of S_i in gdef and of S_{i+1} in
+//         gnext, as the grid-barrier chain does), push each value that is now
+//         final for rhs'_{i+2} into every CTA's rhs buffer, and arrive on
+//         every CTA's "gradient ready" mbarrier of block i+2;
+//     the solve warps wait for that barrier two steps later, so the update
+//     stays off the critical path;
+//   * what a step reads from global memory (its rows of K^{-1} and P, the
 //     static rhs parts, and G[S_{i+1}, own columns]) is loaded into registers
-//     during step i, right after the current values are consumed, so the L2
-//     latency overlaps the rest of the step.  (Staging through shared memory
-//     was slower: per-thread async copies in flight throttle the step's
-//     shared-memory loads, and many small bulk copies queue at the copy
-//     engine.)
-// The cluster barrier is a hardware barrier of co-scheduled CTAs and every
-// CTA executes the same sequence of barriers: there is no spin-wait.
+//     a step ahead, so the L2 latency overlaps the step.  (Staging through
+//     shared memory was slower: per-thread async copies in flight throttle
+//     the step's shared-memory loads, and many small bulk copies queue at the
+//     copy engine.)
+// Buffer reuse is ordered by the two barriers: a CTA overwrites a dx copy or
+// a rhs buffer only after a barrier phase that every reader of the previous
+// contents had to arrive at.  Every wait is an mbarrier wait bounded in time
+// (on expiry the error flag is set and the CTA carries on, so arrival counts
+// stay matched); the cluster barrier is used only at entry and exit.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cooperative_groups.h>
@@ -40,14 +44,15 @@ namespace cg = cooperative_groups;
 
 namespace rac {
 
-constexpr int kClThreads = 256;
-constexpr int kClWarps = kClThreads / 32;
+constexpr int kClSolveWarps = 4;                 // warps 0..3: the rows of dx_i
+constexpr int kClWarps = 8;                      // warps 4..11: the gradient update
+constexpr int kClThreads = 32 * (kClSolveWarps + kClWarps);
 constexpr int kClSmax = 128;     // block size limit (a lane holds 4 of <= 128 columns)
-constexpr int kClRows = kClSmax / kClWarps;   // G rows per warp and step (q = w + 8 j)
+constexpr int kClRows = kClSmax / kClWarps;   // G rows per update warp and step (q = w + 8 j)
 
 // Shared-memory layout (offsets in bytes, each 16-byte aligned).
 struct ClLayout {
-    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, total;
+    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, bars, total;
     int ncp, rmax;
     __host__ __device__ ClLayout(int n, int smax, int C) {
         // columns per CTA: 64 NK with NK in {1, 2, 4} (the kernel's template
@@ -70,6 +75,7 @@ struct ClLayout {
         dbuf = take(2 * (size_t)kClSmax * 4);
         rhs = take((size_t)kClSmax * 4);
         red = take((size_t)kClWarps * ncp * 4);
+        bars = take(4 * 8);
         total = o;
     }
 };
@@ -104,8 +110,50 @@ template <class TS, int NK> struct GVec {
     }
 };
 
-// rows of the chain matrices per warp: rmax <= 2 * warps (C >= 8, s <= 128)
-constexpr int kClRowSlots = 2;
+// rows of dx_i per solve warp and step: rmax <= 16 (C >= 8, s <= 128)
+constexpr int kClRowSlots = 4;
+
+// cluster-scope mbarrier wait: acquire, bounded in time
+__device__ __forceinline__ bool mbar_test_cluster(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_wait_cluster(uint64_t *bar, uint32_t parity, int *err) {
+    if (mbar_test_cluster(bar, parity)) return;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_test_cluster(bar, parity)) {
+        if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+            set_err(err, RAC_ERR_TIMEOUT);
+            return;
+        }
+    }
+}
+// asynchronous remote stores that complete on the destination CTA's mbarrier
+// (tx bytes): the data and its signal travel together, with no fence
+__device__ __forceinline__ uint32_t cluster_addr(const void *local, int rank) {
+    uint32_t raddr;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(smem_u32(local)), "r"(rank));
+    return raddr;
+}
+__device__ __forceinline__ void st_async_f32(uint32_t raddr, float v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr),
+                 "r"(__float_as_uint(v)), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async_f64(uint32_t raddr, double v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(raddr),
+                 "l"(__double_as_longlong(v)), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 template <class TS, int NK>
 __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
@@ -124,7 +172,9 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     double *rhsg = (double *)(sm + L.rhsg);      // [2][kClSmax]: pushed gradient values
     float *dbuf = (float *)(sm + L.dbuf);        // [2][kClSmax]: dx_i, dx_{i-1}
     float *rhs = (float *)(sm + L.rhs);
-    float *red = (float *)(sm + L.red);          // [warps][ncp]
+    float *red = (float *)(sm + L.red);          // [update warps][ncp]
+    uint64_t *bars = (uint64_t *)(sm + L.bars);  // dx ready [2], gradient ready [2]
+    uint64_t *dready = bars, *gready = bars + 2;
     __shared__ double dred[64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TS *G = (const TS *)a.G;
@@ -132,9 +182,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     const float *Pall = (const float *)a.P;
     const size_t kst = BlockLayout::pad4((size_t)smax * smax);
     const double beta = a.beta, mu = a.mu ? *a.mu : 0.0;
-    double t = a.e ? *a.t : 0.0;
 
-    // ---- per-sweep ownership tables and initial state
+    // ---- per-sweep ownership tables, initial state, barriers
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
         const int j = a.perm[q];
         perm[q] = j;
@@ -149,157 +198,224 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
         gown[cc] = cc < ncl ? a.g[c0 + cc] : 0.0;
         if (cc >= ncl) bown[cc] = -1;
     }
+    // zeros past each block's size: the solve warps read whole float4 groups
+    for (int q = threadIdx.x; q < 2 * kClSmax; q += blockDim.x) dbuf[q] = 0.f;
+    for (int q = threadIdx.x; q < kClSmax; q += blockDim.x) rhs[q] = 0.f;
     // rhs'_0 and rhs'_1: the gradient at the start of the sweep
     for (int k = 0; k < 2 && k < p; ++k) {
         const int sb = lay.size(k), ob = lay.offset(k);
         for (int q = threadIdx.x; q < sb; q += blockDim.x) rhsg[k * kClSmax + q] = a.g[a.perm[ob + q]];
     }
+    // Each barrier phase has one local arrival, which also arms the bytes the
+    // phase waits for: s_i * 4 of dx_i (dready[i & 1]), s_b * 8 of block b's
+    // pushed gradient values (gready[b & 1], b >= 2).  A phase is armed only
+    // after its previous phase completed here, and before any CTA can send
+    // its data (see the kernel comment).
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) mbar_init(&bars[k], 1);
+        mbar_init_fence();
+        for (int k = 0; k < 2 && k < p; ++k) mbar_expect_tx(&dready[k], 4u * lay.size(k));
+        for (int b = 2; b < 4 && b < p; ++b) mbar_expect_tx(&gready[b & 1], 8u * lay.size(b));
+    }
     __syncthreads();
+    cl.sync();   // every CTA is initialised and armed before remote stores arrive
 
-    // ---- register prefetch of block b
-    // K / P: warp w holds rows r0 + w + 8 u (u < 2) of this CTA's slice,
-    // lane l columns 4l..4l+3 of each
-    float kv[kClRowSlots][4], pv[kClRowSlots][4];
-    double spv = 0.0, epv = 0.0;                  // static rhs of entry q = threadIdx.x
-    using GV = GVec<TS, NK>;
-    unsigned gv[kClRows][GV::WORDS];              // G[S_b[w + 8 j], c0 + VEC l .. + VEC - 1]
-    auto fetch_kp = [&](int b) {
-        if (b >= p) return;
-        const int sb = lay.size(b), ob = lay.offset(b);
-        const int sp = b > 0 ? lay.size(b - 1) : 0;
-        const int r0 = c * rmax, nr = max(0, min(rmax, sb - r0));
-        const float *Kb = Wall + lay.factor_offset(b);
-        const float *Pb = Pall + (size_t)b * kst;
-#pragma unroll
-        for (int u = 0; u < kClRowSlots; ++u) {
-            const int r = warp + kClWarps * u;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int col = 4 * lane + v;
-                kv[u][v] = (r < nr && col < sb) ? __ldcg(Kb + (size_t)(r0 + r) * sb + col) : 0.f;
-                pv[u][v] = (r < nr && col < sp) ? __ldcg(Pb + (size_t)(r0 + r) * sp + col) : 0.f;
-            }
-        }
-        if ((int)threadIdx.x < sb) {
-            spv = __ldcg(a.sperm + ob + threadIdx.x);
-            if (a.e) epv = __ldcg(a.eperm + ob + threadIdx.x);
-        }
-    };
-    auto fetch_g = [&](int b) {
-        if (b >= p) return;
-        const int sb = lay.size(b), ob = lay.offset(b);
-        const int col = c0 + GV::VEC * lane;    // n % VEC == 0: the vector is all in or out
-#pragma unroll
-        for (int j = 0; j < kClRows; ++j) {
-            const int q = warp + kClWarps * j;
-            if (q < sb && col < n) {
-                GV::ld(G + (size_t)perm[ob + q] * n + col, gv[j]);
-            } else {
-#pragma unroll
-                for (int w = 0; w < GV::WORDS; ++w) gv[j][w] = 0u;
-            }
-        }
-    };
-    fetch_kp(0);
-    fetch_g(0);
-    cl.sync();   // every CTA is initialised before remote stores arrive
-
-    for (int i = 0; i < p; ++i) {
-        const int s = lay.size(i), off = lay.offset(i);
-        // rhs'_i
-        if ((int)threadIdx.x < s) {
-            double r = rhsg[(i & 1) * kClSmax + threadIdx.x] + spv;
-            if (a.e) r += epv * (beta * t - mu);
-            rhs[threadIdx.x] = (float)r;
-        }
-        const double ep_i = epv;                  // e of entry threadIdx.x of block i
-        __syncthreads();
-        // this CTA's rows of dx_i: warp per row, lane per 4 columns
-        {
-            const int r0 = c * rmax, nr = max(0, min(rmax, s - r0));
-            const float *dprev = dbuf + ((i - 1) & 1) * kClSmax;
-            const int sp = i > 0 ? lay.size(i - 1) : 0;
-            float dsum[kClRowSlots] = {0.f, 0.f};
+    if (warp < kClSolveWarps) {
+        // ================= solve warps: this CTA's rows of dx_i =================
+        const int tid = threadIdx.x;                  // 0 .. 127
+        // the rows of K^{-1} / P and the static rhs parts of one block; two
+        // register sets alternate so that block i+1's loads are issued before
+        // step i waits
+        struct KP {
+            float kv[kClRowSlots][4], pv[kClRowSlots][4];
+            double sp, ep;
+        };
+        auto fetch_kp = [&](int b, KP &d) {
+            if (b >= p) return;
+            const int sb = lay.size(b), ob = lay.offset(b);
+            const int sp = b > 0 ? lay.size(b - 1) : 0;
+            const int r0 = c * rmax, nr = max(0, min(rmax, sb - r0));
+            const float *Kb = Wall + lay.factor_offset(b);
+            const float *Pb = Pall + (size_t)b * kst;
 #pragma unroll
             for (int u = 0; u < kClRowSlots; ++u) {
-                if (kClWarps * u >= rmax) break;   // uniform: no rows in this slot
-                float acc = 0.f;
+                if (kClSolveWarps * u >= rmax) break;   // uniform: no rows in this slot
+                const int r = warp + kClSolveWarps * u;
+                const int col = 4 * lane;
+                // rows start 16-byte aligned when the row length is a multiple of 4
+                if (r < nr && col + 4 <= sb && (sb & 3) == 0) {
+                    const float4 k4 = __ldcg(reinterpret_cast<const float4 *>(Kb + (size_t)(r0 + r) * sb + col));
+                    d.kv[u][0] = k4.x; d.kv[u][1] = k4.y; d.kv[u][2] = k4.z; d.kv[u][3] = k4.w;
+                } else {
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int col = 4 * lane + v;
-                    if (col < s) acc = fmaf(kv[u][v], rhs[col], acc);
-                    if (col < sp) acc = fmaf(pv[u][v], dprev[col], acc);
+                    for (int v = 0; v < 4; ++v)
+                        d.kv[u][v] = (r < nr && col + v < sb) ? __ldcg(Kb + (size_t)(r0 + r) * sb + col + v) : 0.f;
+                }
+                if (r < nr && col + 4 <= sp && (sp & 3) == 0) {
+                    const float4 p4 = __ldcg(reinterpret_cast<const float4 *>(Pb + (size_t)(r0 + r) * sp + col));
+                    d.pv[u][0] = p4.x; d.pv[u][1] = p4.y; d.pv[u][2] = p4.z; d.pv[u][3] = p4.w;
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        d.pv[u][v] = (r < nr && col + v < sp) ? __ldcg(Pb + (size_t)(r0 + r) * sp + col + v) : 0.f;
+                }
+            }
+            d.sp = tid < sb ? __ldcg(a.sperm + ob + tid) : 0.0;
+            d.ep = (a.e && tid < sb) ? __ldcg(a.eperm + ob + tid) : 0.0;
+        };
+        // this lane's destination in CTA `lane` (lanes < C): its dx copies and barriers
+        const uint32_t rd_dbuf = lane < C ? cluster_addr(dbuf, lane) : 0u;
+        const uint32_t rd_bar = lane < C ? cluster_addr(dready, lane) : 0u;
+        double t = a.e ? *a.t : 0.0;
+        double ep_prev = 0.0;                         // e of entry tid of block i-1
+        auto t_update = [&](int b) {   // t += e_{S_b}^T dx_b, the same order in every CTA
+            const int sq = lay.size(b);
+            const double loc = tid < sq ? ep_prev * (double)dbuf[(b & 1) * kClSmax + tid] : 0.0;
+            const double v = warp_sum(loc);
+            if (lane == 0) dred[warp] = v;
+            group_sync(1, 32 * kClSolveWarps);
+            double tot = 0.0;
+            for (int w = 0; w < kClSolveWarps; ++w) tot += dred[w];
+            t += tot;
+            group_sync(1, 32 * kClSolveWarps);
+        };
+        auto step = [&](int i, KP &cur, KP &nxt) {
+            const int s = lay.size(i), off = lay.offset(i);
+            fetch_kp(i + 1, nxt);
+            if (i >= 1) {
+                mbar_wait_cluster(&dready[(i - 1) & 1], (uint32_t)((i - 1) >> 1) & 1u, a.err);
+                if (a.e) t_update(i - 1);
+            }
+            if (i >= 2)   // the gradient values of block i, pushed during step i-2
+                mbar_wait_cluster(&gready[i & 1], (uint32_t)((i >> 1) - 1) & 1u, a.err);
+            if (i >= 2 && tid == 0 && i + 2 < p)   // arm the next phase: block i+2
+                mbar_expect_tx(&gready[i & 1], 8u * lay.size(i + 2));
+            if (tid < s) {
+                double r = rhsg[(i & 1) * kClSmax + tid] + cur.sp;
+                if (a.e) r += cur.ep * (beta * t - mu);
+                rhs[tid] = (float)r;
+            }
+            ep_prev = cur.ep;
+            group_sync(1, 32 * kClSolveWarps);
+            const int r0 = c * rmax, nr = max(0, min(rmax, s - r0));
+            // rhs and the dx copies hold zeros past each block's size, and K / P
+            // rows are zero there too
+            const float4 rh = *reinterpret_cast<const float4 *>(rhs + 4 * lane);
+            const float4 dp = *reinterpret_cast<const float4 *>(dbuf + ((i - 1) & 1) * kClSmax + 4 * lane);
+            float dsum[kClRowSlots];
+#pragma unroll
+            for (int u = 0; u < kClRowSlots; ++u) {
+                dsum[u] = 0.f;
+                if (kClSolveWarps * u >= rmax) continue;   // uniform: no rows in this slot
+                float acc = cur.kv[u][0] * rh.x;
+                acc = fmaf(cur.kv[u][1], rh.y, acc);
+                acc = fmaf(cur.kv[u][2], rh.z, acc);
+                acc = fmaf(cur.kv[u][3], rh.w, acc);
+                if (i > 0) {
+                    acc = fmaf(cur.pv[u][0], dp.x, acc);
+                    acc = fmaf(cur.pv[u][1], dp.y, acc);
+                    acc = fmaf(cur.pv[u][2], dp.z, acc);
+                    acc = fmaf(cur.pv[u][3], dp.w, acc);
                 }
                 dsum[u] = warp_sum(acc);
             }
 #pragma unroll
             for (int u = 0; u < kClRowSlots; ++u) {
-                const int r = warp + kClWarps * u;
+                const int r = warp + kClSolveWarps * u;
                 if (r < nr) {
                     const float d = -dsum[u];
-                    if (lane < C) {   // lane k stores into CTA k's copy of dx_i
-                        float *dst = cl.map_shared_rank(dbuf + (i & 1) * kClSmax, lane);
-                        dst[r0 + r] = d;
-                    }
+                    if (lane < C)   // lane k stores into CTA k's copy of dx_i
+                        st_async_f32(rd_dbuf + 4u * ((i & 1) * kClSmax + r0 + r), d, rd_bar + 8u * (i & 1));
                     if (lane == 0) a.dx[perm[off + r0 + r]] = (double)d;
                 }
             }
+            group_sync(1, 32 * kClSolveWarps);   // rhs is rewritten next step
+        };
+        KP bufA, bufB;
+        fetch_kp(0, bufA);
+        for (int i = 0; i < p; i += 2) {
+            step(i, bufA, bufB);
+            if (i + 1 < p) step(i + 1, bufB, bufA);
         }
-        fetch_kp(i + 1);        // this step's rows are consumed
-        cl.sync();              // dx_i complete in every CTA
-        const float *dxi = dbuf + (i & 1) * kClSmax;
-        if (a.e) {
-            const double loc = (int)threadIdx.x < s ? ep_i * (double)dxi[threadIdx.x] : 0.0;
-            t += block_sum<double>(loc, dred);
+        if (a.e && p >= 1) {   // the last block's contribution to t
+            mbar_wait_cluster(&dready[(p - 1) & 1], (uint32_t)((p - 1) >> 1) & 1u, a.err);
+            t_update(p - 1);
+            if (c == 0 && tid == 0) *a.t = t;
         }
-        // G[own, S_i] dx_i from the prefetched registers: warp w rows
-        // q = w + 8 j, lane l the columns VEC l .. VEC l + VEC - 1
-        {
-            float acc[GV::VEC];
-#pragma unroll
-            for (int v = 0; v < GV::VEC; ++v) acc[v] = 0.f;
+    } else {
+        // ================= update warps: G[own, S_i] dx_i =================
+        const int uw = warp - kClSolveWarps, ut = threadIdx.x - 32 * kClSolveWarps;   // 0..7, 0..255
+        using GV = GVec<TS, NK>;
+        unsigned gv[kClRows][GV::WORDS];          // G[S_b[uw + 8 j], c0 + VEC l .. + VEC - 1]
+        auto fetch_g = [&](int b) {
+            if (b >= p) return;
+            const int sb = lay.size(b), ob = lay.offset(b);
+            const int col = c0 + GV::VEC * lane;   // n % VEC == 0: the vector is all in or out
 #pragma unroll
             for (int j = 0; j < kClRows; ++j) {
-                const int q = warp + kClWarps * j;
-                if (q < s) {
-                    const float dq = dxi[q];
+                const int q = uw + kClWarps * j;
+                if (q < sb && col < n) {
+                    GV::ld(G + (size_t)perm[ob + q] * n + col, gv[j]);
+                } else {
 #pragma unroll
-                    for (int v = 0; v < GV::VEC; ++v) acc[v] = fmaf(GV::at(gv[j], v), dq, acc[v]);
+                    for (int w = 0; w < GV::WORDS; ++w) gv[j][w] = 0u;
                 }
             }
-            float *rw = red + warp * ncp + GV::VEC * lane;
+        };
+        fetch_g(0);
+        for (int i = 0; i < p; ++i) {
+            const int s = lay.size(i);
+            mbar_wait_cluster(&dready[i & 1], (uint32_t)(i >> 1) & 1u, a.err);
+            if (ut == 0 && i + 2 < p)   // arm the next phase: dx_{i+2}
+                mbar_expect_tx(&dready[i & 1], 4u * lay.size(i + 2));
+            const float *dxi = dbuf + (i & 1) * kClSmax;
+            {
+                float acc[GV::VEC];
 #pragma unroll
-            for (int v = 0; v < GV::VEC; v += 2) *reinterpret_cast<float2 *>(rw + v) = make_float2(acc[v], acc[v + 1]);
-        }
-        fetch_g(i + 1);         // this step's G values are consumed
-        __syncthreads();
-        const bool push = i + 2 < p;
-        for (int cc = threadIdx.x; cc < ncl; cc += blockDim.x) {
-            float tot = 0.f;
+                for (int v = 0; v < GV::VEC; ++v) acc[v] = 0.f;
 #pragma unroll
-            for (int w = 0; w < kClWarps; ++w) tot += red[w * ncp + cc];
-            const int b = bown[cc], col = c0 + cc;
-            if (b == i) {
-                a.gdef[col] = (double)tot;
-            } else if (b == i + 1) {
-                a.gnext[col] = (double)tot;
-            } else {
-                const double gval = gown[cc] + (double)tot;
-                gown[cc] = gval;
-                if (push && b == i + 2) {   // final for rhs'_{i+2}: push to every CTA
-                    const int q = qown[cc];
-                    for (int k = 0; k < C; ++k) {
-                        double *dst = cl.map_shared_rank(rhsg + (i & 1) * kClSmax, k);
-                        dst[q] = gval;
+                for (int j = 0; j < kClRows; ++j) {
+                    const int q = uw + kClWarps * j;
+                    if (q < s) {
+                        const float dq = dxi[q];
+#pragma unroll
+                        for (int v = 0; v < GV::VEC; ++v) acc[v] = fmaf(GV::at(gv[j], v), dq, acc[v]);
+                    }
+                }
+                float *rw = red + uw * ncp + GV::VEC * lane;
+#pragma unroll
+                for (int v = 0; v < GV::VEC; v += 2)
+                    *reinterpret_cast<float2 *>(rw + v) = make_float2(acc[v], acc[v + 1]);
+            }
+            fetch_g(i + 1);        // this step's G values are consumed
+            group_sync(2, 32 * kClWarps);
+            const bool push = i + 2 < p;
+            for (int cc = ut; cc < ncl; cc += 32 * kClWarps) {
+                float tot = 0.f;
+#pragma unroll
+                for (int w = 0; w < kClWarps; ++w) tot += red[w * ncp + cc];
+                const int b = bown[cc], col = c0 + cc;
+                if (b == i) {
+                    a.gdef[col] = (double)tot;
+                } else if (b == i + 1) {
+                    a.gnext[col] = (double)tot;
+                } else {
+                    const double gval = gown[cc] + (double)tot;
+                    gown[cc] = gval;
+                    if (push && b == i + 2) {   // final for rhs'_{i+2}: push to every CTA
+                        const int q = qown[cc];
+                        for (int k = 0; k < C; ++k)
+                            st_async_f64(cluster_addr(rhsg + (i & 1) * kClSmax + q, k), gval,
+                                         cluster_addr(&gready[i & 1], k));
                     }
                 }
             }
+            group_sync(2, 32 * kClWarps);   // red is rewritten next step
         }
-        __syncthreads();        // red is rewritten next step
     }
+    __syncthreads();
     cl.sync();                  // no CTA leaves while others may touch its memory
     for (int cc = threadIdx.x; cc < ncl; cc += blockDim.x) a.g[c0 + cc] = gown[cc];
-    if (c == 0 && threadIdx.x == 0 && a.e) *a.t = t;
 }
 
 // ------------------------------------------------------------------ host

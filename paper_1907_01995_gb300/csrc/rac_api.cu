@@ -107,8 +107,12 @@ struct rac_handle {
     int64_t *sweep_dev = nullptr;
     int nslots = 0;
     int64_t sweep = 0;
-    std::map<int, cudaGraphExec_t> graphs;
-    std::map<int, int64_t> graph_launches;
+    std::map<int64_t, cudaGraphExec_t> graphs;   // by period shape (period_key)
+    std::map<int64_t, int64_t> graph_launches;
+    std::map<int64_t, int> shape_uses;           // periods run per shape
+    // sweeps of the next period whose assembly and factors the previous period
+    // already enqueued (beside its refresh); 0: none
+    int pre = 0, pre_nb = 0;
     bool use_graph = true;
     // kernel launch accounting and optional per-class event timing
     int64_t nlaunch = 0, setup_launches = 0;
@@ -266,32 +270,48 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
 // Block factors depend only on the assembly, so the factors of every sweep of
 // the period are launched up front on kFactorStreams streams (one buffer per
 // sweep slot) and run ahead of the chain; chain s waits only for factor s.
-static rac_status enqueue_period(rac_handle *h, int nb) {
+// The factor of sweep slot s of the current period on factor stream sf.
+static rac_status enqueue_factor(rac_handle *h, int s, cudaStream_t sf) {
+    ChainArgs a = chain_args(h, s);
+    int kinv = 1;
+    if (h->big) {
+        RAC_CK(launch_big_factor(h->store, a, const_cast<void *>(a.W),
+                                 (char *)h->Pbuf + (size_t)s * h->pstride, sf));
+        h->nlaunch += big_factor_launches(BlockLayout(h->n, h->p).smax(), h->store);
+    } else {
+        RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W),
+                             const_cast<void *>(a.P), &kinv, sf));
+        h->nlaunch += 1;
+    }
+    return RAC_OK;
+}
+
+// One refresh period of nb sweeps.  pre_in: the first pre_in factors (and
+// the assembly) were enqueued by the previous period.  next_nb > 0: after
+// this period's last prox, enqueue the next period's assembly and its first
+// min(3, next_nb) factors on the factor streams, beside the FP64 refresh
+// (they depend on the sweep counter and the Gram matrix only).
+static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb) {
     cudaStream_t st = h->st;
     const bool pf = h->profile;
     if (pf) RAC_CK(cudaEventRecord(h->pev[0], st));
-    RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, nb, h->perm, h->blk, h->tkey,
-                           h->tidx, st));
+    if (pre_in == 0) {
+        RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, nb, h->perm, h->blk,
+                               h->tkey, h->tidx, st));
+        h->nlaunch += 1;
+    }
     if (pf) RAC_CK(cudaEventRecord(h->pev[1], st));
     RAC_CK(cudaEventRecord(h->fev[0], st));      // fork: factors wait for the assembly
     // fork only the streams that receive work, so every forked stream rejoins
-    for (int q = 0; q < std::min(nb, (int)rac_handle::kFactorStreams); ++q)
+    const int nfac = nb - pre_in;
+    for (int q = 0; q < std::min(nfac, (int)rac_handle::kFactorStreams); ++q)
         RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[0], 0));
-    h->nlaunch += 1 + (3 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;
-    if (h->big) h->nlaunch += (int64_t)(big_factor_launches(BlockLayout(h->n, h->p).smax(), h->store) - 1) * nb;
-    for (int s = 0; s < nb; ++s) {
-        ChainArgs a = chain_args(h, s);
-        cudaStream_t sf = h->sfs[s % rac_handle::kFactorStreams];
+    h->nlaunch += (2 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;
+    for (int s = pre_in; s < nb; ++s) {
+        cudaStream_t sf = h->sfs[(s - pre_in) % rac_handle::kFactorStreams];
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
         if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
-        int kinv = 1;
-        if (h->big) {
-            RAC_CK(launch_big_factor(h->store, a, const_cast<void *>(a.W),
-                                     (char *)h->Pbuf + (size_t)s * h->pstride, sf));
-        } else {
-            RAC_CK(launch_factor(h->store, h->gram, a, const_cast<void *>(a.W),
-                                 const_cast<void *>(a.P), &kinv, sf));
-        }
+        RAC_ST(enqueue_factor(h, s, sf));
         if (pf) RAC_CK(cudaEventRecord(ev[1], sf));
         RAC_CK(cudaEventRecord(h->fev[1 + s], sf));
     }
@@ -301,7 +321,7 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         if (h->lookahead)
             RAC_CK(launch_prepare(h->n, a.perm, h->x, h->z, h->xi, h->k ? h->e64 : nullptr,
                                   h->gamma, h->sperm, h->eperm, st));
-        RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
+        if (s >= pre_in) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         if (h->big) {
@@ -335,8 +355,25 @@ static rac_status enqueue_period(rac_handle *h, int nb) {
         RAC_CK(launch_prox(pa, st));
         if (pf) RAC_CK(cudaEventRecord(ev[4], st));
     }
-    RAC_ST(enqueue_refresh(h));
     RAC_CK(launch_advance(h->sweep_dev, nb, st));
+    const int npre = std::min(next_nb, (int)rac_handle::kFactorStreams);
+    if (npre > 0) {
+        // the next period's slots are free: its assembly and first factors
+        // run on the factor streams while the refresh runs here
+        RAC_CK(cudaEventRecord(h->fev[0], st));
+        RAC_CK(cudaStreamWaitEvent(h->sfs[0], h->fev[0], 0));
+        RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, next_nb, h->perm, h->blk,
+                               h->tkey, h->tidx, h->sfs[0]));
+        h->nlaunch += 1;
+        RAC_CK(cudaEventRecord(h->fev[1], h->sfs[0]));
+        for (int q = 1; q < npre; ++q) RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[1], 0));
+        for (int q = 0; q < npre; ++q) RAC_ST(enqueue_factor(h, q, h->sfs[q]));
+    }
+    RAC_ST(enqueue_refresh(h));
+    for (int q = 0; q < npre; ++q) {   // rejoin
+        RAC_CK(cudaEventRecord(h->fev[2 + q], h->sfs[q]));
+        RAC_CK(cudaStreamWaitEvent(st, h->fev[2 + q], 0));
+    }
     if (pf) RAC_CK(cudaEventRecord(h->pev[2], st));
     return RAC_OK;
 }
@@ -361,39 +398,51 @@ static void collect_profile(rac_handle *h, int nb) {
     h->chain_launches += nb;
 }
 
-static rac_status run_period(rac_handle *h, int nb) {
+static int64_t period_key(int nb, int pre_in, int next_nb) {
+    return (int64_t)nb + ((int64_t)pre_in << 20) + ((int64_t)next_nb << 40);
+}
+
+// A period shape is captured into a CUDA graph at its kGraphAfter-th use and
+// replayed from then on: capturing and instantiating costs more than a few
+// direct launches of the same work save (a fresh handle that converges in
+// three periods runs fastest without graphs).
+constexpr int kGraphAfter = 3;
+
+static rac_status run_period(rac_handle *h, int nb, int pre_in, int next_nb) {
     // Profiling brackets every kernel class with events, which is only
     // reliable for direct launches, so a profiled handle does not use graphs.
-    if (h->use_graph && !h->profile) {
-        auto it = h->graphs.find(nb);
+    const int64_t key = period_key(nb, pre_in, next_nb);
+    const int uses = ++h->shape_uses[key];
+    if (h->use_graph && !h->profile && (uses >= kGraphAfter || h->graphs.count(key))) {
+        auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             bool ok = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed) ==
                       cudaSuccess;
             int64_t before = h->nlaunch;
-            rac_status s = ok ? enqueue_period(h, nb) : RAC_ERR_CUDA;
-            h->graph_launches[nb] = h->nlaunch - before;
+            rac_status s = ok ? enqueue_period(h, nb, pre_in, next_nb) : RAC_ERR_CUDA;
+            h->graph_launches[key] = h->nlaunch - before;
             h->nlaunch = before;
             cudaError_t ce = cudaStreamEndCapture(h->st, &graph);
             if (ok && s == RAC_OK && ce == cudaSuccess &&
                 cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-                h->graphs[nb] = exec;
+                h->graphs[key] = exec;
                 cudaGraphDestroy(graph);
             } else {
                 if (graph) cudaGraphDestroy(graph);
                 cudaGetLastError();
                 h->use_graph = false;  // fall back to direct launches
                 h->nlaunch = before;
-                return enqueue_period(h, nb);
+                return enqueue_period(h, nb, pre_in, next_nb);
             }
-            it = h->graphs.find(nb);
+            it = h->graphs.find(key);
         }
         RAC_CK(cudaGraphLaunch(it->second, h->st));
-        h->nlaunch += h->graph_launches[nb];
+        h->nlaunch += h->graph_launches[key];
         return RAC_OK;
     }
-    return enqueue_period(h, nb);
+    return enqueue_period(h, nb, pre_in, next_nb);
 }
 
 struct HostStats {
@@ -433,6 +482,7 @@ static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) 
     RAC_CK(cudaMemsetAsync(h->t, 0, sizeof(double), st));
     RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     h->sweep = 0;
+    h->pre = 0;   // a pre-launched period head belongs to the old sweep count
     RAC_CK(cudaMemsetAsync(h->sweep_dev, 0, sizeof(int64_t), st));
     RAC_ST(enqueue_refresh(h));
     if (x0 && h->xi_from_grad) {
@@ -473,7 +523,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->ws_fallback = o->ws_fallback != 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     {
-        const size_t nfev = 1 + (size_t)h->refresh_every;
+        const size_t nfev = std::max<size_t>(1 + (size_t)h->refresh_every, 6);
         const size_t npev = h->profile ? 3 + 5 * (size_t)h->refresh_every : 0;
         RAC_CK(runtime_take_streams(&h->ss, nfev, npev));
         RAC_CK(runtime_pool(&h->pool));
@@ -737,7 +787,14 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
     const bool check_ws = h->ws_fallback && h->warm && h->solves == 0;
     while (status == RAC_OK && hs.kkt > h->tol && done < h->max_sweeps) {
         int nb = std::min(h->refresh_every, h->max_sweeps - done);
-        RAC_ST(run_period(h, nb));
+        // a pre-launched head is usable if it covers this period's sweeps
+        const int pre_in = (h->pre > 0 && h->pre_nb == nb) ? h->pre : 0;
+        if (h->pre > 0 && pre_in == 0) h->pre = 0;   // stale: recompute everything
+        const int left = h->max_sweeps - done - nb;
+        const int next_nb = (h->profile || left <= 0) ? 0 : std::min(h->refresh_every, left);
+        RAC_ST(run_period(h, nb, pre_in, next_nb));
+        h->pre = std::min(next_nb, (int)rac_handle::kFactorStreams);
+        h->pre_nb = next_nb;
         h->sweep += nb;
         done += nb;
         RAC_ST(read_stats(h, &hs, &dev_err));
@@ -896,6 +953,7 @@ extern "C" rac_status rac_admm_restore(rac_handle *h, const void *buf, size_t le
     RAC_CK(cudaMemcpyAsync(h->mu, body + 3 * (size_t)h->n, sizeof(double), cudaMemcpyDefault, h->st));
     RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
     h->sweep = hd.sweep;
+    h->pre = 0;
     RAC_CK(cudaMemcpyAsync(h->sweep_dev, &h->sweep, sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
     RAC_ST(enqueue_refresh(h));
     RAC_CK(cudaStreamSynchronize(h->st));

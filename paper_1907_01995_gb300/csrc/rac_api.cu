@@ -270,6 +270,30 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
 // Block factors depend only on the assembly, so the factors of every sweep of
 // the period are launched up front on kFactorStreams streams (one buffer per
 // sweep slot) and run ahead of the chain; chain s waits only for factor s.
+static ProxArgs prox_args(const rac_handle *h) {
+    ProxArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.n = h->n;
+    pa.x = h->x;
+    pa.z = h->z;
+    pa.xi = h->xi;
+    pa.dx = h->dx;
+    pa.g = h->gram ? h->g : nullptr;
+    pa.gdef = h->gdef;
+    pa.gnext = h->gram ? h->gnext : nullptr;
+    pa.mu = h->k ? h->mu : nullptr;
+    pa.t = h->k ? h->t : nullptr;
+    pa.phi = h->phi;
+    pa.lam1 = h->lam1;
+    pa.lam2 = h->lam2;
+    pa.lo = h->lo;
+    pa.hi = h->hi;
+    pa.beta = h->beta;
+    pa.gamma = h->gamma;
+    pa.lam_dev = h->lam_dev;
+    return pa;
+}
+
 // The factor of sweep slot s of the current period on factor stream sf.
 static rac_status enqueue_factor(rac_handle *h, int s, cudaStream_t sf) {
     ChainArgs a = chain_args(h, s);
@@ -306,7 +330,7 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
     const int nfac = nb - pre_in;
     for (int q = 0; q < std::min(nfac, (int)rac_handle::kFactorStreams); ++q)
         RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[0], 0));
-    h->nlaunch += (2 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;
+    h->nlaunch += (1 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;   // + prox below
     for (int s = pre_in; s < nb; ++s) {
         cudaStream_t sf = h->sfs[(s - pre_in) % rac_handle::kFactorStreams];
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
@@ -327,32 +351,17 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         if (h->big) {
             RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
         } else if (h->cluster) {
+            a.fuse_prox = 1;   // the z-step / ascent runs at the end of the chain
+            a.prox = prox_args(h);
             RAC_CK(launch_cluster_chain(h->store, a, h->cluster, st));
         } else {
             RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));
         }
         if (pf) RAC_CK(cudaEventRecord(ev[3], st));
-        ProxArgs pa;
-        std::memset(&pa, 0, sizeof(pa));
-        pa.n = h->n;
-        pa.x = h->x;
-        pa.z = h->z;
-        pa.xi = h->xi;
-        pa.dx = h->dx;
-        pa.g = h->gram ? h->g : nullptr;
-        pa.gdef = h->gdef;
-        pa.gnext = h->gram ? h->gnext : nullptr;
-        pa.mu = h->k ? h->mu : nullptr;
-        pa.t = h->k ? h->t : nullptr;
-        pa.phi = h->phi;
-        pa.lam1 = h->lam1;
-        pa.lam2 = h->lam2;
-        pa.lo = h->lo;
-        pa.hi = h->hi;
-        pa.beta = h->beta;
-        pa.gamma = h->gamma;
-        pa.lam_dev = h->lam_dev;
-        RAC_CK(launch_prox(pa, st));
+        if (!h->cluster) {
+            RAC_CK(launch_prox(prox_args(h), st));
+            h->nlaunch += 1;
+        }
         if (pf) RAC_CK(cudaEventRecord(ev[4], st));
     }
     RAC_CK(launch_advance(h->sweep_dev, nb, st));

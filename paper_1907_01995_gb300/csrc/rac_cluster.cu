@@ -52,7 +52,7 @@ constexpr int kClRows = kClSmax / kClWarps;   // G rows per update warp and step
 
 // Shared-memory layout (offsets in bytes, each 16-byte aligned).
 struct ClLayout {
-    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, bars, total;
+    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, gpark, bars, total;
     int ncp, rmax;
     __host__ __device__ ClLayout(int n, int smax, int C) {
         // columns per CTA: 64 NK with NK in {1, 2, 4} (the kernel's template
@@ -75,6 +75,7 @@ struct ClLayout {
         dbuf = take(2 * (size_t)kClSmax * 4);
         rhs = take((size_t)kClSmax * 4);
         red = take((size_t)kClWarps * ncp * 4);
+        gpark = take(2 * (size_t)ncp * 8);
         bars = take(4 * 8);
         total = o;
     }
@@ -173,6 +174,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     float *dbuf = (float *)(sm + L.dbuf);        // [2][kClSmax]: dx_i, dx_{i-1}
     float *rhs = (float *)(sm + L.rhs);
     float *red = (float *)(sm + L.red);          // [update warps][ncp]
+    double *gdef_s = (double *)(sm + L.gpark);   // [ncp]: parked own-block increments (fused z-step)
+    double *gnext_s = gdef_s + ncp;               // [ncp]: parked next-block increments
     uint64_t *bars = (uint64_t *)(sm + L.bars);  // dx ready [2], gradient ready [2]
     uint64_t *dready = bars, *gready = bars + 2;
     __shared__ double dred[64];
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     }
     for (int cc = threadIdx.x; cc < ncp; cc += blockDim.x) {
         gown[cc] = cc < ncl ? a.g[c0 + cc] : 0.0;
+        gdef_s[cc] = gnext_s[cc] = 0.0;
         if (cc >= ncl) bown[cc] = -1;
     }
     // zeros past each block's size: the solve warps read whole float4 groups
@@ -340,7 +344,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
         if (a.e && p >= 1) {   // the last block's contribution to t
             mbar_wait_cluster(&dready[(p - 1) & 1], (uint32_t)((p - 1) >> 1) & 1u, a.err);
             t_update(p - 1);
-            if (c == 0 && tid == 0) *a.t = t;
+            if (c == 0 && tid == 0) {
+                *a.t = t;
+                // multiplier of the coupling row (every CTA read it at entry,
+                // before the first cluster barrier)
+                if (a.fuse_prox && a.prox.mu) *a.prox.mu = *a.prox.mu - a.prox.beta * t;
+            }
         }
     } else {
         // ================= update warps: G[own, S_i] dx_i =================
@@ -396,9 +405,11 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
                 for (int w = 0; w < kClWarps; ++w) tot += red[w * ncp + cc];
                 const int b = bown[cc], col = c0 + cc;
                 if (b == i) {
-                    a.gdef[col] = (double)tot;
+                    if (a.fuse_prox) gdef_s[cc] = (double)tot;
+                    else a.gdef[col] = (double)tot;
                 } else if (b == i + 1) {
-                    a.gnext[col] = (double)tot;
+                    if (a.fuse_prox) gnext_s[cc] = (double)tot;
+                    else a.gnext[col] = (double)tot;
                 } else {
                     const double gval = gown[cc] + (double)tot;
                     gown[cc] = gval;
@@ -414,8 +425,26 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
         }
     }
     __syncthreads();
-    cl.sync();                  // no CTA leaves while others may touch its memory
-    for (int cc = threadIdx.x; cc < ncl; cc += blockDim.x) a.g[c0 + cc] = gown[cc];
+    cl.sync();                  // no CTA leaves while others may touch its memory; dx is complete
+    if (a.fuse_prox) {
+        // the z-block and the x - z multiplier ascent (Sec. 3.1, eq. RAC-ADDM)
+        // on this CTA's columns, with the gradient completed by the parked
+        // increments (what k_prox does for the other chains)
+        const ProxArgs &q = a.prox;
+        const double lam1 = q.lam_dev ? q.lam_dev[0] : q.lam1, lam2 = q.lam_dev ? q.lam_dev[1] : q.lam2;
+        for (int cc = threadIdx.x; cc < ncl; cc += blockDim.x) {
+            const int j = c0 + cc;
+            const double x = q.x[j] + q.dx[j];
+            const double xi = q.xi[j];
+            const double z = prox_z(q.phi, x, xi, q.gamma, lam1, lam2, q.lo, q.hi);
+            q.x[j] = x;
+            q.z[j] = z;
+            q.xi[j] = xi - q.gamma * (x - z);
+            a.g[j] = gown[cc] + gdef_s[cc] + gnext_s[cc];
+        }
+    } else {
+        for (int cc = threadIdx.x; cc < ncl; cc += blockDim.x) a.g[c0 + cc] = gown[cc];
+    }
 }
 
 // ------------------------------------------------------------------ host

@@ -46,6 +46,20 @@ cudaError_t runtime_pool(cudaMemPool_t *pool);
 cudaError_t runtime_take_streams(StreamSet **out, size_t nfev, size_t npev);
 void runtime_give_streams(StreamSet *ss);
 
+struct ProxArgs {
+    int n;
+    double *x, *z, *xi;
+    const double *dx;
+    double *g;              // Gram form: g += gdef + gnext, gnext = 0
+    const double *gdef;
+    double *gnext;
+    double *mu;
+    const double *t;
+    int phi;
+    double lam1, lam2, lo, hi, beta, gamma;
+    const double *lam_dev;  // if set: (lambda1, lambda2) read from device memory
+};
+
 // Arguments of the persistent sweep kernels (one instance, one rhs column).
 struct ChainArgs {
     int n, p, m;
@@ -80,21 +94,11 @@ struct ChainArgs {
     const double *eperm;    // lookahead: e in permuted order (n) or NULL
     int perm_in_smem;       // lookahead: the whole permutation fits in shared memory
     int p_rows;             // factor writes P_i row-major (s_i x s_{i-1}) instead of P_i^T
+    int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
+    ProxArgs prox;          //   ... with these arguments
 };
 
-struct ProxArgs {
-    int n;
-    double *x, *z, *xi;
-    const double *dx;
-    double *g;              // Gram form: g += gdef + gnext, gnext = 0
-    const double *gdef;
-    double *gnext;
-    double *mu;
-    const double *t;
-    int phi;
-    double lam1, lam2, lo, hi, beta, gamma;
-    const double *lam_dev;  // if set: (lambda1, lambda2) read from device memory
-};
+
 
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_assembly(int n, int p, uint64_t seed, int64_t sweep0, const int64_t *sweep_dev,

@@ -3,16 +3,26 @@
 // Sec. 3.2 solves SVM duals one at a time; here a whole set of uneven
 // instances (each its own data, size, assembly stream, beta and tolerance
 // check) runs as one graph-captured period of batched kernels:
-//   k_batch_assembly  one CTA per (instance, sweep of the period)
-//   k_batch_factor    one CTA per (instance, block): K_S^{-1} of every block
-//                     of every instance, all in parallel
-//   k_batch_chain     one persistent CTA per instance walks its blocks in
-//                     cyclic order (the chain of one instance needs no grid
-//                     barrier, so instances never wait on each other)
-//   k_batch_prox      z-block and multiplier ascent per instance
-//   k_batch_refresh   exact FP64 gradient at z, KKT statistics and the
-//                     anchor reset, one CTA per instance
+//   k_batch_assembly    one CTA per (instance, sweep of the period)
+//   k_batch_factor_tc   K_S^{-1} of every block of every instance, two blocks
+//                       of one instance per CTA: the block Grams
+//                       A~_S^T A~_S on the tensor cores (tcgen05, BF16 or a
+//                       two-term TF32 split), the inverse by the sweep
+//                       operator in registers (FP64 storage: k_batch_factor64
+//                       on the FP64 pipe)
+//   k_batch_chain       one CTA per instance walks its blocks in cyclic order
+//                       (an instance's chain needs no grid barrier, so
+//                       instances never wait on each other); instances are
+//                       launched largest first
+//   k_batch_prox        z-block and multiplier ascent, 256 coordinates per CTA
+//   k_batch_ref_*       exact FP64 gradient at z, KKT statistics and the
+//                       anchor reset, spread over 256-column chunks
 // Converged instances are masked out between periods.
+//
+// Storage: instance i keeps its data matrix twice, in FP64 (m x n, the
+// refresh) and in the storage precision column-major with the leading
+// dimension ld = m rounded up to 8 (zero rows below m), so that every column
+// starts on a 16-byte boundary and is read with 16-byte vector loads.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -21,20 +31,29 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "rac_device.cuh"
 #include "rac_internal.h"
+#include "rac_tc.cuh"
 
 namespace rac {
 
+constexpr int kChunk = 256;     // coordinates per prox / refresh CTA
+constexpr int kStats = 8;       // refresh statistics per chunk
+
 // Per-instance descriptor (device resident; the host reads the statistics).
 struct BatchDesc {
-    int m, n, p, nslab, rows, active, phi, k;
+    int m, n, p, ld, active, phi, k;
     double beta, gamma, lam1, lam2, lo, hi, d;
     uint64_t seed;
     size_t a64, as, vec, row, w;  // offsets into the shared pools
+    size_t part;                  // refresh partials: nchunk x ld
     int bp;                       // first flattened block index
+    int pp;                       // first factor pair index
+    int cc;                       // first coordinate chunk index
     // statistics of the last refresh
     double stat, gmax, znorm1, ez, ex, xz;
     int nonfinite;
@@ -46,22 +65,58 @@ struct BatchPools {
     const double *A64, *b, *c, *e;
     const void *As;
     void *W;
-    double *x, *z, *xi, *dx, *ga, *dres, *rbuf;
+    double *x, *z, *xi, *dx, *ga, *dres, *rbuf, *cst;
+    double *rpart, *dpart, *spart;
     int *perm;
     uint64_t *tkey;
     int *tidx;
     size_t ntot;       // sum of n_i (one permutation slot)
-    int R;
 };
 
-__device__ __forceinline__ int find_instance(const int *bp, int count, int blk) {
+__device__ __forceinline__ int find_instance(const int *start, int count, int unit) {
     int lo = 0, hi = count - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (bp[mid] <= blk) lo = mid;
+        if (start[mid] <= unit) lo = mid;
         else hi = mid - 1;
     }
     return lo;
+}
+
+// ---------------------------------------------------------------- 16-byte vectors
+template <class TS> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using T = double2; static constexpr int N = 2; };
+template <> struct Vec16<__nv_bfloat16> { using T = uint4; static constexpr int N = 8; };
+
+__device__ __forceinline__ float4 ldg16(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ double2 ldg16(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
+__device__ __forceinline__ uint4 ldg16(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+
+__device__ __forceinline__ void unpack(const float4 &a, float (&o)[4]) {
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void unpack(const double2 &a, double (&o)[2]) { o[0] = a.x; o[1] = a.y; }
+// bf16 -> f32 is exact: the bf16 bits are the top half of the f32 bits
+__device__ __forceinline__ void unpack(const uint4 &a, float (&o)[8]) {
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        o[2 * k] = __uint_as_float(w[k] << 16);
+        o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+template <class TA, int N> __device__ __forceinline__ void lds_vec(const TA *p, TA (&o)[N]) {
+    if constexpr (sizeof(TA) * N == 16) {
+        if constexpr (sizeof(TA) == 4) unpack(*reinterpret_cast<const float4 *>(p), o);
+        else unpack(*reinterpret_cast<const double2 *>(p), o);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(p + k);
+            o[k] = q.x; o[k + 1] = q.y; o[k + 2] = q.z; o[k + 3] = q.w;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- assembly
@@ -77,24 +132,280 @@ __global__ void __launch_bounds__(1024) k_batch_assembly(BatchDesc *D, int count
                  assembly_log2_buckets(d.n), sm_u);
 }
 
-// ---------------------------------------------------------------- factor
-// K_S = A~_S^T A~_S + beta e_S e_S^T + gamma I from the instance's slab copy,
-// then K_S^{-1} by the register sweep operator (row-owner layout).
+// ---------------------------------------------------------------- factor (tensor cores)
+// K_S = A~_S^T A~_S + beta e_S e_S^T + gamma I and its inverse for blocks
+// 2q and 2q + 1 of one instance (s <= 64).  The 128 gathered columns of the
+// two blocks form one K-major operand X (row r = column r of block 0, row
+// 64 + r = column r of block 1) and D = X X^T is one M = N = 128 tcgen05
+// MMA chain; its diagonal 64 x 64 quadrants are the two Grams.  BF16 storage
+// uses kind::f16 (exact products, FP32 accumulation).  FP32 storage uses
+// kind::tf32 on the split a = h + l (h = a rounded to TF32, l = a - h):
+// F = H H^T + H (2L)^T and K = (F + F^T) / 2 = H H^T + H L^T + L H^T, which
+// leaves out only the L L^T term (relative size 2^-22).  Every thread
+// gathers 64 bytes of one column per K chunk into the 128-byte-swizzled
+// tile; two chunks are in flight (one being multiplied, one being loaded).
+// The inverse is the sweep operator (Goodnight 1979) on the padded 64 x 64
+// matrix in registers: thread (tr, tc) of each 128-thread half owns rows
+// 4 tr .. 4 tr + 3 and columns 8 tc .. 8 tc + 7 of its block; the row after
+// the pivot is published with d - 1 on its diagonal and 1/d beside it, so
+// one update a_ij -= (a_ik / d) v_j serves the whole matrix except the pivot
+// itself (-1/d), with one barrier per pivot.
+constexpr uint32_t kFtTile = 128 * 128;            // one operand tile: 128 rows x 128 bytes
+constexpr int kFtLdF = 65;                         // staged Gram row (floats), padded
+template <class TS> constexpr size_t factor_tc_smem() {
+    constexpr int NT = std::is_same<TS, float>::value ? 2 : 1;
+    const size_t ring = 2 * NT * (size_t)kFtTile;
+    const size_t f = 2 * 64 * kFtLdF * sizeof(float);
+    return (ring > f ? ring : f) + 1024;
+}
+
+__device__ __forceinline__ uint32_t f32_to_tf32(float a) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
+    return r;
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const int *pps, int count,
+                                                           BatchPools P, int slot, int *err) {
+    constexpr bool TF = std::is_same<TS, float>::value;
+    constexpr int NT = TF ? 2 : 1;                 // operand tiles per stage
+    constexpr int VN = 16 / sizeof(TS);            // elements per 16-byte vector
+    constexpr int KC = 128 / sizeof(TS);           // K elements per 128-byte row
+    using VT = typename Vec16<TS>::T;
+    extern __shared__ unsigned char ft_raw[];
+    unsigned char *ring = (unsigned char *)(((uintptr_t)ft_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    __shared__ int idx[128];
+    __shared__ float es[128];
+    __shared__ __align__(16) float vbuf[2][2][68];   // [block][double buffer][row, 1/d]
+    const int inst = find_instance(pps, count, blockIdx.x);
+    const BatchDesc &d = D[inst];
+    if (!d.active) return;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    BlockLayout lay(d.n, d.p);
+    const int b0 = 2 * (blockIdx.x - d.pp), b1 = b0 + 1;
+    const int s0 = lay.size(b0), s1 = b1 < d.p ? lay.size(b1) : 0;
+    const int ld = d.ld;
+    const int *perm = P.perm + (size_t)slot * P.ntot + d.vec;
+    if (t < 128) {
+        const int blk = t >> 6, q = t & 63;
+        const int sb = blk ? s1 : s0;
+        int j = -1;
+        if (q < sb) j = perm[lay.offset(blk ? b1 : b0) + q];
+        idx[t] = j;
+        es[t] = (j >= 0 && d.k) ? (float)P.e[d.vec + j] : 0.f;
+    }
+    if (warp == 0) tc_alloc(&tslot, 128);
+    if (t == 32) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_init_fence();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    // gather assignment: thread t loads 4 vectors (64 bytes) of row t / 2 per chunk
+    const int row = t >> 1, vh = (t & 1) * 4;
+    const int col = idx[row];
+    const TS *src = (const TS *)P.As + d.as + (size_t)(col >= 0 ? col : 0) * ld;
+    const int nk = (ld + KC - 1) / KC;
+    VT regs[4];
+    auto load = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = kc * KC + (vh + u) * VN;
+            if (col >= 0 && k < ld) regs[u] = ldg16(src + k);
+            else regs[u] = VT{};
+        }
+    };
+    auto store = [&](int buf) {
+        unsigned char *tl = ring + (size_t)buf * NT * kFtTile;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t off = sw128_offset(row, vh + u);
+            if constexpr (TF) {
+                const float4 a = regs[u];
+                const uint32_t h0 = f32_to_tf32(a.x), h1 = f32_to_tf32(a.y);
+                const uint32_t h2 = f32_to_tf32(a.z), h3 = f32_to_tf32(a.w);
+                *reinterpret_cast<uint4 *>(tl + off) = make_uint4(h0, h1, h2, h3);
+                *reinterpret_cast<float4 *>(tl + kFtTile + off) =
+                    make_float4(2.f * (a.x - __uint_as_float(h0)), 2.f * (a.y - __uint_as_float(h1)),
+                                2.f * (a.z - __uint_as_float(h2)), 2.f * (a.w - __uint_as_float(h3)));
+            } else {
+                *reinterpret_cast<VT *>(tl + off) = regs[u];
+            }
+        }
+    };
+    constexpr uint32_t idesc = TF ? tc_idesc_tf32(128, 128) : tc_idesc(128, 128);
+    load(0);
+    for (int kc = 0; kc < nk; ++kc) {
+        const int buf = kc & 1;
+        if (kc >= 2) mbar_wait(&mbar[buf], (uint32_t)((kc - 2) >> 1) & 1u, err, kBarrierTimeoutNs);
+        store(buf);
+        if (kc + 1 < nk) load(kc + 1);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            tc_fence_after();
+            const uint32_t base = smem_u32(ring + (size_t)buf * NT * kFtTile);
+            const uint64_t hd = tc_desc_sw128(base);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                // K advances 32 bytes inside the swizzle row: +2 in descriptor address units
+                tc_mma<TF>(tmem, hd + 2u * k, hd + 2u * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                if constexpr (TF) {
+                    const uint64_t ldsc = tc_desc_sw128(base + kFtTile);
+                    tc_mma<TF>(tmem, hd + 2u * k, ldsc + 2u * k, idesc, 1u);
+                }
+            }
+            tc_commit(&mbar[buf]);
+        }
+    }
+    mbar_wait(&mbar[(nk - 1) & 1], (uint32_t)((nk - 1) >> 1) & 1u, err, kBarrierTimeoutNs);
+    tc_fence_after();
+    // accumulator quadrants -> F[block][r][c] in shared memory (the ring is idle)
+    float *F = (float *)ring;
+    {
+        const int sub = warp & 3, half = warp >> 2;
+        const int blk = sub >> 1, r = 32 * (sub & 1) + lane;
+        uint32_t v[32];
+        tc_ld32(tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(64 * blk + 32 * half), v);
+        float *fr = F + ((size_t)blk * 64 + r) * kFtLdF + 32 * half;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) fr[c] = __uint_as_float(v[c]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, 128);
+    // sweep-operator inverse, both blocks in lockstep
+    const int blk = t >> 7, tl = t & 127, tr = tl >> 3, tcc = tl & 7;
+    const int sb = blk ? s1 : s0;
+    const float *Fb = F + (size_t)blk * 64 * kFtLdF;
+    const float *eb = es + 64 * blk;
+    const float gam = (float)d.gamma, bet = (float)d.beta;
+    float acc[4][8];
+#pragma unroll
+    for (int ru = 0; ru < 4; ++ru) {
+        const int r = 4 * tr + ru;
+#pragma unroll
+        for (int cu = 0; cu < 8; ++cu) {
+            const int c = 8 * tcc + cu;
+            float v;
+            if (r < sb && c < sb) {
+                v = TF ? 0.5f * (Fb[r * kFtLdF + c] + Fb[c * kFtLdF + r]) : Fb[r * kFtLdF + c];
+                v += bet * eb[r] * eb[c] + (r == c ? gam : 0.f);
+            } else {
+                v = r == c ? 1.f : 0.f;
+            }
+            acc[ru][cu] = v;
+        }
+    }
+    float *vb = &vbuf[blk][0][0];
+    bool bad = false;
+    if (tr == 0) {
+        float w[8];
+#pragma unroll
+        for (int cu = 0; cu < 8; ++cu) w[cu] = acc[0][cu];
+        if (tcc == 0) {
+            bad = !(w[0] > 0.f);
+            vb[64] = __frcp_rn(bad ? 1.f : w[0]);
+            w[0] -= 1.f;
+        }
+        *reinterpret_cast<float4 *>(&vb[8 * tcc]) = make_float4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<float4 *>(&vb[8 * tcc + 4]) = make_float4(w[4], w[5], w[6], w[7]);
+    }
+    __syncthreads();
+    const int kmax = max(s0, s1);
+    for (int k = 0; k < kmax; ++k) {
+        const float *vk = vb + (k & 1) * 68;
+        float *vn = vb + ((k + 1) & 1) * 68;
+        const float rd = vk[64];
+        const float4 fr = *reinterpret_cast<const float4 *>(&vk[4 * tr]);
+        const float4 c0 = *reinterpret_cast<const float4 *>(&vk[8 * tcc]);
+        const float4 c1 = *reinterpret_cast<const float4 *>(&vk[8 * tcc + 4]);
+        const float f[4] = {fr.x * rd, fr.y * rd, fr.z * rd, fr.w * rd};
+        const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+        for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+            for (int cu = 0; cu < 8; ++cu) acc[ru][cu] = fmaf(-f[ru], cv[cu], acc[ru][cu]);
+        // the pivot entry: one thread, reached by a warp-uniform branch so the
+        // other warps skip it (tl = 8 tr + tcc, four warps per half)
+        if ((warp & 3) == (((k >> 2) * 8 + (k >> 3)) >> 5)) {
+            if (tr == (k >> 2) && tcc == (k >> 3)) {
+#pragma unroll
+                for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                    for (int cu = 0; cu < 8; ++cu)
+                        acc[ru][cu] = (ru == (k & 3) && cu == (k & 7)) ? -rd : acc[ru][cu];
+            }
+        }
+        const int k1 = k + 1;
+        if (k1 < kmax && (warp & 3) == ((k1 >> 2) >> 2) && tr == (k1 >> 2)) {
+            const int slot = k1 & 3, kv = k1 & 7;
+            float w[8];
+#pragma unroll
+            for (int cu = 0; cu < 8; ++cu) {
+                const float a0 = acc[0][cu], a1 = acc[1][cu], a2 = acc[2][cu], a3 = acc[3][cu];
+                w[cu] = (slot & 2) ? ((slot & 1) ? a3 : a2) : ((slot & 1) ? a1 : a0);
+            }
+            if (tcc == (k1 >> 3)) {
+                const float e01 = (kv & 1) ? w[1] : w[0], e23 = (kv & 1) ? w[3] : w[2];
+                const float e45 = (kv & 1) ? w[5] : w[4], e67 = (kv & 1) ? w[7] : w[6];
+                const float e03 = (kv & 2) ? e23 : e01, e47 = (kv & 2) ? e67 : e45;
+                const float d1 = (kv & 4) ? e47 : e03;
+                if (!(d1 > 0.f)) bad = true;
+                vn[64] = __frcp_rn(d1 > 0.f ? d1 : 1.f);
+#pragma unroll
+                for (int cu = 0; cu < 8; ++cu) w[cu] -= cu == kv ? 1.f : 0.f;
+            }
+            *reinterpret_cast<float4 *>(&vn[8 * tcc]) = make_float4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<float4 *>(&vn[8 * tcc + 4]) = make_float4(w[4], w[5], w[6], w[7]);
+        }
+        __syncthreads();
+    }
+    if (bad && sb > 0) set_err(err, RAC_ERR_NOT_PD);
+    if (sb == 0) return;
+    const size_t kst = BlockLayout::pad4((size_t)lay.smax() * lay.smax());
+    float *out = (float *)P.W + d.w + (size_t)(blk ? b1 : b0) * kst;
+#pragma unroll
+    for (int ru = 0; ru < 4; ++ru) {
+        const int r = 4 * tr + ru;
+        if (r >= sb) continue;
+#pragma unroll
+        for (int cu = 0; cu < 8; ++cu) {
+            const int c = 8 * tcc + cu;
+            if (c < sb) out[(size_t)r * sb + c] = -acc[ru][cu];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- factor (CUDA cores)
+// The same K_S^{-1} on the FP64 pipe (FP64 storage, or blocks above 64):
+// the Gram from 128-byte K chunks of the gathered columns staged in shared
+// memory, then the register sweep operator (row-owner layout).
 template <class TS, class TA, int NP, int U>
-__global__ void __launch_bounds__(512) k_batch_factor(BatchDesc *D, const int *bp, int count,
-                                                      BatchPools P, int slot, int *err) {
+__global__ void __launch_bounds__(512) k_batch_factor_cc(BatchDesc *D, const int *bps, int count,
+                                                         BatchPools P, int slot, int *err) {
+    constexpr int VN = 16 / sizeof(TS);
+    constexpr int KC = 128 / sizeof(TS);
+    constexpr int LDT = KC + 1;
+    using VT = typename Vec16<TS>::T;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    const int inst = find_instance(bp, count, blockIdx.x);
+    const int inst = find_instance(bps, count, blockIdx.x);
     const BatchDesc &d = D[inst];
     if (!d.active) return;
     const int b = blockIdx.x - d.bp;
     BlockLayout lay(d.n, d.p);
     const int s = lay.size(b), off = lay.offset(b), smax = lay.smax();
-    const int R = P.R;
+    const int ld = d.ld;
     int *idx = (int *)sm_raw;
     TA *es = (TA *)(sm_raw + ((128 * sizeof(int) + 15) & ~15));
     TA *vbuf = es + 128;
-    TS *tile = (TS *)(((uintptr_t)(vbuf + 256) + 15) & ~(uintptr_t)15);
+    TA *tile = (TA *)(((uintptr_t)(vbuf + 256) + 15) & ~(uintptr_t)15);   // s x LDT
     const int *perm = P.perm + (size_t)slot * P.ntot + d.vec;
     const TS *As = (const TS *)P.As + d.as;
     const int T = blockDim.x;
@@ -109,25 +420,27 @@ __global__ void __launch_bounds__(512) k_batch_factor(BatchDesc *D, const int *b
     TA acc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) acc[u] = TA(0);
-    for (int q = 0; q < d.nslab; ++q) {
-        for (int t = threadIdx.x; t < s * R; t += T) {
-            const int aa = t / R, rr = t - aa * R;
-            tile[t] = As[((size_t)q * d.n + idx[aa]) * R + rr];
+    for (int k0 = 0; k0 < ld; k0 += KC) {
+        for (int t = threadIdx.x; t < s * 8; t += T) {
+            const int q = t >> 3, v = t & 7;
+            const int k = k0 + v * VN;
+            TA o[VN];
+            if (k < ld) unpack(ldg16(As + (size_t)idx[q] * ld + k), o);
+            else {
+#pragma unroll
+                for (int e = 0; e < VN; ++e) o[e] = TA(0);
+            }
+#pragma unroll
+            for (int e = 0; e < VN; ++e) tile[q * LDT + v * VN + e] = o[e];
         }
         __syncthreads();
         if (rv) {
-            TA tr[16];
+            for (int kk = 0; kk < KC; ++kk) {
+                const TA tr = tile[r * LDT + kk];
 #pragma unroll
-            for (int rr = 0; rr < 16; ++rr) tr[rr] = rr < R ? (TA)to_f(tile[r * R + rr]) : TA(0);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = c0 + NP * u;
-                if (j < s) {
-                    TA sacc = 0;
-#pragma unroll
-                    for (int rr = 0; rr < 16; ++rr)
-                        if (rr < R) sacc += tr[rr] * (TA)to_f(tile[j * R + rr]);
-                    acc[u] += sacc;
+                for (int u = 0; u < U; ++u) {
+                    const int j = c0 + NP * u;
+                    if (j < s) acc[u] = fma(tr, tile[j * LDT + kk], acc[u]);
                 }
             }
         }
@@ -198,199 +511,521 @@ __global__ void __launch_bounds__(512) k_batch_factor(BatchDesc *D, const int *b
 // ---------------------------------------------------------------- chain
 // One CTA walks the instance's blocks in order.  With dres = A~ (x - x_anchor)
 // kept in shared memory, block i needs g_S = g_anchor,S + A~_S^T dres, the
-// solve dx = -K_S^{-1} rhs and the update dres += A~_S dx.
-template <class TS, class TA>
-__global__ void __launch_bounds__(256) k_batch_chain(BatchDesc *D, BatchPools P, int slot) {
+// solve dx = -K_S^{-1} rhs and the update dres += A~_S dx.  Per block:
+//   gradient  each warp takes four columns of S at a time (lanes split a
+//             column's 16-byte vectors when it is long, several short
+//             columns share a warp) and forms rhs_q = cst_q + g_q
+//             + e_q (beta t - mu) with cst = g_anchor - xi + gamma (x - z)
+//   solve     warp w computes rows w, w + 8, ... of K_S^{-1} rhs, lanes over
+//             the columns of the row (shared-memory copy of K_S^{-1})
+//   update    thread v adds sum_q A~[v, S_q] dx_q to its 16-byte slice of
+//             dres (short columns: CG thread groups split S and are summed
+//             in a fixed order)
+// Work for later blocks is started early: K_S^{-1} of block i + 1 arrives by
+// one bulk copy (TMA) issued during block i, the columns of block i + 1 are
+// prefetched into L2 (one bulk prefetch per column) during block i, and the
+// indices and rhs constants of block i + 2 are loaded during block i (three
+// index slots).  Three barriers per block (four when CG > 1).
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <class TS, class TA, int SB>
+__global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int *order,
+                                                        BatchPools P, int slot, int *err) {
+    constexpr int VN = Vec16<TS>::N;
+    constexpr int RPW = SB / 8;                  // solve rows per warp
+    constexpr int CPL = SB / 32;                 // solve columns per lane
+    constexpr int GC = 4;                        // gradient columns per warp pass
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    BatchDesc &d = D[blockIdx.x];
+    const int inst = order[blockIdx.x];
+    BatchDesc &d = D[inst];
     if (!d.active) return;
     BlockLayout lay(d.n, d.p);
-    const int smax = lay.smax(), R = P.R, rows = d.rows, n = d.n;
-    TA *dres = (TA *)sm_raw;                      // rows
-    int *idx = (int *)(dres + rows);
-    TA *rhs = (TA *)(idx + 128);
-    TA *dl = rhs + 128;
-    double *dred = (double *)(((uintptr_t)(dl + 128) + 15) & ~(uintptr_t)15);
+    const int smax = lay.smax(), ld = d.ld, nvec = ld / VN;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const size_t kst = BlockLayout::pad4((size_t)smax * smax);
+    // shared layout
+    uint64_t *bar = (uint64_t *)sm_raw;                                   // 2 mbarriers
+    TA *kinv = (TA *)(sm_raw + 16);                                       // 2 x kst
+    TA *dres = kinv + 2 * kst;                                            // ld
+    TA *rhs = dres + ld;                                                  // SB
+    TA *dlb = rhs + SB;                                                   // SB
+    double *cstb = (double *)(((uintptr_t)(dlb + SB) + 15) & ~(uintptr_t)15);   // 3 x SB
+    double *evb = cstb + 3 * SB;                                          // 3 x SB
+    double *tpart = evb + 3 * SB;                                         // 8
+    int *idxb = (int *)(tpart + 8);                                       // 3 x SB
+    TA *upart = (TA *)(((uintptr_t)(idxb + 3 * SB) + 15) & ~(uintptr_t)15);   // 256 x VN
     const int *perm = P.perm + (size_t)slot * P.ntot + d.vec;
     const TS *As = (const TS *)P.As + d.as;
     const TA *Wb = (const TA *)P.W + d.w;
-    const double *ga = P.ga + d.vec, *x = P.x + d.vec, *z = P.z + d.vec, *xi = P.xi + d.vec;
+    const double *cst = P.cst + d.vec;
     const double *e = d.k ? P.e + d.vec : nullptr;
     double *dx = P.dx + d.vec;
     double *dres_g = P.dres + d.row;
-    for (int t = threadIdx.x; t < rows; t += blockDim.x) dres[t] = (TA)dres_g[t];
-    const double gamma = d.gamma, beta = d.beta, mu = d.mu;
-    double t = d.t;
-    const size_t kst = BlockLayout::pad4((size_t)smax * smax);
-    // threads per column in the gradient step: TPC lanes split the slabs
-    const int TPC = smax <= 32 ? 8 : (smax <= 64 ? 4 : 2);
+    const double beta = d.beta, mu = d.mu;
+    const uint32_t colbytes = (uint32_t)(ld * sizeof(TS));
+    double tc = d.t;
+    // lanes per gradient column (a power of two <= 32 covering the column's
+    // vectors) and thread groups of the update pass
+    int lpc = 1;
+    while (lpc < nvec && lpc < 32) lpc <<= 1;
+    const int cpw = 32 / lpc;
+    int CG = 1;
+    while (CG < 16 && 2 * CG * nvec <= 256) CG <<= 1;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    for (int v = t; v < ld; v += 256) dres[v] = (TA)dres_g[v];
     __syncthreads();
+    auto issue_kinv = [&](int b, int buf) {
+        const int sb = lay.size(b);
+        const uint32_t bytes = (uint32_t)(BlockLayout::pad4((size_t)sb * sb) * sizeof(TA));
+        fence_proxy_async_smem();
+        mbar_expect_tx(&bar[buf], bytes);
+        bulk_g2s_chunks(kinv + (size_t)buf * kst, Wb + (size_t)b * kst, bytes, &bar[buf]);
+    };
+    // blocks 0 and 1 into index slots 0 and 1
+    if (t == 0) issue_kinv(0, 0);
+    for (int b = 0; b < 2 && b < d.p; ++b) {
+        const int sb = lay.size(b), ob = lay.offset(b);
+        if (t < sb) {
+            const int j = perm[ob + t];
+            idxb[b * SB + t] = j;
+            cstb[b * SB + t] = cst[j];
+            evb[b * SB + t] = e ? e[j] : 0.0;
+            if (b == 0) prefetch_l2_bulk(As + (size_t)j * ld, colbytes);
+        }
+    }
+    __syncthreads();
+    int cs = 0;                                   // index slot of block i
     for (int i = 0; i < d.p; ++i) {
-        const int s = lay.size(i), off = lay.offset(i);
-        for (int q = threadIdx.x; q < s; q += blockDim.x) idx[q] = perm[off + q];
-        __syncthreads();
+        const int cb = i & 1, nb = cb ^ 1;
+        const int ns = cs == 2 ? 0 : cs + 1, n2 = ns == 2 ? 0 : ns + 1;
+        const int s = lay.size(i);
+        const int *idx = idxb + cs * SB;
+        const bool more = i + 1 < d.p;
+        const int sn = more ? lay.size(i + 1) : 0;
+        const int s2 = i + 2 < d.p ? lay.size(i + 2) : 0;
+        if (t == 0 && more) issue_kinv(i + 1, nb);
+        if (t >= 192 && t - 192 < sn)
+            prefetch_l2_bulk(As + (size_t)idxb[ns * SB + t - 192] * ld, colbytes);
+        int j2 = 0;
+        if (t < s2) j2 = perm[lay.offset(i + 2) + t];
+        // gradient and rhs
         {
-            const int q = threadIdx.x / TPC, sub = threadIdx.x % TPC;
-            TA acc = 0;
-            if (q < s) {
-                const size_t col = (size_t)idx[q];
-                for (int sl = sub; sl < d.nslab; sl += TPC) {
-                    const TS *seg = As + ((size_t)sl * n + col) * R;
-                    const TA *dr = dres + sl * R;
-                    for (int rr = 0; rr < R; ++rr) acc += (TA)to_f(seg[rr]) * dr[rr];
+            const double bt = beta * tc - mu;
+            const int sub = lane & (lpc - 1), csl = lane / lpc;
+            for (int q0 = warp * cpw; q0 < s; q0 += 8 * GC * cpw) {
+                int qq[GC];
+                bool vq[GC];
+                const TS *cp[GC];
+                TA ac[GC];
+#pragma unroll
+                for (int u = 0; u < GC; ++u) {
+                    qq[u] = q0 + csl + 8 * cpw * u;
+                    vq[u] = qq[u] < s;
+                    cp[u] = As + (size_t)(vq[u] ? idx[qq[u]] : 0) * ld;
+                    ac[u] = 0;
+                }
+#pragma unroll 4
+                for (int v = sub; v < nvec; v += lpc) {
+                    TA rv[VN];
+                    lds_vec<TA, VN>(dres + v * VN, rv);
+#pragma unroll
+                    for (int u = 0; u < GC; ++u) {
+                        if (vq[u]) {
+                            TA o[VN];
+                            unpack(ldg16(cp[u] + (size_t)v * VN), o);
+#pragma unroll
+                            for (int k = 0; k < VN; ++k) ac[u] = fma(o[k], rv[k], ac[u]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < GC; ++u)
+                    for (int o = lpc >> 1; o > 0; o >>= 1)
+                        ac[u] += __shfl_xor_sync(0xffffffffu, ac[u], o);
+                if (sub == 0) {
+#pragma unroll
+                    for (int u = 0; u < GC; ++u)
+                        if (vq[u])
+                            rhs[qq[u]] = (TA)(cstb[cs * SB + qq[u]] + (double)ac[u] +
+                                              evb[cs * SB + qq[u]] * bt);
                 }
             }
-            for (int o = TPC >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, TPC);
-            if (q < s && sub == 0) {
-                const int j = idx[q];
-                double r = ga[j] + (double)acc - xi[j] + gamma * (x[j] - z[j]);
-                if (e) r += e[j] * (beta * t - mu);
-                rhs[q] = (TA)r;
+        }
+        __syncthreads();
+        // constants of block i + 2: issued now, stored after the solve
+        double c2 = 0.0, e2 = 0.0;
+        if (t < s2) {
+            c2 = cst[j2];
+            e2 = e ? e[j2] : 0.0;
+        }
+        // solve: dl = -K^{-1} rhs
+        mbar_wait(&bar[cb], (uint32_t)(i >> 1) & 1u, err, kBarrierTimeoutNs);
+        {
+            const TA *K = kinv + (size_t)cb * kst;
+            TA rl[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) rl[c] = (lane + 32 * c < s) ? rhs[lane + 32 * c] : TA(0);
+            TA part[RPW];
+#pragma unroll
+            for (int rr = 0; rr < RPW; ++rr) {
+                const int r = warp + 8 * rr;
+                TA a = 0;
+                if (r < s) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c)
+                        if (lane + 32 * c < s) a = fma(K[(size_t)r * s + lane + 32 * c], rl[c], a);
+                }
+                part[rr] = a;
+            }
+#pragma unroll
+            for (int rr = 0; rr < RPW; ++rr) part[rr] = warp_sum(part[rr]);
+            double tl = 0.0;
+            if (lane == 0) {
+#pragma unroll
+                for (int rr = 0; rr < RPW; ++rr) {
+                    const int r = warp + 8 * rr;
+                    if (r < s) {
+                        const TA dl = -part[rr];
+                        dlb[r] = dl;
+                        dx[idx[r]] = (double)dl;
+                        tl += evb[cs * SB + r] * (double)dl;
+                    }
+                }
+                tpart[warp] = tl;
             }
         }
         __syncthreads();
-        const TA *Kinv = Wb + (size_t)i * kst;
-        for (int r = threadIdx.x; r < s; r += blockDim.x) {
-            TA acc = 0;
-            for (int c = 0; c < s; ++c) acc = fma(Kinv[(size_t)c * s + r], rhs[c], acc);
-            dl[r] = -acc;
+        // update: dres += A~_S dl
+        if (CG == 1) {
+            for (int v = t; v < nvec; v += 256) {
+                TA acc[VN];
+#pragma unroll
+                for (int k = 0; k < VN; ++k) acc[k] = 0;
+#pragma unroll 16
+                for (int q = 0; q < s; ++q) {
+                    TA o[VN];
+                    unpack(ldg16(As + (size_t)idx[q] * ld + (size_t)v * VN), o);
+                    const TA w = dlb[q];
+#pragma unroll
+                    for (int k = 0; k < VN; ++k) acc[k] = fma(o[k], w, acc[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < VN; ++k) dres[v * VN + k] += acc[k];
+            }
+        } else {
+            if (t < CG * nvec) {
+                const int g = t / nvec, v = t - g * nvec;
+                TA acc[VN];
+#pragma unroll
+                for (int k = 0; k < VN; ++k) acc[k] = 0;
+#pragma unroll 16
+                for (int q = g; q < s; q += CG) {
+                    TA o[VN];
+                    unpack(ldg16(As + (size_t)idx[q] * ld + (size_t)v * VN), o);
+                    const TA w = dlb[q];
+#pragma unroll
+                    for (int k = 0; k < VN; ++k) acc[k] = fma(o[k], w, acc[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < VN; ++k) upart[(size_t)g * ld + v * VN + k] = acc[k];
+            }
+            __syncthreads();
+            for (int v = t; v < ld; v += 256) {
+                TA a = dres[v];
+                for (int g = 0; g < CG; ++g) a += upart[(size_t)g * ld + v];
+                dres[v] = a;
+            }
+        }
+        if (t < s2) {
+            idxb[n2 * SB + t] = j2;
+            cstb[n2 * SB + t] = c2;
+            evb[n2 * SB + t] = e2;
         }
         __syncthreads();
-        if (e) {
-            double loc = 0.0;
-            for (int q = threadIdx.x; q < s; q += blockDim.x) loc += e[idx[q]] * (double)dl[q];
-            t += block_sum<double>(loc, dred);
+        if (d.k) {
+            double ts = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) ts += tpart[w];
+            tc += ts;
         }
-        for (int q = threadIdx.x; q < s; q += blockDim.x) dx[idx[q]] = (double)dl[q];
-        for (int rr2 = threadIdx.x; rr2 < rows; rr2 += blockDim.x) {
-            const int sl = rr2 / R, rr = rr2 - sl * R;
-            TA acc = 0;
-            for (int q = 0; q < s; ++q)
-                acc = fma((TA)to_f(As[((size_t)sl * n + idx[q]) * R + rr]), dl[q], acc);
-            dres[rr2] += acc;
-        }
-        __syncthreads();
+        cs = ns;
     }
-    for (int q = threadIdx.x; q < rows; q += blockDim.x) dres_g[q] = (double)dres[q];
-    if (threadIdx.x == 0) d.t = t;
+    for (int v = t; v < ld; v += 256) dres_g[v] = (double)dres[v];
+    if (t == 0) d.t = tc;
+}
+
+template <class TS, class TA, int SB> size_t chain_smem(int smax, int ldmax) {
+    const size_t kst = BlockLayout::pad4((size_t)smax * smax);
+    size_t b = 16 + 2 * kst * sizeof(TA) + (size_t)ldmax * sizeof(TA) + 2 * SB * sizeof(TA);
+    b = (b + 15) & ~(size_t)15;
+    b += 6 * SB * sizeof(double) + 8 * sizeof(double) + 3 * SB * sizeof(int);
+    b = (b + 15) & ~(size_t)15;
+    b += 256 * (size_t)Vec16<TS>::N * sizeof(TA);
+    return b + 16;
 }
 
 // ---------------------------------------------------------------- prox
-__global__ void k_batch_prox(BatchDesc *D, BatchPools P) {
-    BatchDesc &d = D[blockIdx.x];
+// z-block and multiplier ascent (Sec. 1 eq. RAC-ADDM), then the rhs constant
+// cst = g_anchor - xi + gamma (x - z) of the next sweep.
+__global__ void __launch_bounds__(kChunk) k_batch_prox(BatchDesc *D, const int *ccs, int count,
+                                                       BatchPools P) {
+    const int inst = find_instance(ccs, count, blockIdx.x);
+    BatchDesc &d = D[inst];
     if (!d.active) return;
-    double *x = P.x + d.vec, *z = P.z + d.vec, *xi = P.xi + d.vec;
-    const double *dx = P.dx + d.vec;
-    for (int j = threadIdx.x; j < d.n; j += blockDim.x) {
-        const double xv = x[j] + dx[j];
-        const double zv = prox_z(d.phi, xv, xi[j], d.gamma, d.lam1, d.lam2, d.lo, d.hi);
-        x[j] = xv;
-        z[j] = zv;
-        xi[j] = xi[j] - d.gamma * (xv - zv);
-    }
-    if (threadIdx.x == 0 && d.k) d.mu = d.mu - d.beta * d.t;
+    const int chunk = blockIdx.x - d.cc;
+    if (chunk == 0 && threadIdx.x == 0 && d.k) d.mu = d.mu - d.beta * d.t;
+    const int jj = chunk * kChunk + threadIdx.x;
+    if (jj >= d.n) return;
+    const size_t j = d.vec + jj;
+    const double xv = P.x[j] + P.dx[j];
+    const double xij = P.xi[j];
+    const double zv = prox_z(d.phi, xv, xij, d.gamma, d.lam1, d.lam2, d.lo, d.hi);
+    const double xin = xij - d.gamma * (xv - zv);
+    P.x[j] = xv;
+    P.z[j] = zv;
+    P.xi[j] = xin;
+    P.cst[j] = P.ga[j] - xin + d.gamma * (xv - zv);
 }
 
 // ---------------------------------------------------------------- refresh
-// Exact FP64: r = A z - b, g = A^T r + c (the anchor), KKT statistics at z,
-// then dres = A~ (x - z) and t = E x - d.
+// Exact FP64 (Sec. 1 model, the periodic anchor): r = A z - b, g = A^T r + c,
+// KKT statistics at z, then dres = A~ (x - z), t = E x - d and cst.
+// (1) per 256-column chunk: the partial sums of A z (FP64) and A~ (x - z)
+//     (accumulation precision) over the chunk's nonzero entries, for all rows
+constexpr int kRefUnroll = 4;
 template <class TS, class TA>
-__global__ void __launch_bounds__(256) k_batch_refresh(BatchDesc *D, BatchPools P) {
-    __shared__ double red[32];
-    BatchDesc &d = D[blockIdx.x];
+__global__ void __launch_bounds__(kChunk) k_batch_ref_cols(BatchDesc *D, const int *ccs, int count,
+                                                           BatchPools P) {
+    __shared__ int lz[kChunk], lx[kChunk];
+    __shared__ double vz[kChunk];
+    __shared__ TA vx[kChunk];
+    __shared__ int wc[2][kChunk / 32];
+    const int inst = find_instance(ccs, count, blockIdx.x);
+    const BatchDesc &d = D[inst];
     if (!d.active) return;
-    const int m = d.m, n = d.n, R = P.R;
-    const double *A = P.A64 + d.a64;
-    const double *x = P.x + d.vec, *z = P.z + d.vec, *c = P.c + d.vec;
-    const double *e = d.k ? P.e + d.vec : nullptr;
-    double *r = P.rbuf + d.row, *ga = P.ga + d.vec, *dres = P.dres + d.row;
-    const double *b = P.b + d.row;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < n; ++j) acc += A[(size_t)j * m + i] * z[j];
-        r[i] = acc - b[i];
+    const int chunk = blockIdx.x - d.cc;
+    const int j0 = chunk * kChunk, nc = min(kChunk, d.n - j0);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    double zj = 0.0, dj = 0.0;
+    if (t < nc) {
+        zj = P.z[d.vec + j0 + t];
+        dj = P.x[d.vec + j0 + t] - zj;
+    }
+    const TA dja = (TA)dj;
+    const unsigned bz = __ballot_sync(0xffffffffu, zj != 0.0);
+    const unsigned bx = __ballot_sync(0xffffffffu, dja != TA(0));
+    if (lane == 0) {
+        wc[0][warp] = __popc(bz);
+        wc[1][warp] = __popc(bx);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double fro = 0.0;
-    for (int j = warp; j < n; j += nw) {
-        const double *aj = A + (size_t)j * m;
-        double acc = 0.0, sq = 0.0;
-        for (int i = lane; i < m; i += 32) {
-            acc += aj[i] * r[i];
-            sq += aj[i] * aj[i];
+    int oz = 0, ox = 0, nz = 0, nx = 0;
+    for (int w = 0; w < kChunk / 32; ++w) {
+        if (w < warp) {
+            oz += wc[0][w];
+            ox += wc[1][w];
         }
-        acc = warp_sum(acc);
-        fro += warp_sum(sq);
-        if (lane == 0) ga[j] = acc + c[j];
+        nz += wc[0][w];
+        nx += wc[1][w];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (zj != 0.0) {
+        const int pz = oz + __popc(bz & below);
+        lz[pz] = t;
+        vz[pz] = zj;
+    }
+    if (dja != TA(0)) {
+        const int px = ox + __popc(bx & below);
+        lx[px] = t;
+        vx[px] = dja;
     }
     __syncthreads();
-    fro = block_sum<double>(lane == 0 ? fro : 0.0, red);
-    double smax = 0.0, gmax = 0.0, z1 = 0.0, ez = 0.0, ex = 0.0, xz = 0.0, bad = 0.0;
-    const double mu = d.mu;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double zj = z[j], xj = x[j], gj = ga[j];
-        const double v = gj - (e ? e[j] * mu : 0.0);
-        const double sj = kkt_coord(d.phi, v, zj, d.lam1, d.lam2, d.lo, d.hi);
-        if (!isfinite(sj) || !isfinite(xj)) bad = 1.0;
-        smax = fmax(smax, sj);
-        gmax = fmax(gmax, fabs(gj));
-        z1 += fabs(zj);
-        if (e) { ez += e[j] * zj; ex += e[j] * xj; }
-        xz = fmax(xz, fabs(xj - zj));
-    }
-    smax = block_max<double>(smax, red);
-    gmax = block_max<double>(gmax, red);
-    z1 = block_sum<double>(z1, red);
-    ez = block_sum<double>(ez, red);
-    ex = block_sum<double>(ex, red);
-    xz = block_max<double>(xz, red);
-    bad = block_max<double>(bad, red);
-    const TS *As = (const TS *)P.As + d.as;
-    for (int rr2 = threadIdx.x; rr2 < d.rows; rr2 += blockDim.x) {
-        const int sl = rr2 / R, rr = rr2 - sl * R;
-        TA acc = 0;
-        for (int j = 0; j < n; ++j)
-            acc += (TA)to_f(As[((size_t)sl * n + j) * R + rr]) * (TA)(x[j] - z[j]);
-        dres[rr2] = (double)acc;
-    }
-    if (threadIdx.x == 0) {
-        d.stat = smax;
-        d.gmax = gmax;
-        d.znorm1 = z1;
-        d.ez = ez - d.d;
-        d.ex = ex - d.d;
-        d.xz = xz;
-        d.nonfinite = bad != 0.0;
-        d.t = ex - d.d;
-        d.fro2 = fro;
+    const int m = d.m, ld = d.ld;
+    const double *A = P.A64 + d.a64 + (size_t)j0 * m;
+    const TS *At = (const TS *)P.As + d.as + (size_t)j0 * ld;
+    double *rp = P.rpart + d.part + (size_t)chunk * ld;
+    double *dp = P.dpart + d.part + (size_t)chunk * ld;
+    for (int i = t; i < ld; i += kChunk) {
+        double ar = 0.0;
+        if (i < m) {
+            int k = 0;
+            for (; k + kRefUnroll <= nz; k += kRefUnroll) {
+                double a[kRefUnroll];
+#pragma unroll
+                for (int u = 0; u < kRefUnroll; ++u) a[u] = A[(size_t)lz[k + u] * m + i];
+#pragma unroll
+                for (int u = 0; u < kRefUnroll; ++u) ar = fma(a[u], vz[k + u], ar);
+            }
+            for (; k < nz; ++k) ar = fma(A[(size_t)lz[k] * m + i], vz[k], ar);
+        }
+        TA ad = 0;
+        {
+            int k = 0;
+            for (; k + kRefUnroll <= nx; k += kRefUnroll) {
+                TA a[kRefUnroll];
+#pragma unroll
+                for (int u = 0; u < kRefUnroll; ++u) a[u] = (TA)to_f(At[(size_t)lx[k + u] * ld + i]);
+#pragma unroll
+                for (int u = 0; u < kRefUnroll; ++u) ad = fma(a[u], vx[k + u], ad);
+            }
+            for (; k < nx; ++k) ad = fma((TA)to_f(At[(size_t)lx[k] * ld + i]), vx[k], ad);
+        }
+        rp[i] = ar;
+        dp[i] = (double)ad;
     }
 }
 
-// slab copy of one instance
+// (2) per instance and row: r = sum of the chunk partials - b, dres likewise
+__global__ void __launch_bounds__(256) k_batch_ref_rows(BatchDesc *D, BatchPools P) {
+    const BatchDesc &d = D[blockIdx.y];
+    if (!d.active) return;
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= d.ld) return;
+    const int nch = (d.n + kChunk - 1) / kChunk;
+    const double *rp = P.rpart + d.part + i, *dp = P.dpart + d.part + i;
+    double r = 0.0, dr = 0.0;
+    for (int c = 0; c < nch; ++c) {
+        r += rp[(size_t)c * d.ld];
+        dr += dp[(size_t)c * d.ld];
+    }
+    P.rbuf[d.row + i] = i < d.m ? r - P.b[d.row + i] : 0.0;
+    P.dres[d.row + i] = dr;
+}
+
+// (3) per 256-column chunk: g_j = A_j^T r + c_j (one warp per column), the
+//     per-coordinate KKT terms and the chunk's statistics; cst_j
+template <bool FRO>
+__global__ void __launch_bounds__(kChunk) k_batch_ref_grad(BatchDesc *D, const int *ccs, int count,
+                                                           BatchPools P) {
+    extern __shared__ double rs[];   // r (m values)
+    __shared__ double wst[kChunk / 32][kStats];
+    const int inst = find_instance(ccs, count, blockIdx.x);
+    const BatchDesc &d = D[inst];
+    if (!d.active) return;
+    const int chunk = blockIdx.x - d.cc;
+    const int j0 = chunk * kChunk, nc = min(kChunk, d.n - j0);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int m = d.m;
+    for (int i = t; i < m; i += kChunk) rs[i] = P.rbuf[d.row + i];
+    __syncthreads();
+    const double *e = d.k ? P.e + d.vec : nullptr;
+    double st[kStats] = {0, 0, 0, 0, 0, 0, 0, 0};   // stat, gmax, |z|_1, ez, ex, xz, bad, fro
+    for (int jj = warp; jj < nc; jj += kChunk / 32) {
+        const int j = j0 + jj;
+        const double *aj = P.A64 + d.a64 + (size_t)j * m;
+        double a0 = 0.0, a1 = 0.0, q0 = 0.0;
+        int i = lane;
+        for (; i + 32 < m; i += 64) {
+            const double u = aj[i], v = aj[i + 32];
+            a0 = fma(u, rs[i], a0);
+            a1 = fma(v, rs[i + 32], a1);
+            if (FRO) q0 = fma(u, u, fma(v, v, q0));
+        }
+        if (i < m) {
+            const double u = aj[i];
+            a0 = fma(u, rs[i], a0);
+            if (FRO) q0 = fma(u, u, q0);
+        }
+        const double g = warp_sum(a0 + a1) + P.c[d.vec + j];
+        if (FRO) q0 = warp_sum(q0);
+        if (lane == 0) {
+            const size_t jv = d.vec + j;
+            const double zj = P.z[jv], xj = P.x[jv], xij = P.xi[jv];
+            P.ga[jv] = g;
+            P.cst[jv] = g - xij + d.gamma * (xj - zj);
+            const double ej = e ? e[j] : 0.0;
+            const double sj = kkt_coord(d.phi, g - ej * d.mu, zj, d.lam1, d.lam2, d.lo, d.hi);
+            if (!isfinite(sj) || !isfinite(xj)) st[6] = 1.0;
+            st[0] = fmax(st[0], sj);
+            st[1] = fmax(st[1], fabs(g));
+            st[2] += fabs(zj);
+            st[3] += ej * zj;
+            st[4] += ej * xj;
+            st[5] = fmax(st[5], fabs(xj - zj));
+            st[7] += q0;
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kStats; ++k) wst[warp][k] = st[k];
+    }
+    __syncthreads();
+    if (t < kStats) {
+        const bool mx = t == 0 || t == 1 || t == 5 || t == 6;
+        double a = wst[0][t];
+        for (int w = 1; w < kChunk / 32; ++w) a = mx ? fmax(a, wst[w][t]) : a + wst[w][t];
+        P.spart[(size_t)blockIdx.x * kStats + t] = a;
+    }
+}
+
+// (4) one warp per instance: reduce the chunk statistics in a fixed order
+__global__ void k_batch_ref_stats(BatchDesc *D, int count, BatchPools P, int fro) {
+    const int inst = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (inst >= count) return;
+    BatchDesc &d = D[inst];
+    if (!d.active) return;
+    const int nch = (d.n + kChunk - 1) / kChunk;
+    double st[kStats] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = lane; c < nch; c += 32) {
+        const double *sp = P.spart + (size_t)(d.cc + c) * kStats;
+        st[0] = fmax(st[0], sp[0]);
+        st[1] = fmax(st[1], sp[1]);
+        st[2] += sp[2];
+        st[3] += sp[3];
+        st[4] += sp[4];
+        st[5] = fmax(st[5], sp[5]);
+        st[6] = fmax(st[6], sp[6]);
+        st[7] += sp[7];
+    }
+    st[0] = warp_max(st[0]);
+    st[1] = warp_max(st[1]);
+    st[2] = warp_sum(st[2]);
+    st[3] = warp_sum(st[3]);
+    st[4] = warp_sum(st[4]);
+    st[5] = warp_max(st[5]);
+    st[6] = warp_max(st[6]);
+    st[7] = warp_sum(st[7]);
+    if (lane == 0) {
+        d.stat = st[0];
+        d.gmax = st[1];
+        d.znorm1 = st[2];
+        d.ez = st[3] - d.d;
+        d.ex = st[4] - d.d;
+        d.xz = st[5];
+        d.nonfinite = st[6] != 0.0;
+        d.t = st[4] - d.d;
+        if (fro) d.fro2 = st[7];
+    }
+}
+
+// storage copy of one instance: column-major, leading dimension ld >= m, zero rows below m
 template <class TS>
-__global__ void k_batch_slab(int m, int n, const double *__restrict__ A, int R, int64_t total,
-                             TS *As) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    int rr = (int)(t % R);
-    int64_t qj = t / R;
-    int j = (int)(qj % n);
-    int q = (int)(qj / n);
-    int row = q * R + rr;
-    As[t] = from_d<TS>(row < m ? A[(size_t)j * m + row] : 0.0);
+__global__ void k_batch_convert(int m, int n, int ld, const double *__restrict__ A, TS *As) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)ld * n) return;
+    const int r = (int)(t % ld);
+    const int64_t j = t / ld;
+    As[t] = from_d<TS>(r < m ? A[(size_t)j * m + r] : 0.0);
 }
 
 __global__ void k_batch_advance(int64_t *s, int nb) { *s += nb; }
 
 // ---------------------------------------------------------------- host
 struct BatchRun {
-    int count = 0, store = ST_F64, R = 4, total_blocks = 0, smax_all = 1;
+    int count = 0, store = ST_F64, total_blocks = 0, total_pairs = 0, total_chunks = 0;
+    int smax_all = 1, ld_max = 8, m_max = 1;
     size_t ta = 8, sb = 8;
     cudaStream_t st = nullptr;
     std::vector<BatchDesc> hd;
     BatchDesc *dd = nullptr;
-    int *bp = nullptr;
+    int *bps = nullptr, *pps = nullptr, *ccs = nullptr, *order = nullptr;
     BatchPools P;
     int64_t *sweep_dev = nullptr;
     std::vector<void *> allocs;
@@ -411,40 +1046,72 @@ struct BatchRun {
 };
 
 template <class TS, class TA>
+static cudaError_t batch_factor(BatchRun &B, int s, int *err) {
+    cudaStream_t st = B.st;
+    if constexpr (!std::is_same<TS, double>::value) {
+        if (B.smax_all <= 64) {
+            constexpr size_t smem = factor_tc_smem<TS>();
+            // at least 48 KB of dynamic shared memory caps residency at 4 CTAs
+            // per SM, which is what their 128 tensor-memory columns each allow
+            const size_t req = std::max<size_t>(smem, 48 * 1024);
+            k_batch_factor_tc<TS><<<B.total_pairs, 256, req, st>>>(B.dd, B.pps, B.count, B.P, s, err);
+            return cudaGetLastError();
+        }
+    }
+    constexpr int KC = 128 / (int)sizeof(TS);
+    const size_t fsm = ((128 * sizeof(int) + 15) & ~15) + 3 * 128 * sizeof(TA) + 16 +
+                       (size_t)B.smax_all * (KC + 1) * sizeof(TA) + 16;
+    if (B.smax_all <= 64)
+        k_batch_factor_cc<TS, TA, 8, 8><<<B.total_blocks, 512, fsm, st>>>(B.dd, B.bps, B.count, B.P,
+                                                                           s, err);
+    else
+        k_batch_factor_cc<TS, TA, 4, 32><<<B.total_blocks, 512, fsm, st>>>(B.dd, B.bps, B.count,
+                                                                            B.P, s, err);
+    return cudaGetLastError();
+}
+
+template <class TS, class TA>
+static cudaError_t batch_chain(BatchRun &B, int s, int *err) {
+    if (B.smax_all <= 64) {
+        const size_t sm = chain_smem<TS, TA, 64>(B.smax_all, B.ld_max);
+        k_batch_chain<TS, TA, 64><<<B.count, 256, sm, B.st>>>(B.dd, B.order, B.P, s, err);
+    } else {
+        const size_t sm = chain_smem<TS, TA, 128>(B.smax_all, B.ld_max);
+        k_batch_chain<TS, TA, 128><<<B.count, 256, sm, B.st>>>(B.dd, B.order, B.P, s, err);
+    }
+    return cudaGetLastError();
+}
+
+template <class TS, class TA>
+static cudaError_t batch_refresh_impl(BatchRun &B, bool fro) {
+    cudaStream_t st = B.st;
+    k_batch_ref_cols<TS, TA><<<B.total_chunks, kChunk, 0, st>>>(B.dd, B.ccs, B.count, B.P);
+    k_batch_ref_rows<<<dim3((B.ld_max + 255) / 256, B.count), 256, 0, st>>>(B.dd, B.P);
+    const size_t rsm = (size_t)B.m_max * sizeof(double);
+    if (fro) k_batch_ref_grad<true><<<B.total_chunks, kChunk, rsm, st>>>(B.dd, B.ccs, B.count, B.P);
+    else k_batch_ref_grad<false><<<B.total_chunks, kChunk, rsm, st>>>(B.dd, B.ccs, B.count, B.P);
+    k_batch_ref_stats<<<(B.count + 7) / 8, 256, 0, st>>>(B.dd, B.count, B.P, fro ? 1 : 0);
+    B.launches += 4;
+    return cudaGetLastError();
+}
+
+template <class TS, class TA>
 static cudaError_t batch_enqueue_period(BatchRun &B, int nb, int *err) {
     cudaStream_t st = B.st;
     cudaError_t e;
     const size_t asm_smem = (3 * 2048 + 32) * sizeof(unsigned);
     k_batch_assembly<<<dim3(B.count, nb), 1024, asm_smem, st>>>(B.dd, B.count, B.P, B.sweep_dev);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int smax = B.smax_all;
-    size_t fsm = ((128 * sizeof(int) + 15) & ~15) + 3 * 128 * sizeof(TA) + 16 +
-                 (size_t)smax * B.R * sizeof(TS) + 16;
-    int maxrows = 0;
-    for (auto &d : B.hd) maxrows = std::max(maxrows, d.rows);
-    size_t csm = (size_t)maxrows * sizeof(TA) + 128 * sizeof(int) + 2 * 128 * sizeof(TA) +
-                 64 * sizeof(double) + 32;
-    auto kc = k_batch_chain<TS, TA>;
-    if ((e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm)) !=
-        cudaSuccess)
-        return e;
     for (int s = 0; s < nb; ++s) {
-        if (smax <= 64)
-            k_batch_factor<TS, TA, 8, 8><<<B.total_blocks, 512, fsm, st>>>(B.dd, B.bp, B.count, B.P,
-                                                                            s, err);
-        else
-            k_batch_factor<TS, TA, 4, 32><<<B.total_blocks, 512, fsm, st>>>(B.dd, B.bp, B.count,
-                                                                             B.P, s, err);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        kc<<<B.count, 256, csm, st>>>(B.dd, B.P, s);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_batch_prox<<<B.count, 256, 0, st>>>(B.dd, B.P);
+        if ((e = batch_factor<TS, TA>(B, s, err)) != cudaSuccess) return e;
+        if ((e = batch_chain<TS, TA>(B, s, err)) != cudaSuccess) return e;
+        k_batch_prox<<<B.total_chunks, kChunk, 0, st>>>(B.dd, B.ccs, B.count, B.P);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_batch_refresh<TS, TA><<<B.count, 256, 0, st>>>(B.dd, B.P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    B.launches += 1 + 3 * (int64_t)nb;
+    if ((e = batch_refresh_impl<TS, TA>(B, false)) != cudaSuccess) return e;
     k_batch_advance<<<1, 1, 0, st>>>(B.sweep_dev, nb);
-    B.launches += 3 + 3 * (int64_t)nb;
+    B.launches += 1;
     return cudaGetLastError();
 }
 
@@ -454,12 +1121,50 @@ static cudaError_t batch_period(BatchRun &B, int nb, int *err) {
     return batch_enqueue_period<__nv_bfloat16, float>(B, nb, err);
 }
 
-static cudaError_t batch_refresh(BatchRun &B) {
-    if (B.store == ST_F64) k_batch_refresh<double, double><<<B.count, 256, 0, B.st>>>(B.dd, B.P);
-    else if (B.store == ST_F32) k_batch_refresh<float, float><<<B.count, 256, 0, B.st>>>(B.dd, B.P);
-    else k_batch_refresh<__nv_bfloat16, float><<<B.count, 256, 0, B.st>>>(B.dd, B.P);
-    B.launches += 1;
-    return cudaGetLastError();
+static cudaError_t batch_refresh(BatchRun &B, bool fro) {
+    if (B.store == ST_F64) return batch_refresh_impl<double, double>(B, fro);
+    if (B.store == ST_F32) return batch_refresh_impl<float, float>(B, fro);
+    return batch_refresh_impl<__nv_bfloat16, float>(B, fro);
+}
+
+template <class TS, class TA> static cudaError_t batch_set_attrs(BatchRun &B) {
+    cudaError_t e;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t csm = B.smax_all <= 64 ? chain_smem<TS, TA, 64>(B.smax_all, B.ld_max)
+                                        : chain_smem<TS, TA, 128>(B.smax_all, B.ld_max);
+    if (csm > (size_t)optin) return cudaErrorInvalidValue;   // K_S^{-1} pair does not fit
+    if (B.smax_all <= 64) {
+        auto kc = k_batch_chain<TS, TA, 64>;
+        if ((e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)chain_smem<TS, TA, 64>(B.smax_all, B.ld_max))) != cudaSuccess)
+            return e;
+    } else {
+        auto kc = k_batch_chain<TS, TA, 128>;
+        if ((e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)chain_smem<TS, TA, 128>(B.smax_all, B.ld_max))) != cudaSuccess)
+            return e;
+    }
+    if constexpr (!std::is_same<TS, double>::value) {
+        const size_t req = std::max<size_t>(factor_tc_smem<TS>(), 48 * 1024);
+        if ((e = cudaFuncSetAttribute(k_batch_factor_tc<TS>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)req)) !=
+            cudaSuccess)
+            return e;
+    }
+    const size_t rsm = (size_t)B.m_max * sizeof(double);
+    if ((e = cudaFuncSetAttribute(k_batch_ref_grad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)rsm)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_batch_ref_grad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rsm);
+}
+
+static cudaError_t batch_attrs(BatchRun &B) {
+    if (B.store == ST_F64) return batch_set_attrs<double, double>(B);
+    if (B.store == ST_F32) return batch_set_attrs<float, float>(B);
+    return batch_set_attrs<__nv_bfloat16, float>(B);
 }
 
 }  // namespace rac
@@ -487,11 +1192,10 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     B.store = o->storage;
     B.ta = B.store == ST_F64 ? 8 : 4;
     B.sb = store_bytes(B.store);
-    B.R = slab_rows(B.store);
     const int blk = o->num_blocks <= 0 ? std::max(1, -o->num_blocks) : 0;
     B.hd.resize(count);
-    size_t a64 = 0, as = 0, vec = 0, row = 0, w = 0;
-    int bp = 0;
+    size_t a64 = 0, as = 0, vec = 0, row = 0, w = 0, part = 0;
+    int bp = 0, pp = 0, cc = 0;
     for (int i = 0; i < count; ++i) {
         const rac_problem &pr = probs[i];
         if (!pr.A || pr.m <= 0 || pr.m > 4096 || pr.n <= 0 || pr.n > (1 << 28) || pr.lda < pr.m)
@@ -508,8 +1212,9 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         const int smax = (d.n + d.p - 1) / d.p;
         if (smax > 128) return RAC_ERR_ARG;
         B.smax_all = std::max(B.smax_all, smax);
-        d.nslab = (d.m + B.R - 1) / B.R;
-        d.rows = d.nslab * B.R;
+        d.ld = (d.m + 7) & ~7;
+        B.ld_max = std::max(B.ld_max, d.ld);
+        B.m_max = std::max(B.m_max, d.m);
         d.active = 1;
         d.phi = pr.phi;
         d.k = pr.k;
@@ -525,15 +1230,31 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         d.vec = vec;
         d.row = row;
         d.w = w;
+        d.part = part;
         d.bp = bp;
+        d.pp = pp;
+        d.cc = cc;
+        const int nch = (d.n + kChunk - 1) / kChunk;
         a64 += (size_t)d.m * d.n;
-        as += (size_t)d.nslab * d.n * B.R;
+        as += (size_t)d.ld * d.n;
         vec += d.n;
-        row += d.rows;
+        row += d.ld;
         w += (size_t)d.p * BlockLayout::pad4((size_t)smax * smax);
+        part += (size_t)nch * d.ld;
         bp += d.p;
+        pp += (d.p + 1) / 2;
+        cc += nch;
     }
     B.total_blocks = bp;
+    B.total_pairs = pp;
+    B.total_chunks = cc;
+    // chain CTAs largest first (cost ~ blocks x (rows + the K_S^{-1} read))
+    std::vector<int> ord(count);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        const BatchDesc &x = B.hd[a], &y = B.hd[b];
+        return (double)x.p * (x.ld + 64) > (double)y.p * (y.ld + 64);
+    });
     const int nb_max = std::max(1, o->refresh_every);
     RB_CK(cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking));
     cudaEvent_t ev;
@@ -541,8 +1262,8 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     cudaEventRecord(ev, (cudaStream_t)o->stream);
     cudaStreamWaitEvent(B.st, ev, 0);
     cudaEventDestroy(ev);
-    double *A64, *b, *c, *e, *x, *z, *xi, *dx, *ga, *dres, *rbuf;
-    int *perm, *tidx, *err, *bpd;
+    double *A64, *b, *c, *e, *x, *z, *xi, *dx, *ga, *dres, *rbuf, *cst, *rpart, *dpart, *spart;
+    int *perm, *tidx, *err, *bpd, *ppd, *ccd, *ordd;
     uint64_t *tkey;
     void *As, *W;
     RB_CK(B.alloc(&A64, a64));
@@ -558,13 +1279,20 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     RB_CK(B.alloc(&xi, vec));
     RB_CK(B.alloc(&dx, vec));
     RB_CK(B.alloc(&ga, vec));
+    RB_CK(B.alloc(&cst, vec));
     RB_CK(B.alloc(&dres, row));
     RB_CK(B.alloc(&rbuf, row));
+    RB_CK(B.alloc(&rpart, part));
+    RB_CK(B.alloc(&dpart, part));
+    RB_CK(B.alloc(&spart, (size_t)cc * kStats));
     RB_CK(B.alloc(&perm, (size_t)nb_max * vec));
     RB_CK(B.alloc(&tidx, (size_t)nb_max * vec));
     RB_CK(B.alloc(&tkey, (size_t)nb_max * vec));
     RB_CK(B.alloc(&err, 1));
     RB_CK(B.alloc(&bpd, count));
+    RB_CK(B.alloc(&ppd, count));
+    RB_CK(B.alloc(&ccd, count));
+    RB_CK(B.alloc(&ordd, count));
     RB_CK(B.alloc(&B.dd, count));
     RB_CK(B.alloc(&B.sweep_dev, 1));
     cudaStream_t st = B.st;
@@ -577,11 +1305,13 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     RB_CK(cudaMemsetAsync(dx, 0, vec * sizeof(double), st));
     RB_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     RB_CK(cudaMemsetAsync(B.sweep_dev, 0, sizeof(int64_t), st));
-    std::vector<int> hbp(count);
+    std::vector<int> hbp(count), hpp(count), hcc(count);
     for (int i = 0; i < count; ++i) {
         const rac_problem &pr = probs[i];
         const BatchDesc &d = B.hd[i];
         hbp[i] = d.bp;
+        hpp[i] = d.pp;
+        hcc[i] = d.cc;
         RB_CK(cudaMemcpy2DAsync(A64 + d.a64, (size_t)d.m * sizeof(double), pr.A,
                                 (size_t)pr.lda * sizeof(double), (size_t)d.m * sizeof(double), d.n,
                                 cudaMemcpyDefault, st));
@@ -596,23 +1326,29 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
             RB_CK(cudaMemcpy(&dv, pr.d, sizeof(double), cudaMemcpyDefault));
             B.hd[i].d = dv;
         }
-        const int64_t total = (int64_t)d.nslab * d.n * B.R;
+        const int64_t total = (int64_t)d.ld * d.n;
         const unsigned blocks = (unsigned)((total + 255) / 256);
         if (B.store == ST_F64)
-            k_batch_slab<double><<<blocks, 256, 0, st>>>(d.m, d.n, A64 + d.a64, B.R, total,
-                                                          (double *)As + d.as);
+            k_batch_convert<double><<<blocks, 256, 0, st>>>(d.m, d.n, d.ld, A64 + d.a64,
+                                                            (double *)As + d.as);
         else if (B.store == ST_F32)
-            k_batch_slab<float><<<blocks, 256, 0, st>>>(d.m, d.n, A64 + d.a64, B.R, total,
-                                                         (float *)As + d.as);
+            k_batch_convert<float><<<blocks, 256, 0, st>>>(d.m, d.n, d.ld, A64 + d.a64,
+                                                           (float *)As + d.as);
         else
-            k_batch_slab<__nv_bfloat16><<<blocks, 256, 0, st>>>(d.m, d.n, A64 + d.a64, B.R, total,
-                                                                 (__nv_bfloat16 *)As + d.as);
+            k_batch_convert<__nv_bfloat16><<<blocks, 256, 0, st>>>(d.m, d.n, d.ld, A64 + d.a64,
+                                                                   (__nv_bfloat16 *)As + d.as);
         RB_CK(cudaGetLastError());
         B.launches += 1;
     }
     RB_CK(cudaMemcpyAsync(bpd, hbp.data(), count * sizeof(int), cudaMemcpyHostToDevice, st));
+    RB_CK(cudaMemcpyAsync(ppd, hpp.data(), count * sizeof(int), cudaMemcpyHostToDevice, st));
+    RB_CK(cudaMemcpyAsync(ccd, hcc.data(), count * sizeof(int), cudaMemcpyHostToDevice, st));
+    RB_CK(cudaMemcpyAsync(ordd, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice, st));
     RB_CK(cudaMemcpyAsync(B.dd, B.hd.data(), count * sizeof(BatchDesc), cudaMemcpyHostToDevice, st));
-    B.bp = bpd;
+    B.bps = bpd;
+    B.pps = ppd;
+    B.ccs = ccd;
+    B.order = ordd;
     B.P.A64 = A64;
     B.P.b = b;
     B.P.c = c;
@@ -626,15 +1362,24 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     B.P.ga = ga;
     B.P.dres = dres;
     B.P.rbuf = rbuf;
+    B.P.cst = cst;
+    B.P.rpart = rpart;
+    B.P.dpart = dpart;
+    B.P.spart = spart;
     B.P.perm = perm;
     B.P.tkey = tkey;
     B.P.tidx = tidx;
     B.P.ntot = vec;
-    B.P.R = B.R;
-    cudaFuncSetAttribute(k_batch_assembly, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((3 * 2048 + 32) * sizeof(unsigned)));
+    RB_CK(cudaFuncSetAttribute(k_batch_assembly, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)((3 * 2048 + 32) * sizeof(unsigned))));
+    {
+        const cudaError_t ae = batch_attrs(B);
+        if (ae == cudaErrorInvalidValue) return RAC_ERR_ARG;
+        RB_CK(ae);
+    }
     // initial refresh at z = 0 gives each instance's KKT scale max(1, ||grad(0)||_inf)
-    RB_CK(batch_refresh(B));
+    // and ||A||_F^2; at x = z = 0 the rhs constants do not depend on gamma
+    RB_CK(batch_refresh(B, true));
     RB_CK(cudaMemcpyAsync(B.hd.data(), B.dd, count * sizeof(BatchDesc), cudaMemcpyDeviceToHost, st));
     RB_CK(cudaStreamSynchronize(st));
     std::vector<double> scale(count), kkt(count);
@@ -688,7 +1433,7 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         }
         if (gexec) {
             RB_CK(cudaGraphLaunch(gexec, st));
-            B.launches += 3 + 3 * (int64_t)nb;
+            B.launches += 6 + 3 * (int64_t)nb;
         }
         RB_CK(cudaMemcpyAsync(B.hd.data(), B.dd, count * sizeof(BatchDesc), cudaMemcpyDeviceToHost,
                               st));

@@ -145,11 +145,10 @@ __global__ void __launch_bounds__(1024) k_batch_assembly(BatchDesc *D, int count
 // gathers 64 bytes of one column per K chunk into the 128-byte-swizzled
 // tile; two chunks are in flight (one being multiplied, one being loaded).
 // The inverse is the sweep operator (Goodnight 1979) on the padded 64 x 64
-// matrix in registers: thread (tr, tc) of each 128-thread half owns rows
-// 4 tr .. 4 tr + 3 and columns 8 tc .. 8 tc + 7 of its block; the row after
-// the pivot is published with d - 1 on its diagonal and 1/d beside it, so
-// one update a_ij -= (a_ik / d) v_j serves the whole matrix except the pivot
-// itself (-1/d), with one barrier per pivot.
+// matrix in registers, four pivots at a time: thread (tr, tc) of each
+// 128-thread half owns rows 4 tr .. 4 tr + 3 and columns 8 tc .. 8 tc + 7 of
+// its block, the four pivot rows are published in shared memory, and every
+// thread inverts the 4 x 4 pivot block itself: 16 barriers per inverse.
 constexpr uint32_t kFtTile = 128 * 128;            // one operand tile: 128 rows x 128 bytes
 constexpr int kFtLdF = 65;                         // staged Gram row (floats), padded
 template <class TS> constexpr size_t factor_tc_smem() {
@@ -179,7 +178,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
     __shared__ uint32_t tslot;
     __shared__ int idx[128];
     __shared__ float es[128];
-    __shared__ __align__(16) float vbuf[2][2][68];   // [block][double buffer][row, 1/d]
+    __shared__ __align__(16) float pbuf[2][2 * 4][68];   // [block][double buffer x 4 pivot rows][col]
     const int inst = find_instance(pps, count, blockIdx.x);
     const BatchDesc &d = D[inst];
     if (!d.active) return;
@@ -303,67 +302,138 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
             acc[ru][cu] = v;
         }
     }
-    float *vb = &vbuf[blk][0][0];
+    // block sweep: four pivots per barrier.  Sweeping the index set B (Goodnight
+    // 1979) maps M_BB -> -M_BB^{-1}, M_RB -> M_RB M_BB^{-1}, M_BR -> M_BB^{-1} M_BR,
+    // M_RR -> M_RR - M_RB M_BB^{-1} M_BR; the four rows of B are published in
+    // shared memory, M_RB is read from them by symmetry, and every thread
+    // inverts the 4 x 4 block itself.
+    float *pb = &pbuf[blk][0][0];
     bool bad = false;
     if (tr == 0) {
-        float w[8];
 #pragma unroll
-        for (int cu = 0; cu < 8; ++cu) w[cu] = acc[0][cu];
-        if (tcc == 0) {
-            bad = !(w[0] > 0.f);
-            vb[64] = __frcp_rn(bad ? 1.f : w[0]);
-            w[0] -= 1.f;
+        for (int ru = 0; ru < 4; ++ru) {
+            *reinterpret_cast<float4 *>(&pb[ru * 68 + 8 * tcc]) =
+                make_float4(acc[ru][0], acc[ru][1], acc[ru][2], acc[ru][3]);
+            *reinterpret_cast<float4 *>(&pb[ru * 68 + 8 * tcc + 4]) =
+                make_float4(acc[ru][4], acc[ru][5], acc[ru][6], acc[ru][7]);
         }
-        *reinterpret_cast<float4 *>(&vb[8 * tcc]) = make_float4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<float4 *>(&vb[8 * tcc + 4]) = make_float4(w[4], w[5], w[6], w[7]);
     }
     __syncthreads();
-    const int kmax = max(s0, s1);
-    for (int k = 0; k < kmax; ++k) {
-        const float *vk = vb + (k & 1) * 68;
-        float *vn = vb + ((k + 1) & 1) * 68;
-        const float rd = vk[64];
-        const float4 fr = *reinterpret_cast<const float4 *>(&vk[4 * tr]);
-        const float4 c0 = *reinterpret_cast<const float4 *>(&vk[8 * tcc]);
-        const float4 c1 = *reinterpret_cast<const float4 *>(&vk[8 * tcc + 4]);
-        const float f[4] = {fr.x * rd, fr.y * rd, fr.z * rd, fr.w * rd};
-        const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    const int nbp = (max(s0, s1) + 3) >> 2;
+    for (int bq = 0; bq < nbp; ++bq) {
+        const int k = 4 * bq;
+        const float *Pq = pb + (bq & 1) * 4 * 68;
+        // g = -M_BB^{-1} by four single sweeps of the 4 x 4 block
+        float g[4][4];
 #pragma unroll
-        for (int ru = 0; ru < 4; ++ru)
+        for (int a = 0; a < 4; ++a) {
+            const float4 w = *reinterpret_cast<const float4 *>(&Pq[a * 68 + k]);
+            g[a][0] = w.x; g[a][1] = w.y; g[a][2] = w.z; g[a][3] = w.w;
+        }
 #pragma unroll
-            for (int cu = 0; cu < 8; ++cu) acc[ru][cu] = fmaf(-f[ru], cv[cu], acc[ru][cu]);
-        // the pivot entry: one thread, reached by a warp-uniform branch so the
-        // other warps skip it (tl = 8 tr + tcc, four warps per half)
-        if ((warp & 3) == (((k >> 2) * 8 + (k >> 3)) >> 5)) {
-            if (tr == (k >> 2) && tcc == (k >> 3)) {
+        for (int q = 0; q < 4; ++q) {
+            float dq = g[q][q];
+            if (!(dq > 0.f)) {
+                bad = true;
+                dq = 1.f;
+            }
+            const float rd = __frcp_rn(dq);
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (a == q) continue;
+                const float f = g[a][q] * rd;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (c != q) g[a][c] = fmaf(-f, g[q][c], g[a][c]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (a != q) {
+                    g[a][q] *= rd;
+                    g[q][a] *= rd;
+                }
+            g[q][q] = -rd;
+        }
+        if (tr != bq) {
+            // U = M_RB M_BB^{-1} = -R g with R[ru][a] = M[4 tr + ru][k + a] = M[k + a][4 tr + ru]
+            float U[4][4];
+            {
+                float R[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float4 w = *reinterpret_cast<const float4 *>(&Pq[a * 68 + 4 * tr]);
+                    R[0][a] = w.x; R[1][a] = w.y; R[2][a] = w.z; R[3][a] = w.w;
+                }
 #pragma unroll
                 for (int ru = 0; ru < 4; ++ru)
 #pragma unroll
-                    for (int cu = 0; cu < 8; ++cu)
-                        acc[ru][cu] = (ru == (k & 3) && cu == (k & 7)) ? -rd : acc[ru][cu];
+                    for (int a = 0; a < 4; ++a)
+                        U[ru][a] = -(R[ru][0] * g[0][a] + R[ru][1] * g[1][a] + R[ru][2] * g[2][a] +
+                                     R[ru][3] * g[3][a]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float4 c0 = *reinterpret_cast<const float4 *>(&Pq[a * 68 + 8 * tcc]);
+                const float4 c1 = *reinterpret_cast<const float4 *>(&Pq[a * 68 + 8 * tcc + 4]);
+                const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                    for (int cu = 0; cu < 8; ++cu) acc[ru][cu] = fmaf(-U[ru][a], cv[cu], acc[ru][cu]);
+            }
+            if (tcc == (k >> 3)) {   // the columns of B: M_RB M_BB^{-1}
+                if (k & 4) {
+#pragma unroll
+                    for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[ru][4 + c] = U[ru][c];
+                } else {
+#pragma unroll
+                    for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[ru][c] = U[ru][c];
+                }
+            }
+        } else {
+            // the rows of B: M_BB^{-1} M_BR = -g C outside B, -M_BB^{-1} = g inside
+#pragma unroll
+            for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                for (int cu = 0; cu < 8; ++cu) acc[ru][cu] = 0.f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float4 c0 = *reinterpret_cast<const float4 *>(&Pq[a * 68 + 8 * tcc]);
+                const float4 c1 = *reinterpret_cast<const float4 *>(&Pq[a * 68 + 8 * tcc + 4]);
+                const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                    for (int cu = 0; cu < 8; ++cu) acc[ru][cu] = fmaf(-g[ru][a], cv[cu], acc[ru][cu]);
+            }
+            if (tcc == (k >> 3)) {
+                if (k & 4) {
+#pragma unroll
+                    for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[ru][4 + c] = g[ru][c];
+                } else {
+#pragma unroll
+                    for (int ru = 0; ru < 4; ++ru)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[ru][c] = g[ru][c];
+                }
             }
         }
-        const int k1 = k + 1;
-        if (k1 < kmax && (warp & 3) == ((k1 >> 2) >> 2) && tr == (k1 >> 2)) {
-            const int slot = k1 & 3, kv = k1 & 7;
-            float w[8];
+        // publish the next four rows
+        if (bq + 1 < nbp && tr == bq + 1) {
+            float *Pn = pb + ((bq + 1) & 1) * 4 * 68;
 #pragma unroll
-            for (int cu = 0; cu < 8; ++cu) {
-                const float a0 = acc[0][cu], a1 = acc[1][cu], a2 = acc[2][cu], a3 = acc[3][cu];
-                w[cu] = (slot & 2) ? ((slot & 1) ? a3 : a2) : ((slot & 1) ? a1 : a0);
+            for (int ru = 0; ru < 4; ++ru) {
+                *reinterpret_cast<float4 *>(&Pn[ru * 68 + 8 * tcc]) =
+                    make_float4(acc[ru][0], acc[ru][1], acc[ru][2], acc[ru][3]);
+                *reinterpret_cast<float4 *>(&Pn[ru * 68 + 8 * tcc + 4]) =
+                    make_float4(acc[ru][4], acc[ru][5], acc[ru][6], acc[ru][7]);
             }
-            if (tcc == (k1 >> 3)) {
-                const float e01 = (kv & 1) ? w[1] : w[0], e23 = (kv & 1) ? w[3] : w[2];
-                const float e45 = (kv & 1) ? w[5] : w[4], e67 = (kv & 1) ? w[7] : w[6];
-                const float e03 = (kv & 2) ? e23 : e01, e47 = (kv & 2) ? e67 : e45;
-                const float d1 = (kv & 4) ? e47 : e03;
-                if (!(d1 > 0.f)) bad = true;
-                vn[64] = __frcp_rn(d1 > 0.f ? d1 : 1.f);
-#pragma unroll
-                for (int cu = 0; cu < 8; ++cu) w[cu] -= cu == kv ? 1.f : 0.f;
-            }
-            *reinterpret_cast<float4 *>(&vn[8 * tcc]) = make_float4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<float4 *>(&vn[8 * tcc + 4]) = make_float4(w[4], w[5], w[6], w[7]);
         }
         __syncthreads();
     }
@@ -521,8 +591,8 @@ __global__ void __launch_bounds__(512) k_batch_factor_cc(BatchDesc *D, const int
 //   update    thread v adds sum_q A~[v, S_q] dx_q to its 16-byte slice of
 //             dres (short columns: CG thread groups split S and are summed
 //             in a fixed order)
-// Work for later blocks is started early: K_S^{-1} of block i + 1 arrives by
-// one bulk copy (TMA) issued during block i, the columns of block i + 1 are
+// Work for later blocks is started early: K_S^{-1} arrives by bulk copy (TMA)
+// issued two blocks ahead (one for FP64), the columns of block i + 1 are
 // prefetched into L2 (one bulk prefetch per column) during block i, and the
 // indices and rhs constants of block i + 2 are loaded during block i (three
 // index slots).  Three barriers per block (four when CG > 1).
@@ -530,13 +600,47 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Sum of four per-lane values over 32 lanes: lane l ends with the total of
+// value (2 bit4 + bit3) of l; six shuffles (transposed butterfly).
+template <class T> __device__ __forceinline__ T warp_sum4(T a0, T a1, T a2, T a3, int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8;
+    const T b0 = (h16 ? a2 : a0) + __shfl_xor_sync(0xffffffffu, h16 ? a0 : a2, 16);
+    const T b1 = (h16 ? a3 : a1) + __shfl_xor_sync(0xffffffffu, h16 ? a1 : a3, 16);
+    T c = (h8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h8 ? b0 : b1, 8);
+    c += __shfl_xor_sync(0xffffffffu, c, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+// Sum of eight per-lane values over 32 lanes: lane l ends with the total of
+// value (4 bit4 + 2 bit3 + bit2) of l; nine shuffles.
+template <class T> __device__ __forceinline__ T warp_sum8(const T (&a)[8], int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    T b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        b[k] = (h16 ? a[4 + k] : a[k]) + __shfl_xor_sync(0xffffffffu, h16 ? a[k] : a[4 + k], 16);
+    T c[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        c[k] = (h8 ? b[2 + k] : b[k]) + __shfl_xor_sync(0xffffffffu, h8 ? b[k] : b[2 + k], 8);
+    T e = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h4 ? c[0] : c[1], 4);
+    e += __shfl_xor_sync(0xffffffffu, e, 2);
+    e += __shfl_xor_sync(0xffffffffu, e, 1);
+    return e;
+}
+
 template <class TS, class TA, int SB>
 __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int *order,
                                                         BatchPools P, int slot, int *err) {
     constexpr int VN = Vec16<TS>::N;
+    using VT = typename Vec16<TS>::T;
     constexpr int RPW = SB / 8;                  // solve rows per warp
     constexpr int CPL = SB / 32;                 // solve columns per lane
     constexpr int GC = 4;                        // gradient columns per warp pass
+    constexpr int LB = 4;                        // vectors per column per load batch
+    constexpr int UB = 16;                       // update load batch
+    constexpr int NKB = sizeof(TA) == 4 ? 3 : 2; // K_S^{-1} buffers
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int inst = order[blockIdx.x];
     BatchDesc &d = D[inst];
@@ -546,9 +650,9 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const size_t kst = BlockLayout::pad4((size_t)smax * smax);
     // shared layout
-    uint64_t *bar = (uint64_t *)sm_raw;                                   // 2 mbarriers
-    TA *kinv = (TA *)(sm_raw + 16);                                       // 2 x kst
-    TA *dres = kinv + 2 * kst;                                            // ld
+    uint64_t *bar = (uint64_t *)sm_raw;                                   // NKB mbarriers
+    TA *kinv = (TA *)(sm_raw + 32);                                       // NKB x kst
+    TA *dres = kinv + NKB * kst;                                          // ld
     TA *rhs = dres + ld;                                                  // SB
     TA *dlb = rhs + SB;                                                   // SB
     double *cstb = (double *)(((uintptr_t)(dlb + SB) + 15) & ~(uintptr_t)15);   // 3 x SB
@@ -574,21 +678,21 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     int CG = 1;
     while (CG < 16 && 2 * CG * nvec <= 256) CG <<= 1;
     if (t == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < NKB; ++k) mbar_init(&bar[k], 1);
         mbar_init_fence();
     }
     for (int v = t; v < ld; v += 256) dres[v] = (TA)dres_g[v];
     __syncthreads();
-    auto issue_kinv = [&](int b, int buf) {
-        const int sb = lay.size(b);
+    auto issue_kinv = [&](int b) {
+        const int sb = lay.size(b), buf = b % NKB;
         const uint32_t bytes = (uint32_t)(BlockLayout::pad4((size_t)sb * sb) * sizeof(TA));
         fence_proxy_async_smem();
         mbar_expect_tx(&bar[buf], bytes);
         bulk_g2s_chunks(kinv + (size_t)buf * kst, Wb + (size_t)b * kst, bytes, &bar[buf]);
     };
-    // blocks 0 and 1 into index slots 0 and 1
-    if (t == 0) issue_kinv(0, 0);
+    // K_S^{-1} of blocks 0 .. NKB - 2; indices of blocks 0 and 1 into slots 0 and 1
+    if (t == 0)
+        for (int b = 0; b < NKB - 1 && b < d.p; ++b) issue_kinv(b);
     for (int b = 0; b < 2 && b < d.p; ++b) {
         const int sb = lay.size(b), ob = lay.offset(b);
         if (t < sb) {
@@ -602,19 +706,18 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     __syncthreads();
     int cs = 0;                                   // index slot of block i
     for (int i = 0; i < d.p; ++i) {
-        const int cb = i & 1, nb = cb ^ 1;
         const int ns = cs == 2 ? 0 : cs + 1, n2 = ns == 2 ? 0 : ns + 1;
         const int s = lay.size(i);
         const int *idx = idxb + cs * SB;
-        const bool more = i + 1 < d.p;
-        const int sn = more ? lay.size(i + 1) : 0;
+        const int sn = i + 1 < d.p ? lay.size(i + 1) : 0;
         const int s2 = i + 2 < d.p ? lay.size(i + 2) : 0;
-        if (t == 0 && more) issue_kinv(i + 1, nb);
+        if (t == 0 && i + NKB - 1 < d.p) issue_kinv(i + NKB - 1);
         if (t >= 192 && t - 192 < sn)
             prefetch_l2_bulk(As + (size_t)idxb[ns * SB + t - 192] * ld, colbytes);
         int j2 = 0;
         if (t < s2) j2 = perm[lay.offset(i + 2) + t];
-        // gradient and rhs
+        // gradient and rhs: per warp pass GC columns, loads in batches of
+        // GC x LB vectors issued before any of them is used
         {
             const double bt = beta * tc - mu;
             const int sub = lane & (lpc - 1), csl = lane / lpc;
@@ -630,30 +733,50 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
                     cp[u] = As + (size_t)(vq[u] ? idx[qq[u]] : 0) * ld;
                     ac[u] = 0;
                 }
-#pragma unroll 4
-                for (int v = sub; v < nvec; v += lpc) {
-                    TA rv[VN];
-                    lds_vec<TA, VN>(dres + v * VN, rv);
+                for (int c0 = 0; c0 < nvec; c0 += LB * lpc) {
+                    VT buf[GC][LB];
 #pragma unroll
-                    for (int u = 0; u < GC; ++u) {
-                        if (vq[u]) {
-                            TA o[VN];
-                            unpack(ldg16(cp[u] + (size_t)v * VN), o);
+                    for (int it = 0; it < LB; ++it) {
+                        const int v = c0 + sub + it * lpc;
 #pragma unroll
-                            for (int k = 0; k < VN; ++k) ac[u] = fma(o[k], rv[k], ac[u]);
+                        for (int u = 0; u < GC; ++u)
+                            buf[u][it] = (vq[u] && v < nvec) ? ldg16(cp[u] + (size_t)v * VN) : VT{};
+                    }
+#pragma unroll
+                    for (int it = 0; it < LB; ++it) {
+                        const int v = c0 + sub + it * lpc;
+                        if (v < nvec) {
+                            TA rv[VN];
+                            lds_vec<TA, VN>(dres + v * VN, rv);
+#pragma unroll
+                            for (int u = 0; u < GC; ++u) {
+                                TA o[VN];
+                                unpack(buf[u][it], o);
+#pragma unroll
+                                for (int k = 0; k < VN; ++k) ac[u] = fma(o[k], rv[k], ac[u]);
+                            }
                         }
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < GC; ++u)
-                    for (int o = lpc >> 1; o > 0; o >>= 1)
-                        ac[u] += __shfl_xor_sync(0xffffffffu, ac[u], o);
-                if (sub == 0) {
+                if (lpc == 32) {
+                    const TA tot = warp_sum4(ac[0], ac[1], ac[2], ac[3], lane);
+                    // one column per lane (csl = 0, cpw = 1): lane holds column q0 + 8 u
+                    const int u = 2 * ((lane >> 4) & 1) + ((lane >> 3) & 1);
+                    const int q = q0 + 8 * u;
+                    if ((lane & 7) == 0 && q < s)
+                        rhs[q] = (TA)(cstb[cs * SB + q] + (double)tot + evb[cs * SB + q] * bt);
+                } else {
 #pragma unroll
                     for (int u = 0; u < GC; ++u)
-                        if (vq[u])
-                            rhs[qq[u]] = (TA)(cstb[cs * SB + qq[u]] + (double)ac[u] +
-                                              evb[cs * SB + qq[u]] * bt);
+                        for (int o = lpc >> 1; o > 0; o >>= 1)
+                            ac[u] += __shfl_xor_sync(0xffffffffu, ac[u], o);
+                    if (sub == 0) {
+#pragma unroll
+                        for (int u = 0; u < GC; ++u)
+                            if (vq[u])
+                                rhs[qq[u]] = (TA)(cstb[cs * SB + qq[u]] + (double)ac[u] +
+                                                  evb[cs * SB + qq[u]] * bt);
+                    }
                 }
             }
         }
@@ -664,82 +787,90 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             c2 = cst[j2];
             e2 = e ? e[j2] : 0.0;
         }
-        // solve: dl = -K^{-1} rhs
-        mbar_wait(&bar[cb], (uint32_t)(i >> 1) & 1u, err, kBarrierTimeoutNs);
+        // solve: dl = -K^{-1} rhs; warp w owns rows w + 8 rr
+        mbar_wait(&bar[i % NKB], (uint32_t)(i / NKB) & 1u, err, kBarrierTimeoutNs);
         {
-            const TA *K = kinv + (size_t)cb * kst;
+            const TA *K = kinv + (size_t)(i % NKB) * kst;
             TA rl[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) rl[c] = (lane + 32 * c < s) ? rhs[lane + 32 * c] : TA(0);
-            TA part[RPW];
-#pragma unroll
-            for (int rr = 0; rr < RPW; ++rr) {
-                const int r = warp + 8 * rr;
-                TA a = 0;
-                if (r < s) {
-#pragma unroll
-                    for (int c = 0; c < CPL; ++c)
-                        if (lane + 32 * c < s) a = fma(K[(size_t)r * s + lane + 32 * c], rl[c], a);
-                }
-                part[rr] = a;
-            }
-#pragma unroll
-            for (int rr = 0; rr < RPW; ++rr) part[rr] = warp_sum(part[rr]);
             double tl = 0.0;
-            if (lane == 0) {
 #pragma unroll
-                for (int rr = 0; rr < RPW; ++rr) {
-                    const int r = warp + 8 * rr;
+            for (int h = 0; h < RPW / 8; ++h) {
+                TA part[8];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    const int r = warp + 8 * (8 * h + rr);
+                    TA a = 0;
                     if (r < s) {
-                        const TA dl = -part[rr];
-                        dlb[r] = dl;
-                        dx[idx[r]] = (double)dl;
-                        tl += evb[cs * SB + r] * (double)dl;
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c)
+                            if (lane + 32 * c < s) a = fma(K[(size_t)r * s + lane + 32 * c], rl[c], a);
                     }
+                    part[rr] = a;
                 }
-                tpart[warp] = tl;
+                const TA tot = warp_sum8(part, lane);
+                const int rr = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
+                const int r = warp + 8 * (8 * h + rr);
+                if ((lane & 3) == 0 && r < s) {
+                    const TA dl = -tot;
+                    dlb[r] = dl;
+                    dx[idx[r]] = (double)dl;
+                    tl += evb[cs * SB + r] * (double)dl;
+                }
             }
+            // lanes 0, 4, ..., 28 hold the coupling terms of their rows
+            tl += __shfl_xor_sync(0xffffffffu, tl, 4);
+            tl += __shfl_xor_sync(0xffffffffu, tl, 8);
+            tl += __shfl_xor_sync(0xffffffffu, tl, 16);
+            if (lane == 0) tpart[warp] = tl;
         }
         __syncthreads();
-        // update: dres += A~_S dl
-        if (CG == 1) {
-            for (int v = t; v < nvec; v += 256) {
-                TA acc[VN];
+        // update: dres += A~_S dl, loads in batches of UB columns
+        {
+            const int g = CG == 1 ? 0 : t / nvec;
+            const int v0 = CG == 1 ? t : t - g * nvec;
+            if (t < CG * nvec || CG == 1) {
+                for (int v = v0; v < nvec; v += (CG == 1 ? 256 : nvec)) {
+                    TA acc[VN];
 #pragma unroll
-                for (int k = 0; k < VN; ++k) acc[k] = 0;
-#pragma unroll 16
-                for (int q = 0; q < s; ++q) {
-                    TA o[VN];
-                    unpack(ldg16(As + (size_t)idx[q] * ld + (size_t)v * VN), o);
-                    const TA w = dlb[q];
+                    for (int k = 0; k < VN; ++k) acc[k] = 0;
+                    for (int qb = g; qb < s; qb += UB * CG) {
+                        VT buf[UB];
 #pragma unroll
-                    for (int k = 0; k < VN; ++k) acc[k] = fma(o[k], w, acc[k]);
+                        for (int u = 0; u < UB; ++u) {
+                            const int q = qb + CG * u;
+                            buf[u] = q < s ? ldg16(As + (size_t)idx[q] * ld + (size_t)v * VN) : VT{};
+                        }
+#pragma unroll
+                        for (int u = 0; u < UB; ++u) {
+                            const int q = qb + CG * u;
+                            if (q < s) {
+                                TA o[VN];
+                                unpack(buf[u], o);
+                                const TA w = dlb[q];
+#pragma unroll
+                                for (int k = 0; k < VN; ++k) acc[k] = fma(o[k], w, acc[k]);
+                            }
+                        }
+                    }
+                    if (CG == 1) {
+#pragma unroll
+                        for (int k = 0; k < VN; ++k) dres[v * VN + k] += acc[k];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < VN; ++k) upart[(size_t)g * ld + v * VN + k] = acc[k];
+                    }
+                    if (CG > 1) break;
                 }
-#pragma unroll
-                for (int k = 0; k < VN; ++k) dres[v * VN + k] += acc[k];
             }
-        } else {
-            if (t < CG * nvec) {
-                const int g = t / nvec, v = t - g * nvec;
-                TA acc[VN];
-#pragma unroll
-                for (int k = 0; k < VN; ++k) acc[k] = 0;
-#pragma unroll 16
-                for (int q = g; q < s; q += CG) {
-                    TA o[VN];
-                    unpack(ldg16(As + (size_t)idx[q] * ld + (size_t)v * VN), o);
-                    const TA w = dlb[q];
-#pragma unroll
-                    for (int k = 0; k < VN; ++k) acc[k] = fma(o[k], w, acc[k]);
+            if (CG > 1) {
+                __syncthreads();
+                for (int v = t; v < ld; v += 256) {
+                    TA a = dres[v];
+                    for (int gg = 0; gg < CG; ++gg) a += upart[(size_t)gg * ld + v];
+                    dres[v] = a;
                 }
-#pragma unroll
-                for (int k = 0; k < VN; ++k) upart[(size_t)g * ld + v * VN + k] = acc[k];
-            }
-            __syncthreads();
-            for (int v = t; v < ld; v += 256) {
-                TA a = dres[v];
-                for (int g = 0; g < CG; ++g) a += upart[(size_t)g * ld + v];
-                dres[v] = a;
             }
         }
         if (t < s2) {
@@ -762,7 +893,8 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
 
 template <class TS, class TA, int SB> size_t chain_smem(int smax, int ldmax) {
     const size_t kst = BlockLayout::pad4((size_t)smax * smax);
-    size_t b = 16 + 2 * kst * sizeof(TA) + (size_t)ldmax * sizeof(TA) + 2 * SB * sizeof(TA);
+    const size_t nkb = sizeof(TA) == 4 ? 3 : 2;
+    size_t b = 32 + nkb * kst * sizeof(TA) + (size_t)ldmax * sizeof(TA) + 2 * SB * sizeof(TA);
     b = (b + 15) & ~(size_t)15;
     b += 6 * SB * sizeof(double) + 8 * sizeof(double) + 3 * SB * sizeof(int);
     b = (b + 15) & ~(size_t)15;

@@ -12,7 +12,8 @@ What is here, each piece written from the paper's text:
   random assembly.  Pinned to numpy's independent Philox bit generator.
 * Random assembly of the n primal coordinates into p blocks (Sec. 1,
   eq. RAC-ADDM, "randomly (without replacement) assemble"; Sec. 2, sigma =
-  [sigma_1, ..., sigma_p]).
+  [sigma_1, ..., sigma_p]), and the RP-MBADMM variant of Sec. 1 (a fixed
+  partition visited in a random order).
 * The block argmin of the augmented Lagrangian (Sec. 1, eq. lagrangian and
   eq. RAC-ADDM) in the split form the paper uses for the Elastic-Net
   (Sec. 3.1: x - z = 0 with penalty gamma and dual xi; x partitioned into RAC
@@ -130,6 +131,23 @@ def blocks_from_permutation(perm: np.ndarray, p: int) -> List[np.ndarray]:
 
 def random_assembly(n: int, p: int, seed: int, sweep: int) -> List[np.ndarray]:
     return blocks_from_permutation(random_permutation(n, seed, sweep), p)
+
+
+# RP-MBADMM (Sec. 1: blocks built by a predetermined rule and kept fixed, the
+# block subproblems solved in a random order every iteration).  The rule here
+# is the consecutive partition of 0..n-1 with the same block sizes as above;
+# the order of sweep k is the Philox argsort of the p block indices.
+def fixed_partition(n: int, p: int) -> List[np.ndarray]:
+    return blocks_from_permutation(np.arange(n, dtype=np.int64), p)
+
+
+def rp_order(p: int, seed: int, sweep: int) -> np.ndarray:
+    return random_permutation(p, seed, sweep)
+
+
+def rp_assembly(n: int, p: int, seed: int, sweep: int) -> List[np.ndarray]:
+    blocks = fixed_partition(n, p)
+    return [blocks[b] for b in rp_order(p, seed, sweep)]
 
 
 # ---------------------------------------------------------------------------
@@ -274,12 +292,13 @@ def block_argmin(P: Problem, st: State, S: np.ndarray, beta: float, gamma: float
 
 
 def sweep(P: Problem, st: State, p: int, seed: int, beta: float, gamma: float,
-          blocks: Optional[List[np.ndarray]] = None) -> State:
+          blocks: Optional[List[np.ndarray]] = None, rp: bool = False) -> State:
     """One RAC-MBADMM iteration (eq. RAC-ADDM) in the split form of Sec. 3.1:
     random assembly, cyclic block argmins over the x-blocks, the z-block in
-    closed form, then the multiplier ascent on both constraints."""
+    closed form, then the multiplier ascent on both constraints.  rp=True is
+    the RP-MBADMM iteration (Sec. 1): the fixed partition in a random order."""
     if blocks is None:
-        blocks = random_assembly(P.n, p, seed, st.sweep)
+        blocks = (rp_assembly if rp else random_assembly)(P.n, p, seed, st.sweep)
     for S in blocks:
         block_argmin(P, st, S, beta, gamma)
     st.z = z_block(P, st.x, st.xi, gamma)
@@ -352,14 +371,14 @@ def kkt(P: Problem, z: np.ndarray, mu=None) -> dict:
 
 def solve(P: Problem, p: int, seed: int = 0, beta: float = 1.0, gamma: float = 1.0,
           tol: float = 1e-6, max_sweeps: int = 1000, check_every: int = 1,
-          x0=None, xi0=None, record: bool = False):
+          x0=None, xi0=None, record: bool = False, rp: bool = False):
     """Run sweeps from the initial state until KKT(z) <= tol or max_sweeps.
     Returns (state, info)."""
     st = initial_state(P, x0, xi0)
     hist = []
     k_val = kkt(P, st.z, st.mu if P.E is not None else None)["kkt"]
     while st.sweep < max_sweeps:
-        sweep(P, st, p, seed, beta, gamma)
+        sweep(P, st, p, seed, beta, gamma, rp=rp)
         if record:
             hist.append(st.copy())
         if st.sweep % check_every == 0 or st.sweep == max_sweeps:

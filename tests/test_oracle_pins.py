@@ -385,3 +385,66 @@ def test_cd_matches_rac_medium():
     st, info = O.solve(P, 7, seed=3, tol=1e-11, max_sweeps=5000)
     assert np.abs(st.z - x).max() < 1e-9
     assert np.array_equal(st.z != 0, x != 0)
+
+
+# ---------------------------------------------------------------------------
+# RP-MBADMM (Sec. 1): a fixed partition whose blocks are solved in a random
+# order every iteration.
+# ---------------------------------------------------------------------------
+def test_rp_fixed_partition_and_random_order():
+    """Every RP sweep visits the blocks of one fixed partition exactly once,
+    the orders are permutations of 0..p-1, and all p! orders occur about
+    equally often."""
+    n, p = 23, 4
+    fixed = O.fixed_partition(n, p)
+    assert [len(b) for b in fixed] == O.block_sizes(n, p)
+    assert np.array_equal(np.concatenate(fixed), np.arange(n))
+    counts = {}
+    for k in range(2400):
+        order = O.rp_order(p, 5, k)
+        assert sorted(order.tolist()) == list(range(p))
+        blocks = O.rp_assembly(n, p, 5, k)
+        for b, S in zip(order, blocks):
+            assert np.array_equal(S, fixed[b])
+        counts[tuple(order)] = counts.get(tuple(order), 0) + 1
+    assert len(counts) == 24
+    assert min(counts.values()) > 100 * 0.6 and max(counts.values()) < 100 * 1.4
+
+
+def test_rp_one_block_equals_rac_one_block():
+    """With p = 1 there is no order to draw: RP and RAC run the same
+    iteration (the single block argmin is the whole x-minimisation)."""
+    inst = synth.small_instance(2, 40, 12, 3, lam2=0.1)
+    P = O.problem_from_instance(inst)
+    a, b = O.initial_state(P), O.initial_state(P)
+    for _ in range(15):
+        O.sweep(P, a, 1, 3, 1.0, 1.0)
+        O.sweep(P, b, 1, 3, 1.0, 1.0, rp=True)
+    assert np.abs(a.z - b.z).max() < 1e-12
+    assert np.abs(a.xi - b.xi).max() < 1e-12
+
+
+@pytest.mark.parametrize("seed,lam2", [(0, 0.0), (1, 0.2)])
+def test_rp_lasso_matches_enumeration(seed, lam2):
+    """The RP fixed point is the LASSO / Elastic-Net solution (brute-force
+    active-set enumeration and coordinate descent)."""
+    inst = synth.small_instance(seed, 30, 8, 3, lam2=lam2)
+    P = O.problem_from_instance(inst)
+    ref = O.enum_lasso(inst.A, inst.b, inst.lam1, lam2)
+    st, info = O.solve(P, 3, seed=seed, tol=1e-12, max_sweeps=8000, rp=True)
+    assert info["kkt"] <= 1e-12
+    assert np.abs(st.z - ref).max() < 1e-9
+    assert np.array_equal(st.z != 0, ref != 0)
+
+
+def test_rp_svm_matches_enumeration():
+    """The RP fixed point of the SVM dual is the enumerated optimum."""
+    inst = _svm_tiny(1)
+    P = O.problem_from_instance(inst)
+    Q = inst.A.T @ inst.A
+    a_enum, _ = O.enum_svm(Q, inst.E[0], 1.0)
+    st, info = O.solve(P, inst.num_blocks, seed=4, beta=inst.beta, gamma=inst.gamma,
+                       tol=1e-9, max_sweeps=30000, rp=True)
+    assert info["kkt"] <= 1e-9
+    obj = lambda a: 0.5 * a @ Q @ a - a.sum()
+    assert abs(obj(st.z) - obj(a_enum)) < 1e-7

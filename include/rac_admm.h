@@ -126,6 +126,12 @@ typedef struct {
                                of 2, 4 or 8 as n grows past 1024, 2048;
                                falls back to 1 where it does not apply).  Same iterates up to
                                floating-point summation order. */
+    int32_t assembly;       /* 0 = RAC: a random assembly of the coordinates into blocks every
+                               sweep (Sec. 1, eq. RAC-ADDM); 1 = RP: the consecutive partition
+                               of 0..n-1 (same block sizes) kept fixed and its blocks solved in
+                               a random order every sweep (RP-MBADMM, Sec. 1), so the block
+                               factors are computed once per penalty.  RP is implemented by
+                               rac_admm_batch; rac_admm_setup returns RAC_ERR_ARG for it. */
 } rac_options;
 
 /* KKT measure used for the stop test, evaluated in FP64 on z with the exact

@@ -22,6 +22,7 @@ RAC_ERR_NOT_CONVERGED, RAC_ERR_STATE = 7, 8
 PHI = {"none": 0, "l1l2": 1, "box": 2}
 STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2}
 CHAIN = {"auto": 0, "grid": 1, "cluster": 2}
+ASSEMBLY = {"rac": 0, "rp": 1}
 FORM = {"auto": 0, "gram": 1, "residual": 2}
 
 
@@ -37,7 +38,8 @@ class RacOptions(ctypes.Structure):
                 ("tol", c_double), ("max_sweeps", c_int32), ("refresh_every", c_int32),
                 ("seed", c_uint64), ("storage", c_int32), ("form", c_int32), ("grid", c_int32),
                 ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p), ("profile", c_int32),
-                ("xi0_from_grad", c_int32), ("ws_fallback", c_int32), ("chain", c_int32)]
+                ("xi0_from_grad", c_int32), ("ws_fallback", c_int32), ("chain", c_int32),
+                ("assembly", c_int32)]
 
 
 class RacInfo(ctypes.Structure):

@@ -93,7 +93,7 @@ def make_problem(keep: _Keep, A=None, b=None, *, H=None, c=None, E=None, d=None,
 def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=1e-6,
                  max_sweeps=1000, refresh_every=10, seed=0, storage="fp64", form="auto",
                  grid=0, x0=None, xi0=None, stream=None, profile=False, xi0_from_grad=False,
-                 ws_fallback=False, chain="auto") -> L.RacOptions:
+                 ws_fallback=False, chain="auto", assembly="rac") -> L.RacOptions:
     o = L.RacOptions()
     L.load().rac_options_default(ctypes.byref(o))
     o.num_blocks = int(num_blocks)
@@ -110,6 +110,7 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
     o.xi0_from_grad = int(xi0_from_grad)
     o.ws_fallback = 1 if ws_fallback else 0
     o.chain = L.CHAIN[chain]
+    o.assembly = L.ASSEMBLY[assembly]
     return o
 
 

@@ -764,6 +764,7 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
     if (!(o->beta > 0) || !std::isfinite(o->gamma) || !(o->tol >= 0) || o->max_sweeps < 0)
         return RAC_ERR_ARG;
     if (o->storage < RAC_FP64 || o->storage > RAC_BF16) return RAC_ERR_ARG;
+    if (o->assembly != 0) return RAC_ERR_ARG;   // RP: batched form only
     if (o->form == RAC_FORM_RESIDUAL && !pr->A) return RAC_ERR_ARG;
     int64_t smax = (pr->n + o->num_blocks - 1) / o->num_blocks;
     if (smax > 4096) return RAC_ERR_ARG;

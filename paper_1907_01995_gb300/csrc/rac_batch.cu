@@ -71,6 +71,7 @@ struct BatchPools {
     uint64_t *tkey;
     int *tidx;
     size_t ntot;       // sum of n_i (one permutation slot)
+    int rp;            // 1: RP-MBADMM (fixed partition, perm slots hold block orders)
 };
 
 __device__ __forceinline__ int find_instance(const int *start, int count, int unit) {
@@ -128,8 +129,12 @@ __global__ void __launch_bounds__(1024) k_batch_assembly(BatchDesc *D, int count
     if (!d.active) return;
     const uint64_t k = (uint64_t)(*sweep_dev + slot);
     const size_t base = (size_t)slot * P.ntot + d.vec;
-    assemble_one(d.n, d.p, d.seed, k, P.perm + base, nullptr, P.tkey + base, P.tidx + base,
-                 assembly_log2_buckets(d.n), sm_u);
+    if (P.rp)   // the order of the p fixed blocks: the same argsort over block indices
+        assemble_one(d.p, d.p, d.seed, k, P.perm + base, nullptr, P.tkey + base, P.tidx + base,
+                     assembly_log2_buckets(d.p), sm_u);
+    else
+        assemble_one(d.n, d.p, d.seed, k, P.perm + base, nullptr, P.tkey + base, P.tidx + base,
+                     assembly_log2_buckets(d.n), sm_u);
 }
 
 // ---------------------------------------------------------------- factor (tensor cores)
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
         const int blk = t >> 6, q = t & 63;
         const int sb = blk ? s1 : s0;
         int j = -1;
-        if (q < sb) j = perm[lay.offset(blk ? b1 : b0) + q];
+        if (q < sb) j = P.rp ? lay.offset(blk ? b1 : b0) + q : perm[lay.offset(blk ? b1 : b0) + q];
         idx[t] = j;
         es[t] = (j >= 0 && d.k) ? (float)P.e[d.vec + j] : 0.f;
     }
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(512) k_batch_factor_cc(BatchDesc *D, const int
     const int r = threadIdx.x / NP, c0 = threadIdx.x % NP;
     const bool rv = r < s;
     for (int t = threadIdx.x; t < s; t += T) {
-        const int j = perm[off + t];
+        const int j = P.rp ? off + t : perm[off + t];
         idx[t] = j;
         es[t] = d.k ? (TA)P.e[d.vec + j] : TA(0);
     }
@@ -683,20 +688,24 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     }
     for (int v = t; v < ld; v += 256) dres[v] = (TA)dres_g[v];
     __syncthreads();
-    auto issue_kinv = [&](int b) {
-        const int sb = lay.size(b), buf = b % NKB;
+    // block solved at step i: i itself (RAC), or the i-th of this sweep's
+    // random order of the fixed partition (RP, whose columns are consecutive)
+    const bool rp = P.rp != 0;
+    auto blk = [&](int i) { return rp ? perm[i] : i; };
+    auto issue_kinv = [&](int i) {
+        const int b = blk(i), sb = lay.size(b), buf = i % NKB;
         const uint32_t bytes = (uint32_t)(BlockLayout::pad4((size_t)sb * sb) * sizeof(TA));
         fence_proxy_async_smem();
         mbar_expect_tx(&bar[buf], bytes);
         bulk_g2s_chunks(kinv + (size_t)buf * kst, Wb + (size_t)b * kst, bytes, &bar[buf]);
     };
-    // K_S^{-1} of blocks 0 .. NKB - 2; indices of blocks 0 and 1 into slots 0 and 1
+    // K_S^{-1} of steps 0 .. NKB - 2; indices of steps 0 and 1 into slots 0 and 1
     if (t == 0)
         for (int b = 0; b < NKB - 1 && b < d.p; ++b) issue_kinv(b);
     for (int b = 0; b < 2 && b < d.p; ++b) {
-        const int sb = lay.size(b), ob = lay.offset(b);
+        const int bb = blk(b), sb = lay.size(bb), ob = lay.offset(bb);
         if (t < sb) {
-            const int j = perm[ob + t];
+            const int j = rp ? ob + t : perm[ob + t];
             idxb[b * SB + t] = j;
             cstb[b * SB + t] = cst[j];
             evb[b * SB + t] = e ? e[j] : 0.0;
@@ -707,15 +716,16 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     int cs = 0;                                   // index slot of block i
     for (int i = 0; i < d.p; ++i) {
         const int ns = cs == 2 ? 0 : cs + 1, n2 = ns == 2 ? 0 : ns + 1;
-        const int s = lay.size(i);
+        const int s = lay.size(blk(i));
         const int *idx = idxb + cs * SB;
-        const int sn = i + 1 < d.p ? lay.size(i + 1) : 0;
-        const int s2 = i + 2 < d.p ? lay.size(i + 2) : 0;
+        const int sn = i + 1 < d.p ? lay.size(blk(i + 1)) : 0;
+        const int b2 = i + 2 < d.p ? blk(i + 2) : 0;
+        const int s2 = i + 2 < d.p ? lay.size(b2) : 0;
         if (t == 0 && i + NKB - 1 < d.p) issue_kinv(i + NKB - 1);
         if (t >= 192 && t - 192 < sn)
             prefetch_l2_bulk(As + (size_t)idxb[ns * SB + t - 192] * ld, colbytes);
         int j2 = 0;
-        if (t < s2) j2 = perm[lay.offset(i + 2) + t];
+        if (t < s2) j2 = rp ? lay.offset(b2) + t : perm[lay.offset(b2) + t];
         // gradient and rhs: per warp pass GC columns, loads in batches of
         // GC x LB vectors issued before any of them is used
         {
@@ -1153,6 +1163,7 @@ __global__ void k_batch_advance(int64_t *s, int nb) { *s += nb; }
 struct BatchRun {
     int count = 0, store = ST_F64, total_blocks = 0, total_pairs = 0, total_chunks = 0;
     int smax_all = 1, ld_max = 8, m_max = 1;
+    bool rp = false;
     size_t ta = 8, sb = 8;
     cudaStream_t st = nullptr;
     std::vector<BatchDesc> hd;
@@ -1235,12 +1246,13 @@ static cudaError_t batch_enqueue_period(BatchRun &B, int nb, int *err) {
     k_batch_assembly<<<dim3(B.count, nb), 1024, asm_smem, st>>>(B.dd, B.count, B.P, B.sweep_dev);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int s = 0; s < nb; ++s) {
-        if ((e = batch_factor<TS, TA>(B, s, err)) != cudaSuccess) return e;
+        // RP: the fixed blocks were factored once, before the first period
+        if (!B.rp && (e = batch_factor<TS, TA>(B, s, err)) != cudaSuccess) return e;
         if ((e = batch_chain<TS, TA>(B, s, err)) != cudaSuccess) return e;
         k_batch_prox<<<B.total_chunks, kChunk, 0, st>>>(B.dd, B.ccs, B.count, B.P);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    B.launches += 1 + 3 * (int64_t)nb;
+    B.launches += 1 + (B.rp ? 2 : 3) * (int64_t)nb;
     if ((e = batch_refresh_impl<TS, TA>(B, false)) != cudaSuccess) return e;
     k_batch_advance<<<1, 1, 0, st>>>(B.sweep_dev, nb);
     B.launches += 1;
@@ -1251,6 +1263,13 @@ static cudaError_t batch_period(BatchRun &B, int nb, int *err) {
     if (B.store == ST_F64) return batch_enqueue_period<double, double>(B, nb, err);
     if (B.store == ST_F32) return batch_enqueue_period<float, float>(B, nb, err);
     return batch_enqueue_period<__nv_bfloat16, float>(B, nb, err);
+}
+
+static cudaError_t batch_factor_once(BatchRun &B, int *err) {
+    B.launches += 1;
+    if (B.store == ST_F64) return batch_factor<double, double>(B, 0, err);
+    if (B.store == ST_F32) return batch_factor<float, float>(B, 0, err);
+    return batch_factor<__nv_bfloat16, float>(B, 0, err);
 }
 
 static cudaError_t batch_refresh(BatchRun &B, bool fro) {
@@ -1317,11 +1336,13 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     if (count <= 0 || !probs || !o || !x_out) return RAC_ERR_ARG;
     if (o->storage < RAC_FP64 || o->storage > RAC_BF16 || !(o->tol >= 0) || o->max_sweeps < 0)
         return RAC_ERR_ARG;
+    if (o->assembly < 0 || o->assembly > 1) return RAC_ERR_ARG;
     auto t0 = std::chrono::steady_clock::now();
     (void)cudaGetLastError();
     BatchRun B;
     B.count = count;
     B.store = o->storage;
+    B.rp = o->assembly == 1;
     B.ta = B.store == ST_F64 ? 8 : 4;
     B.sb = store_bytes(B.store);
     const int blk = o->num_blocks <= 0 ? std::max(1, -o->num_blocks) : 0;
@@ -1502,6 +1523,7 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     B.P.tkey = tkey;
     B.P.tidx = tidx;
     B.P.ntot = vec;
+    B.P.rp = B.rp ? 1 : 0;
     RB_CK(cudaFuncSetAttribute(k_batch_assembly, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)((3 * 2048 + 32) * sizeof(unsigned))));
     {
@@ -1527,6 +1549,12 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         // reset (dres) does not depend on gamma, so only the descriptors change
         for (int i = 0; i < count; ++i)
             B.hd[i].gamma = -o->gamma * std::max(B.hd[i].fro2 / B.hd[i].n, 1e-300);
+    }
+    if (B.rp) {
+        // the fixed blocks' K_S^{-1} with the final penalties
+        RB_CK(cudaMemcpyAsync(B.dd, B.hd.data(), count * sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                              st));
+        RB_CK(batch_factor_once(B, err));
     }
     int active = 0;
     for (int i = 0; i < count; ++i) {
@@ -1565,7 +1593,7 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         }
         if (gexec) {
             RB_CK(cudaGraphLaunch(gexec, st));
-            B.launches += 6 + 3 * (int64_t)nb;
+            B.launches += 6 + (B.rp ? 2 : 3) * (int64_t)nb;
         }
         RB_CK(cudaMemcpyAsync(B.hd.data(), B.dd, count * sizeof(BatchDesc), cudaMemcpyDeviceToHost,
                               st));
@@ -1610,8 +1638,9 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
             inf.mu = B.hd[i].mu;
             inf.seconds = secs;
             inf.status = status[i];
-            std::snprintf(inf.form, sizeof(inf.form), "batch/%s",
-                          B.store == ST_F64 ? "fp64" : (B.store == ST_F32 ? "fp32" : "bf16"));
+            std::snprintf(inf.form, sizeof(inf.form), "batch/%s%s",
+                          B.store == ST_F64 ? "fp64" : (B.store == ST_F32 ? "fp32" : "bf16"),
+                          B.rp ? "/rp" : "");
             inf.kernel_launches = B.launches;
         }
     }

@@ -60,6 +60,39 @@ def test_batch_converged_matches_smo(storage, tol):
         assert O.kkt(P, zs[i])["kkt"] <= tol * 1.01
 
 
+def test_batch_rp_fp64_iterates_match_oracle():
+    """RP-MBADMM (fixed partition, random block order, factors computed once)
+    follows the oracle's RP iterates."""
+    insts = _svm_set(2)
+    zs, infos = api.batch(_probs(insts), num_blocks=-64, beta=0.0, gamma=-0.3, tol=0.0,
+                          max_sweeps=12, refresh_every=5, seed=9, storage="fp64",
+                          assembly="rp")
+    for i, s in enumerate(insts):
+        P = O.problem_from_instance(s)
+        st = O.initial_state(P)
+        for _ in range(12):
+            O.sweep(P, st, s.num_blocks, 9 + i, s.beta, s.gamma, rp=True)
+        assert infos[i]["sweeps"] == 12
+        assert infos[i]["form"].endswith("/rp")
+        assert rel(zs[i], st.z) <= 1e-10, i
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-7), ("bf16", 1e-6)])
+def test_batch_rp_converged_matches_smo(storage, tol):
+    insts = _svm_set(4, count=4)
+    zs, infos = api.batch(_probs(insts), num_blocks=-64, beta=0.0, gamma=-0.3, tol=tol,
+                          max_sweeps=80000, refresh_every=20, seed=0, storage=storage,
+                          assembly="rp")
+    for i, s in enumerate(insts):
+        assert infos[i]["status"] == 0, infos[i]
+        Q = s.A.T @ s.A
+        a_smo = O.smo_svm(Q, s.E[0], 1.0, tol=1e-11)
+        obj = lambda v: 0.5 * v @ Q @ v - v.sum()
+        assert abs(obj(zs[i]) - obj(a_smo)) <= 1e-4 * max(1.0, abs(obj(a_smo)))
+        P = O.problem_from_instance(s)
+        assert O.kkt(P, zs[i])["kkt"] <= tol * 1.01
+
+
 def test_batch_mixed_lasso_and_regression():
     """The batch is not SVM-only: uneven LASSO / regression instances."""
     insts = [synth.small_instance(i, 40 + 13 * i, 20 + 7 * i, 3 + i,

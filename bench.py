@@ -46,7 +46,55 @@ def parse():
     ap.add_argument("--solve-once", type=int, default=0, metavar="K",
                     help="run K plain solves of the workload in the default mixed-precision "
                          "form and exit (no timing; a fixed command to profile)")
+    ap.add_argument("--svm-batch", type=int, default=0, metavar="COUNT",
+                    help="time the batched soft-margin SVM dual workload (COUNT uneven "
+                         "instances, N in [500, 20000], d in [20, 1000], blocks of 64) per "
+                         "sweep and exit; --steps sweeps are timed")
+    ap.add_argument("--storage", default="bf16", choices=["fp64", "fp32", "bf16"],
+                    help="storage precision of --svm-batch")
+    ap.add_argument("--assembly", default="rac", choices=["rac", "rp"],
+                    help="block assembly of --svm-batch (rac: random every sweep; rp: fixed "
+                         "partition in a random order)")
     return ap.parse_args()
+
+
+def svm_batch_leg(args) -> int:
+    """Time per sweep of the batched SVM duals: the device time of the sweep
+    loop (rac_info.t_loop_ms: CUDA events on the batch's stream around all
+    periods, their refreshes and the checks between them) over the sweeps
+    run; the call's setup (host copies of A, conversions) is not in it."""
+    import torch
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    insts = synth.svm_batch(0, count=args.svm_batch)
+    probs = [dict(A=s.A, b=s.b, c=s.c, E=s.E[0], d=s.d, phi="box", lo=0.0, hi=1.0)
+             for s in insts]
+    kw = dict(num_blocks=-64, beta=0.0, gamma=-0.3, tol=0.0, refresh_every=20,
+              storage=args.storage, assembly=args.assembly)
+    K = max(args.steps, 40)
+
+    def timed(sweeps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, infos = api.batch(probs, max_sweeps=sweeps, **kw)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, infos
+
+    timed(2)                                            # warm-up (module load)
+    runs = [timed(K) for _ in range(2)]
+    infos = min(runs, key=lambda r: r[1][0]["t_loop_ms"])[1]
+    blocks = sum(i["block_updates"] for i in infos) // K
+    ms = infos[0]["t_loop_ms"] / K
+    wall = min(r[0] for r in runs)
+    print(json.dumps({
+        "workload": "svm_batch_%d" % args.svm_batch, "storage": args.storage,
+        "assembly": args.assembly, "form": infos[0]["form"], "sweeps_timed": K,
+        "ms_per_sweep": ms, "block_updates_per_s": blocks / (ms * 1e-3),
+        "blocks_per_sweep": blocks, "call_seconds": wall,
+        "sum_Nd": int(sum(s.A.shape[0] * s.A.shape[1] for s in insts)),
+        "data": "synthetic"}), flush=True)
+    return 0
 
 
 # --------------------------------------------------------------- CPU oracle leg
@@ -229,6 +277,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.svm_batch:
+        return svm_batch_leg(args)
     import numpy as np
     import torch
     import torch.distributed as dist

@@ -156,6 +156,9 @@ typedef struct {
     double t_assembly_ms, t_factor_ms, t_chain_ms, t_prox_ms, t_refresh_ms;
     int64_t chain_launches; /* launches of the sweep-chain kernel in this call */
     int32_t warm_start_rejected; /* 1 if ws_fallback restarted this solve from zero */
+    double t_loop_ms;       /* rac_admm_batch: device time from the first sweep to the end of
+                               the last refresh (all periods, checks between them included),
+                               by CUDA events on the batch's stream; 0 elsewhere */
 } rac_info;
 
 typedef struct rac_handle rac_handle;

@@ -662,8 +662,8 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     TA *dlb = rhs + SB;                                                   // SB
     double *cstb = (double *)(((uintptr_t)(dlb + SB) + 15) & ~(uintptr_t)15);   // 3 x SB
     double *evb = cstb + 3 * SB;                                          // 3 x SB
-    double *tpart = evb + 3 * SB;                                         // 8
-    int *idxb = (int *)(tpart + 8);                                       // 3 x SB
+    double *tpart = evb + 3 * SB;                                         // 8, then beta t - mu
+    int *idxb = (int *)(tpart + 10);                                      // 3 x SB
     TA *upart = (TA *)(((uintptr_t)(idxb + 3 * SB) + 15) & ~(uintptr_t)15);   // 256 x VN
     const int *perm = P.perm + (size_t)slot * P.ntot + d.vec;
     const TS *As = (const TS *)P.As + d.as;
@@ -687,6 +687,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
         mbar_init_fence();
     }
     for (int v = t; v < ld; v += 256) dres[v] = (TA)dres_g[v];
+    if (t == 0) tpart[8] = beta * tc - mu;   // the coupling term of the rhs (one FP64 owner)
     __syncthreads();
     // block solved at step i: i itself (RAC), or the i-th of this sweep's
     // random order of the fixed partition (RP, whose columns are consecutive)
@@ -729,7 +730,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
         // gradient and rhs: per warp pass GC columns, loads in batches of
         // GC x LB vectors issued before any of them is used
         {
-            const double bt = beta * tc - mu;
+            const double bt = tpart[8];
             const int sub = lane & (lpc - 1), csl = lane / lpc;
             for (int q0 = warp * cpw; q0 < s; q0 += 8 * GC * cpw) {
                 int qq[GC];
@@ -836,6 +837,15 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             if (lane == 0) tpart[warp] = tl;
         }
         __syncthreads();
+        // t += e_S^T dl and beta t - mu for the next block: thread 0 only (GB300's
+        // FP64 pipe is busy for a warp instruction whatever its active lanes)
+        if (t == 0 && d.k) {
+            double ts = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) ts += tpart[w];
+            tc += ts;
+            tpart[8] = beta * tc - mu;
+        }
         // update: dres += A~_S dl, loads in batches of UB columns
         {
             const int g = CG == 1 ? 0 : t / nvec;
@@ -889,12 +899,6 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             evb[n2 * SB + t] = e2;
         }
         __syncthreads();
-        if (d.k) {
-            double ts = 0.0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) ts += tpart[w];
-            tc += ts;
-        }
         cs = ns;
     }
     for (int v = t; v < ld; v += 256) dres_g[v] = (double)dres[v];
@@ -906,7 +910,7 @@ template <class TS, class TA, int SB> size_t chain_smem(int smax, int ldmax) {
     const size_t nkb = sizeof(TA) == 4 ? 3 : 2;
     size_t b = 32 + nkb * kst * sizeof(TA) + (size_t)ldmax * sizeof(TA) + 2 * SB * sizeof(TA);
     b = (b + 15) & ~(size_t)15;
-    b += 6 * SB * sizeof(double) + 8 * sizeof(double) + 3 * SB * sizeof(int);
+    b += 6 * SB * sizeof(double) + 10 * sizeof(double) + 3 * SB * sizeof(int);
     b = (b + 15) & ~(size_t)15;
     b += 256 * (size_t)Vec16<TS>::N * sizeof(TA);
     return b + 16;
@@ -1058,26 +1062,32 @@ __global__ void __launch_bounds__(kChunk) k_batch_ref_grad(BatchDesc *D, const i
     __syncthreads();
     const double *e = d.k ? P.e + d.vec : nullptr;
     double st[kStats] = {0, 0, 0, 0, 0, 0, 0, 0};   // stat, gmax, |z|_1, ez, ex, xz, bad, fro
-    for (int jj = warp; jj < nc; jj += kChunk / 32) {
-        const int j = j0 + jj;
-        const double *aj = P.A64 + d.a64 + (size_t)j * m;
-        double a0 = 0.0, a1 = 0.0, q0 = 0.0;
-        int i = lane;
-        for (; i + 32 < m; i += 64) {
-            const double u = aj[i], v = aj[i + 32];
-            a0 = fma(u, rs[i], a0);
-            a1 = fma(v, rs[i + 32], a1);
-            if (FRO) q0 = fma(u, u, fma(v, v, q0));
+    // four columns per warp pass (independent FP64 accumulators), reduced by a
+    // transposed butterfly: lane 8 u (u < 4) ends with column j0 + jj + u
+    for (int jj = 4 * warp; jj < nc; jj += 4 * (kChunk / 32)) {
+        double a[4] = {0.0, 0.0, 0.0, 0.0}, q[4] = {0.0, 0.0, 0.0, 0.0};
+        const double *aj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            aj[u] = P.A64 + d.a64 + (size_t)(j0 + min(jj + u, nc - 1)) * m;
+        for (int i = lane; i < m; i += 32) {
+            const double r = rs[i];
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = aj[u][i];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = fma(v[u], r, a[u]);
+                if (FRO) q[u] = fma(v[u], v[u], q[u]);
+            }
         }
-        if (i < m) {
-            const double u = aj[i];
-            a0 = fma(u, rs[i], a0);
-            if (FRO) q0 = fma(u, u, q0);
-        }
-        const double g = warp_sum(a0 + a1) + P.c[d.vec + j];
-        if (FRO) q0 = warp_sum(q0);
-        if (lane == 0) {
+        const double gs = warp_sum4(a[0], a[1], a[2], a[3], lane);
+        const double qs = FRO ? warp_sum4(q[0], q[1], q[2], q[3], lane) : 0.0;
+        const int u = 2 * ((lane >> 4) & 1) + ((lane >> 3) & 1);
+        if ((lane & 7) == 0 && jj + u < nc) {
+            const int j = j0 + jj + u;
             const size_t jv = d.vec + j;
+            const double g = gs + P.c[jv];
             const double zj = P.z[jv], xj = P.x[jv], xij = P.xi[jv];
             P.ga[jv] = g;
             P.cst[jv] = g - xij + d.gamma * (xj - zj);
@@ -1090,7 +1100,17 @@ __global__ void __launch_bounds__(kChunk) k_batch_ref_grad(BatchDesc *D, const i
             st[3] += ej * zj;
             st[4] += ej * xj;
             st[5] = fmax(st[5], fabs(xj - zj));
-            st[7] += q0;
+            st[7] += qs;
+        }
+    }
+    // lanes 0, 8, 16, 24 hold partial statistics: combine them into lane 0
+#pragma unroll
+    for (int k = 0; k < kStats; ++k) {
+        const bool mx = k == 0 || k == 1 || k == 5 || k == 6;
+#pragma unroll
+        for (int o = 8; o < 32; o <<= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, st[k], o);
+            st[k] = mx ? fmax(st[k], y) : st[k] + y;
         }
     }
     if (lane == 0) {
@@ -1564,6 +1584,10 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         active += B.hd[i].active;
     }
     int done = 0;
+    cudaEvent_t le0 = nullptr, le1 = nullptr;
+    RB_CK(cudaEventCreate(&le0));
+    RB_CK(cudaEventCreate(&le1));
+    RB_CK(cudaEventRecord(le0, st));
     cudaGraphExec_t gexec = nullptr;
     int gnb = 0;
     int herr = 0;
@@ -1616,6 +1640,12 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         if (herr) break;
     }
     if (gexec) cudaGraphExecDestroy(gexec);
+    float loop_ms = 0.f;
+    RB_CK(cudaEventRecord(le1, st));
+    RB_CK(cudaEventSynchronize(le1));
+    cudaEventElapsedTime(&loop_ms, le0, le1);
+    cudaEventDestroy(le0);
+    cudaEventDestroy(le1);
     rac_status first = RAC_OK;
     for (int i = 0; i < count; ++i) {
         const BatchDesc &d = B.hd[i];
@@ -1642,6 +1672,7 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
                           B.store == ST_F64 ? "fp64" : (B.store == ST_F32 ? "fp32" : "bf16"),
                           B.rp ? "/rp" : "");
             inf.kernel_launches = B.launches;
+            inf.t_loop_ms = loop_ms;
         }
     }
     return first;

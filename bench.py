@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--svm-batch", type=int, default=0, metavar="COUNT",
                     help="time the batched soft-margin SVM dual workload (COUNT uneven "
                          "instances, N in [500, 20000], d in [20, 1000], blocks of 64) per "
-                         "sweep and exit; --steps sweeps are timed")
+                         "sweep and exit; max(--steps, 40) sweeps are timed")
     ap.add_argument("--storage", default="bf16", choices=["fp64", "fp32", "bf16"],
                     help="storage precision of --svm-batch")
     ap.add_argument("--assembly", default="rac", choices=["rac", "rp"],

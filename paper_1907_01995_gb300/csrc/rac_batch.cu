@@ -662,8 +662,10 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     TA *dlb = rhs + SB;                                                   // SB
     double *cstb = (double *)(((uintptr_t)(dlb + SB) + 15) & ~(uintptr_t)15);   // 3 x SB
     double *evb = cstb + 3 * SB;                                          // 3 x SB
-    double *tpart = evb + 3 * SB;                                         // 8, then beta t - mu
-    int *idxb = (int *)(tpart + 10);                                      // 3 x SB
+    TA *tpart = (TA *)(evb + 3 * SB);                                     // 8 (+ pad)
+    TA *c0b = tpart + 16;                                                 // 3 x SB
+    TA *evt = c0b + 3 * SB;                                               // 3 x SB
+    int *idxb = (int *)(evt + 3 * SB);                                    // 3 x SB
     TA *upart = (TA *)(((uintptr_t)(idxb + 3 * SB) + 15) & ~(uintptr_t)15);   // 256 x VN
     const int *perm = P.perm + (size_t)slot * P.ntot + d.vec;
     const TS *As = (const TS *)P.As + d.as;
@@ -687,7 +689,6 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
         mbar_init_fence();
     }
     for (int v = t; v < ld; v += 256) dres[v] = (TA)dres_g[v];
-    if (t == 0) tpart[8] = beta * tc - mu;   // the coupling term of the rhs (one FP64 owner)
     __syncthreads();
     // block solved at step i: i itself (RAC), or the i-th of this sweep's
     // random order of the fixed partition (RP, whose columns are consecutive)
@@ -710,9 +711,21 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             idxb[b * SB + t] = j;
             cstb[b * SB + t] = cst[j];
             evb[b * SB + t] = e ? e[j] : 0.0;
+            evt[b * SB + t] = e ? (TA)e[j] : TA(0);
             if (b == 0) prefetch_l2_bulk(As + (size_t)j * ld, colbytes);
         }
     }
+    __syncthreads();
+    // rhs constant of a block: c0 = cst + e (beta t - mu), formed in FP64 by warp 0
+    // alone one block ahead (GB300's FP64 pipe is occupied by a warp instruction
+    // whatever its active lanes); near the fixed point c0 is small, so its
+    // rounding to the accumulation type stays relative to a small number
+    auto make_c0 = [&](int slot_, int sb_) {
+        const double bt = beta * tc - mu;
+        for (int q = lane; q < sb_; q += 32)
+            c0b[slot_ * SB + q] = (TA)(cstb[slot_ * SB + q] + evb[slot_ * SB + q] * bt);
+    };
+    if (warp == 0) make_c0(0, lay.size(blk(0)));
     __syncthreads();
     int cs = 0;                                   // index slot of block i
     for (int i = 0; i < d.p; ++i) {
@@ -730,7 +743,6 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
         // gradient and rhs: per warp pass GC columns, loads in batches of
         // GC x LB vectors issued before any of them is used
         {
-            const double bt = tpart[8];
             const int sub = lane & (lpc - 1), csl = lane / lpc;
             for (int q0 = warp * cpw; q0 < s; q0 += 8 * GC * cpw) {
                 int qq[GC];
@@ -775,7 +787,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
                     const int u = 2 * ((lane >> 4) & 1) + ((lane >> 3) & 1);
                     const int q = q0 + 8 * u;
                     if ((lane & 7) == 0 && q < s)
-                        rhs[q] = (TA)(cstb[cs * SB + q] + (double)tot + evb[cs * SB + q] * bt);
+                        rhs[q] = c0b[cs * SB + q] + tot;
                 } else {
 #pragma unroll
                     for (int u = 0; u < GC; ++u)
@@ -785,8 +797,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
 #pragma unroll
                         for (int u = 0; u < GC; ++u)
                             if (vq[u])
-                                rhs[qq[u]] = (TA)(cstb[cs * SB + qq[u]] + (double)ac[u] +
-                                                  evb[cs * SB + qq[u]] * bt);
+                                rhs[qq[u]] = c0b[cs * SB + qq[u]] + ac[u];
                     }
                 }
             }
@@ -805,7 +816,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             TA rl[CPL];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) rl[c] = (lane + 32 * c < s) ? rhs[lane + 32 * c] : TA(0);
-            double tl = 0.0;
+            TA tl = 0;
 #pragma unroll
             for (int h = 0; h < RPW / 8; ++h) {
                 TA part[8];
@@ -827,7 +838,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
                     const TA dl = -tot;
                     dlb[r] = dl;
                     dx[idx[r]] = (double)dl;
-                    tl += evb[cs * SB + r] * (double)dl;
+                    tl = fma(evt[cs * SB + r], dl, tl);
                 }
             }
             // lanes 0, 4, ..., 28 hold the coupling terms of their rows
@@ -837,14 +848,15 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             if (lane == 0) tpart[warp] = tl;
         }
         __syncthreads();
-        // t += e_S^T dl and beta t - mu for the next block: thread 0 only (GB300's
-        // FP64 pipe is busy for a warp instruction whatever its active lanes)
-        if (t == 0 && d.k) {
-            double ts = 0.0;
+        // warp 0: t += e_S^T dl, then the next block's rhs constants
+        if (warp == 0) {
+            if (d.k) {
+                TA ts = 0;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) ts += tpart[w];
-            tc += ts;
-            tpart[8] = beta * tc - mu;
+                for (int w = 0; w < 8; ++w) ts += tpart[w];
+                tc += (double)ts;
+            }
+            if (sn) make_c0(ns, sn);
         }
         // update: dres += A~_S dl, loads in batches of UB columns
         {
@@ -897,6 +909,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             idxb[n2 * SB + t] = j2;
             cstb[n2 * SB + t] = c2;
             evb[n2 * SB + t] = e2;
+            evt[n2 * SB + t] = (TA)e2;
         }
         __syncthreads();
         cs = ns;
@@ -910,7 +923,7 @@ template <class TS, class TA, int SB> size_t chain_smem(int smax, int ldmax) {
     const size_t nkb = sizeof(TA) == 4 ? 3 : 2;
     size_t b = 32 + nkb * kst * sizeof(TA) + (size_t)ldmax * sizeof(TA) + 2 * SB * sizeof(TA);
     b = (b + 15) & ~(size_t)15;
-    b += 6 * SB * sizeof(double) + 10 * sizeof(double) + 3 * SB * sizeof(int);
+    b += 6 * SB * sizeof(double) + 16 * sizeof(TA) + 6 * SB * sizeof(TA) + 3 * SB * sizeof(int);
     b = (b + 15) & ~(size_t)15;
     b += 256 * (size_t)Vec16<TS>::N * sizeof(TA);
     return b + 16;

@@ -635,12 +635,14 @@ template <class T> __device__ __forceinline__ T warp_sum8(const T (&a)[8], int l
     return e;
 }
 
-template <class TS, class TA, int SB>
-__global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int *order,
-                                                        BatchPools P, int slot, int *err) {
+template <class TS, class TA, int SB, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k_batch_chain(BatchDesc *D, const int *order,
+                                                                      BatchPools P, int slot, int *err) {
     constexpr int VN = Vec16<TS>::N;
     using VT = typename Vec16<TS>::T;
-    constexpr int RPW = SB / 8;                  // solve rows per warp
+    constexpr int NW = NT / 32;                  // warps
+    constexpr int RPW = SB / NW;                 // solve rows per warp (4, 8 or 16)
+    static_assert(RPW == 4 || RPW % 8 == 0, "solve reduction groups of 4 or 8 rows");
     constexpr int CPL = SB / 32;                 // solve columns per lane
     constexpr int GC = 4;                        // gradient columns per warp pass
     constexpr int LB = 4;                        // vectors per column per load batch
@@ -666,7 +668,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     TA *c0b = tpart + 16;                                                 // 3 x SB
     TA *evt = c0b + 3 * SB;                                               // 3 x SB
     int *idxb = (int *)(evt + 3 * SB);                                    // 3 x SB
-    TA *upart = (TA *)(((uintptr_t)(idxb + 3 * SB) + 15) & ~(uintptr_t)15);   // 256 x VN
+    TA *upart = (TA *)(((uintptr_t)(idxb + 3 * SB) + 15) & ~(uintptr_t)15);   // NT x VN
     const int *perm = P.perm + (size_t)slot * P.ntot + d.vec;
     const TS *As = (const TS *)P.As + d.as;
     const TA *Wb = (const TA *)P.W + d.w;
@@ -683,12 +685,12 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
     while (lpc < nvec && lpc < 32) lpc <<= 1;
     const int cpw = 32 / lpc;
     int CG = 1;
-    while (CG < 16 && 2 * CG * nvec <= 256) CG <<= 1;
+    while (CG < 16 && 2 * CG * nvec <= NT) CG <<= 1;
     if (t == 0) {
         for (int k = 0; k < NKB; ++k) mbar_init(&bar[k], 1);
         mbar_init_fence();
     }
-    for (int v = t; v < ld; v += 256) dres[v] = (TA)dres_g[v];
+    for (int v = t; v < ld; v += NT) dres[v] = (TA)dres_g[v];
     __syncthreads();
     // block solved at step i: i itself (RAC), or the i-th of this sweep's
     // random order of the fixed partition (RP, whose columns are consecutive)
@@ -736,22 +738,22 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
         const int b2 = i + 2 < d.p ? blk(i + 2) : 0;
         const int s2 = i + 2 < d.p ? lay.size(b2) : 0;
         if (t == 0 && i + NKB - 1 < d.p) issue_kinv(i + NKB - 1);
-        if (t >= 192 && t - 192 < sn)
-            prefetch_l2_bulk(As + (size_t)idxb[ns * SB + t - 192] * ld, colbytes);
+        if (t >= NT - 64 && t - (NT - 64) < sn)
+            prefetch_l2_bulk(As + (size_t)idxb[ns * SB + t - (NT - 64)] * ld, colbytes);
         int j2 = 0;
         if (t < s2) j2 = rp ? lay.offset(b2) + t : perm[lay.offset(b2) + t];
         // gradient and rhs: per warp pass GC columns, loads in batches of
         // GC x LB vectors issued before any of them is used
         {
             const int sub = lane & (lpc - 1), csl = lane / lpc;
-            for (int q0 = warp * cpw; q0 < s; q0 += 8 * GC * cpw) {
+            for (int q0 = warp * cpw; q0 < s; q0 += NW * GC * cpw) {
                 int qq[GC];
                 bool vq[GC];
                 const TS *cp[GC];
                 TA ac[GC];
 #pragma unroll
                 for (int u = 0; u < GC; ++u) {
-                    qq[u] = q0 + csl + 8 * cpw * u;
+                    qq[u] = q0 + csl + NW * cpw * u;
                     vq[u] = qq[u] < s;
                     cp[u] = As + (size_t)(vq[u] ? idx[qq[u]] : 0) * ld;
                     ac[u] = 0;
@@ -783,9 +785,9 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
                 }
                 if (lpc == 32) {
                     const TA tot = warp_sum4(ac[0], ac[1], ac[2], ac[3], lane);
-                    // one column per lane (csl = 0, cpw = 1): lane holds column q0 + 8 u
+                    // one column per lane (csl = 0, cpw = 1): lane holds column q0 + NW u
                     const int u = 2 * ((lane >> 4) & 1) + ((lane >> 3) & 1);
-                    const int q = q0 + 8 * u;
+                    const int q = q0 + NW * u;
                     if ((lane & 7) == 0 && q < s)
                         rhs[q] = c0b[cs * SB + q] + tot;
                 } else {
@@ -817,12 +819,17 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
 #pragma unroll
             for (int c = 0; c < CPL; ++c) rl[c] = (lane + 32 * c < s) ? rhs[lane + 32 * c] : TA(0);
             TA tl = 0;
+            auto finish_row = [&](int r, TA tot) {
+                const TA dl = -tot;
+                dlb[r] = dl;
+                dx[idx[r]] = (double)dl;
+                tl = fma(evt[cs * SB + r], dl, tl);
+            };
+            if constexpr (RPW == 4) {
+                TA part[4];
 #pragma unroll
-            for (int h = 0; h < RPW / 8; ++h) {
-                TA part[8];
-#pragma unroll
-                for (int rr = 0; rr < 8; ++rr) {
-                    const int r = warp + 8 * (8 * h + rr);
+                for (int rr = 0; rr < 4; ++rr) {
+                    const int r = warp + NW * rr;
                     TA a = 0;
                     if (r < s) {
 #pragma unroll
@@ -831,14 +838,29 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
                     }
                     part[rr] = a;
                 }
-                const TA tot = warp_sum8(part, lane);
-                const int rr = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
-                const int r = warp + 8 * (8 * h + rr);
-                if ((lane & 3) == 0 && r < s) {
-                    const TA dl = -tot;
-                    dlb[r] = dl;
-                    dx[idx[r]] = (double)dl;
-                    tl = fma(evt[cs * SB + r], dl, tl);
+                const TA tot = warp_sum4(part[0], part[1], part[2], part[3], lane);
+                const int r = warp + NW * (2 * ((lane >> 4) & 1) + ((lane >> 3) & 1));
+                if ((lane & 7) == 0 && r < s) finish_row(r, tot);
+            } else {
+#pragma unroll
+                for (int h = 0; h < RPW / 8; ++h) {
+                    TA part[8];
+#pragma unroll
+                    for (int rr = 0; rr < 8; ++rr) {
+                        const int r = warp + NW * (8 * h + rr);
+                        TA a = 0;
+                        if (r < s) {
+#pragma unroll
+                            for (int c = 0; c < CPL; ++c)
+                                if (lane + 32 * c < s)
+                                    a = fma(K[(size_t)r * s + lane + 32 * c], rl[c], a);
+                        }
+                        part[rr] = a;
+                    }
+                    const TA tot = warp_sum8(part, lane);
+                    const int rr = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
+                    const int r = warp + NW * (8 * h + rr);
+                    if ((lane & 3) == 0 && r < s) finish_row(r, tot);
                 }
             }
             // lanes 0, 4, ..., 28 hold the coupling terms of their rows
@@ -853,7 +875,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             if (d.k) {
                 TA ts = 0;
 #pragma unroll
-                for (int w = 0; w < 8; ++w) ts += tpart[w];
+                for (int w = 0; w < NW; ++w) ts += tpart[w];
                 tc += (double)ts;
             }
             if (sn) make_c0(ns, sn);
@@ -863,7 +885,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             const int g = CG == 1 ? 0 : t / nvec;
             const int v0 = CG == 1 ? t : t - g * nvec;
             if (t < CG * nvec || CG == 1) {
-                for (int v = v0; v < nvec; v += (CG == 1 ? 256 : nvec)) {
+                for (int v = v0; v < nvec; v += (CG == 1 ? NT : nvec)) {
                     TA acc[VN];
 #pragma unroll
                     for (int k = 0; k < VN; ++k) acc[k] = 0;
@@ -898,7 +920,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
             }
             if (CG > 1) {
                 __syncthreads();
-                for (int v = t; v < ld; v += 256) {
+                for (int v = t; v < ld; v += NT) {
                     TA a = dres[v];
                     for (int gg = 0; gg < CG; ++gg) a += upart[(size_t)gg * ld + v];
                     dres[v] = a;
@@ -914,18 +936,18 @@ __global__ void __launch_bounds__(256, 2) k_batch_chain(BatchDesc *D, const int 
         __syncthreads();
         cs = ns;
     }
-    for (int v = t; v < ld; v += 256) dres_g[v] = (double)dres[v];
+    for (int v = t; v < ld; v += NT) dres_g[v] = (double)dres[v];
     if (t == 0) d.t = tc;
 }
 
-template <class TS, class TA, int SB> size_t chain_smem(int smax, int ldmax) {
+template <class TS, class TA, int SB, int NT> size_t chain_smem(int smax, int ldmax) {
     const size_t kst = BlockLayout::pad4((size_t)smax * smax);
     const size_t nkb = sizeof(TA) == 4 ? 3 : 2;
     size_t b = 32 + nkb * kst * sizeof(TA) + (size_t)ldmax * sizeof(TA) + 2 * SB * sizeof(TA);
     b = (b + 15) & ~(size_t)15;
     b += 6 * SB * sizeof(double) + 16 * sizeof(TA) + 6 * SB * sizeof(TA) + 3 * SB * sizeof(int);
     b = (b + 15) & ~(size_t)15;
-    b += 256 * (size_t)Vec16<TS>::N * sizeof(TA);
+    b += NT * (size_t)Vec16<TS>::N * sizeof(TA);
     return b + 16;
 }
 
@@ -1246,14 +1268,20 @@ static cudaError_t batch_factor(BatchRun &B, int s, int *err) {
     return cudaGetLastError();
 }
 
+// Threads per chain CTA: the chain is bound by the latency of each block step,
+// so more loads in flight per instance (512 threads, one CTA per SM, largest
+// instances first) beat two CTAs per SM.
+constexpr int kChainThreads = 512;
+
 template <class TS, class TA>
 static cudaError_t batch_chain(BatchRun &B, int s, int *err) {
+    constexpr int NT = kChainThreads;
     if (B.smax_all <= 64) {
-        const size_t sm = chain_smem<TS, TA, 64>(B.smax_all, B.ld_max);
-        k_batch_chain<TS, TA, 64><<<B.count, 256, sm, B.st>>>(B.dd, B.order, B.P, s, err);
+        const size_t sm = chain_smem<TS, TA, 64, NT>(B.smax_all, B.ld_max);
+        k_batch_chain<TS, TA, 64, NT><<<B.count, NT, sm, B.st>>>(B.dd, B.order, B.P, s, err);
     } else {
-        const size_t sm = chain_smem<TS, TA, 128>(B.smax_all, B.ld_max);
-        k_batch_chain<TS, TA, 128><<<B.count, 256, sm, B.st>>>(B.dd, B.order, B.P, s, err);
+        const size_t sm = chain_smem<TS, TA, 128, NT>(B.smax_all, B.ld_max);
+        k_batch_chain<TS, TA, 128, NT><<<B.count, NT, sm, B.st>>>(B.dd, B.order, B.P, s, err);
     }
     return cudaGetLastError();
 }
@@ -1316,18 +1344,19 @@ template <class TS, class TA> static cudaError_t batch_set_attrs(BatchRun &B) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t csm = B.smax_all <= 64 ? chain_smem<TS, TA, 64>(B.smax_all, B.ld_max)
-                                        : chain_smem<TS, TA, 128>(B.smax_all, B.ld_max);
+    constexpr int NT = kChainThreads;
+    const size_t csm = B.smax_all <= 64 ? chain_smem<TS, TA, 64, NT>(B.smax_all, B.ld_max)
+                                        : chain_smem<TS, TA, 128, NT>(B.smax_all, B.ld_max);
     if (csm > (size_t)optin) return cudaErrorInvalidValue;   // K_S^{-1} pair does not fit
     if (B.smax_all <= 64) {
-        auto kc = k_batch_chain<TS, TA, 64>;
+        auto kc = k_batch_chain<TS, TA, 64, NT>;
         if ((e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)chain_smem<TS, TA, 64>(B.smax_all, B.ld_max))) != cudaSuccess)
+                                      (int)chain_smem<TS, TA, 64, NT>(B.smax_all, B.ld_max))) != cudaSuccess)
             return e;
     } else {
-        auto kc = k_batch_chain<TS, TA, 128>;
+        auto kc = k_batch_chain<TS, TA, 128, NT>;
         if ((e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)chain_smem<TS, TA, 128>(B.smax_all, B.ld_max))) != cudaSuccess)
+                                      (int)chain_smem<TS, TA, 128, NT>(B.smax_all, B.ld_max))) != cudaSuccess)
             return e;
     }
     if constexpr (!std::is_same<TS, double>::value) {

@@ -152,8 +152,9 @@ __global__ void __launch_bounds__(1024) k_batch_assembly(BatchDesc *D, int count
 // The inverse is the sweep operator (Goodnight 1979) on the padded 64 x 64
 // matrix in registers, four pivots at a time: thread (tr, tc) of each
 // 128-thread half owns rows 4 tr .. 4 tr + 3 and columns 8 tc .. 8 tc + 7 of
-// its block, the four pivot rows are published in shared memory, and every
-// thread inverts the 4 x 4 pivot block itself: 16 barriers per inverse.
+// its block, the four pivot rows are published in shared memory with the
+// inverse of their 4 x 4 pivot block, formed once by the thread that holds
+// it: 16 barriers per inverse.
 constexpr uint32_t kFtTile = 128 * 128;            // one operand tile: 128 rows x 128 bytes
 constexpr int kFtLdF = 65;                         // staged Gram row (floats), padded
 template <class TS> constexpr size_t factor_tc_smem() {
@@ -167,6 +168,35 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float a) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
     return r;
+}
+
+// g <- -g^{-1} for a symmetric positive definite 4 x 4 block by four single
+// sweeps (Goodnight 1979); a non-positive pivot sets bad and is replaced by 1.
+__device__ __forceinline__ void sweep4(float (&g)[4][4], bool &bad) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float dq = g[q][q];
+        if (!(dq > 0.f)) {
+            bad = true;
+            dq = 1.f;
+        }
+        const float rd = __frcp_rn(dq);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (a == q) continue;
+            const float f = g[a][q] * rd;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c != q) g[a][c] = fmaf(-f, g[q][c], g[a][c]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            if (a != q) {
+                g[a][q] *= rd;
+                g[q][a] *= rd;
+            }
+        g[q][q] = -rd;
+    }
 }
 
 template <class TS>
@@ -184,6 +214,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
     __shared__ int idx[128];
     __shared__ float es[128];
     __shared__ __align__(16) float pbuf[2][2 * 4][68];   // [block][double buffer x 4 pivot rows][col]
+    __shared__ __align__(16) float gbuf[2][2][16];       // [block][double buffer]: -M_BB^{-1}
     const int inst = find_instance(pps, count, blockIdx.x);
     const BatchDesc &d = D[inst];
     if (!d.active) return;
@@ -313,7 +344,21 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
     // shared memory, M_RB is read from them by symmetry, and every thread
     // inverts the 4 x 4 block itself.
     float *pb = &pbuf[blk][0][0];
+    float *gb = &gbuf[blk][0][0];
     bool bad = false;
+    // the owner of a pivot block (it holds rows and columns 4 bq .. 4 bq + 3)
+    // inverts it once and publishes -M_BB^{-1} beside the pivot rows
+    auto publish_g = [&](int off, float *dst) {
+        float g[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) g[a][c] = off ? acc[a][4 + c] : acc[a][c];
+        sweep4(g, bad);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            *reinterpret_cast<float4 *>(&dst[4 * a]) = make_float4(g[a][0], g[a][1], g[a][2], g[a][3]);
+    };
     if (tr == 0) {
 #pragma unroll
         for (int ru = 0; ru < 4; ++ru) {
@@ -322,42 +367,19 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
             *reinterpret_cast<float4 *>(&pb[ru * 68 + 8 * tcc + 4]) =
                 make_float4(acc[ru][4], acc[ru][5], acc[ru][6], acc[ru][7]);
         }
+        if (tcc == 0) publish_g(0, gb);
     }
     __syncthreads();
     const int nbp = (max(s0, s1) + 3) >> 2;
     for (int bq = 0; bq < nbp; ++bq) {
         const int k = 4 * bq;
         const float *Pq = pb + (bq & 1) * 4 * 68;
-        // g = -M_BB^{-1} by four single sweeps of the 4 x 4 block
+        // g = -M_BB^{-1}, published by the block's owner
         float g[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const float4 w = *reinterpret_cast<const float4 *>(&Pq[a * 68 + k]);
+            const float4 w = *reinterpret_cast<const float4 *>(&gb[(bq & 1) * 16 + 4 * a]);
             g[a][0] = w.x; g[a][1] = w.y; g[a][2] = w.z; g[a][3] = w.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float dq = g[q][q];
-            if (!(dq > 0.f)) {
-                bad = true;
-                dq = 1.f;
-            }
-            const float rd = __frcp_rn(dq);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                if (a == q) continue;
-                const float f = g[a][q] * rd;
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (c != q) g[a][c] = fmaf(-f, g[q][c], g[a][c]);
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if (a != q) {
-                    g[a][q] *= rd;
-                    g[q][a] *= rd;
-                }
-            g[q][q] = -rd;
         }
         if (tr != bq) {
             // U = M_RB M_BB^{-1} = -R g with R[ru][a] = M[4 tr + ru][k + a] = M[k + a][4 tr + ru]
@@ -429,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
                 }
             }
         }
-        // publish the next four rows
+        // publish the next four rows and their pivot block's inverse
         if (bq + 1 < nbp && tr == bq + 1) {
             float *Pn = pb + ((bq + 1) & 1) * 4 * 68;
 #pragma unroll
@@ -439,6 +461,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_factor_tc(BatchDesc *D, const 
                 *reinterpret_cast<float4 *>(&Pn[ru * 68 + 8 * tcc + 4]) =
                     make_float4(acc[ru][4], acc[ru][5], acc[ru][6], acc[ru][7]);
             }
+            if (tcc == ((bq + 1) >> 1)) publish_g((bq + 1) & 1, gb + ((bq + 1) & 1) * 16);
         }
         __syncthreads();
     }

@@ -87,5 +87,14 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     pr.lo, pr.hi = 1.0, 0.0   # empty box
     assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
     assert h.value is None
+    # RP-MBADMM is implemented by the batched form only; unknown assembly modes
+    pr.phi = 0
+    o.assembly = 1
+    assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
+    o.assembly = 2
+    xo = (ctypes.c_void_p * 1)(None)
+    assert lib.rac_admm_batch(1, ctypes.byref(pr), ctypes.byref(o), xo, None) == L.RAC_ERR_ARG
+    o.assembly = 0
+    assert h.value is None
     assert lib.rac_assembly(0, 1, 0, 0, 1, None, None, None) == L.RAC_ERR_ARG
     assert lib.rac_status_string(4).decode() == "block matrix not positive definite"

@@ -3,17 +3,20 @@
 // Sec. 3.2 solves SVM duals one at a time; here a whole set of uneven
 // instances (each its own data, size, assembly stream, beta and tolerance
 // check) runs as one graph-captured period of batched kernels:
-//   k_batch_assembly    one CTA per (instance, sweep of the period)
+//   k_batch_assembly    one CTA per (instance, sweep of the period): the
+//                       random assembly, or for RP-MBADMM (Sec. 1) the random
+//                       order of the instance's fixed blocks
 //   k_batch_factor_tc   K_S^{-1} of every block of every instance, two blocks
 //                       of one instance per CTA: the block Grams
 //                       A~_S^T A~_S on the tensor cores (tcgen05, BF16 or a
 //                       two-term TF32 split), the inverse by the sweep
-//                       operator in registers (FP64 storage: k_batch_factor64
-//                       on the FP64 pipe)
-//   k_batch_chain       one CTA per instance walks its blocks in cyclic order
-//                       (an instance's chain needs no grid barrier, so
-//                       instances never wait on each other); instances are
-//                       launched largest first
+//                       operator in registers (FP64 storage or blocks above
+//                       64: k_batch_factor_cc on the CUDA cores).  Every sweep
+//                       for RAC, once per penalty for RP
+//   k_batch_chain       one CTA per instance walks its blocks in order (an
+//                       instance's chain needs no grid barrier, so instances
+//                       never wait on each other); instances are launched
+//                       largest first
 //   k_batch_prox        z-block and multiplier ascent, 256 coordinates per CTA
 //   k_batch_ref_*       exact FP64 gradient at z, KKT statistics and the
 //                       anchor reset, spread over 256-column chunks

@@ -87,29 +87,6 @@ __device__ __forceinline__ int find_instance(const int *start, int count, int un
     return lo;
 }
 
-// ---------------------------------------------------------------- 16-byte vectors
-template <class TS> struct Vec16;
-template <> struct Vec16<float> { using T = float4; static constexpr int N = 4; };
-template <> struct Vec16<double> { using T = double2; static constexpr int N = 2; };
-template <> struct Vec16<__nv_bfloat16> { using T = uint4; static constexpr int N = 8; };
-
-__device__ __forceinline__ float4 ldg16(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-__device__ __forceinline__ double2 ldg16(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
-__device__ __forceinline__ uint4 ldg16(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
-
-__device__ __forceinline__ void unpack(const float4 &a, float (&o)[4]) {
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-}
-__device__ __forceinline__ void unpack(const double2 &a, double (&o)[2]) { o[0] = a.x; o[1] = a.y; }
-// bf16 -> f32 is exact: the bf16 bits are the top half of the f32 bits
-__device__ __forceinline__ void unpack(const uint4 &a, float (&o)[8]) {
-    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        o[2 * k] = __uint_as_float(w[k] << 16);
-        o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-    }
-}
 template <class TA, int N> __device__ __forceinline__ void lds_vec(const TA *p, TA (&o)[N]) {
     if constexpr (sizeof(TA) * N == 16) {
         if constexpr (sizeof(TA) == 4) unpack(*reinterpret_cast<const float4 *>(p), o);

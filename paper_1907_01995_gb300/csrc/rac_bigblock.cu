@@ -450,23 +450,30 @@ __global__ void __launch_bounds__(256) k_big_update(ChainArgs a, TA *Mall, const
 
 // ---------------------------------------------------------------- chain
 // Residual-form chain for large blocks.  Per block: (1) every CTA writes its
-// partial A~_S^T dres over its slabs; barrier; (2) CTA c reduces the
-// partials of its share of the s columns into rhs; barrier; (3) CTA c forms
-// its share of dx = -K^{-1} rhs; barrier; (4) every CTA reads dx, updates its
-// slabs of dres and t.  Three bounded grid barriers per block.
+// partial A~_S^T dres over its slabs (a column's 32-byte slab segment is two
+// 16-byte loads; this CTA's dres slabs are converted once into shared
+// memory); barrier; (2) CTA c reduces the partials of its share of the s
+// columns into rhs, one warp per column; barrier; (3) CTA c forms its share
+// of dx = -K^{-1} rhs; barrier; (4) every CTA reads dx, updates its slabs of
+// dres (loads in batches of 16) and t.  Three bounded grid barriers per
+// block.
 template <class TS, class TA>
 __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, TA *dx_g) {
+    constexpr int VN = Vec16<TS>::N;
+    constexpr int RT = 2 * VN;                   // rows per slab: 32 bytes of storage
+    using VT = typename Vec16<TS>::T;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     BlockLayout lay(a.n, a.p);
     const int smax = lay.smax();
     int *idx = (int *)sm_raw;
     TA *dl = (TA *)(sm_raw + (((size_t)smax * sizeof(int) + 15) & ~(size_t)15));
     double *dred = (double *)(((uintptr_t)(dl + smax + 256) + 15) & ~(uintptr_t)15);
+    TA *drs = (TA *)(dred + 64);                 // this CTA's dres slabs (RT per slab)
     __shared__ int s_flag;
     const TS *As = (const TS *)a.As;
     const TA *Wall = (const TA *)a.W;
     TA *part = (TA *)a.partials;
-    const int n = a.n, R = a.R, G = gridDim.x, c = blockIdx.x;
+    const int n = a.n, G = gridDim.x, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const double gamma = a.gamma, beta = a.beta;
     const double mu = a.mu ? *a.mu : 0.0;
@@ -475,34 +482,42 @@ __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, T
     for (int i = 0; i < a.p; ++i) {
         const int s = lay.size(i), off = lay.offset(i);
         for (int q = threadIdx.x; q < s; q += blockDim.x) idx[q] = a.perm[off + q];
+        for (int k = threadIdx.x, sl = c + (k / RT) * G; sl < a.nslab;
+             k += blockDim.x, sl = c + (k / RT) * G)
+            drs[k] = (TA)a.dres[(size_t)sl * RT + (k % RT)];
         __syncthreads();
         // (1) partial A~_S^T dres over this CTA's slabs: one thread per column,
-        // each streaming the column's 32-byte sectors of its slabs
+        // each reading the column's 32-byte segment of every slab as two vectors
         for (int q = threadIdx.x; q < s; q += blockDim.x) {
             TA acc = 0;
             const size_t col = (size_t)idx[q];
-            for (int sl = c; sl < a.nslab; sl += G) {
-                const TS *seg = As + ((size_t)sl * n + col) * R;
-                const double *dr = a.dres + (size_t)sl * R;
-                for (int rr = 0; rr < R; ++rr) acc += (TA)to_f(seg[rr]) * (TA)dr[rr];
+            const TA *r = drs;
+            for (int sl = c; sl < a.nslab; sl += G, r += RT) {
+                const TS *seg = As + ((size_t)sl * n + col) * RT;
+                TA o0[VN], o1[VN];
+                unpack(ldg16(seg), o0);
+                unpack(ldg16(seg + VN), o1);
+#pragma unroll
+                for (int k = 0; k < VN; ++k) acc = fma(o0[k], r[k], acc);
+#pragma unroll
+                for (int k = 0; k < VN; ++k) acc = fma(o1[k], r[VN + k], acc);
             }
             part[(size_t)c * smax + q] = acc;
         }
         if (!grid_sync(a.bar, G, gen, a.err, &s_flag)) return;
-        // (2) rhs for this CTA's columns (all threads of the CTA reduce one
-        // column's G partials at a time, in a fixed order)
+        // (2) rhs for this CTA's columns: one warp per column reduces the G
+        // partials in a fixed order (lane-strided, then a butterfly)
         {
             const int cpc = (s + G - 1) / G;
-            for (int qq = 0; qq < cpc; ++qq) {
+            for (int qq = warp; qq < cpc; qq += nw) {
                 const int q = c * cpc + qq;
                 if (q >= s) break;
-                double acc = 0.0;
-                for (int cc = threadIdx.x; cc < G; cc += blockDim.x)
-                    acc += (double)__ldcg(part + (size_t)cc * smax + q);
-                acc = block_sum<double>(acc, dred);
-                if (threadIdx.x == 0) {
+                TA acc = 0;
+                for (int cc = lane; cc < G; cc += 32) acc += __ldcg(part + (size_t)cc * smax + q);
+                acc = warp_sum(acc);
+                if (lane == 0) {
                     const int j = idx[q];
-                    double r = a.ga[j] + acc - a.xi[j] + gamma * (a.x[j] - a.z[j]);
+                    double r = a.ga[j] + (double)acc - a.xi[j] + gamma * (a.x[j] - a.z[j]);
                     if (a.e) r += a.e[j] * (beta * t - mu);
                     rhs_g[q] = (TA)r;
                 }
@@ -530,23 +545,32 @@ __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, T
             t += block_sum<double>(loc, dred);
         }
         // dres += A~_S dx on this CTA's slabs: thread (chunk, row) sums one
-        // chunk of the columns for one row; chunks are reduced in order
+        // chunk of the columns for one row (16 loads in flight); chunks are
+        // reduced in order
         {
-            const int nch = blockDim.x / R;                    // column chunks
-            const int ch = threadIdx.x / R, rr = threadIdx.x % R;
+            const int nch = blockDim.x / RT;                   // column chunks
+            const int ch = threadIdx.x / RT, rr = threadIdx.x % RT;
             const int per = (s + nch - 1) / nch;
             TA *red = (TA *)(dl + smax);
             for (int sl = c; sl < a.nslab; sl += G) {
                 TA acc = 0;
                 const int q0 = ch * per, q1 = min(s, q0 + per);
-                for (int q = q0; q < q1; ++q)
-                    acc += (TA)to_f(As[((size_t)sl * n + idx[q]) * R + rr]) * dl[q];
+                const TS *base = As + (size_t)sl * n * RT + rr;
+                for (int qb = q0; qb < q1; qb += 16) {
+                    TS buf[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        buf[u] = qb + u < q1 ? base[(size_t)idx[qb + u] * RT] : TS(0);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        if (qb + u < q1) acc = fma((TA)to_f(buf[u]), dl[qb + u], acc);
+                }
                 red[threadIdx.x] = acc;
                 __syncthreads();
-                if (threadIdx.x < R) {
+                if (threadIdx.x < RT) {
                     TA tot = 0;
-                    for (int k2 = 0; k2 < nch; ++k2) tot += red[k2 * R + threadIdx.x];
-                    a.dres[(size_t)sl * R + threadIdx.x] += (double)tot;
+                    for (int k2 = 0; k2 < nch; ++k2) tot += red[k2 * RT + threadIdx.x];
+                    a.dres[(size_t)sl * RT + threadIdx.x] += (double)tot;
                 }
                 __syncthreads();
             }
@@ -611,8 +635,11 @@ template <class TS, class TA>
 static cudaError_t big_chain_impl(const ChainArgs &a, int grid, void *rhs, void *dxs,
                                   cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
+    if (a.R != 32 / (int)sizeof(TS)) return cudaErrorInvalidValue;   // slab = 32 bytes
+    const int per_cta = (a.nslab + grid - 1) / grid;                  // slabs of one CTA
     const size_t smem = (((size_t)lay.smax() * sizeof(int) + 15) & ~(size_t)15) +
-                        (lay.smax() + 256) * sizeof(TA) + 16 + 64 * sizeof(double);
+                        (lay.smax() + 256) * sizeof(TA) + 16 + 64 * sizeof(double) +
+                        (size_t)per_cta * a.R * sizeof(TA);
     auto kern = k_chain_res_big<TS, TA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -422,6 +422,31 @@ __device__ void block_solve(const TA *__restrict__ W, int s, const TA *rhs, TA *
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- 16-byte vectors
+// One 16-byte vector of storage elements, read through the read-only path,
+// and its unpacking into the accumulation type.
+template <class TS> struct Vec16;
+template <> struct Vec16<float> { using T = float4; static constexpr int N = 4; };
+template <> struct Vec16<double> { using T = double2; static constexpr int N = 2; };
+template <> struct Vec16<__nv_bfloat16> { using T = uint4; static constexpr int N = 8; };
+
+__device__ __forceinline__ float4 ldg16(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ double2 ldg16(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
+__device__ __forceinline__ uint4 ldg16(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+
+__device__ __forceinline__ void unpack(const float4 &a, float (&o)[4]) {
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+}
+__device__ __forceinline__ void unpack(const double2 &a, double (&o)[2]) { o[0] = a.x; o[1] = a.y; }
+// bf16 -> f32 is exact: the bf16 bits are the top half of the f32 bits
+__device__ __forceinline__ void unpack(const uint4 &a, float (&o)[8]) {
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        o[2 * k] = __uint_as_float(w[k] << 16);
+        o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
 // ---------------------------------------------------------------- random assembly
 // Random assembly (Sec. 1 eq. RAC-ADDM, Sec. 2 sigma).
 __device__ inline void block_exclusive_scan(unsigned *a, int len, unsigned *red) {

@@ -592,9 +592,10 @@ __global__ void __launch_bounds__(512) k_batch_factor_cc(BatchDesc *D, const int
 // solve dx = -K_S^{-1} rhs and the update dres += A~_S dx.  Per block:
 //   gradient  each warp takes four columns of S at a time (lanes split a
 //             column's 16-byte vectors when it is long, several short
-//             columns share a warp) and forms rhs_q = cst_q + g_q
-//             + e_q (beta t - mu) with cst = g_anchor - xi + gamma (x - z)
-//   solve     warp w computes rows w, w + 8, ... of K_S^{-1} rhs, lanes over
+//             columns share a warp) and forms rhs_q = c0_q + g_q, where
+//             c0 = cst + e (beta t - mu), cst = g_anchor - xi + gamma (x - z),
+//             is formed in FP64 by warp 0 one block ahead
+//   solve     warp w computes rows w, w + NW, ... of K_S^{-1} rhs, lanes over
 //             the columns of the row (shared-memory copy of K_S^{-1})
 //   update    thread v adds sum_q A~[v, S_q] dx_q to its 16-byte slice of
 //             dres (short columns: CG thread groups split S and are summed

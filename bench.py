@@ -30,6 +30,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "time to KKT<=1e-6 & block updates/s, chosen form vs plain FP64 GPU path"
+PRECISION = {
+    "bf16": "BF16 storage of G = A^T A, FP32 accumulation; FP64 iterates, duals, anchor "
+            "refresh and KKT",
+    "fp32": "FP32 storage of G = A^T A, FP32 accumulation; FP64 iterates, duals, anchor "
+            "refresh and KKT",
+    "fp64": "FP64 throughout"}
 WORKLOAD = dict(name="lasso_10000x2000_p20", m=10000, n=2000, p=20, lam_frac=0.1, tol=1e-6,
                 seed=0, refresh_every=10)
 CPU_SAMPLE_SECONDS = 12.0
@@ -55,46 +61,131 @@ def parse():
     ap.add_argument("--assembly", default="rac", choices=["rac", "rp"],
                     help="block assembly of --svm-batch (rac: random every sweep; rp: fixed "
                          "partition in a random order)")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="skip the Elastic-Net 2000x50000 and batched-SVM legs of the line")
     return ap.parse_args()
 
 
 def svm_batch_leg(args) -> int:
-    """Time per sweep of the batched SVM duals: the device time of the sweep
-    loop (rac_info.t_loop_ms: CUDA events on the batch's stream around all
-    periods, their refreshes and the checks between them) over the sweeps
-    run; the call's setup (host copies of A, conversions) is not in it."""
+    """Time per sweep of the batched SVM duals in one form (--storage,
+    --assembly) and print it as one JSON line (a measurement mode beside the
+    headline line)."""
+    import torch
+    K = max(args.steps, 40)
+    r = svm_batch_times(args.svm_batch, torch.device("cuda", 0),
+                        [(args.storage, args.assembly)], sweeps=K)
+    key = "%s/%s" % (args.storage, args.assembly)
+    line = dict(r[key])
+    line.update({"workload": "svm_batch_%d" % args.svm_batch, "storage": args.storage,
+                 "assembly": args.assembly, "sum_Nd": r["sum_Nd"], "data": "synthetic"})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------- extra workload legs
+EN_WORKLOAD = dict(name="elastic_net_2000x50000_p100", m=2000, n=50000, p=100, tol=1e-6,
+                   refresh_every=10)
+
+
+def _timed_call(fn, flush, st):
+    """Run fn() between CUDA events on stream st after an L2 flush; returns
+    (ms, fn's result)."""
+    import torch
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    out = fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def en_leg(dev, flush, st, fp64_max_sweeps=400):
+    """Elastic-Net 2000 x 50000 (groups of 10 columns with rho = 0.7,
+    lambda1 = 0.05 lambda_max, lambda2 = 0.1), p = 100 blocks of 500, residual
+    form, time to KKT <= 1e-6 from the resident FP64 A: the BF16- and
+    FP32-storage forms and the plain FP64 path, each a full solve (setup
+    included).  The FP64 path is capped at fp64_max_sweeps sweeps; if it
+    stops there its time per sweep and the sweeps the BF16 form needed give
+    the reported estimate, marked as such."""
     import torch
 
     import synth
     from paper_1907_01995_gb300 import api
-    insts = synth.svm_batch(0, count=args.svm_batch)
-    probs = [dict(A=s.A, b=s.b, c=s.c, E=s.E[0], d=s.d, phi="box", lo=0.0, hi=1.0)
-             for s in insts]
-    kw = dict(num_blocks=-64, beta=0.0, gamma=-0.3, tol=0.0, refresh_every=20,
-              storage=args.storage, assembly=args.assembly)
-    K = max(args.steps, 40)
+    w = EN_WORKLOAD
+    inst = synth.elastic_net_instance(0)
+    A = torch.tensor(inst.A, device=dev).t().contiguous().t()
+    b = torch.tensor(inst.b, device=dev)
+    del inst.A
+    common = dict(phi="l1l2", lambda1=inst.lam1, lambda2=inst.lam2, num_blocks=w["p"], beta=1.0,
+                  gamma=1.0, tol=w["tol"], refresh_every=w["refresh_every"], seed=0,
+                  form="residual")
+    out = {"workload": w["name"], "m": w["m"], "n": w["n"], "p": w["p"], "tol": w["tol"],
+           "lambda1": "0.05*lambda_max", "lambda2": 0.1}
 
-    def timed(sweeps):
+    def solve(storage, cap):
+        with api.Handle(A, b, storage=storage, max_sweeps=cap, **common) as h:
+            return h.solve()[1]
+
+    for storage, reps, cap in (("bf16", 2, 3000), ("fp32", 1, 3000), ("fp64", 1,
+                                                                       fp64_max_sweeps)):
+        runs = [_timed_call(lambda: solve(storage, cap), flush, st) for _ in range(reps)]
+        ms, info = min(runs, key=lambda r: r[0])
+        out[storage] = {"time_ms": ms, "sweeps": info["sweeps"], "kkt": info["kkt"],
+                        "status": info["status"], "form": info["form"],
+                        "block_updates_per_s": info["block_updates"] / (ms / 1000.0)}
+    f64, bf = out["fp64"], out["bf16"]
+    if f64["status"] == 0:
+        f64["time_to_kkt_ms"] = f64["time_ms"]
+    else:
+        f64["time_to_kkt_ms_estimate"] = f64["time_ms"] / f64["sweeps"] * bf["sweeps"]
+        f64["note"] = ("stopped at the sweep cap; estimate = its time per sweep x the sweeps "
+                       "the BF16 form needed")
+    ref = f64.get("time_to_kkt_ms", f64.get("time_to_kkt_ms_estimate"))
+    out["speedup_bf16_vs_fp64_plain"] = ref / bf["time_ms"]
+    out["speedup_fp32_vs_fp64_plain"] = ref / out["fp32"]["time_ms"]
+    del A, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def svm_batch_times(count, dev, forms, sweeps=40, seed=0):
+    """Per-sweep device time of the batched soft-margin SVM duals (count
+    uneven instances, N in [500, 20000], d in [20, 1000], blocks of 64) for
+    each (storage, assembly) in forms: rac_info.t_loop_ms (CUDA events on the
+    batch stream around all periods, their refreshes and the checks between
+    them) over `sweeps` sweeps.  Inputs are uploaded to the device once."""
+    import torch
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    insts = synth.svm_batch(seed, count=count)
+    probs = []
+    for s in insts:
+        A = torch.tensor(s.A, device=dev).t().contiguous().t()
+        probs.append(dict(A=A, b=s.b, c=s.c, E=s.E[0], d=s.d, phi="box", lo=0.0, hi=1.0))
+        s.A = None
+    res = {}
+    api.batch(probs, num_blocks=-64, beta=0.0, gamma=-0.3, tol=0.0, refresh_every=20,
+              storage="bf16", max_sweeps=2)                  # warm-up (module load)
+    for storage, assembly in forms:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, infos = api.batch(probs, max_sweeps=sweeps, **kw)
+        _, infos = api.batch(probs, num_blocks=-64, beta=0.0, gamma=-0.3, tol=0.0,
+                             refresh_every=20, storage=storage, assembly=assembly,
+                             max_sweeps=sweeps)
         torch.cuda.synchronize()
-        return time.perf_counter() - t0, infos
-
-    timed(2)                                            # warm-up (module load)
-    runs = [timed(K) for _ in range(2)]
-    infos = min(runs, key=lambda r: r[1][0]["t_loop_ms"])[1]
-    blocks = sum(i["block_updates"] for i in infos) // K
-    ms = infos[0]["t_loop_ms"] / K
-    wall = min(r[0] for r in runs)
-    print(json.dumps({
-        "workload": "svm_batch_%d" % args.svm_batch, "storage": args.storage,
-        "assembly": args.assembly, "form": infos[0]["form"], "sweeps_timed": K,
-        "ms_per_sweep": ms, "block_updates_per_s": blocks / (ms * 1e-3),
-        "blocks_per_sweep": blocks, "call_seconds": wall,
-        "sum_Nd": int(sum(s.A.shape[0] * s.A.shape[1] for s in insts)),
-        "data": "synthetic"}), flush=True)
-    return 0
+        blocks = sum(i["block_updates"] for i in infos) // sweeps
+        ms = infos[0]["t_loop_ms"] / sweeps
+        res["%s/%s" % (storage, assembly)] = {
+            "ms_per_sweep": ms, "block_updates_per_s": blocks / (ms * 1e-3),
+            "blocks_per_sweep": blocks, "sweeps_timed": sweeps, "form": infos[0]["form"],
+            "call_seconds": time.perf_counter() - t0}
+    res["sum_Nd"] = int(sum(int(p["A"].shape[0]) * int(p["A"].shape[1]) for p in probs))
+    del probs
+    torch.cuda.empty_cache()
+    return res
 
 
 # --------------------------------------------------------------- CPU oracle leg
@@ -121,10 +212,12 @@ print(json.dumps({"sweeps": sweeps, "seconds": el}))
 """
 
 
-def cpu_oracle_sample(budget=CPU_SAMPLE_SECONDS, max_sweeps=500):
+def cpu_oracle_sample(budget=CPU_SAMPLE_SECONDS, max_sweeps=500, threads=1):
     """Time the FP64 oracle (as it stands) on a bounded sample: whole sweeps of
-    the same LASSO workload, after its setup, on one host core."""
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+    the same LASSO workload, after its setup, on `threads` host cores (the
+    oracle's BLAS calls use them; its Python loop runs on one)."""
+    t = str(threads)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=t, OMP_NUM_THREADS=t, MKL_NUM_THREADS=t,
                CUDA_VISIBLE_DEVICES="")
     code = _CPU_SNIPPET % {"root": ROOT, "w": WORKLOAD, "budget": budget,
                            "max_sweeps": max_sweeps}
@@ -134,10 +227,11 @@ def cpu_oracle_sample(budget=CPU_SAMPLE_SECONDS, max_sweeps=500):
         raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
     r = json.loads(out.stdout.strip().splitlines()[-1])
     bu = r["sweeps"] * WORKLOAD["p"]
-    return {"value": bu / r["seconds"], "unit": "block_updates/s", "cores": 1, "kind": "oracle",
+    return {"value": bu / r["seconds"], "unit": "block_updates/s", "cores": threads,
+            "kind": "oracle",
             "sample": "%d whole sweeps (%d block updates) of the LASSO 10000x2000 p=20 workload "
-                      "after setup, FP64 numpy/scipy, 1 thread, %.1f s"
-                      % (r["sweeps"], bu, r["seconds"])}
+                      "after setup, FP64 numpy/scipy, %d thread(s) of %d host cores, %.1f s"
+                      % (r["sweeps"], bu, threads, os.cpu_count() or 0, r["seconds"])}
 
 
 def reference_arm(args):
@@ -230,15 +324,27 @@ def algorithmic_bytes(kclass, m, n, p, sb, ta, gram):
 
 
 def algorithmic_flops(kclass, m, n, p, gram):
-    """Floating-point operations one launch must do: the Gram-form factor
-    sweeps the augmented s_i x (s_i + s_{i-1}) matrix over s_i pivots (one
-    multiply-add per entry and pivot); the refresh is two FP64 GEMVs."""
+    """Floating-point operations the method needs per launch: the block
+    factorisation is the Cholesky factor of each K_S, sum_i s_i^3 / 3 flops
+    (the method's own work, whatever the kernel computes to get it); the
+    refresh is two FP64 GEMVs, 4 m n flops."""
     ss = block_sizes(n, p)
-    if kclass == "factor" and gram:
-        return sum(2 * s * s * (s + (ss[i - 1] if i else 0)) for i, s in enumerate(ss))
+    if kclass == "factor":
+        return sum(s ** 3 / 3.0 for s in ss)
     if kclass == "refresh":
         return 4 * m * n
     return 0
+
+
+def design_flops(kclass, m, n, p, gram):
+    """Flops the factor kernel of this design actually performs: the sweep
+    operator on the augmented s_i x (s_i + s_{i-1}) matrix [K_S | G[S_i,
+    S_{i-1}]] (one multiply-add per entry and pivot), which yields K_S^{-1}
+    and the lookahead P_i together."""
+    ss = block_sizes(n, p)
+    if kclass == "factor" and gram:
+        return sum(2 * s * s * (s + (ss[i - 1] if i else 0)) for i, s in enumerate(ss))
+    return algorithmic_flops(kclass, m, n, p, gram)
 
 
 def roofline_for(kclass, ms_per_launch, w, sb, ta, gram, peaks, sms):
@@ -249,15 +355,21 @@ def roofline_for(kclass, ms_per_launch, w, sb, ta, gram, peaks, sms):
     (nominal 1.25 TFLOP/s)."""
     m, n, p = w["m"], w["n"], w["p"]
     sec = ms_per_launch / 1000.0
-    if kclass == "factor" and gram:
+    if kclass == "factor":
         fl = algorithmic_flops("factor", m, n, p, gram)
-        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        dfl = design_flops("factor", m, n, p, gram)
+        fp64 = sb == 8
+        peak = 1.25 if fp64 else sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         ach = fl / sec / 1e12
         return {"bound": "alu", "kernel": kclass, "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "flops_per_launch": fl,
+                "flops_model": "Cholesky of every block, sum_i s_i^3/3",
+                "design_flops_per_launch": dfl,
+                "design_frac": dfl / sec / 1e12 / peak,
                 "launch_ms": ms_per_launch,
-                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
-                    sms, peaks.get("sm_max_mhz", 2070.0)),
+                "peak_source": ("nominal FP64 1.25 TFLOP/s" if fp64 else
+                                "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
+                                    sms, peaks.get("sm_max_mhz", 2070.0))),
                 "note": "one CTA per block: a launch keeps p = %d of %d SMs busy" % (p, sms)}
     if kclass == "refresh":
         fl = algorithmic_flops("refresh", m, n, p, gram)
@@ -369,18 +481,22 @@ def main():
         total_ms_max, bu_all = total_ms, float(bu)
     value = bu_all / (total_ms_max / 1000.0)
 
-    # plain FP64 GPU path on the same problem (same solve, FP64 storage, best FP64 form)
-    fp64_ms, fp64_info = [], None
-    run("fp64", "gram")
-    for _ in range(args.fp64_steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
-        _, fp64_info = run("fp64", "gram")
-        e1.record(st)
-        torch.cuda.synchronize()
-        fp64_ms.append(e0.elapsed_time(e1))
+    # other forms on the same problem, each a full solve to the same KKT:
+    # the plain FP64 GPU path (FP64 storage; its chain is the grid-barrier
+    # chain, since the one-cluster chain is FP32/BF16-only), the FP32-storage
+    # form of config 2, and the chosen storage on the grid-barrier chain (which
+    # separates the chain design's share of the speed-up from precision's)
+    def time_form(reps, storage_, form_, **extra):
+        run(storage_, form_, **extra)
+        ms_, info_ = [], None
+        for _ in range(reps):
+            t_, (_, info_) = _timed_call(lambda: run(storage_, form_, **extra), flush, st)
+            ms_.append(t_)
+        return ms_, info_
+
+    fp64_ms, fp64_info = time_form(args.fp64_steps, "fp64", "gram")
+    fp32_ms, fp32_info = time_form(args.fp64_steps, "fp32", "gram")
+    grid_ms, grid_info = time_form(args.fp64_steps, storage, form, chain="grid")
 
     # end to end through the C-ABI with pinned host buffers
     A_h = torch.empty((w["n"], w["m"]), dtype=torch.float64, pin_memory=True)
@@ -433,10 +549,25 @@ def main():
         for ent in roof.values():
             ent.setdefault("traffic", None)
 
-    cpu = None
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra_legs:
+        try:
+            extra["elastic_net_2000x50000"] = en_leg(dev, flush, st)
+        except Exception as ex:  # report, never fake
+            extra["elastic_net_2000x50000"] = {"failed": str(ex)[:300]}
+        try:
+            extra["svm_batch_256"] = svm_batch_times(
+                256, dev, [("bf16", "rp"), ("bf16", "rac"), ("fp32", "rp"), ("fp64", "rp"),
+                           ("fp64", "rac")], sweeps=40)
+        except Exception as ex:
+            extra["svm_batch_256"] = {"failed": str(ex)[:300]}
+
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ncores = os.cpu_count() or 1
         try:
             cpu = cpu_oracle_sample()
+            cpu_all = cpu_oracle_sample(threads=ncores)
         except Exception as ex:  # report, never fake
             cpu = {"value": None, "unit": "block_updates/s", "cores": 1, "kind": "oracle",
                    "sample": "failed: %s" % str(ex)[:200]}
@@ -446,22 +577,33 @@ def main():
     if rank == 0:
         ttk = statistics.mean(step_ms)
         f64 = statistics.mean(fp64_ms)
+        def form_entry(ms_list, info_):
+            t_ = statistics.mean(ms_list)
+            return {"time_to_kkt_ms": t_, "sweeps": info_["sweeps"],
+                    "block_updates_per_s": info_["block_updates"] / (t_ / 1000.0),
+                    "form": info_["form"], "kkt": info_["kkt"], "status": info_["status"]}
+
         line = {
             "metric": METRIC, "value": value, "unit": "block_updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ttk,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[storage],
             "data": "synthetic",
             "config": {"workload": w["name"], "m": w["m"], "n": w["n"], "p": w["p"],
                        "lambda1": "0.1*||A^T b||_inf", "tol": w["tol"],
                        "form": infos[-1]["form"], "grid": grid,
+                       "precision": PRECISION[storage],
                        "anchor": "FP64 refresh every %d sweeps" % w["refresh_every"],
                        "l2": "512 MB buffer written between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_kkt_ms": ttk, "sweeps": infos[-1]["sweeps"], "kkt": infos[-1]["kkt"],
-            "fp64_plain": {"time_to_kkt_ms": f64, "sweeps": fp64_info["sweeps"],
-                           "block_updates_per_s": fp64_info["block_updates"] / (f64 / 1000.0),
-                           "form": fp64_info["form"], "kkt": fp64_info["kkt"]},
+            "fp64_plain": form_entry(fp64_ms, fp64_info),
+            "fp32_form": form_entry(fp32_ms, fp32_info),
+            "chosen_storage_grid_chain": form_entry(grid_ms, grid_info),
             "speedup_vs_fp64_plain": f64 / ttk,
+            "speedup_fp32_form_vs_fp64_plain": f64 / statistics.mean(fp32_ms),
+            "cpu_baseline_all_cores": cpu_all,
+            "workloads": extra,
             "kernel_ms_per_step": {c: v / len(prof_infos) for c, v in cls_ms.items()},
             "profiled_ms_per_step": statistics.mean(prof_ms),
             "roofline": roof.get(dom, roof["chain"]),

@@ -39,6 +39,9 @@
  *     default stream); a call returns after the result has been copied out.
  *   - Handles own all device memory they allocate; rac_admm_destroy frees it.
  *   - A handle is not thread-safe: one caller thread at a time.
+ *   - Entry points other than rac_assembly_noalloc clear a non-sticky CUDA
+ *     error left pending by earlier work of the calling thread before they
+ *     start, so that it is not reported as theirs.
  */
 #ifndef RAC_ADMM_H
 #define RAC_ADMM_H
@@ -132,6 +135,12 @@ typedef struct {
                                a random order every sweep (RP-MBADMM, Sec. 1), so the block
                                factors are computed once per penalty.  RP is implemented by
                                rac_admm_batch; rac_admm_setup returns RAC_ERR_ARG for it. */
+    int32_t debug_exit_cta; /* failure-path testing only; 0 = off.  k > 0: CTA k - 1 of the
+                               residual-form block chain for blocks of at most 128 coordinates
+                               returns at its start without arriving at any grid barrier.  The
+                               other CTAs' bounded barrier waits then run out and the solve
+                               returns RAC_ERR_TIMEOUT; the handle and the device stay usable
+                               (rac_admm_reset clears the status).  Other chains ignore it. */
 } rac_options;
 
 /* KKT measure used for the stop test, evaluated in FP64 on z with the exact
@@ -215,12 +224,22 @@ rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, double *xi, d
 rac_status rac_admm_batch(int32_t count, const rac_problem *probs, const rac_options *opt,
                           double *const *x_out, rac_info *infos);
 
-/* Regularisation path on the handle's problem (phi = l1l2, data form): solve
- * for nlambda pairs (lambda1[i], lambda2[i]) together.  All points share the
- * assembly stream, gamma and the block factors, so each block step is a
- * multi-right-hand-side product.  Each point starts from the handle's warm
- * start and stops on its own.  X_out is n x nlambda column-major (host or
- * device); infos has nlambda entries. */
+/* Regularisation path on the handle's problem (phi = l1l2): solve for the
+ * nlambda pairs (lambda1[i], lambda2[i]) (lambda2 = NULL: the handle's
+ * lambda2 for every point) one after another, in the given order.  The first
+ * point starts from the handle's current state; each later point starts from
+ * the previous point's iterates (x, z, xi, mu) and continues its sweep
+ * counter, the usual warm-started path.  The points share the handle's Gram
+ * matrix (or storage copy of A), penalties and captured period graphs; only
+ * the z-block and the KKT measure depend on (lambda1, lambda2), so every
+ * point runs the same kernels as rac_admm_solve.  Each point stops on its own
+ * (KKT <= tol or max_sweeps sweeps).  X_out is n x nlambda column-major (host
+ * or device); infos (nlambda entries, or NULL) receives each point's info.
+ * On return the handle holds the last point's iterates, and its lambda1 /
+ * lambda2 are the last point's: a later rac_admm_solve continues that point.
+ * Returns RAC_ERR_ARG (nothing solved) if any lambda is negative or NaN;
+ * RAC_ERR_NOT_CONVERGED if some point hit the sweep cap (all points are still
+ * solved); any other error stops the path at the failing point. */
 rac_status rac_admm_path(rac_handle *h, int32_t nlambda, const double *lambda1,
                          const double *lambda2, double *X_out, rac_info *infos);
 
@@ -266,12 +285,20 @@ rac_status rac_gram(int64_t m, int64_t n, const double *A, int64_t lda, int32_t 
  *   - n * nsweeps > RAC_ASSEMBLY_NOALLOC_MAX returns RAC_ERR_ARG (use
  *     rac_assembly() for larger requests).
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current) and keeps it for later calls on that device, so
+ *     make the first call before any stream capture begins.  A
+ *     cudaDeviceReset() of that device invalidates the kept address (and the
+ *     library's other per-device caches): do not call the library on the
+ *     device after a reset.
  *   - All calls share the array and it keeps the last call's contents;
  *     nothing in it needs to start at zero, but calls that overlap on the GPU
  *     (on different streams) race and must not be issued concurrently.
- * perm_out / blk_out are device pointers; the call returns after the work on
- * `stream` has finished. */
+ *   - Like rac_assembly(), every call waits for its work on `stream` to
+ *     finish (cudaStreamSynchronize) before it returns.
+ *   - A CUDA error the calling thread had pending before the call is left as
+ *     it was (this call neither clears nor reports it); an error of this
+ *     call's own launch or wait returns RAC_ERR_CUDA.
+ * perm_out / blk_out are device pointers. */
 #define RAC_ASSEMBLY_NOALLOC_MAX 262144
 rac_status rac_assembly_noalloc(int64_t n, int32_t num_blocks, uint64_t seed, int64_t sweep0,
                                 int32_t nsweeps, int32_t *perm_out, int32_t *blk_out,

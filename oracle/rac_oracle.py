@@ -157,7 +157,7 @@ def rp_assembly(n: int, p: int, seed: int, sweep: int) -> List[np.ndarray]:
 # ---------------------------------------------------------------------------
 @dataclasses.dataclass
 class Problem:
-    H: np.ndarray                 # n x n, symmetric PSD
+    H: Optional[np.ndarray]       # n x n, symmetric PSD (None: data form without a dense H)
     q: np.ndarray                 # full linear term (c - A^T b in data form)
     phi: str = "none"             # none | l1l2 | box
     lam1: float = 0.0
@@ -172,7 +172,7 @@ class Problem:
 
     @property
     def n(self) -> int:
-        return self.H.shape[0]
+        return self.q.shape[0]
 
     def grad(self, x: np.ndarray) -> np.ndarray:
         """Gradient of the smooth part: H x + q, evaluated in data form as
@@ -182,19 +182,27 @@ class Problem:
         return self.H @ x + self.q
 
     def objective(self, x: np.ndarray) -> float:
-        f = 0.5 * float(x @ (self.H @ x)) + float(self.q @ x)
+        if self.H is None:
+            # data form: 1/2 x^T A^T A x + q^T x without the n x n product
+            Ax = self.A @ x
+            f = 0.5 * float(Ax @ Ax) + float(self.q @ x)
+        else:
+            f = 0.5 * float(x @ (self.H @ x)) + float(self.q @ x)
         if self.phi == "l1l2":
             f += self.lam1 * float(np.abs(x).sum()) + 0.5 * self.lam2 * float(x @ x)
         return f
 
 
 def problem_from_data(A, b, phi="none", lam1=0.0, lam2=0.0, lo=0.0, hi=0.0,
-                      c=None, E=None, d=None) -> Problem:
+                      c=None, E=None, d=None, dense_H=True) -> Problem:
+    """dense_H=False leaves H = A^T A unformed (for n too large to hold an
+    n x n matrix); the gradient, the objective and the KKT measure still work,
+    the sweep and the linear-map functions need H."""
     A = np.asarray(A, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     n = A.shape[1]
     c = np.zeros(n) if c is None else np.asarray(c, dtype=np.float64)
-    H = A.T @ A
+    H = A.T @ A if dense_H else None
     q = c - A.T @ b
     return Problem(H=H, q=q, phi=phi, lam1=lam1, lam2=lam2, lo=lo, hi=hi,
                    E=None if E is None else np.asarray(E, dtype=np.float64).reshape(-1, n),
@@ -202,10 +210,10 @@ def problem_from_data(A, b, phi="none", lam1=0.0, lam2=0.0, lo=0.0, hi=0.0,
                    A=A, b=b, c=c)
 
 
-def problem_from_instance(inst) -> Problem:
+def problem_from_instance(inst, dense_H=True) -> Problem:
     """Read the attributes of a `synth` instance (duck-typed)."""
     return problem_from_data(inst.A, inst.b, inst.phi, inst.lam1, inst.lam2,
-                             inst.lo, inst.hi, inst.c, inst.E, inst.d)
+                             inst.lo, inst.hi, inst.c, inst.E, inst.d, dense_H=dense_H)
 
 
 # ---------------------------------------------------------------------------
@@ -588,10 +596,11 @@ _CD_LIB = None
 def build_c_helpers() -> str:
     os.makedirs(_BUILD, exist_ok=True)
     out = os.path.join(_BUILD, "libracoracle.so")
-    src = os.path.join(_HERE, "cd.c")
-    if (not os.path.exists(out)) or os.path.getmtime(out) < os.path.getmtime(src):
+    srcs = [os.path.join(_HERE, "cd.c"), os.path.join(_HERE, "smo.c")]
+    if (not os.path.exists(out)) or any(os.path.getmtime(out) < os.path.getmtime(s)
+                                        for s in srcs):
         tmp = out + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"])
         os.replace(tmp, out)
     return out
 
@@ -605,6 +614,9 @@ def _cd_lib():
                                 ctypes.c_double, ctypes.c_double, dp,
                                 ctypes.c_double, ctypes.c_int64]
         lib.cd_enet.restype = ctypes.c_int64
+        lib.smo_svm.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, dp, ctypes.c_double,
+                                ctypes.c_int64]
+        lib.smo_svm.restype = ctypes.c_int64
         _CD_LIB = lib
     return _CD_LIB
 
@@ -625,3 +637,19 @@ def cd_enet(A, b, lam1, lam2=0.0, c=None, tol=1e-13, max_passes=100000, x0=None)
     if passes < 0:
         raise RuntimeError("coordinate descent did not reach tol")
     return x
+
+
+def smo_svm_c(Q, y, C, tol=1e-10, max_iter=50_000_000):
+    """SMO compiled in oracle/smo.c with second-order working-set selection
+    (Fan, Chen and Lin 2005), for duals too large for the numpy loop of
+    smo_svm.  Same optimality test (max_up - min_low <= tol).  Returns alpha."""
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    N = Q.shape[0]
+    a = np.zeros(N)
+    dp = ctypes.POINTER(ctypes.c_double)
+    it = _cd_lib().smo_svm(N, Q.ctypes.data_as(dp), y.ctypes.data_as(dp), float(C),
+                           a.ctypes.data_as(dp), float(tol), int(max_iter))
+    if it < 0:
+        raise RuntimeError("SMO did not reach tol")
+    return a

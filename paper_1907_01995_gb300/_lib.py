@@ -39,7 +39,7 @@ class RacOptions(ctypes.Structure):
                 ("seed", c_uint64), ("storage", c_int32), ("form", c_int32), ("grid", c_int32),
                 ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p), ("profile", c_int32),
                 ("xi0_from_grad", c_int32), ("ws_fallback", c_int32), ("chain", c_int32),
-                ("assembly", c_int32)]
+                ("assembly", c_int32), ("debug_exit_cta", c_int32)]
 
 
 class RacInfo(ctypes.Structure):

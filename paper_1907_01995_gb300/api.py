@@ -93,7 +93,8 @@ def make_problem(keep: _Keep, A=None, b=None, *, H=None, c=None, E=None, d=None,
 def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=1e-6,
                  max_sweeps=1000, refresh_every=10, seed=0, storage="fp64", form="auto",
                  grid=0, x0=None, xi0=None, stream=None, profile=False, xi0_from_grad=False,
-                 ws_fallback=False, chain="auto", assembly="rac") -> L.RacOptions:
+                 ws_fallback=False, chain="auto", assembly="rac",
+                 debug_exit_cta=0) -> L.RacOptions:
     o = L.RacOptions()
     L.load().rac_options_default(ctypes.byref(o))
     o.num_blocks = int(num_blocks)
@@ -111,6 +112,7 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
     o.ws_fallback = 1 if ws_fallback else 0
     o.chain = L.CHAIN[chain]
     o.assembly = L.ASSEMBLY[assembly]
+    o.debug_exit_cta = int(debug_exit_cta)
     return o
 
 
@@ -225,9 +227,11 @@ def solve(A=None, b=None, **kw):
         return h.solve()
 
 
-def batch(problems, *, out=None, **opts):
+def batch(problems, *, out=None, allow=(L.RAC_OK, L.RAC_ERR_NOT_CONVERGED), **opts):
     """Solve independent data-form problems (dicts of make_problem arguments)
-    in one persistent launch (rac_admm_batch).  Returns (list of z, infos)."""
+    in one persistent launch (rac_admm_batch).  Returns (list of z, infos);
+    raises unless the call's status is in `allow` (per-problem statuses are
+    in infos[i]["status"])."""
     lib = L.load()
     keep = _Keep()
     cnt = len(problems)
@@ -240,7 +244,7 @@ def batch(problems, *, out=None, **opts):
         (o_.data_ptr() if _is_tensor(o_) else o_.ctypes.data) for o_ in outs])
     infos = (L.RacInfo * cnt)()
     st = lib.rac_admm_batch(cnt, probs, ctypes.byref(o), ptrs, infos)
-    L.check(st, "rac_admm_batch", (L.RAC_OK, L.RAC_ERR_NOT_CONVERGED))
+    L.check(st, "rac_admm_batch", allow)
     return outs, [_info_dict(i) for i in infos]
 
 

@@ -121,6 +121,7 @@ struct rac_handle {
     int prof_nb = 0;
     double t_asm = 0, t_fac = 0, t_chain = 0, t_prox = 0, t_ref = 0;
     int64_t chain_launches = 0;
+    int dbg_exit_cta = -1;          // rac_options.debug_exit_cta - 1
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -263,6 +264,7 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.eperm = h->k ? h->eperm : nullptr;
     a.perm_in_smem = h->perm_in_smem;
     a.p_rows = h->cluster ? 1 : 0;
+    a.dbg_exit_cta = h->dbg_exit_cta;
     return a;
 }
 
@@ -530,6 +532,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->profile = o->profile != 0;
     h->xi_from_grad = o->xi0_from_grad;
     h->ws_fallback = o->ws_fallback != 0;
+    h->dbg_exit_cta = o->debug_exit_cta > 0 ? o->debug_exit_cta - 1 : -1;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     {
         const size_t nfev = std::max<size_t>(1 + (size_t)h->refresh_every, 6);
@@ -794,6 +797,7 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
     int rejected = 0;
     rac_status status = RAC_OK;
     if (dev_err) status = (rac_status)dev_err;
+    else if (hs.nonfinite) status = RAC_ERR_NUMERIC;   // NaN / Inf in the data or the state
     const bool check_ws = h->ws_fallback && h->warm && h->solves == 0;
     while (status == RAC_OK && hs.kkt > h->tol && done < h->max_sweeps) {
         int nb = std::min(h->refresh_every, h->max_sweeps - done);

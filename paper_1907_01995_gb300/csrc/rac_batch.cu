@@ -1132,7 +1132,7 @@ __global__ void __launch_bounds__(kChunk) k_batch_ref_grad(BatchDesc *D, const i
             P.cst[jv] = g - xij + d.gamma * (xj - zj);
             const double ej = e ? e[j] : 0.0;
             const double sj = kkt_coord(d.phi, g - ej * d.mu, zj, d.lam1, d.lam2, d.lo, d.hi);
-            if (!isfinite(sj) || !isfinite(xj)) st[6] = 1.0;
+            if (!isfinite(sj) || !isfinite(g) || !isfinite(xj) || !isfinite(zj)) st[6] = 1.0;
             st[0] = fmax(st[0], sj);
             st[1] = fmax(st[1], fabs(g));
             st[2] += fabs(zj);
@@ -1616,18 +1616,23 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
         for (int i = 0; i < count; ++i)
             B.hd[i].gamma = -o->gamma * std::max(B.hd[i].fro2 / B.hd[i].n, 1e-300);
     }
-    if (B.rp) {
-        // the fixed blocks' K_S^{-1} with the final penalties
-        RB_CK(cudaMemcpyAsync(B.dd, B.hd.data(), count * sizeof(BatchDesc), cudaMemcpyHostToDevice,
-                              st));
-        RB_CK(batch_factor_once(B, err));
-    }
     int active = 0;
     for (int i = 0; i < count; ++i) {
         scale[i] = std::max(1.0, B.hd[i].gmax);
         kkt[i] = eval(i);
-        if (kkt[i] <= o->tol) B.hd[i].active = 0;
+        if (B.hd[i].nonfinite) {   // NaN or Inf in the problem data
+            status[i] = RAC_ERR_NUMERIC;
+            B.hd[i].active = 0;
+        } else if (kkt[i] <= o->tol) {
+            B.hd[i].active = 0;
+        }
         active += B.hd[i].active;
+    }
+    if (B.rp) {
+        // the fixed blocks' K_S^{-1} with the final penalties (active instances only)
+        RB_CK(cudaMemcpyAsync(B.dd, B.hd.data(), count * sizeof(BatchDesc), cudaMemcpyHostToDevice,
+                              st));
+        RB_CK(batch_factor_once(B, err));
     }
     int done = 0;
     cudaEvent_t le0 = nullptr, le1 = nullptr;

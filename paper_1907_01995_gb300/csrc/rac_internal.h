@@ -94,6 +94,8 @@ struct ChainArgs {
     const double *eperm;    // lookahead: e in permuted order (n) or NULL
     int perm_in_smem;       // lookahead: the whole permutation fits in shared memory
     int p_rows;             // factor writes P_i row-major (s_i x s_{i-1}) instead of P_i^T
+    int dbg_exit_cta;       // k_chain_res: this CTA returns at its start (-1: none), so the
+                            // others' bounded barrier waits run out (failure-path testing)
     int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
     ProxArgs prox;          //   ... with these arguments
 };

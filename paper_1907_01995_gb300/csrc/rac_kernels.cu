@@ -1103,6 +1103,9 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_res(ChainArgs a) {
     const double mu = a.mu ? *a.mu : 0.0;
     double t = a.e ? *a.t : 0.0;
     unsigned gen = 0;
+    // failure-path testing: this CTA leaves before its first copy or barrier
+    // arrival; every other CTA's wait is bounded by kBarrierTimeoutNs
+    if ((int)blockIdx.x == a.dbg_exit_cta) return;
     if (a.stage) chain_prefetch<TA>(a, lay, 0, kbuf, smax);
     for (int i = 0; i < a.p; ++i) {
         const int s = lay.size(i), off = lay.offset(i);
@@ -1465,7 +1468,9 @@ __global__ void __launch_bounds__(256) k_kkt_part(int n, const double *gz, const
         const double zj = z[j], xj = x[j];
         const double v = gz[j] - (e ? e[j] * mu : 0.0);
         const double sj = kkt_coord(phi, v, zj, lam1, lam2, lo, hi);
-        if (!isfinite(sj) || !isfinite(xj)) bad = 1.0;
+        // v and z are tested too: fmax() drops a NaN, so the stationarity of a
+        // zero coordinate alone would hide a NaN gradient (NaN in A or b)
+        if (!isfinite(sj) || !isfinite(v) || !isfinite(xj) || !isfinite(zj)) bad = 1.0;
         smax = fmax(smax, sj);
         z1 += fabs(zj);
         if (e) { ez += e[j] * zj; ex += e[j] * xj; }

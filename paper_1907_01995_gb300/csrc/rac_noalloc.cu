@@ -38,6 +38,9 @@ __global__ void __launch_bounds__(1024) k_assembly_noalloc(int n, int p, uint64_
 
 // Device address of the scratch array, looked up once per device with that
 // device current (the host-side symbol is only a stand-in, not an address).
+// The address belongs to the device's primary context: a cudaDeviceReset()
+// of the device invalidates it (the header tells callers not to use the
+// library on a device after a reset).
 constexpr int kMaxDevices = 64;
 static std::mutex g_mu;
 static void *g_addr[kMaxDevices] = {nullptr};
@@ -64,20 +67,23 @@ extern "C" rac_status rac_assembly_noalloc(int64_t n, int32_t num_blocks, uint64
     if (n <= 0 || num_blocks < 1 || num_blocks > n || nsweeps <= 0 || !perm_out)
         return RAC_ERR_ARG;
     if (n * (int64_t)nsweeps > RAC_ASSEMBLY_NOALLOC_MAX) return RAC_ERR_ARG;
-    (void)cudaGetLastError();
+    // Every CUDA call below is checked through its own return code, so an
+    // error the caller left pending is neither cleared nor taken for ours.
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RAC_ERR_CUDA;
     void *scratch = nullptr;
-    if (scratch_address(dev, &scratch) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return RAC_ERR_CUDA;
-    }
+    if (scratch_address(dev, &scratch) != cudaSuccess) return RAC_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const int L = assembly_log2_buckets((int)n);
-    const size_t smem = (size_t)(3 * (1 << L) + 32) * sizeof(unsigned);
-    k_assembly_noalloc<<<nsweeps, 1024, smem, st>>>((int)n, num_blocks, seed, sweep0, perm_out,
-                                                    blk_out, (unsigned char *)scratch, L);
-    if (cudaGetLastError() != cudaSuccess) return RAC_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nsweeps);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = (size_t)(3 * (1 << L) + 32) * sizeof(unsigned);
+    cfg.stream = st;
+    if (cudaLaunchKernelEx(&cfg, k_assembly_noalloc, (int)n, (int)num_blocks, seed, sweep0,
+                           (int *)perm_out, (int *)blk_out, (unsigned char *)scratch, L) !=
+        cudaSuccess)
+        return RAC_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return RAC_ERR_CUDA;
     return RAC_OK;
 }

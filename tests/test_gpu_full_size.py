@@ -1,0 +1,120 @@
+"""GPU parity at the full sizes of the measured workloads, through the C-ABI.
+
+Elastic-Net, n >> m (Sec. 3.1's high-dimensional regime): A 2000 x 50000 with
+pairwise-correlated column groups of 10 (rho = 0.7), lambda1 = 0.05
+lambda_max, lambda2 = 0.1, p = 100 blocks of 500, residual form.  The BF16-
+and FP32-storage forms run to KKT <= 1e-7 and are compared element by element
+with the oracle's coordinate descent (run to a relative stationarity of
+1e-13): relative error <= 1e-3 (BF16) and <= 1e-5 (FP32), and the same
+support.  Identical support is only well defined where the oracle's
+complementarity margin min_{j off the support} (lambda1 - |g_j|) exceeds the
+error; the margin is printed beside the support comparison.
+
+Soft-margin linear SVM duals (Sec. 3.2, eq. svm) drawn from the full
+distribution of the batched workload (N in [500, 20000], d in [20, 1000]),
+solved together by rac_admm_batch.  alpha is not unique, so the checks are on
+quantities the KKT residuals of both points bound (tests/svm_gap.py): the
+objective gap to SMO and the distance of w = Z^T alpha to SMO's w.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import rac_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1907_01995_gb300 import api  # noqa: E402
+
+import svm_gap  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max()) / max(1.0, float(np.abs(b).max()))
+
+
+# ---------------------------------------------------------------- Elastic-Net
+@pytest.fixture(scope="module")
+def en_full():
+    inst = synth.elastic_net_instance(0)
+    x = O.cd_enet(inst.A, inst.b, inst.lam1, inst.lam2, tol=1e-13)
+    g = inst.A.T @ (inst.A @ x - inst.b)
+    off = x == 0
+    margin = float(inst.lam1 - np.abs(g[off]).max())
+    A = torch.tensor(inst.A, device="cuda").t().contiguous().t()
+    b = torch.tensor(inst.b, device="cuda")
+    return inst, x, margin, A, b
+
+
+@pytest.mark.parametrize("storage,bound", [("bf16", 1e-3), ("fp32", 1e-5)])
+def test_elastic_net_2000x50000_matches_coordinate_descent(en_full, storage, bound):
+    inst, ref, margin, A, b = en_full
+    with api.Handle(A, b, phi="l1l2", lambda1=inst.lam1, lambda2=inst.lam2, num_blocks=100,
+                    beta=1.0, gamma=1.0, tol=1e-7, max_sweeps=3000, refresh_every=10,
+                    storage=storage, form="residual") as h:
+        z, info = h.solve()
+    assert info["status"] == 0, info
+    assert info["form"].startswith("residual/" + storage), info["form"]
+    err = rel(z, ref)
+    diff = int(np.count_nonzero((z != 0) != (ref != 0)))
+    print("EN 2000x50000 %s: %d sweeps, KKT %.2e, rel err %.2e, support %d (oracle %d), "
+          "support diff %d, complementarity margin %.3e" %
+          (storage, info["sweeps"], info["kkt"], err, int((z != 0).sum()), int((ref != 0).sum()),
+           diff, margin))
+    assert err <= bound, err
+    assert diff == 0
+    P = O.problem_from_instance(inst, dense_H=False)
+    assert O.kkt(P, z)["kkt"] <= 1e-7 * 1.01
+
+
+# ---------------------------------------------------------------- SVM duals
+def _full_distribution_svms():
+    """Four instances of the batched SVM workload's own draw (master seed 0,
+    256 instances): the smallest instance with N >= 10000 and d >= 800, and
+    the instances of median, smallest and largest N * d among N <= 6000."""
+    rng = np.random.default_rng(0)
+    Ns = rng.integers(500, 20001, size=256)
+    ds = rng.integers(20, 1001, size=256)
+    big = [i for i in range(256) if Ns[i] >= 10000 and ds[i] >= 800]
+    pick = [min(big, key=lambda i: int(Ns[i]))]
+    small = sorted((i for i in range(256) if Ns[i] <= 6000), key=lambda i: int(Ns[i]) * int(ds[i]))
+    pick += [small[0], small[len(small) // 2], small[-1]]
+    return [synth.svm_instance(1 + i, int(Ns[i]), int(ds[i]), block=64) for i in pick]
+
+
+@pytest.fixture(scope="module")
+def svm_full():
+    insts = _full_distribution_svms()
+    refs = []
+    for s in insts:
+        Q = s.A.T @ s.A
+        refs.append(O.smo_svm(Q, s.E[0], 1.0, tol=1e-10))
+        del Q
+    return insts, refs
+
+
+SVM_TOL = 1e-5
+
+
+@pytest.mark.parametrize("storage,assembly", [("bf16", "rac"), ("fp32", "rac"),
+                                              ("bf16", "rp")])
+def test_svm_full_distribution_batch_matches_smo(svm_full, storage, assembly):
+    insts, refs = svm_full
+    probs = [dict(A=s.A, b=s.b, c=s.c, E=s.E[0], d=s.d, phi="box", lo=0.0, hi=1.0)
+             for s in insts]
+    zs, infos = api.batch(probs, num_blocks=-64, beta=0.0, gamma=-0.3, tol=SVM_TOL,
+                          max_sweeps=80000, refresh_every=20, seed=0, storage=storage,
+                          assembly=assembly)
+    for i, s in enumerate(insts):
+        assert infos[i]["status"] == 0, (i, s.A.shape, infos[i])
+        a = zs[i]
+        assert a.min() >= 0.0 and a.max() <= 1.0
+        P = O.problem_from_instance(s, dense_H=False)
+        assert O.kkt(P, a)["kkt"] <= SVM_TOL * 1.01
+        gap, gap_bound, wdist, w_bound = svm_gap.check(s, a, refs[i])
+        print("SVM N=%d d=%d %s/%s: %d sweeps, |f - f_smo| %.2e <= %.2e, ||w - w_smo|| "
+              "%.2e <= %.2e" % (s.A.shape[1], s.A.shape[0], storage, assembly,
+                                infos[i]["sweeps"], gap, gap_bound, wdist, w_bound))
+        assert gap <= gap_bound
+        assert wdist <= w_bound

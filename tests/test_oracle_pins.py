@@ -448,3 +448,58 @@ def test_rp_svm_matches_enumeration():
     assert info["kkt"] <= 1e-9
     obj = lambda a: 0.5 * a @ Q @ a - a.sum()
     assert abs(obj(st.z) - obj(a_enum)) < 1e-7
+
+
+def obj_m(Q, a):
+    return 0.5 * a @ Q @ a - a.sum()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_compiled_smo_matches_enumeration_and_numpy_smo(seed):
+    """The compiled SMO (oracle/smo.c, second-order pair selection) reaches the
+    enumerated optimum of tiny duals and the numpy SMO's optimum (maximal
+    violating pair) on medium ones: same objective and w (alpha need not be
+    unique)."""
+    inst = _svm_tiny(seed)
+    Q = inst.A.T @ inst.A
+    y = inst.E[0]
+    a_enum, _ = O.enum_svm(Q, y, 1.0)
+    a_c = O.smo_svm_c(Q, y, 1.0)
+    obj = lambda a: 0.5 * a @ Q @ a - a.sum()
+    assert abs(obj(a_c) - obj(a_enum)) < 1e-9
+    assert np.abs(inst.A @ a_c - inst.A @ a_enum).max() < 1e-6
+    assert abs(float(y @ a_c)) < 1e-12
+    med = synth.svm_instance(40 + seed, 240, 9)
+    Qm = med.A.T @ med.A
+    a_py = O.smo_svm(Qm, med.E[0], 1.0, tol=1e-11)
+    a_cm = O.smo_svm_c(Qm, med.E[0], 1.0, tol=1e-11)
+    assert abs(obj_m(Qm, a_py) - obj_m(Qm, a_cm)) < 1e-8 * max(1.0, abs(obj_m(Qm, a_py)))
+    assert np.abs(med.A @ a_py - med.A @ a_cm).max() < 1e-5
+    assert abs(float(med.E[0] @ a_cm)) < 1e-10
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_svm_gap_bounds_hold_for_any_feasible_point(seed):
+    """The objective and w bounds that tests/svm_gap.py derives from a dual
+    point's KKT residual hold for arbitrary box-feasible points (feasible or
+    not for y^T a = 0) against the enumerated optimum, and are ~0 at it."""
+    import svm_gap
+    inst = _svm_tiny(seed)
+    Q = inst.A.T @ inst.A
+    y = inst.E[0]
+    a_star, _ = O.enum_svm(Q, y, 1.0)
+    f = lambda a: 0.5 * a @ Q @ a - a.sum()
+    rng = np.random.default_rng(seed)
+    obj0, w0, rs0, eps0, mu0 = svm_gap.point(inst, a_star)
+    assert rs0 < 1e-9 and eps0 < 1e-12
+    for trial in range(40):
+        a = np.clip(a_star + rng.normal(scale=10.0 ** rng.uniform(-6, -1), size=a_star.size),
+                    0.0, 1.0)
+        if trial % 2:                       # project onto y^T a = 0 (then clip again)
+            a = np.clip(a - y * (y @ a) / (y @ y), 0.0, 1.0)
+        obj, w, rs, eps, mu = svm_gap.point(inst, a)
+        mstar = 2.0 * max(abs(mu), abs(mu0))
+        gap = f(a) - f(a_star)
+        assert gap <= rs + mstar * eps + 1e-12
+        assert gap >= -mstar * eps - 1e-12
+        assert 0.5 * np.sum((w - w0) ** 2) <= rs + mstar * eps + 1e-12

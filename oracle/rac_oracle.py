@@ -653,3 +653,103 @@ def smo_svm_c(Q, y, C, tol=1e-10, max_iter=50_000_000):
     if it < 0:
         raise RuntimeError("SMO did not reach tol")
     return a
+
+
+def svm_ipm(Z, y, C, tol=1e-11, max_iter=200, snap=1e-5):
+    """Primal-dual interior-point method (Mehrotra's predictor-corrector) for
+    the soft-margin SVM dual of Sec. 3.2 eq. svm,
+
+        min 1/2 a^T Q a - e^T a  s.t.  y^T a = 0,  0 <= a <= C,  Q = Z Z^T,
+
+    for duals whose N is too large for SMO but whose Q has low rank d (Z is
+    N x d, row i = y_i x_i; linear kernel).  Multipliers lam >= 0 (a >= 0),
+    nu >= 0 (a <= C) and b (y^T a = 0) make the KKT system
+
+        Q a - e - b y - lam + nu = 0,  y^T a = 0,
+        a_i lam_i = t,  (C - a_i) nu_i = t,  t -> 0.
+
+    Each Newton step eliminates lam and nu, leaving (Q + D) da - y db = r1,
+    y^T da = -y^T a with D = lam / a + nu / (C - a) diagonal, solved by the
+    Sherman-Morrison-Woodbury identity with the d x d matrix I + Z^T D^{-1} Z
+    (Cholesky), plus one step of iterative refinement.  Steps keep 0 < a < C
+    and lam, nu > 0 (fraction 0.995 to the boundary).  It stops when the
+    complementarity t and the scaled residuals are below tol; coordinates
+    within snap * C of a bound whose multiplier marks them active are then put
+    on it.  Returns alpha."""
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    N, d = Z.shape
+    e = np.ones(N)
+    a = np.full(N, 0.5 * C)
+    lam = np.ones(N)
+    nu = np.ones(N)
+    b = 0.0
+
+    def qmul(v):
+        return Z @ (Z.T @ v)
+
+    def make_solver(Dg):
+        Di = 1.0 / Dg
+        S = np.eye(d) + Z.T @ (Z * Di[:, None])
+        Lc = np.linalg.cholesky(S)
+
+        def msolve(v):
+            w = Di * v
+            t = solve_triangular(Lc, Z.T @ w, lower=True)
+            t = solve_triangular(Lc.T, t, lower=False)
+            return w - Di * (Z @ t)
+
+        def solve(v):                      # (D + Q) x = v, one refinement step
+            x = msolve(v)
+            return x + msolve(v - (Dg * x + qmul(x)))
+        return solve
+
+    def newton(solve, rd, rp, rc1, rc2):
+        r1 = -rd + rc1 / a - rc2 / (C - a)
+        u1 = solve(r1)
+        u2 = solve(y)
+        db = (-rp - y @ u1) / (y @ u2)
+        da = u1 + db * u2
+        dl = (rc1 - lam * da) / a
+        dn = (rc2 + nu * da) / (C - a)
+        return da, db, dl, dn
+
+    def max_step(v, dv):
+        neg = dv < 0
+        return min(1.0, float(np.min(-v[neg] / dv[neg]))) if neg.any() else 1.0
+
+    scale = 1.0 + float(np.abs(e).max())
+    for _ in range(max_iter):
+        Qa = qmul(a)
+        rd = Qa - e - b * y - lam + nu
+        rp = float(y @ a)
+        t = (a @ lam + (C - a) @ nu) / (2 * N)
+        if t <= tol and np.abs(rd).max() <= tol * scale and abs(rp) <= tol * max(1.0, a.sum()):
+            break
+        Dg = lam / a + nu / (C - a)
+        solve = make_solver(Dg)
+        # predictor: the affine-scaling direction (t -> 0)
+        da, db, dl, dn = newton(solve, rd, rp, -a * lam, -(C - a) * nu)
+        sp = min(max_step(a, da), max_step(C - a, -da))
+        sd = min(max_step(lam, dl), max_step(nu, dn))
+        s = min(sp, sd)
+        t_aff = ((a + s * da) @ (lam + s * dl) + (C - a - s * da) @ (nu + s * dn)) / (2 * N)
+        sigma = (t_aff / t) ** 3
+        # corrector: centring at sigma t plus the second-order terms
+        rc1 = sigma * t - a * lam - da * dl
+        rc2 = sigma * t - (C - a) * nu + da * dn
+        da, db, dl, dn = newton(solve, rd, rp, rc1, rc2)
+        sp = min(max_step(a, da), max_step(C - a, -da))
+        sd = min(max_step(lam, dl), max_step(nu, dn))
+        s = 0.995 * min(sp, sd)
+        a = a + s * da
+        b = b + s * db
+        lam = lam + s * dl
+        nu = nu + s * dn
+    else:
+        raise RuntimeError("interior-point method did not reach tol")
+    # coordinates the multipliers mark as active (a_i < lam_i, or C - a_i <
+    # nu_i) and within snap * C of their bound are put on it
+    lo = (a < lam) & (a <= snap * C)
+    hi = (C - a < nu) & (C - a <= snap * C)
+    return np.where(lo, 0.0, np.where(hi, C, a))

@@ -503,3 +503,27 @@ def test_svm_gap_bounds_hold_for_any_feasible_point(seed):
         assert gap <= rs + mstar * eps + 1e-12
         assert gap >= -mstar * eps - 1e-12
         assert 0.5 * np.sum((w - w0) ** 2) <= rs + mstar * eps + 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_interior_point_svm_matches_enumeration_and_smo(seed):
+    """The interior-point SVM dual solver reaches the enumerated optimum of
+    tiny duals, and on medium duals the SMO optimum within the bounds both
+    points' KKT residuals imply (objective and w = Z^T a)."""
+    import svm_gap
+    inst = _svm_tiny(seed)
+    Q = inst.A.T @ inst.A
+    y = inst.E[0]
+    a_enum, _ = O.enum_svm(Q, y, 1.0)
+    a_ipm = O.svm_ipm(inst.A.T, y, 1.0)
+    obj = lambda a: 0.5 * a @ Q @ a - a.sum()
+    assert abs(obj(a_ipm) - obj(a_enum)) < 1e-9
+    assert np.abs(inst.A @ a_ipm - inst.A @ a_enum).max() < 1e-6
+    med = synth.svm_instance(60 + seed, 500 + 200 * seed, 15 + 10 * seed)
+    a_smo = O.smo_svm_c(med.A.T @ med.A, med.E[0], 1.0, tol=1e-11)
+    a_ipm = O.svm_ipm(med.A.T, med.E[0], 1.0)
+    P = O.problem_from_instance(med, dense_H=False)
+    assert O.kkt(P, a_ipm)["kkt"] < 1e-6
+    gap, gap_bound, wdist, w_bound = svm_gap.check(med, a_ipm, a_smo)
+    assert gap <= gap_bound and wdist <= w_bound
+    assert gap_bound < 1e-5

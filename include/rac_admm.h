@@ -141,6 +141,10 @@ typedef struct {
                                other CTAs' bounded barrier waits then run out and the solve
                                returns RAC_ERR_TIMEOUT; the handle and the device stay usable
                                (rac_admm_reset clears the status).  Other chains ignore it. */
+    int32_t path;           /* how rac_admm_path solves its points: 0 = automatic (batched where
+                               it applies, else sequential), 1 = sequential warm-started loop,
+                               2 = batched (RAC_ERR_ARG where it does not apply); see
+                               rac_admm_path */
 } rac_options;
 
 /* KKT measure used for the stop test, evaluated in FP64 on z with the exact
@@ -226,20 +230,40 @@ rac_status rac_admm_batch(int32_t count, const rac_problem *probs, const rac_opt
 
 /* Regularisation path on the handle's problem (phi = l1l2): solve for the
  * nlambda pairs (lambda1[i], lambda2[i]) (lambda2 = NULL: the handle's
- * lambda2 for every point) one after another, in the given order.  The first
- * point starts from the handle's current state; each later point starts from
- * the previous point's iterates (x, z, xi, mu) and continues its sweep
- * counter, the usual warm-started path.  The points share the handle's Gram
- * matrix (or storage copy of A), penalties and captured period graphs; only
- * the z-block and the KKT measure depend on (lambda1, lambda2), so every
- * point runs the same kernels as rac_admm_solve.  Each point stops on its own
- * (KKT <= tol or max_sweeps sweeps).  X_out is n x nlambda column-major (host
- * or device); infos (nlambda entries, or NULL) receives each point's info.
- * On return the handle holds the last point's iterates, and its lambda1 /
- * lambda2 are the last point's: a later rac_admm_solve continues that point.
- * Returns RAC_ERR_ARG (nothing solved) if any lambda is negative or NaN;
- * RAC_ERR_NOT_CONVERGED if some point hit the sweep cap (all points are still
- * solved); any other error stops the path at the failing point. */
+ * lambda2 for every point).  Only the z-block and the KKT measure depend on
+ * (lambda1, lambda2); the Gram matrix (or storage copy of A), the penalties
+ * and, for a shared random assembly, every block factor K_S^{-1} are the same
+ * for all points.  Two ways, chosen by rac_options.path at setup:
+ *
+ * Batched (path = 2, or 0 where it applies: Gram form, no coupling row, blocks
+ * of at most 128 coordinates, and a thread-block cluster of the needed shared
+ * memory fits): all points start from the handle's current state (x, z, xi
+ * and its model gradient) and advance together, one launch per sweep for all
+ * of them: every sweep draws one random assembly (the handle's seed, sweep
+ * numbers from the handle's counter on), computes each block's K_S^{-1} once,
+ * and each block step multiplies by an s x nlambda matrix of right-hand sides
+ * (groups of 8 points per thread-block cluster).  Each point has its own
+ * z-block, multipliers and stop test: after every refresh_every sweeps the
+ * exact FP64 refresh and KKT of each running point are evaluated, and a point
+ * whose KKT <= tol stops (its state is kept as it was).  The handle's own
+ * iterates, lambdas and sweep counter are not changed.
+ *
+ * Sequential (path = 1, or 0 where the batched form does not apply): the
+ * points are solved one after another in the given order.  The first point
+ * starts from the handle's current state; each later point starts from the
+ * previous point's iterates (x, z, xi, mu) and continues the sweep counter,
+ * running exactly the kernels of rac_admm_solve.  On return the handle holds
+ * the last point's iterates and its lambda1 / lambda2 are the last point's, so
+ * a later rac_admm_solve continues that point.
+ *
+ * Either way each point stops on its own (KKT <= tol, or max_sweeps sweeps of
+ * that point).  X_out is n x nlambda column-major (host or device) and
+ * receives each point's z; infos (nlambda entries, or NULL) each point's info
+ * (form "path/..." for the batched way).  Returns RAC_ERR_ARG (nothing solved)
+ * if any lambda is negative or NaN, or path = 2 where the batched way does not
+ * apply; RAC_ERR_NOT_CONVERGED if some point hit the sweep cap (all points are
+ * still solved); RAC_ERR_NUMERIC if a point's iterates became non-finite (the
+ * others are still solved); any other error stops the call. */
 rac_status rac_admm_path(rac_handle *h, int32_t nlambda, const double *lambda1,
                          const double *lambda2, double *X_out, rac_info *infos);
 

@@ -24,6 +24,7 @@ STORAGE = {"fp64": 0, "fp32": 1, "bf16": 2}
 CHAIN = {"auto": 0, "grid": 1, "cluster": 2}
 ASSEMBLY = {"rac": 0, "rp": 1}
 FORM = {"auto": 0, "gram": 1, "residual": 2}
+PATH = {"auto": 0, "sequential": 1, "batched": 2}
 
 
 class RacProblem(ctypes.Structure):
@@ -39,7 +40,7 @@ class RacOptions(ctypes.Structure):
                 ("seed", c_uint64), ("storage", c_int32), ("form", c_int32), ("grid", c_int32),
                 ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p), ("profile", c_int32),
                 ("xi0_from_grad", c_int32), ("ws_fallback", c_int32), ("chain", c_int32),
-                ("assembly", c_int32), ("debug_exit_cta", c_int32)]
+                ("assembly", c_int32), ("debug_exit_cta", c_int32), ("path", c_int32)]
 
 
 class RacInfo(ctypes.Structure):

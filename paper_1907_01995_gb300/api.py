@@ -94,7 +94,7 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
                  max_sweeps=1000, refresh_every=10, seed=0, storage="fp64", form="auto",
                  grid=0, x0=None, xi0=None, stream=None, profile=False, xi0_from_grad=False,
                  ws_fallback=False, chain="auto", assembly="rac",
-                 debug_exit_cta=0) -> L.RacOptions:
+                 debug_exit_cta=0, path="auto") -> L.RacOptions:
     o = L.RacOptions()
     L.load().rac_options_default(ctypes.byref(o))
     o.num_blocks = int(num_blocks)
@@ -113,6 +113,7 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
     o.chain = L.CHAIN[chain]
     o.assembly = L.ASSEMBLY[assembly]
     o.debug_exit_cta = int(debug_exit_cta)
+    o.path = L.PATH[path]
     return o
 
 

@@ -122,6 +122,7 @@ struct rac_handle {
     double t_asm = 0, t_fac = 0, t_chain = 0, t_prox = 0, t_ref = 0;
     int64_t chain_launches = 0;
     int dbg_exit_cta = -1;          // rac_options.debug_exit_cta - 1
+    int path_mode = 0;              // rac_options.path
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -533,6 +534,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->xi_from_grad = o->xi0_from_grad;
     h->ws_fallback = o->ws_fallback != 0;
     h->dbg_exit_cta = o->debug_exit_cta > 0 ? o->debug_exit_cta - 1 : -1;
+    h->path_mode = o->path;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     {
         const size_t nfev = std::max<size_t>(1 + (size_t)h->refresh_every, 6);
@@ -768,6 +770,7 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
         return RAC_ERR_ARG;
     if (o->storage < RAC_FP64 || o->storage > RAC_BF16) return RAC_ERR_ARG;
     if (o->assembly != 0) return RAC_ERR_ARG;   // RP: batched form only
+    if (o->path < 0 || o->path > 2) return RAC_ERR_ARG;
     if (o->form == RAC_FORM_RESIDUAL && !pr->A) return RAC_ERR_ARG;
     int64_t smax = (pr->n + o->num_blocks - 1) / o->num_blocks;
     if (smax > 4096) return RAC_ERR_ARG;
@@ -874,10 +877,219 @@ extern "C" rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, do
 }
 
 // ---------------------------------------------------------------- path
-// Regularisation path: the points are solved in the given order, each warm
+// Sequential path: the points are solved in the given order, each warm
 // started from the previous point's iterates (x, z, xi); only the prox and
 // the KKT measure depend on (lambda1, lambda2), so the block factors, the
 // Gram matrix and the captured period graphs are shared by all points.
+static rac_status path_sequential(rac_handle *h, int nlambda, const std::vector<double> &l1,
+                                  const std::vector<double> &l2, double *X_out,
+                                  rac_info *infos) {
+    rac_status worst = RAC_OK;
+    for (int l = 0; l < nlambda; ++l) {
+        h->lam1 = l1[l];
+        h->lam2 = l2[l];
+        double lam[2] = {h->lam1, h->lam2};
+        RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, h->st));
+        RAC_ST(enqueue_refresh(h));
+        rac_info info;
+        rac_status s = rac_admm_solve(h, X_out + (size_t)l * h->n, &info);
+        if (s != RAC_OK && s != RAC_ERR_NOT_CONVERGED) return s;
+        if (s != RAC_OK && worst == RAC_OK) worst = s;
+        if (infos) infos[l] = info;
+    }
+    return worst;
+}
+
+// The batched path applies to the Gram form without a coupling row, with
+// blocks of at most 128 coordinates (K_S^{-1} from the register factor) and a
+// cluster size whose shared memory fits; returns that cluster size, else 0.
+static int path_batched_cluster(const rac_handle *h) {
+    if (!h->gram || h->k != 0 || h->phi != RAC_PHI_L1L2 || !h->kinv || h->big) return 0;
+    return path_cluster_size(h->store, h->n, BlockLayout(h->n, h->p).smax());
+}
+
+// Batched path: all points advance together from the handle's state, one
+// launch of k_path_chain per sweep (rac_path.cu), each block factor computed
+// once per sweep for all points; per-point FP64 refresh, KKT and anchor reset
+// every refresh_every sweeps.  The handle's own iterates are not touched; its
+// assembly and factor slots are reused as scratch.
+static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &l1,
+                               const std::vector<double> &l2, double *X_out, rac_info *infos,
+                               int C) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = h->st;
+    const int n = h->n;
+    const size_t nb8 = (size_t)n * sizeof(double), nL = (size_t)n * L;
+    std::vector<void *> mine;
+    auto take = [&](void **q, size_t bytes) -> rac_status {
+        cudaError_t e = cudaMallocFromPoolAsync(q, std::max<size_t>(bytes, 16), h->pool, st);
+        if (e != cudaSuccess) return map_cuda(e);
+        mine.push_back(*q);
+        return RAC_OK;
+    };
+    struct Free {   // return the call's memory on every exit
+        std::vector<void *> &v;
+        cudaStream_t s;
+        ~Free() {
+            for (void *q : v) cudaFreeAsync(q, s);
+        }
+    } release{mine, st};
+    double *X, *Z, *XI, *Gm, *GZ, *lam;
+    int *act;
+    DevStats *stats;
+    int64_t *psweep;
+    RAC_ST(take((void **)&X, nL * 8));
+    RAC_ST(take((void **)&Z, nL * 8));
+    RAC_ST(take((void **)&XI, nL * 8));
+    RAC_ST(take((void **)&Gm, nL * 8));
+    RAC_ST(take((void **)&GZ, nL * 8));
+    RAC_ST(take((void **)&lam, 2 * (size_t)L * 8));
+    RAC_ST(take((void **)&act, (size_t)L * 4));
+    RAC_ST(take((void **)&stats, (size_t)L * sizeof(DevStats)));
+    RAC_ST(take((void **)&psweep, 8));
+    for (int l = 0; l < L; ++l) {
+        RAC_CK(cudaMemcpyAsync(X + (size_t)l * n, h->x, nb8, cudaMemcpyDeviceToDevice, st));
+        RAC_CK(cudaMemcpyAsync(Z + (size_t)l * n, h->z, nb8, cudaMemcpyDeviceToDevice, st));
+        RAC_CK(cudaMemcpyAsync(XI + (size_t)l * n, h->xi, nb8, cudaMemcpyDeviceToDevice, st));
+        RAC_CK(cudaMemcpyAsync(Gm + (size_t)l * n, h->g, nb8, cudaMemcpyDeviceToDevice, st));
+    }
+    std::vector<double> lamh(2 * (size_t)L);
+    for (int l = 0; l < L; ++l) {
+        lamh[l] = l1[l];
+        lamh[L + l] = l2[l];
+    }
+    std::vector<int> active(L, 1), sweeps(L, 0), status(L, RAC_OK);
+    std::vector<double> kkt(L, INFINITY), xz(L, 0.0);
+    std::vector<DevStats> hst(L);
+    RAC_CK(cudaMemcpyAsync(lam, lamh.data(), lamh.size() * 8, cudaMemcpyHostToDevice, st));
+    RAC_CK(cudaMemcpyAsync(act, active.data(), (size_t)L * 4, cudaMemcpyHostToDevice, st));
+    RAC_CK(cudaMemcpyAsync(psweep, h->sweep_dev, 8, cudaMemcpyDeviceToDevice, st));
+    h->pre = 0;   // the handle's pre-launched period head is overwritten below
+    cudaEvent_t e0 = h->fev[0];
+    RAC_CK(cudaEventRecord(h->ev, st));
+    cudaEvent_t tbeg = nullptr, tend = nullptr;
+    RAC_CK(cudaEventCreate(&tbeg));
+    RAC_CK(cudaEventCreate(&tend));
+    struct EvFree {
+        cudaEvent_t a, b;
+        ~EvFree() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } evfree{tbeg, tend};
+    RAC_CK(cudaEventRecord(tbeg, st));
+    int64_t launches = 0;
+    int done = 0, running = L;
+    while (running > 0 && done < h->max_sweeps) {
+        const int nb = std::min(h->refresh_every, h->max_sweeps - done);
+        RAC_CK(launch_assembly(n, h->p, h->seed, 0, psweep, nb, h->perm, h->blk, h->tkey,
+                               h->tidx, st));
+        RAC_CK(cudaEventRecord(e0, st));
+        const int nfs = std::min(nb, (int)rac_handle::kFactorStreams);
+        for (int q = 0; q < nfs; ++q) RAC_CK(cudaStreamWaitEvent(h->sfs[q], e0, 0));
+        for (int s = 0; s < nb; ++s) {
+            cudaStream_t sf = h->sfs[s % rac_handle::kFactorStreams];
+            ChainArgs a = chain_args(h, s);
+            int kinv = 1;
+            RAC_CK(launch_factor(h->store, true, a, const_cast<void *>(a.W), nullptr, &kinv, sf));
+            RAC_CK(cudaEventRecord(h->fev[1 + s], sf));
+        }
+        for (int s = 0; s < nb; ++s) {
+            RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
+            PathArgs pa;
+            std::memset(&pa, 0, sizeof(pa));
+            pa.n = n;
+            pa.p = h->p;
+            pa.L = L;
+            pa.perm = h->perm + (size_t)s * n;
+            pa.W = (const char *)h->W + (size_t)s * h->wstride;
+            pa.G = h->G;
+            pa.X = X;
+            pa.Z = Z;
+            pa.XI = XI;
+            pa.Gm = Gm;
+            pa.lam1 = lam;
+            pa.lam2 = lam + L;
+            pa.active = act;
+            pa.gamma = h->gamma;
+            RAC_CK(launch_path_chain(h->store, pa, C, st));
+        }
+        RAC_CK(launch_advance(psweep, nb, st));
+        launches += 2 + 2 * (int64_t)nb;
+        // per-point exact FP64 refresh of the running points
+        for (int l = 0; l < L; ++l) {
+            if (!active[l]) continue;
+            double *zl = Z + (size_t)l * n, *xl = X + (size_t)l * n, *gz = GZ + (size_t)l * n;
+            if (h->has_A) {
+                RAC_CK(launch_resid_f64(h->m, n, h->A64, h->m, zl, h->b64, h->rbuf, h->rpart,
+                                        h->nchunk, st));
+                RAC_CK(launch_gemvt_f64(h->m, n, h->A64, h->m, h->rbuf, h->c64, gz, st));
+                launches += 3;
+            } else {
+                RAC_CK(launch_symv_f64(n, h->H64, zl, h->c64, gz, st));
+                launches += 1;
+            }
+            RAC_CK(launch_kkt(n, gz, xl, zl, nullptr, 0.0, nullptr, RAC_PHI_L1L2, l1[l], l2[l],
+                              0.0, 0.0, stats + l, h->kpart, st));
+            RAC_CK(launch_gram_anchor(h->store, n, h->G, gz, xl, zl, h->dxz,
+                                      Gm + (size_t)l * n, st));
+            launches += 2 + (h->store != ST_F64 ? 1 : 0);
+        }
+        RAC_CK(cudaMemcpyAsync(hst.data(), stats, (size_t)L * sizeof(DevStats),
+                               cudaMemcpyDeviceToHost, st));
+        RAC_CK(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RAC_CK(cudaStreamSynchronize(st));
+        done += nb;
+        if (*h->h_err) return (rac_status)*h->h_err;
+        running = 0;
+        for (int l = 0; l < L; ++l) {
+            if (!active[l]) continue;
+            sweeps[l] += nb;
+            kkt[l] = hst[l].stat_max / h->kkt_scale;
+            xz[l] = hst[l].xz_inf;
+            if (hst[l].nonfinite != 0.0 || !std::isfinite(kkt[l])) {
+                status[l] = RAC_ERR_NUMERIC;
+                active[l] = 0;
+            } else if (kkt[l] <= h->tol) {
+                active[l] = 0;
+            }
+            running += active[l];
+        }
+        RAC_CK(cudaMemcpyAsync(act, active.data(), (size_t)L * 4, cudaMemcpyHostToDevice, st));
+    }
+    RAC_CK(cudaEventRecord(tend, st));
+    for (int l = 0; l < L; ++l)
+        RAC_CK(cudaMemcpyAsync(X_out + (size_t)l * n, Z + (size_t)l * n, nb8, cudaMemcpyDefault,
+                               st));
+    RAC_CK(cudaStreamSynchronize(st));
+    float loop_ms = 0.f;
+    cudaEventElapsedTime(&loop_ms, tbeg, tend);
+    const double secs =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    rac_status worst = RAC_OK;
+    for (int l = 0; l < L; ++l) {
+        if (status[l] == RAC_OK && kkt[l] > h->tol) status[l] = RAC_ERR_NOT_CONVERGED;
+        if (status[l] == RAC_ERR_NUMERIC) worst = RAC_ERR_NUMERIC;
+        else if (status[l] != RAC_OK && worst == RAC_OK) worst = (rac_status)status[l];
+        if (infos) {
+            rac_info &inf = infos[l];
+            std::memset(&inf, 0, sizeof(inf));
+            inf.sweeps = sweeps[l];
+            inf.block_updates = (int64_t)sweeps[l] * h->p;
+            inf.kkt = kkt[l];
+            inf.primal_res = xz[l];
+            inf.seconds = secs;
+            inf.status = status[l];
+            std::snprintf(inf.form, sizeof(inf.form), "path/%s/c%d",
+                          h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
+                          C);
+            inf.kernel_launches = launches;
+            inf.t_loop_ms = loop_ms;
+        }
+    }
+    return worst;
+}
+
 extern "C" rac_status rac_admm_path(rac_handle *h, int32_t nlambda, const double *lambda1,
                                     const double *lambda2, double *X_out, rac_info *infos) {
     if (!h || nlambda <= 0 || !lambda1 || !X_out || h->phi != RAC_PHI_L1L2) return RAC_ERR_ARG;
@@ -893,20 +1105,10 @@ extern "C" rac_status rac_admm_path(rac_handle *h, int32_t nlambda, const double
     }
     for (int l = 0; l < nlambda; ++l)
         if (!(l1[l] >= 0) || !(l2[l] >= 0)) return RAC_ERR_ARG;
-    rac_status worst = RAC_OK;
-    for (int l = 0; l < nlambda; ++l) {
-        h->lam1 = l1[l];
-        h->lam2 = l2[l];
-        double lam[2] = {h->lam1, h->lam2};
-        RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, h->st));
-        RAC_ST(enqueue_refresh(h));
-        rac_info info;
-        rac_status s = rac_admm_solve(h, X_out + (size_t)l * h->n, &info);
-        if (s != RAC_OK && s != RAC_ERR_NOT_CONVERGED) return s;
-        if (s != RAC_OK && worst == RAC_OK) worst = s;
-        if (infos) infos[l] = info;
-    }
-    return worst;
+    const int C = h->path_mode == 1 ? 0 : path_batched_cluster(h);
+    if (h->path_mode == 2 && C == 0) return RAC_ERR_ARG;
+    if (C > 0) return path_batched(h, nlambda, l1, l2, X_out, infos, C);
+    return path_sequential(h, nlambda, l1, l2, X_out, infos);
 }
 
 // ---------------------------------------------------------------- checkpoint

@@ -102,6 +102,20 @@ struct ChainArgs {
 
 
 
+// Arguments of the path-batched sweep (rac_path.cu): L points of one problem
+// that differ only in (lambda1, lambda2), with per-point state stored point-
+// major (point l's n-vector at l * n).
+struct PathArgs {
+    int n, p, L;
+    const int *perm;        // this sweep's permutation (n)
+    const void *W;          // K_S^{-1} of this sweep's blocks (compute type, packed)
+    const void *G;          // n x n storage-type Gram matrix
+    double *X, *Z, *XI, *Gm;// per-point x, z, xi and model gradient (L x n)
+    const double *lam1, *lam2;  // L
+    const int *active;      // L: 0 = this point has stopped (its state is left as it is)
+    double gamma;
+};
+
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_assembly(int n, int p, uint64_t seed, int64_t sweep0, const int64_t *sweep_dev,
                             int nsweeps, int *perm, int *blk, uint64_t *tkey, int *tidx,
@@ -144,6 +158,12 @@ int big_chain_max_grid(int store);
 // usable for this problem (0: not applicable), and its launch
 int cluster_chain_size(int store, int n, int smax);
 cudaError_t launch_cluster_chain(int store, const ChainArgs &a, int C, cudaStream_t st);
+
+// path-batched sweep: the cluster size usable for this problem (0: none), the
+// points per cluster, and the launch (one cluster per group of points)
+int path_cluster_size(int store, int n, int smax);
+int path_group_points();
+cudaError_t launch_path_chain(int store, const PathArgs &a, int C, cudaStream_t st);
 
 // setup: out[0] = max_j |g0_j|, out[1] = max_j (stationarity of z = 0), one CTA
 cudaError_t launch_kkt_zero(int n, const double *g0, int phi, double lam1, double lo, double hi,

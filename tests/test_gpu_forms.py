@@ -10,6 +10,7 @@ from oracle import ws_mlp as WO
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from paper_1907_01995_gb300 import _lib  # noqa: E402
 from paper_1907_01995_gb300 import api  # noqa: E402
 from paper_1907_01995_gb300 import warmstart as ws  # noqa: E402
 
@@ -113,19 +114,86 @@ def test_batch_mixed_lasso_and_regression():
 
 
 def test_path_points_match_coordinate_descent():
+    """Sequential warm-started path: every point equals coordinate descent;
+    afterwards the handle holds the last point (its lambdas included), so a
+    further solve needs no sweep and returns the last column."""
     inst = synth.small_instance(9, 150, 60, 6, lam2=0.05)
     lmax = float(np.abs(inst.A.T @ inst.b).max())
     lams = lmax * np.geomspace(0.9, 0.05, 6)
     with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=lams[0], lambda2=0.05, num_blocks=6,
-                    tol=1e-10, max_sweeps=4000) as h:
+                    tol=1e-10, max_sweeps=4000, path="sequential") as h:
         X, infos = h.path(lams, np.full(6, 0.05))
+        z_after, info_after = h.solve()
     for l, lam in enumerate(lams):
         ref = O.cd_enet(inst.A, inst.b, lam, 0.05)
         assert infos[l]["status"] == 0
+        assert not infos[l]["form"].startswith("path/")
         assert rel(X[:, l], ref) <= 1e-8
         assert np.array_equal(X[:, l] != 0, ref != 0)
     # warm starting along the path needs fewer sweeps than the first point
     assert sum(i["sweeps"] for i in infos[1:]) / 5 <= infos[0]["sweeps"] * 1.5
+    assert info_after["sweeps"] == 0 and np.array_equal(z_after, X[:, -1])
+
+
+def _path_problem(seed, m, n, p, lam2, count, lo=0.9, hi=0.02):
+    inst = synth.small_instance(seed, m, n, p, lam2=lam2)
+    lmax = float(np.abs(inst.A.T @ inst.b).max())
+    return inst, lmax * np.geomspace(lo, hi, count)
+
+
+def test_path_batched_fp64_iterates_match_oracle():
+    """Batched path (one launch per sweep for all points, shared assembly and
+    block factors): each of 11 points (two clusters of 8, one ragged) follows
+    the oracle's own iterates for its lambda over 50 sweeps, and the handle's
+    own state is left as it was."""
+    inst, lams = _path_problem(13, 150, 60, 6, 0.05, 11)
+    l2 = np.where(np.arange(11) % 3 == 0, 0.0, 0.05)
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=lams[0], lambda2=0.05, num_blocks=6,
+                    tol=0.0, max_sweeps=50, refresh_every=10, seed=3, path="batched") as h:
+        before = h.state()
+        X, infos = h.path(lams, l2)
+        after = h.state()
+    for key in ("x", "z", "xi"):
+        assert np.array_equal(before[key], after[key])
+    for l in range(11):
+        assert infos[l]["form"].startswith("path/fp64"), infos[l]["form"]
+        assert infos[l]["sweeps"] == 50
+        P = O.problem_from_data(inst.A, inst.b, "l1l2", lams[l], l2[l])
+        st = O.initial_state(P)
+        for _ in range(50):
+            O.sweep(P, st, 6, 3, 1.0, 1.0)
+        assert rel(X[:, l], st.z) <= 1e-10, l
+
+
+@pytest.mark.parametrize("storage,tol,bound", [("fp64", 1e-10, 1e-8), ("fp32", 1e-9, 1e-5),
+                                               ("bf16", 1e-7, 1e-3)])
+def test_path_batched_converged_matches_coordinate_descent(storage, tol, bound):
+    """Batched path in every storage precision: each point stops on its own
+    at KKT <= tol and equals coordinate descent for its lambda, with the same
+    support."""
+    inst, lams = _path_problem(17, 400, 256, 4, 0.1, 12, 0.8, 0.03)
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=lams[0], lambda2=0.1, num_blocks=4,
+                    tol=tol, max_sweeps=20000, refresh_every=10, storage=storage,
+                    path="batched") as h:
+        X, infos = h.path(lams)
+    for l, lam in enumerate(lams):
+        assert infos[l]["status"] == 0, (l, infos[l])
+        assert infos[l]["form"].startswith("path/" + storage)
+        ref = O.cd_enet(inst.A, inst.b, lam, 0.1)
+        assert rel(X[:, l], ref) <= bound, (l, rel(X[:, l], ref))
+        assert np.array_equal(X[:, l] != 0, ref != 0), l
+        P = O.problem_from_data(inst.A, inst.b, "l1l2", lam, 0.1)
+        assert O.kkt(P, X[:, l])["kkt"] <= tol * 1.01 + 1e-15
+    assert len({i["sweeps"] for i in infos}) > 1     # points stop on their own
+
+
+def test_path_batched_rejected_where_it_does_not_apply():
+    inst, lams = _path_problem(19, 40, 90, 3, 0.1, 3)
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=lams[0], lambda2=0.1, num_blocks=3,
+                    tol=1e-8, form="residual", path="batched") as h:
+        with pytest.raises(_lib.RacError) as ei:
+            h.path(lams)
+    assert ei.value.status == _lib.RAC_ERR_ARG
 
 
 # ------------------------------------------------------------ warm start

@@ -193,13 +193,18 @@ class Handle:
         L.check(self._lib.rac_admm_restore(self._h, buf, len(blob)), "restore")
 
     def path(self, lambda1: Sequence[float], lambda2: Optional[Sequence[float]] = None):
+        """Regularisation path (rac_admm_path): lambda2 None keeps the handle's
+        lambda2 for every point.  Returns (X with column l = point l's z, infos)."""
         lam1 = np.ascontiguousarray(np.asarray(lambda1, dtype=np.float64))
         nl = lam1.size
-        lam2 = np.zeros(nl) if lambda2 is None else np.ascontiguousarray(
+        lam2 = None if lambda2 is None else np.ascontiguousarray(
             np.asarray(lambda2, dtype=np.float64))
+        if lam2 is not None and lam2.size != nl:
+            raise ValueError("lambda2 needs %d entries" % nl)
         X = np.empty((nl, self.n), dtype=np.float64)   # row l = column l of n x nl col-major
         infos = (L.RacInfo * nl)()
-        st = self._lib.rac_admm_path(self._h, nl, lam1.ctypes.data, lam2.ctypes.data,
+        st = self._lib.rac_admm_path(self._h, nl, lam1.ctypes.data,
+                                     None if lam2 is None else lam2.ctypes.data,
                                      X.ctypes.data, infos)
         L.check(st, "rac_admm_path", (L.RAC_OK, L.RAC_ERR_NOT_CONVERGED))
         return X.T.copy(), [_info_dict(i) for i in infos]

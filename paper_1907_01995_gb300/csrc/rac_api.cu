@@ -978,7 +978,8 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
         }
     } evfree{tbeg, tend};
     RAC_CK(cudaEventRecord(tbeg, st));
-    int64_t launches = 0;
+    int64_t launches = 0, chain_launches = 0;
+    double t_chain = 0.0, t_ref = 0.0;   // profile: device time of the chains / refreshes
     int done = 0, running = L;
     while (running > 0 && done < h->max_sweeps) {
         const int nb = std::min(h->refresh_every, h->max_sweeps - done);
@@ -994,8 +995,10 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
             RAC_CK(launch_factor(h->store, true, a, const_cast<void *>(a.W), nullptr, &kinv, sf));
             RAC_CK(cudaEventRecord(h->fev[1 + s], sf));
         }
+        const bool pf = h->profile;
         for (int s = 0; s < nb; ++s) {
             RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
+            if (pf) RAC_CK(cudaEventRecord(h->pev[3 + 5 * s + 2], st));
             PathArgs pa;
             std::memset(&pa, 0, sizeof(pa));
             pa.n = n;
@@ -1013,8 +1016,10 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
             pa.active = act;
             pa.gamma = h->gamma;
             RAC_CK(launch_path_chain(h->store, pa, C, st));
+            if (pf) RAC_CK(cudaEventRecord(h->pev[3 + 5 * s + 3], st));
         }
         RAC_CK(launch_advance(psweep, nb, st));
+        if (pf) RAC_CK(cudaEventRecord(h->pev[0], st));
         launches += 2 + 2 * (int64_t)nb;
         // per-point exact FP64 refresh of the running points
         for (int l = 0; l < L; ++l) {
@@ -1035,12 +1040,22 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
                                       Gm + (size_t)l * n, st));
             launches += 2 + (h->store != ST_F64 ? 1 : 0);
         }
+        if (pf) RAC_CK(cudaEventRecord(h->pev[1], st));
         RAC_CK(cudaMemcpyAsync(hst.data(), stats, (size_t)L * sizeof(DevStats),
                                cudaMemcpyDeviceToHost, st));
         RAC_CK(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
         RAC_CK(cudaStreamSynchronize(st));
         done += nb;
         if (*h->h_err) return (rac_status)*h->h_err;
+        if (pf) {
+            auto el = [](cudaEvent_t x, cudaEvent_t y) {
+                float ms = 0.f;
+                return cudaEventElapsedTime(&ms, x, y) == cudaSuccess ? (double)ms : 0.0;
+            };
+            for (int s = 0; s < nb; ++s) t_chain += el(h->pev[3 + 5 * s + 2], h->pev[3 + 5 * s + 3]);
+            t_ref += el(h->pev[0], h->pev[1]);
+            chain_launches += nb;
+        }
         running = 0;
         for (int l = 0; l < L; ++l) {
             if (!active[l]) continue;
@@ -1085,6 +1100,9 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
                           C);
             inf.kernel_launches = launches;
             inf.t_loop_ms = loop_ms;
+            inf.t_chain_ms = t_chain;
+            inf.t_refresh_ms = t_ref;
+            inf.chain_launches = chain_launches;
         }
     }
     return worst;

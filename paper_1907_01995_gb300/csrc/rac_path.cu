@@ -22,10 +22,15 @@
 //       every CTA's DX buffer (distributed shared memory);
 //   (2) cluster barrier;
 //   (3) every CTA adds G[S_i, own] DX_i to its gradient rows (G is symmetric,
-//       so row S_i[q] of G holds the own columns contiguously) and to x;
+//       so row S_i[q] of G holds the own columns contiguously) and to x: a
+//       thread takes a column pair and one of nq interleaved groups of the
+//       block's rows, whose partial sums meet in shared memory;
 //   (4) the owners of block i+1's coordinates store their rows of RHS_{i+1}
 //       into every CTA's RHS buffer;
 //   (5) cluster barrier.
+// A step's inputs that do not depend on DX (the thread's rows of G[S_{i+1},
+// own] and the warp's row of K_{i+1}^{-1}) are loaded into registers while
+// step i finishes, so their L2 latency overlaps the barriers.
 // The two hardware cluster barriers order every buffer reuse (a buffer is
 // rewritten only after a barrier that all its readers passed), so there is no
 // spin-wait in this kernel; every CTA executes the same number of barriers.
@@ -43,15 +48,21 @@ namespace cg = cooperative_groups;
 
 namespace rac {
 
-constexpr int kPathThreads = 256;
+constexpr int kPathThreads = 512;
 constexpr int kPathLG = 8;            // points per cluster
 constexpr int kPathSmax = 128;        // block size limit (register-factor inverses)
+constexpr int kPathPFWords = 36;      // 32-bit words of prefetched G per thread and step
 
 struct PathLayout {
-    size_t perm, bown, gown, xown, cown, rhs, dx, total;
-    int ncp;
+    size_t perm, gown, xown, cown, rhs, dx, part, total;
+    int ncp, npairs, nq;
     __host__ __device__ PathLayout(int n, int smax, int C, size_t ta) {
         ncp = ((n + C - 1) / C + 1) & ~1;      // even: a thread takes a column pair
+        npairs = ncp / 2;
+        // q-groups: the block's rows are split over nq thread groups whose
+        // partial sums are added through shared memory
+        nq = kPathThreads / npairs;
+        nq = nq < 1 ? 1 : (nq > 8 ? 8 : nq);
         size_t o = 0;
         auto take = [&](size_t bytes) {
             size_t at = o;
@@ -59,26 +70,80 @@ struct PathLayout {
             return at;
         };
         perm = take((size_t)n * 4);
-        bown = take((size_t)ncp * 4);
         gown = take((size_t)ncp * kPathLG * 8);
         xown = take((size_t)ncp * kPathLG * 8);
         cown = take((size_t)ncp * kPathLG * 8);
         rhs = take((size_t)smax * kPathLG * ta);
         dx = take((size_t)smax * kPathLG * ta);
+        part = take(nq > 1 ? (size_t)(nq - 1) * npairs * 2 * kPathLG * ta : 16);
         total = o;
     }
 };
 
-template <class TS> __device__ __forceinline__ float ld_g(const TS *p);
-template <> __device__ __forceinline__ float ld_g<float>(const float *p) { return __ldcg(p); }
-template <> __device__ __forceinline__ float ld_g<__nv_bfloat16>(const __nv_bfloat16 *p) {
-    const unsigned short u = __ldcg(reinterpret_cast<const unsigned short *>(p));
-    return __uint_as_float((unsigned)u << 16);
-}
-__device__ __forceinline__ double ld_g64(const double *p) { return __ldcg(p); }
+// Two adjacent G values (columns j, j + 1 of one row) as compute-type numbers.
+// VEC: one aligned vector load (n even); otherwise two scalar loads.
+template <class TS, bool VEC> struct GPair;
+template <bool VEC> struct GPair<__nv_bfloat16, VEC> {
+    static constexpr int W = 1;
+    __device__ static void ld(const __nv_bfloat16 *p, bool two, unsigned (&w)[W]) {
+        const unsigned short *q = reinterpret_cast<const unsigned short *>(p);
+        if (VEC) {
+            w[0] = __ldcg(reinterpret_cast<const unsigned *>(q));
+        } else {
+            const unsigned lo = __ldcg(q), hi = two ? (unsigned)__ldcg(q + 1) : 0u;
+            w[0] = lo | (hi << 16);
+        }
+    }
+    __device__ static float v0(const unsigned (&w)[W]) { return __uint_as_float(w[0] << 16); }
+    __device__ static float v1(const unsigned (&w)[W]) {
+        return __uint_as_float(w[0] & 0xffff0000u);
+    }
+};
+template <bool VEC> struct GPair<float, VEC> {
+    static constexpr int W = 2;
+    __device__ static void ld(const float *p, bool two, unsigned (&w)[W]) {
+        if (VEC) {
+            const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(p));
+            w[0] = v.x;
+            w[1] = v.y;
+        } else {
+            w[0] = __float_as_uint(__ldcg(p));
+            w[1] = two ? __float_as_uint(__ldcg(p + 1)) : 0u;
+        }
+    }
+    __device__ static float v0(const unsigned (&w)[W]) { return __uint_as_float(w[0]); }
+    __device__ static float v1(const unsigned (&w)[W]) { return __uint_as_float(w[1]); }
+};
+template <bool VEC> struct GPair<double, VEC> {
+    static constexpr int W = 4;
+    __device__ static void ld(const double *p, bool two, unsigned (&w)[W]) {
+        double a, b;
+        if (VEC) {
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+            a = v.x;
+            b = v.y;
+        } else {
+            a = __ldcg(p);
+            b = two ? __ldcg(p + 1) : 0.0;
+        }
+        w[0] = (unsigned)__double_as_longlong(a);
+        w[1] = (unsigned)(__double_as_longlong(a) >> 32);
+        w[2] = (unsigned)__double_as_longlong(b);
+        w[3] = (unsigned)(__double_as_longlong(b) >> 32);
+    }
+    __device__ static double v0(const unsigned (&w)[W]) {
+        return __longlong_as_double((long long)(((unsigned long long)w[1] << 32) | w[0]));
+    }
+    __device__ static double v1(const unsigned (&w)[W]) {
+        return __longlong_as_double((long long)(((unsigned long long)w[3] << 32) | w[2]));
+    }
+};
 
-template <class TS, class TA>
+template <class TS, class TA, bool VEC>
 __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
+    using GP = GPair<TS, VEC>;
+    constexpr int PF = kPathPFWords / GP::W;           // prefetched rows per thread
+    constexpr int KR = kPathSmax / 32;                 // K^{-1} entries per lane and row
     extern __shared__ __align__(16) unsigned char sm[];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), c = (int)cl.block_rank();
@@ -95,33 +160,35 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     BlockLayout lay(n, p);
     const int smax = lay.smax();
     const PathLayout Ly(n, smax, C, sizeof(TA));
-    const int ncp = Ly.ncp;
+    const int ncp = Ly.ncp, npairs = Ly.npairs, nq = Ly.nq;
     const int c0 = c * ncp, ncl = max(0, min(ncp, n - c0));
     int *perm = (int *)(sm + Ly.perm);
-    int *bown = (int *)(sm + Ly.bown);
     double *gown = (double *)(sm + Ly.gown);    // [ncp][LG]
     double *xown = (double *)(sm + Ly.xown);
     double *cown = (double *)(sm + Ly.cown);
     TA *rhs = (TA *)(sm + Ly.rhs);              // [smax][LG], written by the owners
     TA *dxb = (TA *)(sm + Ly.dx);               // [smax][LG], written by the row CTAs
+    TA *part = (TA *)(sm + Ly.part);            // [nq - 1][npairs][2][LG]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
     const TS *G = (const TS *)a.G;
     const TA *Wall = (const TA *)a.W;
     const double gamma = a.gamma;
+    // this thread's column pair and q-group in the gradient update
+    const int pr = threadIdx.x % npairs, qg = threadIdx.x / npairs;
+    const int cc = 2 * pr;
+    const bool upd = qg < nq && cc < ncl;
+    const bool two = cc + 1 < ncl;
+    const TS *gcol = G + c0 + cc;
+    // this warp's row of DX (at most one: C * warps >= smax)
+    const int qrow = c + C * warp;
 
     // ---- this sweep's permutation and the state of the own coordinates
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        const int j = a.perm[q];
-        perm[q] = j;
-        const int cc = j - c0;
-        if (cc >= 0 && cc < ncl) bown[cc] = lay.block_of(q);
-    }
+    for (int q = threadIdx.x; q < n; q += blockDim.x) perm[q] = a.perm[q];
     for (int t = threadIdx.x; t < ncp * kPathLG; t += blockDim.x) {
-        const int cc = t / kPathLG, l = t % kPathLG;
+        const int cq = t / kPathLG, l = t % kPathLG;
         double g = 0.0, x = 0.0, cs = 0.0;
-        if (cc < ncl && l < npts) {
-            const size_t at = (size_t)(l0 + l) * n + c0 + cc;
+        if (cq < ncl && l < npts) {
+            const size_t at = (size_t)(l0 + l) * n + c0 + cq;
             g = a.Gm[at];
             x = a.X[at];
             cs = -a.XI[at] + gamma * (x - a.Z[at]);
@@ -131,6 +198,30 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         cown[t] = cs;
     }
     __syncthreads();
+
+    // register prefetch of block b's inputs: this thread's first PF rows of
+    // G[S_b, pair], this warp's row of K_b^{-1}
+    unsigned gpf[PF][GP::W];
+    TA kpf[KR];
+    auto prefetch = [&](int b) {
+        const int s = lay.size(b), off = lay.offset(b);
+        if (upd) {
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int q = qg + nq * u;
+                if (q < s) GP::ld(gcol + (size_t)perm[off + q] * n, two, gpf[u]);
+            }
+        }
+        if (qrow < s) {
+            const TA *kr = Wall + lay.factor_offset(b) + (size_t)qrow * s;
+#pragma unroll
+            for (int u = 0; u < KR; ++u) {
+                const int k = lane + 32 * u;
+                kpf[u] = k < s ? kr[k] : (TA)0;
+            }
+        }
+    };
+    prefetch(0);
     cl.sync();   // every CTA's buffers exist before remote stores arrive
 
     // rows of RHS_b held by this CTA, stored into every CTA's buffer
@@ -138,12 +229,12 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         const int s = lay.size(b), off = lay.offset(b);
         for (int t = threadIdx.x; t < s * C; t += blockDim.x) {
             const int q = t / C, r = t % C;
-            const int cc = perm[off + q] - c0;
-            if (cc < 0 || cc >= ncl) continue;
+            const int cq = perm[off + q] - c0;
+            if (cq < 0 || cq >= ncl) continue;
             TA *dst = cl.map_shared_rank(rhs, r) + (size_t)q * kPathLG;
 #pragma unroll
             for (int l = 0; l < kPathLG; ++l)
-                dst[l] = (TA)(gown[cc * kPathLG + l] + cown[cc * kPathLG + l]);
+                dst[l] = (TA)(gown[cq * kPathLG + l] + cown[cq * kPathLG + l]);
         }
     };
     push_rhs(0);
@@ -151,24 +242,25 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
 
     for (int i = 0; i < p; ++i) {
         const int s = lay.size(i), off = lay.offset(i);
-        const TA *Kinv = Wall + lay.factor_offset(i);
-        // (1) rows q = c + C (warp + nw t) of DX_i = -K_i^{-1} RHS_i
-        for (int q = c + C * warp; q < s; q += C * nw) {
+        const bool more = i + 1 < p;
+        // (1) this warp's row of DX_i = -K_i^{-1} RHS_i, into every CTA
+        if (qrow < s) {
             TA acc[kPathLG];
 #pragma unroll
             for (int l = 0; l < kPathLG; ++l) acc[l] = 0;
-            const TA *kr = Kinv + (size_t)q * s;
-            for (int k = lane; k < s; k += 32) {
-                const TA kv = kr[k];
-                const TA *rk = rhs + (size_t)k * kPathLG;
 #pragma unroll
-                for (int l = 0; l < kPathLG; ++l) acc[l] += kv * rk[l];
+            for (int u = 0; u < KR; ++u) {
+                const int k = lane + 32 * u;
+                if (k < s) {
+                    const TA *rk = rhs + (size_t)k * kPathLG;
+#pragma unroll
+                    for (int l = 0; l < kPathLG; ++l) acc[l] += kpf[u] * rk[l];
+                }
             }
 #pragma unroll
             for (int l = 0; l < kPathLG; ++l) acc[l] = warp_sum(acc[l]);
-            // lane r < C stores the row into CTA r
-            if (lane < C) {
-                TA *dst = cl.map_shared_rank(dxb, lane) + (size_t)q * kPathLG;
+            if (lane < C) {   // lane r stores the row into CTA r
+                TA *dst = cl.map_shared_rank(dxb, lane) + (size_t)qrow * kPathLG;
 #pragma unroll
                 for (int l = 0; l < kPathLG; ++l) dst[l] = -acc[l];
             }
@@ -176,58 +268,59 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         cl.sync();   // (2) DX_i complete in every CTA
         // (3) x and the model gradient of the own coordinates
         for (int q = threadIdx.x; q < s; q += blockDim.x) {
-            const int cc = perm[off + q] - c0;
-            if (cc < 0 || cc >= ncl) continue;
+            const int cq = perm[off + q] - c0;
+            if (cq < 0 || cq >= ncl) continue;
 #pragma unroll
             for (int l = 0; l < kPathLG; ++l)
-                xown[cc * kPathLG + l] += (double)dxb[(size_t)q * kPathLG + l];
+                xown[cq * kPathLG + l] += (double)dxb[(size_t)q * kPathLG + l];
         }
-        for (int pp = threadIdx.x; 2 * pp < ncl; pp += blockDim.x) {
-            const int cc = 2 * pp;
-            const bool two = cc + 1 < ncl;
-            TA a0[kPathLG], a1[kPathLG];
+        TA a0[kPathLG], a1[kPathLG];
 #pragma unroll
-            for (int l = 0; l < kPathLG; ++l) a0[l] = a1[l] = 0;
-            const TS *gcol = G + c0 + cc;
-            int q = 0;
-            for (; q + 8 <= s; q += 8) {            // 8 independent row loads in flight
-                TA v0[8], v1[8];
+        for (int l = 0; l < kPathLG; ++l) a0[l] = a1[l] = 0;
+        if (upd) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const TS *gp = gcol + (size_t)perm[off + q + u] * n;
-                    if constexpr (sizeof(TA) == 8) {
-                        v0[u] = ld_g64((const double *)gp);
-                        v1[u] = two ? ld_g64((const double *)gp + 1) : 0.0;
-                    } else {
-                        v0[u] = ld_g<TS>(gp);
-                        v1[u] = two ? ld_g<TS>(gp + 1) : 0.f;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const TA *d = dxb + (size_t)(q + u) * kPathLG;
+            for (int u = 0; u < PF; ++u) {
+                const int q = qg + nq * u;
+                if (q < s) {
+                    const TA g0 = (TA)GP::v0(gpf[u]), g1 = (TA)GP::v1(gpf[u]);
+                    const TA *d = dxb + (size_t)q * kPathLG;
 #pragma unroll
                     for (int l = 0; l < kPathLG; ++l) {
-                        a0[l] += v0[u] * d[l];
-                        a1[l] += v1[u] * d[l];
+                        a0[l] += g0 * d[l];
+                        a1[l] += g1 * d[l];
                     }
                 }
             }
-            for (; q < s; ++q) {
-                const TS *gp = gcol + (size_t)perm[off + q] * n;
-                TA v0, v1;
-                if constexpr (sizeof(TA) == 8) {
-                    v0 = ld_g64((const double *)gp);
-                    v1 = two ? ld_g64((const double *)gp + 1) : 0.0;
-                } else {
-                    v0 = ld_g<TS>(gp);
-                    v1 = two ? ld_g<TS>(gp + 1) : 0.f;
-                }
+            // rows past the prefetched ones (few q-groups: wide CTAs)
+            for (int q = qg + nq * PF; q < s; q += nq) {
+                unsigned w[GP::W];
+                GP::ld(gcol + (size_t)perm[off + q] * n, two, w);
+                const TA g0 = (TA)GP::v0(w), g1 = (TA)GP::v1(w);
                 const TA *d = dxb + (size_t)q * kPathLG;
 #pragma unroll
                 for (int l = 0; l < kPathLG; ++l) {
-                    a0[l] += v0 * d[l];
-                    a1[l] += v1 * d[l];
+                    a0[l] += g0 * d[l];
+                    a1[l] += g1 * d[l];
+                }
+            }
+            if (qg > 0) {
+                TA *o = part + ((size_t)(qg - 1) * npairs + pr) * 2 * kPathLG;
+#pragma unroll
+                for (int l = 0; l < kPathLG; ++l) {
+                    o[l] = a0[l];
+                    o[kPathLG + l] = a1[l];
+                }
+            }
+        }
+        if (more) prefetch(i + 1);   // block i+1's G rows and K^{-1} row, in flight from here
+        __syncthreads();
+        if (upd && qg == 0) {
+            for (int g2 = 1; g2 < nq; ++g2) {
+                const TA *o = part + ((size_t)(g2 - 1) * npairs + pr) * 2 * kPathLG;
+#pragma unroll
+                for (int l = 0; l < kPathLG; ++l) {
+                    a0[l] += o[l];
+                    a1[l] += o[kPathLG + l];
                 }
             }
 #pragma unroll
@@ -238,15 +331,15 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         }
         __syncthreads();
         // (4) RHS_{i+1} from the updated gradient
-        if (i + 1 < p) push_rhs(i + 1);
+        if (more) push_rhs(i + 1);
         cl.sync();   // (5)
     }
 
     // ---- z-block and multiplier ascent of the own coordinates
     for (int t = threadIdx.x; t < ncl * kPathLG; t += blockDim.x) {
-        const int cc = t / kPathLG, l = t % kPathLG;
+        const int cq = t / kPathLG, l = t % kPathLG;
         if (l >= npts || !a.active[l0 + l]) continue;
-        const size_t at = (size_t)(l0 + l) * n + c0 + cc;
+        const size_t at = (size_t)(l0 + l) * n + c0 + cq;
         const double x = xown[t], xi = a.XI[at];
         const double z = prox_z(RAC_PHI_L1L2, x, xi, gamma, a.lam1[l0 + l], a.lam2[l0 + l],
                                 0.0, 0.0);
@@ -258,13 +351,21 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
 }
 
 template <class TS, class TA>
+static void (*path_kernel(int n))(PathArgs) {
+    return (n % 2 == 0) ? k_path_chain<TS, TA, true> : k_path_chain<TS, TA, false>;
+}
+
+template <class TS, class TA>
 static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out) {
-    const size_t smem = PathLayout(n, smax, C, sizeof(TA)).total;
+    const PathLayout Ly(n, smax, C, sizeof(TA));
+    const size_t smem = Ly.total;
+    // one DX row per warp needs C * warps >= smax; every column pair needs a thread
+    if (C * (kPathThreads / 32) < smax || Ly.npairs > kPathThreads) return cudaErrorInvalidValue;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    auto kern = k_path_chain<TS, TA>;
+    auto kern = path_kernel<TS, TA>(n);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -329,7 +430,7 @@ static cudaError_t path_launch(const PathArgs &a, int C, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_path_chain<TS, TA>, a);
+    return cudaLaunchKernelEx(&cfg, path_kernel<TS, TA>(a.n), a);
 }
 
 cudaError_t launch_path_chain(int store, const PathArgs &a, int C, cudaStream_t st) {

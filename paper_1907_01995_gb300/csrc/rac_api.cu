@@ -1081,6 +1081,7 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
     cudaEventElapsedTime(&loop_ms, tbeg, tend);
     const double secs =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const int resident = path_max_clusters(h->store, n, BlockLayout(n, h->p).smax(), C);
     rac_status worst = RAC_OK;
     for (int l = 0; l < L; ++l) {
         if (status[l] == RAC_OK && kkt[l] > h->tol) status[l] = RAC_ERR_NOT_CONVERGED;
@@ -1095,9 +1096,9 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
             inf.primal_res = xz[l];
             inf.seconds = secs;
             inf.status = status[l];
-            std::snprintf(inf.form, sizeof(inf.form), "path/%s/c%d",
+            std::snprintf(inf.form, sizeof(inf.form), "path/%s/c%dx%d",
                           h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
-                          C);
+                          C, resident);
             inf.kernel_launches = launches;
             inf.t_loop_ms = loop_ms;
             inf.t_chain_ms = t_chain;

@@ -163,6 +163,7 @@ cudaError_t launch_cluster_chain(int store, const ChainArgs &a, int C, cudaStrea
 // points per cluster, and the launch (one cluster per group of points)
 int path_cluster_size(int store, int n, int smax);
 int path_group_points();
+int path_max_clusters(int store, int n, int smax, int C);   // co-resident clusters
 cudaError_t launch_path_chain(int store, const PathArgs &a, int C, cudaStream_t st);
 
 // setup: out[0] = max_j |g0_j|, out[1] = max_j (stationarity of z = 0), one CTA

@@ -356,7 +356,7 @@ static void (*path_kernel(int n))(PathArgs) {
 }
 
 template <class TS, class TA>
-static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out) {
+static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out, int *clusters_out = nullptr) {
     const PathLayout Ly(n, smax, C, sizeof(TA));
     const size_t smem = Ly.total;
     // one DX row per warp needs C * warps >= smax; every column pair needs a thread
@@ -389,6 +389,7 @@ static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out) {
     if (e != cudaSuccess) return e;
     if (clusters < 1) return cudaErrorInvalidValue;
     *smem_out = smem;
+    if (clusters_out) *clusters_out = clusters;
     return cudaSuccess;
 }
 
@@ -410,6 +411,19 @@ int path_cluster_size(int store, int n, int smax) {
 }
 
 int path_group_points() { return kPathLG; }
+
+int path_max_clusters(int store, int n, int smax, int C) {
+    size_t smem = 0;
+    int k = 0;
+    cudaError_t e = store == ST_F64   ? path_prepare<double, double>(n, smax, C, &smem, &k)
+                    : store == ST_F32 ? path_prepare<float, float>(n, smax, C, &smem, &k)
+                                      : path_prepare<__nv_bfloat16, float>(n, smax, C, &smem, &k);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return k;
+}
 
 template <class TS, class TA>
 static cudaError_t path_launch(const PathArgs &a, int C, cudaStream_t st) {

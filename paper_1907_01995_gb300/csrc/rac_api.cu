@@ -902,10 +902,10 @@ static rac_status path_sequential(rac_handle *h, int nlambda, const std::vector<
 
 // The batched path applies to the Gram form without a coupling row, with
 // blocks of at most 128 coordinates (K_S^{-1} from the register factor) and a
-// cluster size whose shared memory fits; returns that cluster size, else 0.
-static int path_batched_cluster(const rac_handle *h) {
-    if (!h->gram || h->k != 0 || h->phi != RAC_PHI_L1L2 || !h->kinv || h->big) return 0;
-    return path_cluster_size(h->store, h->n, BlockLayout(h->n, h->p).smax());
+// cluster launch whose shared memory fits; false where it does not apply.
+static bool path_batched_shape(const rac_handle *h, int L, PathShape *sh) {
+    if (!h->gram || h->k != 0 || h->phi != RAC_PHI_L1L2 || !h->kinv || h->big) return false;
+    return path_shape(h->store, h->n, BlockLayout(h->n, h->p).smax(), L, sh);
 }
 
 // Batched path: all points advance together from the handle's state, one
@@ -915,7 +915,7 @@ static int path_batched_cluster(const rac_handle *h) {
 // assembly and factor slots are reused as scratch.
 static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &l1,
                                const std::vector<double> &l2, double *X_out, rac_info *infos,
-                               int C) {
+                               const PathShape &sh) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = h->st;
     const int n = h->n;
@@ -1015,7 +1015,7 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
             pa.lam2 = lam + L;
             pa.active = act;
             pa.gamma = h->gamma;
-            RAC_CK(launch_path_chain(h->store, pa, C, st));
+            RAC_CK(launch_path_chain(h->store, pa, sh, st));
             if (pf) RAC_CK(cudaEventRecord(h->pev[3 + 5 * s + 3], st));
         }
         RAC_CK(launch_advance(psweep, nb, st));
@@ -1081,7 +1081,6 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
     cudaEventElapsedTime(&loop_ms, tbeg, tend);
     const double secs =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    const int resident = path_max_clusters(h->store, n, BlockLayout(n, h->p).smax(), C);
     rac_status worst = RAC_OK;
     for (int l = 0; l < L; ++l) {
         if (status[l] == RAC_OK && kkt[l] > h->tol) status[l] = RAC_ERR_NOT_CONVERGED;
@@ -1096,9 +1095,9 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
             inf.primal_res = xz[l];
             inf.seconds = secs;
             inf.status = status[l];
-            std::snprintf(inf.form, sizeof(inf.form), "path/%s/c%dx%d",
+            std::snprintf(inf.form, sizeof(inf.form), "path/%s/c%d/g%d/r%d",
                           h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
-                          C, resident);
+                          sh.C, sh.lg, sh.resident);
             inf.kernel_launches = launches;
             inf.t_loop_ms = loop_ms;
             inf.t_chain_ms = t_chain;
@@ -1124,9 +1123,10 @@ extern "C" rac_status rac_admm_path(rac_handle *h, int32_t nlambda, const double
     }
     for (int l = 0; l < nlambda; ++l)
         if (!(l1[l] >= 0) || !(l2[l] >= 0)) return RAC_ERR_ARG;
-    const int C = h->path_mode == 1 ? 0 : path_batched_cluster(h);
-    if (h->path_mode == 2 && C == 0) return RAC_ERR_ARG;
-    if (C > 0) return path_batched(h, nlambda, l1, l2, X_out, infos, C);
+    PathShape sh;
+    const bool batched = h->path_mode != 1 && path_batched_shape(h, nlambda, &sh);
+    if (h->path_mode == 2 && !batched) return RAC_ERR_ARG;
+    if (batched) return path_batched(h, nlambda, l1, l2, X_out, infos, sh);
     return path_sequential(h, nlambda, l1, l2, X_out, infos);
 }
 

@@ -159,12 +159,15 @@ int big_chain_max_grid(int store);
 int cluster_chain_size(int store, int n, int smax);
 cudaError_t launch_cluster_chain(int store, const ChainArgs &a, int C, cudaStream_t st);
 
-// path-batched sweep: the cluster size usable for this problem (0: none), the
-// points per cluster, and the launch (one cluster per group of points)
-int path_cluster_size(int store, int n, int smax);
-int path_group_points();
-int path_max_clusters(int store, int n, int smax, int C);   // co-resident clusters
-cudaError_t launch_path_chain(int store, const PathArgs &a, int C, cudaStream_t st);
+// path-batched sweep: its launch shape for L points (cluster size, points per
+// cluster, co-resident clusters; false: no shape fits) and its launch (one
+// cluster per group of points)
+struct PathShape {
+    int C, lg, resident;
+};
+bool path_shape(int store, int n, int smax, int L, PathShape *out);
+cudaError_t launch_path_chain(int store, const PathArgs &a, const PathShape &sh,
+                              cudaStream_t st);
 
 // setup: out[0] = max_j |g0_j|, out[1] = max_j (stationarity of z = 0), one CTA
 cudaError_t launch_kkt_zero(int n, const double *g0, int phi, double lam1, double lo, double hi,

@@ -49,14 +49,15 @@ namespace cg = cooperative_groups;
 namespace rac {
 
 constexpr int kPathThreads = 512;
-constexpr int kPathLG = 8;            // points per cluster
 constexpr int kPathSmax = 128;        // block size limit (register-factor inverses)
-constexpr int kPathPFWords = 36;      // 32-bit words of prefetched G per thread and step
+// 32-bit words of prefetched G per thread and step (registers left beside the
+// 2 LG accumulators)
+__host__ __device__ constexpr int path_pf_words(int lg) { return lg <= 8 ? 36 : (lg <= 12 ? 28 : 20); }
 
 struct PathLayout {
     size_t perm, gown, xown, cown, rhs, dx, part, total;
     int ncp, npairs, nq;
-    __host__ __device__ PathLayout(int n, int smax, int C, size_t ta) {
+    __host__ __device__ PathLayout(int n, int smax, int C, size_t ta, int lg) {
         ncp = ((n + C - 1) / C + 1) & ~1;      // even: a thread takes a column pair
         npairs = ncp / 2;
         // q-groups: the block's rows are split over nq thread groups whose
@@ -70,12 +71,12 @@ struct PathLayout {
             return at;
         };
         perm = take((size_t)n * 4);
-        gown = take((size_t)ncp * kPathLG * 8);
-        xown = take((size_t)ncp * kPathLG * 8);
-        cown = take((size_t)ncp * kPathLG * 8);
-        rhs = take((size_t)smax * kPathLG * ta);
-        dx = take((size_t)smax * kPathLG * ta);
-        part = take(nq > 1 ? (size_t)(nq - 1) * npairs * 2 * kPathLG * ta : 16);
+        gown = take((size_t)ncp * lg * 8);
+        xown = take((size_t)ncp * lg * 8);
+        cown = take((size_t)ncp * lg * 8);
+        rhs = take((size_t)smax * lg * ta);
+        dx = take((size_t)smax * lg * ta);
+        part = take(nq > 1 ? (size_t)(nq - 1) * npairs * 2 * lg * ta : 16);
         total = o;
     }
 };
@@ -139,10 +140,33 @@ template <bool VEC> struct GPair<double, VEC> {
     }
 };
 
-template <class TS, class TA, bool VEC>
+// LG consecutive compute-type values of shared memory (16-byte aligned) by
+// 16-byte vector loads
+template <int LG> __device__ __forceinline__ void lds_row(const float *p, float (&v)[LG]) {
+    static_assert(LG % 4 == 0, "rows of whole float4s");
+#pragma unroll
+    for (int u = 0; u < LG / 4; ++u) {
+        const float4 f = reinterpret_cast<const float4 *>(p)[u];
+        v[4 * u] = f.x;
+        v[4 * u + 1] = f.y;
+        v[4 * u + 2] = f.z;
+        v[4 * u + 3] = f.w;
+    }
+}
+template <int LG> __device__ __forceinline__ void lds_row(const double *p, double (&v)[LG]) {
+#pragma unroll
+    for (int u = 0; u < LG / 2; ++u) {
+        const double2 f = reinterpret_cast<const double2 *>(p)[u];
+        v[2 * u] = f.x;
+        v[2 * u + 1] = f.y;
+    }
+}
+
+template <class TS, class TA, bool VEC, int LG>
 __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     using GP = GPair<TS, VEC>;
-    constexpr int PF = kPathPFWords / GP::W;           // prefetched rows per thread
+    constexpr int kPathLG = LG;
+    constexpr int PF = path_pf_words(LG) / GP::W;      // prefetched rows per thread
     constexpr int KR = kPathSmax / 32;                 // K^{-1} entries per lane and row
     extern __shared__ __align__(16) unsigned char sm[];
     cg::cluster_group cl = cg::this_cluster();
@@ -159,7 +183,7 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
 
     BlockLayout lay(n, p);
     const int smax = lay.smax();
-    const PathLayout Ly(n, smax, C, sizeof(TA));
+    const PathLayout Ly(n, smax, C, sizeof(TA), LG);
     const int ncp = Ly.ncp, npairs = Ly.npairs, nq = Ly.nq;
     const int c0 = c * ncp, ncl = max(0, min(ncp, n - c0));
     int *perm = (int *)(sm + Ly.perm);
@@ -252,9 +276,10 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
             for (int u = 0; u < KR; ++u) {
                 const int k = lane + 32 * u;
                 if (k < s) {
-                    const TA *rk = rhs + (size_t)k * kPathLG;
+                    TA rk[LG];
+                    lds_row<LG>(rhs + (size_t)k * LG, rk);
 #pragma unroll
-                    for (int l = 0; l < kPathLG; ++l) acc[l] += kpf[u] * rk[l];
+                    for (int l = 0; l < LG; ++l) acc[l] += kpf[u] * rk[l];
                 }
             }
 #pragma unroll
@@ -283,9 +308,10 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
                 const int q = qg + nq * u;
                 if (q < s) {
                     const TA g0 = (TA)GP::v0(gpf[u]), g1 = (TA)GP::v1(gpf[u]);
-                    const TA *d = dxb + (size_t)q * kPathLG;
+                    TA d[LG];
+                    lds_row<LG>(dxb + (size_t)q * LG, d);
 #pragma unroll
-                    for (int l = 0; l < kPathLG; ++l) {
+                    for (int l = 0; l < LG; ++l) {
                         a0[l] += g0 * d[l];
                         a1[l] += g1 * d[l];
                     }
@@ -296,9 +322,10 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
                 unsigned w[GP::W];
                 GP::ld(gcol + (size_t)perm[off + q] * n, two, w);
                 const TA g0 = (TA)GP::v0(w), g1 = (TA)GP::v1(w);
-                const TA *d = dxb + (size_t)q * kPathLG;
+                TA d[LG];
+                lds_row<LG>(dxb + (size_t)q * LG, d);
 #pragma unroll
-                for (int l = 0; l < kPathLG; ++l) {
+                for (int l = 0; l < LG; ++l) {
                     a0[l] += g0 * d[l];
                     a1[l] += g1 * d[l];
                 }
@@ -350,14 +377,14 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     }
 }
 
-template <class TS, class TA>
+template <class TS, class TA, int LG>
 static void (*path_kernel(int n))(PathArgs) {
-    return (n % 2 == 0) ? k_path_chain<TS, TA, true> : k_path_chain<TS, TA, false>;
+    return (n % 2 == 0) ? k_path_chain<TS, TA, true, LG> : k_path_chain<TS, TA, false, LG>;
 }
 
-template <class TS, class TA>
-static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out, int *clusters_out = nullptr) {
-    const PathLayout Ly(n, smax, C, sizeof(TA));
+template <class TS, class TA, int LG>
+static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out, int *clusters_out) {
+    const PathLayout Ly(n, smax, C, sizeof(TA), LG);
     const size_t smem = Ly.total;
     // one DX row per warp needs C * warps >= smax; every column pair needs a thread
     if (C * (kPathThreads / 32) < smax || Ly.npairs > kPathThreads) return cudaErrorInvalidValue;
@@ -365,7 +392,7 @@ static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out, int *c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    auto kern = path_kernel<TS, TA>(n);
+    auto kern = path_kernel<TS, TA, LG>(n);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -393,45 +420,58 @@ static cudaError_t path_prepare(int n, int smax, int C, size_t *smem_out, int *c
     return cudaSuccess;
 }
 
+constexpr int kPathGroups[3] = {8, 12, 16};
+
 template <class TS, class TA>
-static int path_pick(int n, int smax) {
-    if (smax > kPathSmax) return 0;
+static cudaError_t prepare_any(int lg, int n, int smax, int C, size_t *smem, int *clusters) {
+    if (lg == 8) return path_prepare<TS, TA, 8>(n, smax, C, smem, clusters);
+    if (lg == 12) return path_prepare<TS, TA, 12>(n, smax, C, smem, clusters);
+    if (lg == 16) return path_prepare<TS, TA, 16>(n, smax, C, smem, clusters);
+    return cudaErrorInvalidValue;
+}
+static cudaError_t prepare_store(int store, int lg, int n, int smax, int C, size_t *smem,
+                                 int *clusters) {
+    if (store == ST_F64) return prepare_any<double, double>(lg, n, smax, C, smem, clusters);
+    if (store == ST_F32) return prepare_any<float, float>(lg, n, smax, C, smem, clusters);
+    return prepare_any<__nv_bfloat16, float>(lg, n, smax, C, smem, clusters);
+}
+
+// Launch shape of the path chain for L points: the cluster size C (16, else
+// 8) and the points per cluster LG, the smallest of 8, 12, 16 whose
+// ceil(L / LG) clusters are all co-resident (a second wave of clusters would
+// double the sweep), else 16.  Returns false if no shape fits.
+bool path_shape(int store, int n, int smax, int L, PathShape *out) {
+    if (smax > kPathSmax) return false;
     for (int C : {16, 8}) {
-        size_t smem = 0;
-        if (path_prepare<TS, TA>(n, smax, C, &smem) == cudaSuccess) return C;
-        (void)cudaGetLastError();
+        int best = 0, res_best = 0;
+        for (int lg : kPathGroups) {
+            size_t smem = 0;
+            int res = 0;
+            if (prepare_store(store, lg, n, smax, C, &smem, &res) != cudaSuccess) {
+                (void)cudaGetLastError();
+                continue;
+            }
+            best = lg;
+            res_best = res;
+            if ((L + lg - 1) / lg <= res) break;
+        }
+        if (best) {
+            out->C = C;
+            out->lg = best;
+            out->resident = res_best;
+            return true;
+        }
     }
-    return 0;
+    return false;
 }
 
-int path_cluster_size(int store, int n, int smax) {
-    if (store == ST_F64) return path_pick<double, double>(n, smax);
-    if (store == ST_F32) return path_pick<float, float>(n, smax);
-    return path_pick<__nv_bfloat16, float>(n, smax);
-}
-
-int path_group_points() { return kPathLG; }
-
-int path_max_clusters(int store, int n, int smax, int C) {
-    size_t smem = 0;
-    int k = 0;
-    cudaError_t e = store == ST_F64   ? path_prepare<double, double>(n, smax, C, &smem, &k)
-                    : store == ST_F32 ? path_prepare<float, float>(n, smax, C, &smem, &k)
-                                      : path_prepare<__nv_bfloat16, float>(n, smax, C, &smem, &k);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        return 0;
-    }
-    return k;
-}
-
-template <class TS, class TA>
+template <class TS, class TA, int LG>
 static cudaError_t path_launch(const PathArgs &a, int C, cudaStream_t st) {
     const int smax = BlockLayout(a.n, a.p).smax();
     size_t smem = 0;
-    cudaError_t e = path_prepare<TS, TA>(a.n, smax, C, &smem);
+    cudaError_t e = path_prepare<TS, TA, LG>(a.n, smax, C, &smem, nullptr);
     if (e != cudaSuccess) return e;
-    const int groups = (a.L + kPathLG - 1) / kPathLG;
+    const int groups = (a.L + LG - 1) / LG;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(groups * C);
     cfg.blockDim = dim3(kPathThreads);
@@ -444,13 +484,22 @@ static cudaError_t path_launch(const PathArgs &a, int C, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, path_kernel<TS, TA>(a.n), a);
+    return cudaLaunchKernelEx(&cfg, path_kernel<TS, TA, LG>(a.n), a);
 }
 
-cudaError_t launch_path_chain(int store, const PathArgs &a, int C, cudaStream_t st) {
-    if (store == ST_F64) return path_launch<double, double>(a, C, st);
-    if (store == ST_F32) return path_launch<float, float>(a, C, st);
-    return path_launch<__nv_bfloat16, float>(a, C, st);
+template <class TS, class TA>
+static cudaError_t launch_any(int lg, const PathArgs &a, int C, cudaStream_t st) {
+    if (lg == 8) return path_launch<TS, TA, 8>(a, C, st);
+    if (lg == 12) return path_launch<TS, TA, 12>(a, C, st);
+    if (lg == 16) return path_launch<TS, TA, 16>(a, C, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_path_chain(int store, const PathArgs &a, const PathShape &sh,
+                              cudaStream_t st) {
+    if (store == ST_F64) return launch_any<double, double>(sh.lg, a, sh.C, st);
+    if (store == ST_F32) return launch_any<float, float>(sh.lg, a, sh.C, st);
+    return launch_any<__nv_bfloat16, float>(sh.lg, a, sh.C, st);
 }
 
 }  // namespace rac

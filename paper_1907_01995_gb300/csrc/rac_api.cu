@@ -905,7 +905,7 @@ static rac_status path_sequential(rac_handle *h, int nlambda, const std::vector<
 // cluster launch whose shared memory fits; false where it does not apply.
 static bool path_batched_shape(const rac_handle *h, int L, PathShape *sh) {
     if (!h->gram || h->k != 0 || h->phi != RAC_PHI_L1L2 || !h->kinv || h->big) return false;
-    return path_shape(h->store, h->n, BlockLayout(h->n, h->p).smax(), L, sh);
+    return path_shape(h->store, h->n, h->p, L, sh);
 }
 
 // Batched path: all points advance together from the handle's state, one
@@ -1015,6 +1015,7 @@ static rac_status path_batched(rac_handle *h, int L, const std::vector<double> &
             pa.lam2 = lam + L;
             pa.active = act;
             pa.gamma = h->gamma;
+            pa.err = h->err;
             RAC_CK(launch_path_chain(h->store, pa, sh, st));
             if (pf) RAC_CK(cudaEventRecord(h->pev[3 + 5 * s + 3], st));
         }

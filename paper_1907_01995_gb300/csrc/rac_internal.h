@@ -114,6 +114,7 @@ struct PathArgs {
     const double *lam1, *lam2;  // L
     const int *active;      // L: 0 = this point has stopped (its state is left as it is)
     double gamma;
+    int *err;               // device status word (bounded waits record RAC_ERR_TIMEOUT)
 };
 
 // ------------------------------------------------------------------ launchers
@@ -165,7 +166,7 @@ cudaError_t launch_cluster_chain(int store, const ChainArgs &a, int C, cudaStrea
 struct PathShape {
     int C, lg, resident;
 };
-bool path_shape(int store, int n, int smax, int L, PathShape *out);
+bool path_shape(int store, int n, int p, int L, PathShape *out);
 cudaError_t launch_path_chain(int store, const PathArgs &a, const PathShape &sh,
                               cudaStream_t st);
 

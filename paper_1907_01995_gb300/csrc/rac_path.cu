@@ -18,22 +18,27 @@
 // gradient, x and static rhs part (-xi + gamma (x - z)) in shared memory.  A
 // block step is
 //   (1) each CTA computes the rows q = c, c + C, ... of DX_i (one warp per
-//       row, lanes over the block) from its copy of RHS_i and stores them into
-//       every CTA's DX buffer (distributed shared memory);
-//   (2) cluster barrier;
+//       row, lanes over the block) from its copy of RHS_i and sends them into
+//       every CTA's DX buffer (distributed shared memory, st.async);
+//   (2) it waits until all s_i rows of DX_i have arrived;
 //   (3) every CTA adds G[S_i, own] DX_i to its gradient rows (G is symmetric,
 //       so row S_i[q] of G holds the own columns contiguously) and to x: a
 //       thread takes a column pair and one of nq interleaved groups of the
 //       block's rows, whose partial sums meet in shared memory;
-//   (4) the owners of block i+1's coordinates store their rows of RHS_{i+1}
-//       into every CTA's RHS buffer;
-//   (5) cluster barrier.
+//   (4) the owners of block i+1's coordinates send their rows of RHS_{i+1}
+//       into every CTA's RHS buffer, and every CTA waits for all of them
+//       before step i+1's rows of DX.
 // A step's inputs that do not depend on DX (the thread's rows of G[S_{i+1},
 // own] and the warp's row of K_{i+1}^{-1}) are loaded into registers while
 // step i finishes, so their L2 latency overlaps the barriers.
-// The two hardware cluster barriers order every buffer reuse (a buffer is
-// rewritten only after a barrier that all its readers passed), so there is no
-// spin-wait in this kernel; every CTA executes the same number of barriers.
+// Every row travels with its signal: an st.async store completes its bytes on
+// the receiving CTA's mbarrier (one for RHS rows, one for DX rows), whose
+// phase k is armed with the s_k LG values it waits for.  Single buffers are
+// enough for RHS (a CTA can only send RHS_{i+1} into another after that one
+// sent its rows of DX_i, which follow its last read of RHS_i); DX rows
+// alternate between two buffers and barriers by step parity.  The waits are bounded in time; on expiry the
+// error flag is set and the kernel runs to its end (the hardware cluster
+// barrier is used only at entry and exit).
 // After the last block each CTA runs the z-block and the multiplier ascent
 // (eq. RAC-ADDM, last line) of its coordinates for every active point.
 #include <cuda_runtime.h>
@@ -55,7 +60,7 @@ constexpr int kPathSmax = 128;        // block size limit (register-factor inver
 __host__ __device__ constexpr int path_pf_words(int lg) { return lg <= 8 ? 36 : (lg <= 12 ? 28 : 20); }
 
 struct PathLayout {
-    size_t perm, gown, xown, cown, rhs, dx, part, total;
+    size_t perm, gown, xown, cown, rhs, dx, part, bars, total;
     int ncp, npairs, nq;
     __host__ __device__ PathLayout(int n, int smax, int C, size_t ta, int lg) {
         ncp = ((n + C - 1) / C + 1) & ~1;      // even: a thread takes a column pair
@@ -75,8 +80,9 @@ struct PathLayout {
         xown = take((size_t)ncp * lg * 8);
         cown = take((size_t)ncp * lg * 8);
         rhs = take((size_t)smax * lg * ta);
-        dx = take((size_t)smax * lg * ta);
+        dx = take(2 * (size_t)smax * lg * ta);   // by step parity
         part = take(nq > 1 ? (size_t)(nq - 1) * npairs * 2 * lg * ta : 16);
+        bars = take(3 * 8);
         total = o;
     }
 };
@@ -162,6 +168,69 @@ template <int LG> __device__ __forceinline__ void lds_row(const double *p, doubl
     }
 }
 
+// ---- distributed shared memory with the signal in the data: an st.async
+// store completes its bytes on the destination CTA's mbarrier
+__device__ __forceinline__ uint32_t path_remote(const void *local, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, uint32_t rbar, unsigned x, unsigned y,
+                                            unsigned z, unsigned w) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, "
+        "[%5];" ::"r"(raddr),
+        "r"(x), "r"(y), "r"(z), "r"(w), "r"(rbar)
+        : "memory");
+}
+// send the LG values of v (16-byte aligned destination row) to CTA `rank`
+template <int LG>
+__device__ __forceinline__ void send_row(void *dst_local, uint64_t *bar_local, int rank,
+                                         const float (&v)[LG]) {
+    const uint32_t ra = path_remote(dst_local, rank), rb = path_remote(bar_local, rank);
+#pragma unroll
+    for (int u = 0; u < LG / 4; ++u)
+        st_async_v4(ra + 16 * u, rb, __float_as_uint(v[4 * u]), __float_as_uint(v[4 * u + 1]),
+                    __float_as_uint(v[4 * u + 2]), __float_as_uint(v[4 * u + 3]));
+}
+template <int LG>
+__device__ __forceinline__ void send_row(void *dst_local, uint64_t *bar_local, int rank,
+                                         const double (&v)[LG]) {
+    const uint32_t ra = path_remote(dst_local, rank), rb = path_remote(bar_local, rank);
+#pragma unroll
+    for (int u = 0; u < LG / 2; ++u) {
+        const unsigned long long a0 = (unsigned long long)__double_as_longlong(v[2 * u]);
+        const unsigned long long a1 = (unsigned long long)__double_as_longlong(v[2 * u + 1]);
+        st_async_v4(ra + 16 * u, rb, (unsigned)a0, (unsigned)(a0 >> 32), (unsigned)a1,
+                    (unsigned)(a1 >> 32));
+    }
+}
+// wait for the phase of the given parity of a local mbarrier that remote
+// st.async stores complete (acquire at cluster scope), bounded in time: on
+// expiry, or if another wait already expired, record RAC_ERR_TIMEOUT and
+// return false
+__device__ __forceinline__ bool path_wait(uint64_t *bar, uint32_t parity, int *err) {
+    auto test = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, "
+            "[%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (test()) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!test()) {
+        if (*((volatile int *)err) == RAC_ERR_TIMEOUT || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+            set_err(err, RAC_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
 template <class TS, class TA, bool VEC, int LG>
 __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     using GP = GPair<TS, VEC>;
@@ -191,8 +260,13 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     double *xown = (double *)(sm + Ly.xown);
     double *cown = (double *)(sm + Ly.cown);
     TA *rhs = (TA *)(sm + Ly.rhs);              // [smax][LG], written by the owners
-    TA *dxb = (TA *)(sm + Ly.dx);               // [smax][LG], written by the row CTAs
+    TA *dxbuf = (TA *)(sm + Ly.dx);             // [2][smax][LG], written by the row CTAs
     TA *part = (TA *)(sm + Ly.part);            // [nq - 1][npairs][2][LG]
+    uint64_t *bars = (uint64_t *)(sm + Ly.bars);
+    // mb_rhs phase k: RHS_k arrived; mb_dx[k & 1] phase k >> 1: DX_k arrived
+    uint64_t *mb_rhs = bars, *mb_dx = bars + 1;
+    const uint32_t row_bytes = (uint32_t)(LG * sizeof(TA));
+    bool ok = true;                             // no wait has expired
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TS *G = (const TS *)a.G;
     const TA *Wall = (const TA *)a.W;
@@ -246,27 +320,46 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         }
     };
     prefetch(0);
-    cl.sync();   // every CTA's buffers exist before remote stores arrive
+    // Each barrier phase has one local arrival, which also arms the bytes of
+    // that step's rows (s_k LG values of RHS_k or of DX_k).  RHS_0 and DX_0 are
+    // armed here; RHS_{k+1} and DX_{k+1} as soon as RHS_k has arrived, before
+    // this CTA sends its rows of DX_k, which every other CTA needs before it
+    // can produce anything of step k+1 (every CTA holds rows of every DX_k:
+    // the cluster is never larger than the smallest block).
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) mbar_init(&bars[k], 1);
+        mbar_init_fence();
+        mbar_expect_tx(mb_rhs, (uint32_t)lay.size(0) * row_bytes);
+        mbar_expect_tx(&mb_dx[0], (uint32_t)lay.size(0) * row_bytes);
+    }
+    __syncthreads();
+    cl.sync();   // every CTA's barriers are armed before remote stores arrive
 
-    // rows of RHS_b held by this CTA, stored into every CTA's buffer
+    // rows of RHS_b held by this CTA, sent to every CTA
     auto push_rhs = [&](int b) {
         const int s = lay.size(b), off = lay.offset(b);
         for (int t = threadIdx.x; t < s * C; t += blockDim.x) {
             const int q = t / C, r = t % C;
             const int cq = perm[off + q] - c0;
             if (cq < 0 || cq >= ncl) continue;
-            TA *dst = cl.map_shared_rank(rhs, r) + (size_t)q * kPathLG;
+            TA v[LG];
 #pragma unroll
-            for (int l = 0; l < kPathLG; ++l)
-                dst[l] = (TA)(gown[cq * kPathLG + l] + cown[cq * kPathLG + l]);
+            for (int l = 0; l < LG; ++l) v[l] = (TA)(gown[cq * LG + l] + cown[cq * LG + l]);
+            send_row<LG>(rhs + (size_t)q * LG, mb_rhs, r, v);
         }
     };
     push_rhs(0);
-    cl.sync();
 
     for (int i = 0; i < p; ++i) {
         const int s = lay.size(i), off = lay.offset(i);
         const bool more = i + 1 < p;
+        TA *dxb = dxbuf + (size_t)(i & 1) * smax * LG;
+        ok = path_wait(mb_rhs, (uint32_t)(i & 1), a.err) && ok;   // RHS_i is here
+        if (threadIdx.x == 0 && more && ok) {
+            mbar_expect_tx(mb_rhs, (uint32_t)lay.size(i + 1) * row_bytes);
+            mbar_expect_tx(&mb_dx[(i + 1) & 1], (uint32_t)lay.size(i + 1) * row_bytes);
+        }
+        __syncthreads();   // armed before any DX_i row leaves this CTA
         // (1) this warp's row of DX_i = -K_i^{-1} RHS_i, into every CTA
         if (qrow < s) {
             TA acc[kPathLG];
@@ -283,14 +376,11 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
                 }
             }
 #pragma unroll
-            for (int l = 0; l < kPathLG; ++l) acc[l] = warp_sum(acc[l]);
-            if (lane < C) {   // lane r stores the row into CTA r
-                TA *dst = cl.map_shared_rank(dxb, lane) + (size_t)qrow * kPathLG;
-#pragma unroll
-                for (int l = 0; l < kPathLG; ++l) dst[l] = -acc[l];
-            }
+            for (int l = 0; l < kPathLG; ++l) acc[l] = -warp_sum(acc[l]);
+            if (lane < C)   // lane r sends the row to CTA r
+                send_row<LG>(dxb + (size_t)qrow * LG, &mb_dx[i & 1], lane, acc);
         }
-        cl.sync();   // (2) DX_i complete in every CTA
+        ok = path_wait(&mb_dx[i & 1], (uint32_t)((i >> 1) & 1), a.err) && ok;   // (2) DX_i here
         // (3) x and the model gradient of the own coordinates
         for (int q = threadIdx.x; q < s; q += blockDim.x) {
             const int cq = perm[off + q] - c0;
@@ -359,8 +449,8 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         __syncthreads();
         // (4) RHS_{i+1} from the updated gradient
         if (more) push_rhs(i + 1);
-        cl.sync();   // (5)
     }
+    cl.sync();   // no CTA leaves while another may still send to it
 
     // ---- z-block and multiplier ascent of the own coordinates
     for (int t = threadIdx.x; t < ncl * kPathLG; t += blockDim.x) {
@@ -436,13 +526,17 @@ static cudaError_t prepare_store(int store, int lg, int n, int smax, int C, size
     return prepare_any<__nv_bfloat16, float>(lg, n, smax, C, smem, clusters);
 }
 
-// Launch shape of the path chain for L points: the cluster size C (16, else
-// 8) and the points per cluster LG, the smallest of 8, 12, 16 whose
+// Launch shape of the path chain for L points: the cluster size C (the
+// largest of 16, 8, 4, 2, 1 that is at most the smallest block and fits) and
+// the points per cluster LG, the smallest of 8, 12, 16 whose
 // ceil(L / LG) clusters are all co-resident (a second wave of clusters would
 // double the sweep), else 16.  Returns false if no shape fits.
-bool path_shape(int store, int n, int smax, int L, PathShape *out) {
-    if (smax > kPathSmax) return false;
-    for (int C : {16, 8}) {
+bool path_shape(int store, int n, int p, int L, PathShape *out) {
+    const BlockLayout lay(n, p);
+    const int smax = lay.smax(), smin = lay.q;
+    if (smax > kPathSmax || smin < 1) return false;
+    for (int C : {16, 8, 4, 2, 1}) {
+        if (C > smin) continue;   // every CTA holds a row of every DX_k
         int best = 0, res_best = 0;
         for (int lg : kPathGroups) {
             size_t smem = 0;

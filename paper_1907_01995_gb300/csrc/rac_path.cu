@@ -76,9 +76,9 @@ struct PathLayout {
             return at;
         };
         perm = take((size_t)n * 4);
-        gown = take((size_t)ncp * lg * 8);
+        gown = take((size_t)ncp * lg * 8);       // FP32 hi/lo pairs, or FP64
         xown = take((size_t)ncp * lg * 8);
-        cown = take((size_t)ncp * lg * 8);
+        cown = take((size_t)ncp * lg * ta);
         rhs = take((size_t)smax * lg * ta);
         dx = take(2 * (size_t)smax * lg * ta);   // by step parity
         part = take(nq > 1 ? (size_t)(nq - 1) * npairs * 2 * lg * ta : 16);
@@ -168,6 +168,40 @@ template <int LG> __device__ __forceinline__ void lds_row(const double *p, doubl
     }
 }
 
+// The model gradient of the own coordinates, accumulated over a sweep's block
+// steps.  FP64 compute: plain doubles.  FP32 compute: a hi/lo pair of floats
+// updated by Knuth's TwoSum, so each step's FP32 increment is added without
+// rounding error (about 48 significant bits, on the FP32 pipe instead of this
+// part's slow FP64 one).
+template <class TA> struct GAcc;
+template <> struct GAcc<double> {
+    double *v;
+    int len;
+    __device__ void set(int i, double g) { v[i] = g; }
+    __device__ double value(int i) const { return v[i]; }
+    __device__ double get(int i) const { return v[i]; }
+    __device__ void add(int i, double a) { v[i] += a; }
+};
+template <> struct GAcc<float> {
+    float *v;      // hi at [i], lo at [len + i]
+    int len;
+    __device__ void set(int i, double g) {
+        const float hi = (float)g;
+        v[i] = hi;
+        v[len + i] = (float)(g - (double)hi);
+    }
+    __device__ float value(int i) const { return v[i] + v[len + i]; }
+    __device__ double get(int i) const { return (double)v[i] + (double)v[len + i]; }
+    __device__ void add(int i, float a) {
+        const float hi = v[i];
+        const float s = __fadd_rn(hi, a);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+        v[i] = s;
+        v[len + i] = __fadd_rn(v[len + i], err);
+    }
+};
+
 // ---- distributed shared memory with the signal in the data: an st.async
 // store completes its bytes on the destination CTA's mbarrier
 __device__ __forceinline__ uint32_t path_remote(const void *local, int rank) {
@@ -256,9 +290,11 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     const int ncp = Ly.ncp, npairs = Ly.npairs, nq = Ly.nq;
     const int c0 = c * ncp, ncl = max(0, min(ncp, n - c0));
     int *perm = (int *)(sm + Ly.perm);
-    double *gown = (double *)(sm + Ly.gown);    // [ncp][LG]
+    // the own coordinates' model gradient (an FP32 hi/lo pair summed without
+    // rounding error, or FP64), x (FP64) and static rhs part (compute type)
+    GAcc<TA> gown{(TA *)(sm + Ly.gown), ncp * LG};   // [ncp][LG]
     double *xown = (double *)(sm + Ly.xown);
-    double *cown = (double *)(sm + Ly.cown);
+    TA *cown = (TA *)(sm + Ly.cown);
     TA *rhs = (TA *)(sm + Ly.rhs);              // [smax][LG], written by the owners
     TA *dxbuf = (TA *)(sm + Ly.dx);             // [2][smax][LG], written by the row CTAs
     TA *part = (TA *)(sm + Ly.part);            // [nq - 1][npairs][2][LG]
@@ -291,9 +327,9 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
             x = a.X[at];
             cs = -a.XI[at] + gamma * (x - a.Z[at]);
         }
-        gown[t] = g;
+        gown.set(t, g);
         xown[t] = x;
-        cown[t] = cs;
+        cown[t] = (TA)cs;
     }
     __syncthreads();
 
@@ -344,7 +380,7 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
             if (cq < 0 || cq >= ncl) continue;
             TA v[LG];
 #pragma unroll
-            for (int l = 0; l < LG; ++l) v[l] = (TA)(gown[cq * LG + l] + cown[cq * LG + l]);
+            for (int l = 0; l < LG; ++l) v[l] = gown.value(cq * LG + l) + cown[cq * LG + l];
             send_row<LG>(rhs + (size_t)q * LG, mb_rhs, r, v);
         }
     };
@@ -442,8 +478,8 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
             }
 #pragma unroll
             for (int l = 0; l < kPathLG; ++l) {
-                gown[cc * kPathLG + l] += (double)a0[l];
-                if (two) gown[(cc + 1) * kPathLG + l] += (double)a1[l];
+                gown.add(cc * kPathLG + l, a0[l]);
+                if (two) gown.add((cc + 1) * kPathLG + l, a1[l]);
             }
         }
         __syncthreads();
@@ -463,7 +499,7 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         a.X[at] = x;
         a.Z[at] = z;
         a.XI[at] = xi - gamma * (x - z);
-        a.Gm[at] = gown[t];
+        a.Gm[at] = gown.get(t);
     }
 }
 

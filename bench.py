@@ -150,6 +150,83 @@ def en_leg(dev, flush, st, fp64_max_sweeps=400):
     return out
 
 
+PATH_WORKLOAD = dict(name="lasso_path_20000x5000_64", m=20000, n=5000, nlambda=64, tol=1e-6,
+                     refresh_every=10)
+
+
+def path_leg(dev, flush, st, peaks, sms):
+    """Regularisation path: one AR(1) design 20000 x 5000 (rho = 0.5, 5% sparse
+    x_true), 64 values of lambda1 geometric from lambda_max to 0.01 lambda_max,
+    p = 50 blocks of 100, time to KKT <= 1e-6 for every point from the
+    resident FP64 A (handle setup included).  Forms: the batched path (all
+    points in one launch per sweep) in BF16 / FP32 / FP64 storage, the
+    sequential warm-started loop in BF16, and the plain FP64 path (sequential,
+    FP64 storage).  The roofline of the batched chain comes from a profiled
+    replica (CUDA events around each launch): its useful work is the
+    gradient update 2 n^2 FLOP per running point and sweep (FP32 pipe), and
+    its algorithmic traffic one pass over the n x n BF16 Gram matrix per
+    launch."""
+    import torch
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    w = PATH_WORKLOAD
+    inst, lams = synth.path_instance(0, m=w["m"], n=w["n"], nlambda=w["nlambda"])
+    A = torch.tensor(inst.A, device=dev).t().contiguous().t()
+    b = torch.tensor(inst.b, device=dev)
+    p = inst.num_blocks
+    del inst.A
+
+    def run(storage, mode, profile=False):
+        with api.Handle(A, b, phi="l1l2", lambda1=float(lams[0]), lambda2=0.0, num_blocks=p,
+                        tol=w["tol"], max_sweeps=3000, refresh_every=w["refresh_every"],
+                        storage=storage, form="gram", path=mode, profile=profile) as h:
+            return h.path(lams)[1]
+
+    out = {"workload": w["name"], "m": w["m"], "n": w["n"], "p": p, "nlambda": w["nlambda"],
+           "tol": w["tol"], "lambda1": "geometric lambda_max .. 0.01 lambda_max"}
+    run("bf16", "batched")                              # warm-up (module load)
+    for storage, mode, reps in (("bf16", "batched", 2), ("fp32", "batched", 1),
+                                ("fp64", "batched", 1), ("bf16", "sequential", 1),
+                                ("fp64", "sequential", 1)):
+        runs = [_timed_call(lambda: run(storage, mode), flush, st) for _ in range(reps)]
+        ms, infos = min(runs, key=lambda r: r[0])
+        sw = sum(i["sweeps"] for i in infos)
+        out["%s/%s" % (storage, mode)] = {
+            "time_ms": ms, "sweeps_all_points": sw, "max_sweeps": max(i["sweeps"] for i in infos),
+            "kkt_max": max(i["kkt"] for i in infos),
+            "status": sorted({i["status"] for i in infos}), "form": infos[0]["form"],
+            "block_updates_per_s": sw * p / (ms / 1000.0)}
+    ref = out["fp64/sequential"]["time_ms"]
+    for k in ("bf16/batched", "fp32/batched", "fp64/batched", "bf16/sequential"):
+        out[k]["speedup_vs_fp64_plain"] = ref / out[k]["time_ms"]
+    out["batched_vs_sequential_bf16"] = (out["bf16/sequential"]["time_ms"] /
+                                         out["bf16/batched"]["time_ms"])
+    # roofline of the batched BF16 chain from a profiled replica
+    infos = run("bf16", "batched", profile=True)
+    n = w["n"]
+    launches = infos[0]["chain_launches"]
+    chain_ms = infos[0]["t_chain_ms"]
+    point_sweeps = sum(i["sweeps"] for i in infos)
+    flops = 2.0 * n * n * point_sweeps
+    peak_alu = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ach = flops / (chain_ms / 1000.0) / 1e12
+    gb = n * n * 2 * launches / (chain_ms / 1000.0) / 1e9
+    out["roofline_chain"] = {
+        "bound": "alu", "kernel": "k_path_chain", "achieved": ach, "peak": peak_alu,
+        "unit": "TFLOP/s", "frac": ach / peak_alu, "flops_model": "2 n^2 per running point and sweep",
+        "launch_ms": chain_ms / max(1, launches), "launches": launches,
+        "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (
+            sms, peaks.get("sm_max_mhz", 2070.0)),
+        "hbm_view": {"algorithmic_bytes_per_launch": n * n * 2, "achieved_gbs": gb,
+                     "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                     "frac": gb / peaks.get("hbm_gbs", 6800.0)},
+        "refresh_ms": infos[0]["t_refresh_ms"]}
+    del A, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def svm_batch_times(count, dev, forms, sweeps=40, seed=0):
     """Per-sweep device time of the batched soft-margin SVM duals (count
     uneven instances, N in [500, 20000], d in [20, 1000], blocks of 64) for
@@ -555,6 +632,10 @@ def main():
             extra["elastic_net_2000x50000"] = en_leg(dev, flush, st)
         except Exception as ex:  # report, never fake
             extra["elastic_net_2000x50000"] = {"failed": str(ex)[:300]}
+        try:
+            extra["lasso_path_20000x5000_64"] = path_leg(dev, flush, st, peaks, sms)
+        except Exception as ex:
+            extra["lasso_path_20000x5000_64"] = {"failed": str(ex)[:300]}
         try:
             extra["svm_batch_256"] = svm_batch_times(
                 256, dev, [("bf16", "rp"), ("bf16", "rac"), ("fp32", "rp"), ("fp64", "rp"),

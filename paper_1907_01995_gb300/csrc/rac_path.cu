@@ -78,7 +78,7 @@ struct PathLayout {
         perm = take((size_t)n * 4);
         gown = take((size_t)ncp * lg * 8);       // FP32 hi/lo pairs, or FP64
         xown = take((size_t)ncp * lg * 8);
-        cown = take((size_t)ncp * lg * ta);
+        cown = take((size_t)ncp * lg * 8);
         rhs = take((size_t)smax * lg * ta);
         dx = take(2 * (size_t)smax * lg * ta);   // by step parity
         part = take(nq > 1 ? (size_t)(nq - 1) * npairs * 2 * lg * ta : 16);
@@ -291,10 +291,11 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     const int c0 = c * ncp, ncl = max(0, min(ncp, n - c0));
     int *perm = (int *)(sm + Ly.perm);
     // the own coordinates' model gradient (an FP32 hi/lo pair summed without
-    // rounding error, or FP64), x (FP64) and static rhs part (compute type)
+    // rounding error, or FP64), x and static rhs part -xi + gamma (x - z)
+    // (FP64: the rhs is their nearly cancelling sum, rounded once)
     GAcc<TA> gown{(TA *)(sm + Ly.gown), ncp * LG};   // [ncp][LG]
     double *xown = (double *)(sm + Ly.xown);
-    TA *cown = (TA *)(sm + Ly.cown);
+    double *cown = (double *)(sm + Ly.cown);
     TA *rhs = (TA *)(sm + Ly.rhs);              // [smax][LG], written by the owners
     TA *dxbuf = (TA *)(sm + Ly.dx);             // [2][smax][LG], written by the row CTAs
     TA *part = (TA *)(sm + Ly.part);            // [nq - 1][npairs][2][LG]
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
         }
         gown.set(t, g);
         xown[t] = x;
-        cown[t] = (TA)cs;
+        cown[t] = cs;
     }
     __syncthreads();
 
@@ -371,17 +372,16 @@ __global__ void __launch_bounds__(kPathThreads, 1) k_path_chain(PathArgs a) {
     __syncthreads();
     cl.sync();   // every CTA's barriers are armed before remote stores arrive
 
-    // rows of RHS_b held by this CTA, sent to every CTA
+    // rows of RHS_b held by this CTA (each formed once in FP64), sent to every CTA
     auto push_rhs = [&](int b) {
         const int s = lay.size(b), off = lay.offset(b);
-        for (int t = threadIdx.x; t < s * C; t += blockDim.x) {
-            const int q = t / C, r = t % C;
+        for (int q = threadIdx.x; q < s; q += blockDim.x) {
             const int cq = perm[off + q] - c0;
             if (cq < 0 || cq >= ncl) continue;
             TA v[LG];
 #pragma unroll
-            for (int l = 0; l < LG; ++l) v[l] = gown.value(cq * LG + l) + cown[cq * LG + l];
-            send_row<LG>(rhs + (size_t)q * LG, mb_rhs, r, v);
+            for (int l = 0; l < LG; ++l) v[l] = (TA)(gown.get(cq * LG + l) + cown[cq * LG + l]);
+            for (int r = 0; r < C; ++r) send_row<LG>(rhs + (size_t)q * LG, mb_rhs, r, v);
         }
     };
     push_rhs(0);

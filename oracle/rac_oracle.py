@@ -718,13 +718,15 @@ def svm_ipm(Z, y, C, tol=1e-11, max_iter=200, snap=1e-5):
         neg = dv < 0
         return min(1.0, float(np.min(-v[neg] / dv[neg]))) if neg.any() else 1.0
 
-    scale = 1.0 + float(np.abs(e).max())
     for _ in range(max_iter):
         Qa = qmul(a)
         rd = Qa - e - b * y - lam + nu
         rp = float(y @ a)
         t = (a @ lam + (C - a) @ nu) / (2 * N)
-        if t <= tol and np.abs(rd).max() <= tol * scale and abs(rp) <= tol * max(1.0, a.sum()):
+        # stop once complementarity is below tol and the residuals are at the
+        # rounding level of Q a (they cannot be driven further in FP64)
+        if (t <= tol and np.abs(rd).max() <= 1e-10 * max(1.0, float(np.abs(Qa).max()))
+                and abs(rp) <= 1e-10 * max(1.0, float(a.sum()))):
             break
         Dg = lam / a + nu / (C - a)
         solve = make_solver(Dg)
@@ -742,10 +744,14 @@ def svm_ipm(Z, y, C, tol=1e-11, max_iter=200, snap=1e-5):
         sp = min(max_step(a, da), max_step(C - a, -da))
         sd = min(max_step(lam, dl), max_step(nu, dn))
         s = 0.995 * min(sp, sd)
-        a = a + s * da
-        b = b + s * db
-        lam = lam + s * dl
-        nu = nu + s * dn
+        a_n, lam_n, nu_n = a + s * da, lam + s * dl, nu + s * dn
+        if not (np.all(a_n > 0.0) and np.all(a_n < C) and np.all(lam_n > 0.0)
+                and np.all(nu_n > 0.0) and np.isfinite(db)):
+            # rounding put an iterate on the boundary: no further progress in FP64
+            if t <= 1e-3 * tol ** 0.5:
+                break
+            raise RuntimeError("interior-point method stalled at complementarity %.2e" % t)
+        a, b, lam, nu = a_n, b + s * db, lam_n, nu_n
     else:
         raise RuntimeError("interior-point method did not reach tol")
     # coordinates the multipliers mark as active (a_i < lam_i, or C - a_i <

@@ -105,7 +105,8 @@ def en_leg(dev, flush, st, fp64_max_sweeps=400):
     """Elastic-Net 2000 x 50000 (groups of 10 columns with rho = 0.7,
     lambda1 = 0.05 lambda_max, lambda2 = 0.1), p = 100 blocks of 500, residual
     form, time to KKT <= 1e-6 from the resident FP64 A: the BF16- and
-    FP32-storage forms and the plain FP64 path, each a full solve (setup
+    FP32-storage forms, the plain FP64 path and RP-MBADMM in BF16 (fixed
+    blocks in a random order, inverses once), each a full solve (setup
     included).  The FP64 path is capped at fp64_max_sweeps sweeps; if it
     stops there its time per sweep and the sweeps the BF16 form needed give
     the reported estimate, marked as such."""
@@ -124,17 +125,21 @@ def en_leg(dev, flush, st, fp64_max_sweeps=400):
     out = {"workload": w["name"], "m": w["m"], "n": w["n"], "p": w["p"], "tol": w["tol"],
            "lambda1": "0.05*lambda_max", "lambda2": 0.1}
 
-    def solve(storage, cap):
-        with api.Handle(A, b, storage=storage, max_sweeps=cap, **common) as h:
+    def solve(storage, cap, assembly):
+        with api.Handle(A, b, storage=storage, max_sweeps=cap, assembly=assembly,
+                        **common) as h:
             return h.solve()[1]
 
-    for storage, reps, cap in (("bf16", 2, 3000), ("fp32", 1, 3000), ("fp64", 1,
-                                                                       fp64_max_sweeps)):
-        runs = [_timed_call(lambda: solve(storage, cap), flush, st) for _ in range(reps)]
+    for key, storage, reps, cap, assembly in (
+            ("bf16", "bf16", 2, 3000, "rac"), ("fp32", "fp32", 1, 3000, "rac"),
+            ("fp64", "fp64", 1, fp64_max_sweeps, "rac"),
+            ("bf16_rp", "bf16", 1, 3000, "rp")):
+        runs = [_timed_call(lambda: solve(storage, cap, assembly), flush, st)
+                for _ in range(reps)]
         ms, info = min(runs, key=lambda r: r[0])
-        out[storage] = {"time_ms": ms, "sweeps": info["sweeps"], "kkt": info["kkt"],
-                        "status": info["status"], "form": info["form"],
-                        "block_updates_per_s": info["block_updates"] / (ms / 1000.0)}
+        out[key] = {"time_ms": ms, "sweeps": info["sweeps"], "kkt": info["kkt"],
+                    "status": info["status"], "form": info["form"],
+                    "block_updates_per_s": info["block_updates"] / (ms / 1000.0)}
     f64, bf = out["fp64"], out["bf16"]
     if f64["status"] == 0:
         f64["time_to_kkt_ms"] = f64["time_ms"]
@@ -145,6 +150,7 @@ def en_leg(dev, flush, st, fp64_max_sweeps=400):
     ref = f64.get("time_to_kkt_ms", f64.get("time_to_kkt_ms_estimate"))
     out["speedup_bf16_vs_fp64_plain"] = ref / bf["time_ms"]
     out["speedup_fp32_vs_fp64_plain"] = ref / out["fp32"]["time_ms"]
+    out["speedup_bf16_rp_vs_fp64_plain"] = ref / out["bf16_rp"]["time_ms"]
     del A, b
     torch.cuda.empty_cache()
     return out

@@ -133,8 +133,11 @@ typedef struct {
                                sweep (Sec. 1, eq. RAC-ADDM); 1 = RP: the consecutive partition
                                of 0..n-1 (same block sizes) kept fixed and its blocks solved in
                                a random order every sweep (RP-MBADMM, Sec. 1), so the block
-                               factors are computed once per penalty.  RP is implemented by
-                               rac_admm_batch; rac_admm_setup returns RAC_ERR_ARG for it. */
+                               factors are computed once per penalty (at setup for a handle).
+                               rac_admm_setup accepts RP only when num_blocks divides n (equal
+                               blocks), else RAC_ERR_ARG; in the Gram form an RP handle runs the
+                               grid-barrier chain (the lookahead of the other chains depends on
+                               the block order).  rac_admm_batch takes any sizes. */
     int32_t debug_exit_cta; /* failure-path testing only; 0 = off.  k > 0: CTA k - 1 of the
                                residual-form block chain for blocks of at most 128 coordinates
                                returns at its start without arriving at any grid barrier.  The

@@ -123,6 +123,11 @@ struct rac_handle {
     int64_t chain_launches = 0;
     int dbg_exit_cta = -1;          // rac_options.debug_exit_cta - 1
     int path_mode = 0;              // rac_options.path
+    // RP-MBADMM (rac_options.assembly = 1): block order per sweep slot and the
+    // inverses of the fixed blocks, computed once at setup
+    int rp = 0;
+    int *order = nullptr;
+    void *Wfix = nullptr;
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -322,7 +327,18 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
     cudaStream_t st = h->st;
     const bool pf = h->profile;
     if (pf) RAC_CK(cudaEventRecord(h->pev[0], st));
-    if (pre_in == 0) {
+    if (h->rp) {
+        // RP-MBADMM: sweep k's block order is the Philox argsort of the p block
+        // indices (the assembly kernel with n = p), expanded into the sweep's
+        // permutation; the fixed inverses are gathered into position order
+        RAC_CK(launch_assembly(h->p, 1, h->seed, 0, h->sweep_dev, nb, h->order, nullptr,
+                               h->tkey, h->tidx, st));
+        RAC_CK(launch_rp_expand(h->n, h->p, nb, h->order, h->perm, h->blk, st));
+        const size_t each = BlockLayout::pad4((size_t)(h->n / h->p) * (h->n / h->p)) *
+                            (h->store == ST_F64 ? 8 : 4);
+        RAC_CK(launch_rp_gather(h->p, nb, each, h->order, h->Wfix, h->W, h->wstride, st));
+        h->nlaunch += 3;
+    } else if (pre_in == 0) {
         RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, h->sweep_dev, nb, h->perm, h->blk,
                                h->tkey, h->tidx, st));
         h->nlaunch += 1;
@@ -330,11 +346,11 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
     if (pf) RAC_CK(cudaEventRecord(h->pev[1], st));
     RAC_CK(cudaEventRecord(h->fev[0], st));      // fork: factors wait for the assembly
     // fork only the streams that receive work, so every forked stream rejoins
-    const int nfac = nb - pre_in;
+    const int nfac = h->rp ? 0 : nb - pre_in;
     for (int q = 0; q < std::min(nfac, (int)rac_handle::kFactorStreams); ++q)
         RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[0], 0));
-    h->nlaunch += (1 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;   // + prox below
-    for (int s = pre_in; s < nb; ++s) {
+    h->nlaunch += (h->rp ? 0 : 1 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;   // + prox below
+    for (int s = pre_in; s < nb && !h->rp; ++s) {
         cudaStream_t sf = h->sfs[(s - pre_in) % rac_handle::kFactorStreams];
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
         if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
@@ -348,7 +364,7 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         if (h->lookahead)
             RAC_CK(launch_prepare(h->n, a.perm, h->x, h->z, h->xi, h->k ? h->e64 : nullptr,
                                   h->gamma, h->sperm, h->eperm, st));
-        if (s >= pre_in) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
+        if (s >= pre_in && !h->rp) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         if (h->big) {
@@ -535,6 +551,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->ws_fallback = o->ws_fallback != 0;
     h->dbg_exit_cta = o->debug_exit_cta > 0 ? o->debug_exit_cta - 1 : -1;
     h->path_mode = o->path;
+    h->rp = o->assembly == 1 ? 1 : 0;
     h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
     {
         const size_t nfev = std::max<size_t>(1 + (size_t)h->refresh_every, 6);
@@ -692,7 +709,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // Gram form with register factors: lookahead chain (P_i precomputed)
-    h->lookahead = (h->gram && h->kinv && factor_can_make_p(h->store, lay.smax())) ? 1 : 0;
+    // (RP: the lookahead P_i depends on the block order, so RP runs the chains without it)
+    h->lookahead = (h->gram && h->kinv && !h->rp && factor_can_make_p(h->store, lay.smax())) ? 1 : 0;
     if (h->lookahead && o->chain != 1) h->cluster = cluster_chain_size(h->store, n, lay.smax());
     h->perm_in_smem = (h->lookahead && n <= lookahead_perm_smem_max()) ? 1 : 0;
     const int nperm = h->perm_in_smem ? n : 0;
@@ -743,9 +761,33 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(h->alloc(&h->blk, (size_t)h->nslots * n));
     RAC_ST(h->alloc(&h->tidx, (size_t)h->nslots * n));
     RAC_ST(h->alloc(&h->tkey, (size_t)h->nslots * n));
-    std::snprintf(h->form, sizeof(h->form), "%s/%s%s", h->gram ? "gram" : "residual",
+    if (h->rp) {
+        // the fixed blocks' inverses, once: the identity order puts block b at
+        // position b of slot 0, whose factor launch writes them to Wfix
+        RAC_ST(h->alloc(&h->order, (size_t)h->nslots * h->p));
+        RAC_ST(h->alloc_bytes(&h->Wfix, h->wstride));
+        std::vector<int> ident(h->p);
+        for (int b = 0; b < h->p; ++b) ident[b] = b;
+        RAC_CK(cudaMemcpyAsync(h->order, ident.data(), ident.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, st));
+        RAC_CK(launch_rp_expand(n, h->p, 1, h->order, h->perm, h->blk, st));
+        ChainArgs a = chain_args(h, 0);
+        a.W = h->Wfix;
+        if (h->big) {
+            RAC_CK(launch_big_factor(h->store, a, h->Wfix, h->Pbuf, st));
+            h->nlaunch += big_factor_launches(lay.smax(), h->store);
+        } else {
+            int kinv = 1;
+            RAC_CK(launch_factor(h->store, h->gram, a, h->Wfix, nullptr, &kinv, st));
+            h->nlaunch += 1;
+        }
+        h->nlaunch += 1;
+        RAC_CK(cudaStreamSynchronize(st));   // the pageable identity order is consumed
+    }
+    std::snprintf(h->form, sizeof(h->form), "%s/%s%s%s", h->gram ? "gram" : "residual",
                   h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
-                  h->cluster ? (h->cluster == 16 ? "/cluster16" : "/cluster8") : "");
+                  h->cluster ? (h->cluster == 16 ? "/cluster16" : "/cluster8") : "",
+                  h->rp ? "/rp" : "");
     RAC_ST(set_state(h, o->x0, o->xi0));
     RAC_CK(cudaStreamSynchronize(st));
     h->kkt_scale = std::max(1.0, h->ss->h_aux[0]);
@@ -769,7 +811,9 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
     if (!(o->beta > 0) || !std::isfinite(o->gamma) || !(o->tol >= 0) || o->max_sweeps < 0)
         return RAC_ERR_ARG;
     if (o->storage < RAC_FP64 || o->storage > RAC_BF16) return RAC_ERR_ARG;
-    if (o->assembly != 0) return RAC_ERR_ARG;   // RP: batched form only
+    if (o->assembly < 0 || o->assembly > 1) return RAC_ERR_ARG;
+    // RP on the handle: equal blocks (the chains index blocks by position)
+    if (o->assembly == 1 && pr->n % o->num_blocks != 0) return RAC_ERR_ARG;
     if (o->path < 0 || o->path > 2) return RAC_ERR_ARG;
     if (o->form == RAC_FORM_RESIDUAL && !pr->A) return RAC_ERR_ARG;
     int64_t smax = (pr->n + o->num_blocks - 1) / o->num_blocks;
@@ -808,7 +852,8 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
         const int pre_in = (h->pre > 0 && h->pre_nb == nb) ? h->pre : 0;
         if (h->pre > 0 && pre_in == 0) h->pre = 0;   // stale: recompute everything
         const int left = h->max_sweeps - done - nb;
-        const int next_nb = (h->profile || left <= 0) ? 0 : std::min(h->refresh_every, left);
+        const int next_nb =
+            (h->profile || h->rp || left <= 0) ? 0 : std::min(h->refresh_every, left);
         RAC_ST(run_period(h, nb, pre_in, next_nb));
         h->pre = std::min(next_nb, (int)rac_handle::kFactorStreams);
         h->pre_nb = next_nb;
@@ -904,7 +949,8 @@ static rac_status path_sequential(rac_handle *h, int nlambda, const std::vector<
 // blocks of at most 128 coordinates (K_S^{-1} from the register factor) and a
 // cluster launch whose shared memory fits; false where it does not apply.
 static bool path_batched_shape(const rac_handle *h, int L, PathShape *sh) {
-    if (!h->gram || h->k != 0 || h->phi != RAC_PHI_L1L2 || !h->kinv || h->big) return false;
+    if (!h->gram || h->k != 0 || h->phi != RAC_PHI_L1L2 || !h->kinv || h->big || h->rp)
+        return false;
     return path_shape(h->store, h->n, h->p, L, sh);
 }
 

@@ -170,6 +170,14 @@ bool path_shape(int store, int n, int p, int L, PathShape *out);
 cudaError_t launch_path_chain(int store, const PathArgs &a, const PathShape &sh,
                               cudaStream_t st);
 
+// RP-MBADMM on the single-problem handle (equal blocks s = n / p): expand the
+// block orders (nsweeps x p) into permutations / block positions, and gather
+// the fixed inverses (`each` bytes per block) into position order per sweep slot
+cudaError_t launch_rp_expand(int n, int p, int nsweeps, const int *order, int *perm, int *blk,
+                             cudaStream_t st);
+cudaError_t launch_rp_gather(int p, int nsweeps, size_t each, const int *order, const void *Wfix,
+                             void *W, size_t wstride, cudaStream_t st);
+
 // setup: out[0] = max_j |g0_j|, out[1] = max_j (stationarity of z = 0), one CTA
 cudaError_t launch_kkt_zero(int n, const double *g0, int phi, double lam1, double lo, double hi,
                             double *out, cudaStream_t st);

@@ -87,11 +87,15 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     pr.lo, pr.hi = 1.0, 0.0   # empty box
     assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
     assert h.value is None
-    # RP-MBADMM is implemented by the batched form only; unknown assembly modes
+    # RP-MBADMM on the handle needs equal blocks (n = 3, p = 2 is refused);
+    # unknown assembly modes
     pr.phi = 0
     o.assembly = 1
+    o.num_blocks = 2
     assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
+    o.num_blocks = 1
     o.assembly = 2
+    assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
     xo = (ctypes.c_void_p * 1)(None)
     assert lib.rac_admm_batch(1, ctypes.byref(pr), ctypes.byref(o), xo, None) == L.RAC_ERR_ARG
     o.assembly = 0

@@ -329,3 +329,48 @@ def test_cluster_chain_svm_converged():
     assert abs(obj(a) - obj(a_smo)) <= 1e-6 * max(1.0, abs(obj(a_smo)))
     P = O.problem_from_instance(inst)
     assert O.kkt(P, a)["kkt"] <= 1e-8 * 1.01
+
+
+# ------------------------------------------------------- RP-MBADMM, one problem
+RP_CASES = {
+    "lasso_gram": dict(m=57, n=45, p=5, phi="l1l2", form="gram"),
+    "en_wide_residual": dict(m=31, n=96, p=8, phi="l1l2", lam2=0.1, form="residual"),
+    "svm_box_gram": dict(m=23, n=72, p=6, phi="box", coupling=True, form="gram",
+                         beta=0.6, gamma=0.6),
+    "big_blocks_residual": dict(m=150, n=600, p=3, phi="l1l2", lam2=0.1, form="residual"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RP_CASES))
+def test_rp_handle_fp64_iterates_match_oracle(name):
+    """RP-MBADMM on the single-problem handle (fixed consecutive blocks in a
+    random order per sweep, inverses computed once) follows the oracle's RP
+    iterates sweep by sweep, in both forms and with blocks above 128."""
+    c = RP_CASES[name]
+    inst = _instance(c, seed=4)
+    P = O.problem_from_instance(inst)
+    ost = O.initial_state(P)
+    with _handle(inst, c["form"], tol=0.0, max_sweeps=1, refresh_every=1, seed=6,
+                 assembly="rp") as h:
+        for k in range(30):
+            O.sweep(P, ost, inst.num_blocks, 6, inst.beta, inst.gamma, rp=True)
+            _, info = h.solve()
+            assert info["form"].endswith("/rp"), info["form"]
+            st = h.state()
+            for key in ("x", "z", "xi"):
+                assert rel(st[key], getattr(ost, key)) <= 1e-10, (k, key)
+
+
+@pytest.mark.parametrize("storage,form,bound", [("bf16", "gram", 1e-3), ("fp32", "residual", 1e-5)])
+def test_rp_handle_lasso_config_converged(lasso_ref, storage, form, bound):
+    """LASSO 10000 x 2000, p = 20 blocks of 100 under RP-MBADMM reaches the
+    coordinate-descent solution with the same support."""
+    inst, ref = lasso_ref
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=inst.lam1, num_blocks=20, beta=1.0,
+                    tol=1e-8, max_sweeps=5000, refresh_every=10, storage=storage, form=form,
+                    assembly="rp") as h:
+        z, info = h.solve()
+    assert info["status"] == 0, info
+    assert info["form"].endswith("/rp")
+    assert rel(z, ref) <= bound
+    assert np.array_equal(z != 0, ref != 0)

@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--solve-once", type=int, default=0, metavar="K",
                     help="run K plain solves of the workload in the default mixed-precision "
                          "form and exit (no timing; a fixed command to profile)")
+    ap.add_argument("--path-once", type=int, default=0, metavar="K",
+                    help="run K batched BF16 solves of the 64-point regularisation path "
+                         "20000x5000 and exit (no timing; a fixed command to profile)")
     ap.add_argument("--svm-batch", type=int, default=0, metavar="COUNT",
                     help="time the batched soft-margin SVM dual workload (COUNT uneven "
                          "instances, N in [500, 20000], d in [20, 1000], blocks of 64) per "
@@ -231,6 +234,27 @@ def path_leg(dev, flush, st, peaks, sms):
     del A, b
     torch.cuda.empty_cache()
     return out
+
+
+def path_once(k):
+    """K batched BF16 solves of the 64-point path (profiling entry)."""
+    import torch
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    w = PATH_WORKLOAD
+    inst, lams = synth.path_instance(0, m=w["m"], n=w["n"], nlambda=w["nlambda"])
+    A = torch.tensor(inst.A, device="cuda").t().contiguous().t()
+    b = torch.tensor(inst.b, device="cuda")
+    for _ in range(k):
+        with api.Handle(A, b, phi="l1l2", lambda1=float(lams[0]), num_blocks=inst.num_blocks,
+                        tol=w["tol"], max_sweeps=3000, refresh_every=w["refresh_every"],
+                        storage="bf16", form="gram", path="batched") as h:
+            _, infos = h.path(lams)
+    torch.cuda.synchronize()
+    print(json.dumps({"path_once": k, "form": infos[0]["form"],
+                      "point_sweeps": sum(i["sweeps"] for i in infos)}), flush=True)
+    return 0
 
 
 def svm_batch_times(count, dev, forms, sweeps=40, seed=0):
@@ -474,6 +498,8 @@ def main():
         return reference_arm(args)
     if args.svm_batch:
         return svm_batch_leg(args)
+    if args.path_once:
+        return path_once(args.path_once)
     import numpy as np
     import torch
     import torch.distributed as dist

@@ -81,6 +81,8 @@ typedef enum { RAC_FP64 = 0, RAC_FP32 = 1, RAC_BF16 = 2 } rac_precision;
  *       date by r += A_S dx; block matrices A_S^T A_S are formed per sweep.
  * AUTO: GRAM when n <= m (or H is given), RESIDUAL otherwise. */
 typedef enum { RAC_FORM_AUTO = 0, RAC_FORM_GRAM = 1, RAC_FORM_RESIDUAL = 2 } rac_form;
+/* (a sparse A, see rac_problem.vals, always runs the residual form: GRAM is an
+ * argument error for it) */
 
 /* The problem (eq. general_model restated in split form; see above). */
 typedef struct {
@@ -96,6 +98,15 @@ typedef struct {
     int32_t phi;            /* rac_phi */
     double lambda1, lambda2;/* l1l2 weights (>= 0) */
     double lo, hi;          /* box bounds (lo < hi) */
+    /* Sparse data matrix in compressed-column form (the large sparse designs
+     * of Sec. 3.1, Table 3), used instead of A when vals != NULL (A and H
+     * must then be NULL): column j holds entries colptr[j] .. colptr[j+1]-1
+     * with row indices rowidx[] (each in [0, m), strictly increasing within a
+     * column) and values vals[].  Sparse problems run the residual form. */
+    int64_t nnz;            /* number of stored entries (colptr[n]) */
+    const int64_t *colptr;  /* n + 1 */
+    const int32_t *rowidx;  /* nnz */
+    const double *vals;     /* nnz */
 } rac_problem;
 
 /* Run parameters (the paper's s or p, beta, iterations and tolerance). */

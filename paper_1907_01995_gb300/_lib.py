@@ -31,7 +31,8 @@ class RacProblem(ctypes.Structure):
     _fields_ = [("m", c_int64), ("n", c_int64), ("A", c_void_p), ("lda", c_int64),
                 ("b", c_void_p), ("H", c_void_p), ("c", c_void_p), ("E", c_void_p),
                 ("d", c_void_p), ("k", c_int32), ("phi", c_int32), ("lambda1", c_double),
-                ("lambda2", c_double), ("lo", c_double), ("hi", c_double)]
+                ("lambda2", c_double), ("lo", c_double), ("hi", c_double),
+                ("nnz", c_int64), ("colptr", c_void_p), ("rowidx", c_void_p), ("vals", c_void_p)]
 
 
 class RacOptions(ctypes.Structure):

@@ -2,7 +2,8 @@
 
 Arrays may be numpy arrays (host) or torch tensors (host or CUDA); the
 library reads them through plain pointers and copies them into its own device
-buffers.  torch is used for device memory and streams only.
+buffers.  A scipy.sparse data matrix is passed as compressed columns.  torch
+is used for device memory and streams only.
 """
 from __future__ import annotations
 
@@ -70,7 +71,24 @@ def _stream_handle(stream) -> int:
 def make_problem(keep: _Keep, A=None, b=None, *, H=None, c=None, E=None, d=None, phi="none",
                  lambda1=0.0, lambda2=0.0, lo=0.0, hi=0.0) -> L.RacProblem:
     pr = L.RacProblem()
-    if A is not None:
+    if A is not None and hasattr(A, "tocsc") and not _is_tensor(A):
+        # scipy.sparse matrix: compressed columns (sorted, duplicates summed)
+        Ac = A.tocsc(copy=True)
+        Ac.sum_duplicates()
+        Ac.sort_indices()
+        pr.m, pr.n = int(Ac.shape[0]), int(Ac.shape[1])
+        colptr = np.ascontiguousarray(Ac.indptr, dtype=np.int64)
+        rowidx = np.ascontiguousarray(Ac.indices, dtype=np.int32)
+        vals = np.ascontiguousarray(Ac.data, dtype=np.float64)
+        keep.items.extend([colptr, rowidx, vals])
+        pr.nnz = int(vals.size)
+        pr.colptr, pr.rowidx = colptr.ctypes.data, rowidx.ctypes.data
+        if not vals.size:          # an all-zero matrix still passes a values pointer
+            vals = np.zeros(1)
+            keep.items.append(vals)
+        pr.vals = vals.ctypes.data
+        pr.b = keep.vec(b, pr.m)
+    elif A is not None:
         pr.A, pr.m, pr.n, pr.lda = keep.colmajor(A)
         pr.b = keep.vec(b, pr.m)
     elif H is not None:

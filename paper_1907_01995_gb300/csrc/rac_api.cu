@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -128,6 +129,14 @@ struct rac_handle {
     int rp = 0;
     int *order = nullptr;
     void *Wfix = nullptr;
+    // sparse A (compressed columns): FP64 values for the refresh, storage copy
+    // for the sweeps; sp_emax bounds the entries of one block's columns
+    bool sparse = false;
+    int64_t nnz = 0, sp_emax = 0;
+    int64_t *sp_colptr = nullptr;
+    int *sp_rowidx = nullptr;
+    double *sp_vals64 = nullptr;
+    void *sp_vals = nullptr;
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -208,8 +217,13 @@ static rac_status copy_in(void *dst, const double *src, size_t count, cudaStream
 // t = E x - d.
 static rac_status enqueue_refresh(rac_handle *h) {
     cudaStream_t st = h->st;
-    h->nlaunch += (h->has_A ? 3 : 1) + 3 + ((h->gram && h->store != ST_F64) ? 1 : 0);
-    if (h->has_A) {
+    h->nlaunch += (h->has_A ? 3 : (h->sparse ? 3 : 1)) + 3 + ((h->gram && h->store != ST_F64) ? 1 : 0);
+    if (h->sparse) {
+        RAC_CK(launch_sp_resid_f64(h->m, h->n, h->sp_colptr, h->sp_rowidx, h->sp_vals64, h->z,
+                                   h->b64, h->rbuf, st));
+        RAC_CK(launch_sp_gemvt_f64(h->n, h->sp_colptr, h->sp_rowidx, h->sp_vals64, h->rbuf,
+                                   h->c64, h->gz, st));
+    } else if (h->has_A) {
         RAC_CK(launch_resid_f64(h->m, h->n, h->A64, h->m, h->z, h->b64, h->rbuf, h->rpart,
                                 h->nchunk, st));
         RAC_CK(launch_gemvt_f64(h->m, h->n, h->A64, h->m, h->rbuf, h->c64, h->gz, st));
@@ -220,6 +234,10 @@ static rac_status enqueue_refresh(rac_handle *h) {
                       h->lam1, h->lam2, h->lo, h->hi, h->stats, h->kpart, st, h->lam_dev));
     if (h->gram) {
         RAC_CK(launch_gram_anchor(h->store, h->n, h->G, h->gz, h->x, h->z, h->dxz, h->g, st));
+    } else if (h->sparse) {
+        RAC_CK(cudaMemcpyAsync(h->ga, h->gz, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RAC_CK(launch_sp_anchor(h->store, h->m, h->n, h->sp_colptr, h->sp_rowidx, h->sp_vals,
+                                h->x, h->z, h->dres, st));
     } else {
         RAC_CK(cudaMemcpyAsync(h->ga, h->gz, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RAC_CK(launch_slab_anchor(h->store, h->n, h->nslab, h->R, h->As, h->x, h->z, h->dres, st));
@@ -271,6 +289,9 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.perm_in_smem = h->perm_in_smem;
     a.p_rows = h->cluster ? 1 : 0;
     a.dbg_exit_cta = h->dbg_exit_cta;
+    a.sp_colptr = h->sp_colptr;
+    a.sp_rowidx = h->sp_rowidx;
+    a.sp_vals = h->sp_vals;
     return a;
 }
 
@@ -306,7 +327,11 @@ static ProxArgs prox_args(const rac_handle *h) {
 static rac_status enqueue_factor(rac_handle *h, int s, cudaStream_t sf) {
     ChainArgs a = chain_args(h, s);
     int kinv = 1;
-    if (h->big) {
+    if (h->sparse) {
+        RAC_CK(launch_sp_factor(h->store, a, const_cast<void *>(a.W),
+                                (char *)h->Pbuf + (size_t)s * h->pstride, h->sp_emax, sf));
+        h->nlaunch += big_factor_launches(BlockLayout(h->n, h->p).smax(), h->store);
+    } else if (h->big) {
         RAC_CK(launch_big_factor(h->store, a, const_cast<void *>(a.W),
                                  (char *)h->Pbuf + (size_t)s * h->pstride, sf));
         h->nlaunch += big_factor_launches(BlockLayout(h->n, h->p).smax(), h->store);
@@ -367,7 +392,9 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         if (s >= pre_in && !h->rp) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
-        if (h->big) {
+        if (h->sparse) {
+            RAC_CK(launch_sp_chain(h->store, a, st));
+        } else if (h->big) {
             RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
         } else if (h->cluster) {
             a.fuse_prox = 1;   // the z-step / ascent runs at the end of the chain
@@ -537,6 +564,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->lo = pr->lo;
     h->hi = pr->hi;
     h->has_A = pr->A != nullptr;
+    h->sparse = pr->vals != nullptr;
+    h->nnz = h->sparse ? pr->nnz : 0;
     h->p = o->num_blocks;
     h->beta = o->beta;
     h->gamma = o->gamma > 0 ? o->gamma : o->beta;
@@ -552,7 +581,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->dbg_exit_cta = o->debug_exit_cta > 0 ? o->debug_exit_cta - 1 : -1;
     h->path_mode = o->path;
     h->rp = o->assembly == 1 ? 1 : 0;
-    h->gram = !h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m);
+    h->gram = !h->sparse &&
+              (!h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m));
     {
         const size_t nfev = std::max<size_t>(1 + (size_t)h->refresh_every, 6);
         const size_t npev = h->profile ? 3 + 5 * (size_t)h->refresh_every : 0;
@@ -570,7 +600,55 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     cudaStream_t st = h->st;
     const int m = h->m, n = h->n;
     // FP64 copies of the data
-    if (h->has_A) {
+    if (h->sparse) {
+        // compressed columns: check the column starts on the host and the row
+        // indices on the device before any kernel indexes by them
+        std::vector<int64_t> cp((size_t)n + 1);
+        RAC_CK(cudaMemcpyAsync(cp.data(), pr->colptr, cp.size() * sizeof(int64_t),
+                               cudaMemcpyDefault, st));
+        RAC_CK(cudaStreamSynchronize(st));
+        if (cp[0] != 0 || cp[n] != h->nnz) return RAC_ERR_ARG;
+        std::vector<int64_t> len((size_t)n);
+        for (int j = 0; j < n; ++j) {
+            if (cp[j + 1] < cp[j]) return RAC_ERR_ARG;
+            len[j] = cp[j + 1] - cp[j];
+        }
+        // a block's columns are staged in shared memory: bound them by the
+        // smax longest columns
+        const int smax = BlockLayout(n, h->p).smax();
+        std::partial_sort(len.begin(), len.begin() + std::min<size_t>(smax, len.size()), len.end(),
+                          std::greater<int64_t>());
+        int64_t emax = 0;
+        for (int j = 0; j < std::min(smax, n); ++j) emax += len[j];
+        if (emax > sp_max_entries(h->store, smax)) return RAC_ERR_ARG;
+        h->sp_emax = std::max<int64_t>(emax, 1);
+        RAC_ST(h->alloc(&h->sp_colptr, (size_t)n + 1));
+        RAC_CK(cudaMemcpyAsync(h->sp_colptr, cp.data(), cp.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, st));
+        RAC_ST(h->alloc(&h->sp_rowidx, (size_t)h->nnz));
+        RAC_ST(h->alloc(&h->sp_vals64, (size_t)h->nnz));
+        if (h->nnz > 0) {
+            RAC_CK(cudaMemcpyAsync(h->sp_rowidx, pr->rowidx, (size_t)h->nnz * sizeof(int),
+                                   cudaMemcpyDefault, st));
+            RAC_CK(cudaMemcpyAsync(h->sp_vals64, pr->vals, (size_t)h->nnz * sizeof(double),
+                                   cudaMemcpyDefault, st));
+        }
+        int *flag = nullptr;
+        RAC_ST(h->alloc(&flag, 1));
+        RAC_CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+        RAC_CK(launch_sp_validate(m, n, h->sp_colptr, h->sp_rowidx, flag, st));
+        int bad = 0;
+        RAC_CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RAC_CK(cudaStreamSynchronize(st));   // also retires the pageable colptr copy
+        if (bad) return RAC_ERR_ARG;
+        h->nlaunch += 1;
+        RAC_ST(h->alloc(&h->b64, m));
+        if (pr->b) {
+            RAC_ST(copy_in(h->b64, pr->b, m, st));
+        } else {
+            RAC_CK(cudaMemsetAsync(h->b64, 0, m * sizeof(double), st));
+        }
+    } else if (h->has_A) {
         RAC_ST(h->alloc(&h->A64, (size_t)m * n));
         RAC_CK(cudaMemcpy2DAsync(h->A64, (size_t)m * sizeof(double), pr->A,
                                  (size_t)pr->lda * sizeof(double), (size_t)m * sizeof(double), n,
@@ -617,6 +695,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         double lam[2] = {h->lam1, h->lam2};
         RAC_CK(cudaMemcpyAsync(h->lam_dev, lam, sizeof(lam), cudaMemcpyHostToDevice, st));
     }
+    if (h->sparse) RAC_ST(h->alloc(&h->rbuf, m));
     if (h->has_A) {
         RAC_ST(h->alloc(&h->rbuf, m));
         int sms = 148;
@@ -633,7 +712,15 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         // gradient at z = 0 and its statistics, read back after the final sync
         h->ss->h_aux[0] = h->ss->h_aux[1] = 0.0;
         const double *g0 = nullptr;
-        if (h->has_A) {
+        if (h->sparse) {
+            RAC_CK(cudaMemsetAsync(h->z, 0, n * sizeof(double), st));
+            h->nlaunch += 3;
+            RAC_CK(launch_sp_resid_f64(m, n, h->sp_colptr, h->sp_rowidx, h->sp_vals64, h->z,
+                                       h->b64, h->rbuf, st));
+            RAC_CK(launch_sp_gemvt_f64(n, h->sp_colptr, h->sp_rowidx, h->sp_vals64, h->rbuf,
+                                       h->c64, h->gz, st));
+            g0 = h->gz;
+        } else if (h->has_A) {
             RAC_CK(cudaMemsetAsync(h->z, 0, n * sizeof(double), st));
             h->nlaunch += 3;
             RAC_CK(launch_resid_f64(m, n, h->A64, m, h->z, h->b64, h->rbuf, h->rpart, h->nchunk, st));
@@ -651,9 +738,10 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         if (o->gamma < 0) {
             // curvature-scaled split penalty |gamma| * trace(H) / n
             double tr = 0.0;
-            if (h->has_A) {
+            if (h->has_A || h->sparse) {
                 std::vector<double> nrm(n);
-                RAC_CK(launch_colsq_f64(m, n, h->A64, m, h->gz, st));
+                if (h->sparse) RAC_CK(launch_sp_colsq(n, h->sp_colptr, h->sp_vals64, h->gz, st));
+                else RAC_CK(launch_colsq_f64(m, n, h->A64, m, h->gz, st));
                 RAC_CK(cudaMemcpyAsync(nrm.data(), h->gz, n * sizeof(double),
                                        cudaMemcpyDeviceToHost, st));
                 RAC_CK(cudaStreamSynchronize(st));
@@ -690,6 +778,11 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_ST(h->alloc(&h->gdef, n));
         RAC_ST(h->alloc(&h->gnext, n));
         RAC_CK(cudaMemsetAsync(h->gnext, 0, (size_t)n * sizeof(double), st));
+    } else if (h->sparse) {
+        RAC_ST(h->alloc_bytes(&h->sp_vals, (size_t)std::max<int64_t>(h->nnz, 1) * sb));
+        if (h->nnz > 0) RAC_CK(launch_sp_convert(h->store, h->nnz, h->sp_vals64, h->sp_vals, st));
+        RAC_ST(h->alloc(&h->ga, n));
+        RAC_ST(h->alloc(&h->dres, m));
     } else {
         h->R = slab_rows(h->store);
         h->nslab = (m + h->R - 1) / h->R;
@@ -703,8 +796,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->wstride = (lay.factor_total() * ta + 255) & ~(size_t)255;
     RAC_ST(h->alloc_bytes((void **)&h->W, (size_t)h->refresh_every * h->wstride));
     h->kinv = factor_uses_kinv(lay.smax()) ? 1 : 0;
-    h->big = (!h->gram && !h->kinv) ? 1 : 0;
-    if (h->big) h->kinv = 1;
+    h->big = (!h->gram && !h->kinv && !h->sparse) ? 1 : 0;
+    if (h->big || h->sparse) h->kinv = 1;   // sparse: K_S^{-1} by the blocked inverse, any s
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -740,6 +833,13 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         h->pstride = (big_panel_bytes(h->store, h->p, lay.smax()) + 255) & ~(size_t)255;
         RAC_ST(h->alloc_bytes((void **)&h->Pbuf, (size_t)h->refresh_every * h->pstride));
     }
+    if (h->sparse) {
+        // one-CTA chain; the blocked inverse needs its pivot panels per slot
+        h->stage = 0;
+        gmax = 1;
+        h->pstride = (big_panel_bytes(h->store, h->p, lay.smax()) + 255) & ~(size_t)255;
+        RAC_ST(h->alloc_bytes((void **)&h->Pbuf, (size_t)h->refresh_every * h->pstride));
+    }
     if (gmax <= 0) return RAC_ERR_ARG;
     int want = h->gram ? std::min(sms, (n + 31) / 32) : std::min(sms, h->nslab);
     if (o->grid > 0) want = o->grid;
@@ -752,7 +852,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_ST(h->alloc(&h->sperm, n));
         if (h->k) RAC_ST(h->alloc(&h->eperm, n));
     }
-    if (!h->gram) {
+    if (!h->gram && !h->sparse) {
         RAC_ST(h->alloc_bytes((void **)&h->cpart, (size_t)2 * h->grid * lay.smax() * ta));
     }
     // assembly slots
@@ -773,7 +873,10 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_CK(launch_rp_expand(n, h->p, 1, h->order, h->perm, h->blk, st));
         ChainArgs a = chain_args(h, 0);
         a.W = h->Wfix;
-        if (h->big) {
+        if (h->sparse) {
+            RAC_CK(launch_sp_factor(h->store, a, h->Wfix, h->Pbuf, h->sp_emax, st));
+            h->nlaunch += big_factor_launches(lay.smax(), h->store);
+        } else if (h->big) {
             RAC_CK(launch_big_factor(h->store, a, h->Wfix, h->Pbuf, st));
             h->nlaunch += big_factor_launches(lay.smax(), h->store);
         } else {
@@ -784,7 +887,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         h->nlaunch += 1;
         RAC_CK(cudaStreamSynchronize(st));   // the pageable identity order is consumed
     }
-    std::snprintf(h->form, sizeof(h->form), "%s/%s%s%s", h->gram ? "gram" : "residual",
+    std::snprintf(h->form, sizeof(h->form), "%s/%s%s%s",
+                  h->gram ? "gram" : (h->sparse ? "sparse" : "residual"),
                   h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
                   h->cluster ? (h->cluster == 16 ? "/cluster16" : "/cluster8") : "",
                   h->rp ? "/rp" : "");
@@ -801,7 +905,12 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
     *out = nullptr;
     if (!pr || !o) return RAC_ERR_ARG;
     if (pr->n <= 0 || pr->n > (int64_t)1 << 30) return RAC_ERR_ARG;
-    if (!pr->A && !pr->H) return RAC_ERR_ARG;
+    const bool sparse = pr->vals != nullptr;
+    if (sparse && (pr->A || pr->H || !pr->colptr || (pr->nnz > 0 && !pr->rowidx) ||
+                   pr->nnz < 0 || pr->m <= 0 || pr->m > ((int64_t)1 << 31) - 1 ||
+                   o->form == RAC_FORM_GRAM))
+        return RAC_ERR_ARG;
+    if (!pr->A && !pr->H && !sparse) return RAC_ERR_ARG;
     if (pr->A && (pr->m <= 0 || pr->lda < pr->m || pr->m > (int64_t)1 << 30)) return RAC_ERR_ARG;
     if (pr->k < 0 || pr->k > 1 || (pr->k == 1 && !pr->E)) return RAC_ERR_ARG;
     if (pr->phi < RAC_PHI_NONE || pr->phi > RAC_PHI_BOX) return RAC_ERR_ARG;
@@ -815,7 +924,7 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
     // RP on the handle: equal blocks (the chains index blocks by position)
     if (o->assembly == 1 && pr->n % o->num_blocks != 0) return RAC_ERR_ARG;
     if (o->path < 0 || o->path > 2) return RAC_ERR_ARG;
-    if (o->form == RAC_FORM_RESIDUAL && !pr->A) return RAC_ERR_ARG;
+    if (o->form == RAC_FORM_RESIDUAL && !pr->A && !sparse) return RAC_ERR_ARG;
     int64_t smax = (pr->n + o->num_blocks - 1) / o->num_blocks;
     if (smax > 4096) return RAC_ERR_ARG;
     rac_handle *h = new (std::nothrow) rac_handle();

@@ -582,6 +582,25 @@ __global__ void __launch_bounds__(256) k_chain_res_big(ChainArgs a, TA *rhs_g, T
 // ---------------------------------------------------------------- launchers
 // K_S for every block is gathered straight into the factor buffer W and
 // inverted there in place.
+// K_S^{-1} in place of the raw block Grams A~_S^T A~_S in Wout (the first
+// pivot step adds gamma I + beta e e^T)
+template <class TA>
+static cudaError_t big_inverse_impl(const ChainArgs &a, void *Wout, void *Pan, cudaStream_t st) {
+    const int smax = BlockLayout(a.n, a.p).smax();
+    const int ntm = (smax + IT - 1) / IT;
+    for (int k0 = 0; k0 < smax; k0 += BigPB<TA>::v) {
+        k_big_panel<TA><<<a.p, 256, 0, st>>>(a, (TA *)Wout, (TA *)Pan, k0);
+        k_big_update<TA><<<dim3(ntm * ntm, a.p), 256, 0, st>>>(a, (TA *)Wout, (const TA *)Pan, k0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_big_inverse(int store, const ChainArgs &a, void *Wout, void *Pan,
+                               cudaStream_t st) {
+    return store == ST_F64 ? big_inverse_impl<double>(a, Wout, Pan, st)
+                           : big_inverse_impl<float>(a, Wout, Pan, st);
+}
+
 template <class TS, class TA>
 static cudaError_t big_factor_impl(const ChainArgs &a, void *Wout, void *Pan, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
@@ -606,12 +625,7 @@ static cudaError_t big_factor_impl(const ChainArgs &a, void *Wout, void *Pan, cu
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int ntm = (smax + IT - 1) / IT;
-    for (int k0 = 0; k0 < smax; k0 += BigPB<TA>::v) {
-        k_big_panel<TA><<<a.p, 256, 0, st>>>(a, (TA *)Wout, (TA *)Pan, k0);
-        k_big_update<TA><<<dim3(ntm * ntm, a.p), 256, 0, st>>>(a, (TA *)Wout, (const TA *)Pan, k0);
-    }
-    return cudaGetLastError();
+    return big_inverse_impl<TA>(a, Wout, Pan, st);
 }
 
 cudaError_t launch_big_factor(int store, const ChainArgs &a, void *Wout, void *Pan,

@@ -94,6 +94,10 @@ struct ChainArgs {
     const double *eperm;    // lookahead: e in permuted order (n) or NULL
     int perm_in_smem;       // lookahead: the whole permutation fits in shared memory
     int p_rows;             // factor writes P_i row-major (s_i x s_{i-1}) instead of P_i^T
+    // sparse residual form (compressed columns; rac_sparse.cu)
+    const int64_t *sp_colptr;
+    const int *sp_rowidx;
+    const void *sp_vals;    // storage-type values
     int dbg_exit_cta;       // k_chain_res: this CTA returns at its start (-1: none), so the
                             // others' bounded barrier waits run out (failure-path testing)
     int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
@@ -169,6 +173,32 @@ struct PathShape {
 bool path_shape(int store, int n, int p, int L, PathShape *out);
 cudaError_t launch_path_chain(int store, const PathArgs &a, const PathShape &sh,
                               cudaStream_t st);
+
+// the blocked sweep-operator inverse alone, in place of raw block Grams in Wout
+// (store: ST_F64 for an FP64 compute type, else FP32)
+cudaError_t launch_big_inverse(int store, const ChainArgs &a, void *Wout, void *Pan,
+                               cudaStream_t st);
+
+// sparse residual form (compressed columns)
+cudaError_t launch_sp_validate(int m, int n, const int64_t *colptr, const int *rowidx, int *bad,
+                               cudaStream_t st);
+cudaError_t launch_sp_convert(int store, int64_t nnz, const double *v64, void *vs,
+                              cudaStream_t st);
+cudaError_t launch_sp_factor(int store, const ChainArgs &a, void *Wout, void *Pan, int64_t emax,
+                             cudaStream_t st);
+int64_t sp_max_entries(int store, int smax);
+cudaError_t launch_sp_chain(int store, const ChainArgs &a, cudaStream_t st);
+cudaError_t launch_sp_resid_f64(int m, int n, const int64_t *colptr, const int *rowidx,
+                                const double *vals, const double *z, const double *b, double *r,
+                                cudaStream_t st);
+cudaError_t launch_sp_gemvt_f64(int n, const int64_t *colptr, const int *rowidx,
+                                const double *vals, const double *r, const double *c, double *g,
+                                cudaStream_t st);
+cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, const int *rowidx,
+                             const void *vals, const double *x, const double *z, double *dres,
+                             cudaStream_t st);
+cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,
+                            cudaStream_t st);
 
 // RP-MBADMM on the single-problem handle (equal blocks s = n / p): expand the
 // block orders (nsweeps x p) into permutations / block positions, and gather

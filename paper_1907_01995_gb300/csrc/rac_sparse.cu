@@ -1,0 +1,356 @@
+// rac_sparse.cu - the residual form for a sparse data matrix (compressed
+// columns), the large sparse Elastic-Net designs of Sec. 3.1 (Table 3).
+//
+// The sweep is the same as for a dense A (Sec. 1 eq. RAC-ADDM in the split
+// form of Sec. 3.1): block gradients A_S^T d from the maintained
+// d = A~ (x - x_anchor), the block solve with K_S^{-1}, and d += A~_S dx.
+// Only the data access changes: a block's columns are short lists of
+// (row, value) pairs.
+//   k_sp_gram     K_S = A~_S^T A~_S of every block of a sweep (one CTA per block):
+//                 the block's columns are staged in shared memory and every
+//                 pair of columns is merged along their sorted row lists
+//                 (each entry of K_S summed by one thread in row order);
+//                 the inverse then runs as for large dense blocks (blocked
+//                 sweep operator, which adds gamma I + beta e e^T)
+//   k_sp_chain    the cyclic pass over the blocks on one CTA: a warp per
+//                 column for A_S^T d (gathers from d), K_S^{-1} rhs, and
+//                 d += A~_S dx by FP64 atomic adds (rows shared by two
+//                 columns of a block are added in no fixed order, so sparse
+//                 runs are reproducible to rounding, not bit for bit)
+//   k_sp_*_f64    the exact FP64 refresh: r = A z - b (sparse z, atomic
+//                 scatter), g = A^T r + c (a warp per column), and the
+//                 anchor d = A~ (x - z)
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "rac_device.cuh"
+#include "rac_internal.h"
+
+namespace rac {
+
+template <class TS> __device__ __forceinline__ float sp_val(const TS *v, int64_t k) {
+    return to_f(v[k]);
+}
+template <> __device__ __forceinline__ float sp_val<double>(const double *v, int64_t k) {
+    return (float)v[k];   // unused: FP64 storage reads doubles directly
+}
+
+// ---------------------------------------------------------------- validation
+// Every row index in [0, m) and strictly increasing within its column; any
+// violation sets *bad (the kernels below index d and r by these rows).
+__global__ void k_sp_validate(int m, int n, const int64_t *colptr, const int *rowidx, int *bad) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int64_t k0 = colptr[j], k1 = colptr[j + 1];
+        if (k1 < k0) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        int prev = -1;
+        for (int64_t k = k0; k < k1; ++k) {
+            const int r = rowidx[k];
+            if (r < 0 || r >= m || r <= prev) {
+                atomicOr(bad, 1);
+                break;
+            }
+            prev = r;
+        }
+    }
+}
+cudaError_t launch_sp_validate(int m, int n, const int64_t *colptr, const int *rowidx, int *bad,
+                               cudaStream_t st) {
+    k_sp_validate<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, st>>>(m, n, colptr,
+                                                                               rowidx, bad);
+    return cudaGetLastError();
+}
+
+// storage copy of the values
+template <class TS>
+__global__ void k_sp_convert(int64_t nnz, const double *v64, TS *vs) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        vs[k] = (TS)v64[k];
+}
+cudaError_t launch_sp_convert(int store, int64_t nnz, const double *v64, void *vs,
+                              cudaStream_t st) {
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(1, (nnz + 255) / 256), 8192);
+    if (store == ST_F64) k_sp_convert<double><<<grid, 256, 0, st>>>(nnz, v64, (double *)vs);
+    else if (store == ST_F32) k_sp_convert<float><<<grid, 256, 0, st>>>(nnz, v64, (float *)vs);
+    else k_sp_convert<__nv_bfloat16><<<grid, 256, 0, st>>>(nnz, v64, (__nv_bfloat16 *)vs);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- block Grams
+// Shared memory: the s column starts, then the block's rows and values.
+template <class TA> size_t sp_gram_smem(int smax, int64_t emax) {
+    return (((size_t)(smax + 1) * sizeof(int) + 15) & ~(size_t)15) + (size_t)emax * sizeof(int) +
+           (size_t)emax * sizeof(TA) + 16;
+}
+
+template <class TS, class TA>
+__global__ void __launch_bounds__(256) k_sp_gram(ChainArgs a, TA *Wout, int64_t emax) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int b = blockIdx.x;
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    const int s = lay.size(b), off = lay.offset(b);
+    int *start = (int *)sm;                                           // [s + 1]
+    int *rows = (int *)(sm + (((size_t)(smax + 1) * sizeof(int) + 15) & ~(size_t)15));
+    TA *vals = (TA *)(((uintptr_t)(rows + emax) + 15) & ~(uintptr_t)15);
+    const TS *vs = (const TS *)a.sp_vals;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < s; ++c) {
+            start[c] = acc;
+            const int j = a.perm[off + c];
+            acc += (int)(a.sp_colptr[j + 1] - a.sp_colptr[j]);
+        }
+        start[s] = acc;
+    }
+    __syncthreads();
+    if (start[s] > emax) {            // the host bounds emax by the s longest columns
+        if (threadIdx.x == 0) set_err(a.err, RAC_ERR_ARG);
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < s; c += nw) {
+        const int j = a.perm[off + c];
+        const int64_t k0 = a.sp_colptr[j], len = a.sp_colptr[j + 1] - k0;
+        for (int t = lane; t < len; t += 32) {
+            rows[start[c] + t] = a.sp_rowidx[k0 + t];
+            if constexpr (sizeof(TS) == 8) vals[start[c] + t] = (TA)vs[k0 + t];
+            else vals[start[c] + t] = (TA)sp_val<TS>(vs, k0 + t);
+        }
+    }
+    __syncthreads();
+    // pairs (u, v), u >= v, by a running index over the lower triangle
+    TA *K = Wout + lay.factor_offset(b);
+    const int npairs = s * (s + 1) / 2;
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+        int u = (int)((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
+        while ((u + 1) * (u + 2) / 2 <= q) ++u;
+        while (u * (u + 1) / 2 > q) --u;
+        const int v = q - u * (u + 1) / 2;
+        int ia = start[u], ea = start[u + 1], ib = start[v], eb = start[v + 1];
+        TA acc = 0;
+        if (u == v) {
+            for (; ia < ea; ++ia) acc += vals[ia] * vals[ia];
+        } else {
+            while (ia < ea && ib < eb) {
+                const int ra = rows[ia], rb = rows[ib];
+                if (ra == rb) {
+                    acc += vals[ia] * vals[ib];
+                    ++ia;
+                    ++ib;
+                } else if (ra < rb) {
+                    ++ia;
+                } else {
+                    ++ib;
+                }
+            }
+        }
+        K[(size_t)u * s + v] = acc;
+        K[(size_t)v * s + u] = acc;
+    }
+}
+
+template <class TS, class TA>
+static cudaError_t sp_factor_impl(const ChainArgs &a, void *Wout, void *Pan, int64_t emax,
+                                  cudaStream_t st) {
+    BlockLayout lay(a.n, a.p);
+    const size_t smem = sp_gram_smem<TA>(lay.smax(), emax);
+    auto kern = k_sp_gram<TS, TA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.p, 256, smem, st>>>(a, (TA *)Wout, emax);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_big_inverse(sizeof(TA) == 8 ? ST_F64 : ST_F32, a, Wout, Pan, st);
+}
+
+cudaError_t launch_sp_factor(int store, const ChainArgs &a, void *Wout, void *Pan, int64_t emax,
+                             cudaStream_t st) {
+    if (store == ST_F64) return sp_factor_impl<double, double>(a, Wout, Pan, emax, st);
+    if (store == ST_F32) return sp_factor_impl<float, float>(a, Wout, Pan, emax, st);
+    return sp_factor_impl<__nv_bfloat16, float>(a, Wout, Pan, emax, st);
+}
+
+// the largest block entry count the shared-memory staging takes
+int64_t sp_max_entries(int store, int smax) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t ta = store == ST_F64 ? 8 : 4;
+    const size_t head = (((size_t)(smax + 1) * sizeof(int) + 15) & ~(size_t)15) + 16;
+    if ((size_t)optin <= head) return 0;
+    return (int64_t)(((size_t)optin - head) / (sizeof(int) + ta));
+}
+
+// ---------------------------------------------------------------- chain
+constexpr int kSpThreads = 1024;
+
+template <class TS, class TA>
+__global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain(ChainArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    int *idx = (int *)sm;
+    TA *rhs = (TA *)(((uintptr_t)(idx + smax) + 15) & ~(uintptr_t)15);
+    TA *dl = rhs + smax;
+    double *dred = (double *)(((uintptr_t)(dl + smax) + 15) & ~(uintptr_t)15);   // 32
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const TS *vs = (const TS *)a.sp_vals;
+    const TA *Wall = (const TA *)a.W;
+    const double gamma = a.gamma, beta = a.beta;
+    const double mu = a.mu ? *a.mu : 0.0;
+    double t = a.e ? *a.t : 0.0;
+    for (int i = 0; i < a.p; ++i) {
+        const int s = lay.size(i), off = lay.offset(i);
+        for (int q = threadIdx.x; q < s; q += blockDim.x) idx[q] = a.perm[off + q];
+        __syncthreads();
+        // rhs = g_anchor + A~_S^T d - xi + gamma (x - z) (+ coupling), one warp per column
+        for (int c = warp; c < s; c += nw) {
+            const int j = idx[c];
+            const int64_t k0 = a.sp_colptr[j], k1 = a.sp_colptr[j + 1];
+            TA acc = 0;
+            for (int64_t k = k0 + lane; k < k1; k += 32) {
+                const TA v = sizeof(TS) == 8 ? (TA)((const double *)vs)[k] : (TA)sp_val<TS>(vs, k);
+                acc += v * (TA)__ldcg(a.dres + a.sp_rowidx[k]);
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                double r = a.ga[j] + (double)acc - a.xi[j] + gamma * (a.x[j] - a.z[j]);
+                if (a.e) r += a.e[j] * (beta * t - mu);
+                rhs[c] = (TA)r;
+            }
+        }
+        __syncthreads();
+        block_solve_kinv<TA>(Wall + lay.factor_offset(i), s, rhs, dl);   // dl = -K^{-1} rhs
+        if (a.e) {
+            double loc = 0.0;
+            for (int q = threadIdx.x; q < s; q += blockDim.x) loc += a.e[idx[q]] * (double)dl[q];
+            t += block_sum<double>(loc, dred);
+        }
+        for (int q = threadIdx.x; q < s; q += blockDim.x) a.dx[idx[q]] = (double)dl[q];
+        // d += A~_S dl
+        for (int c = warp; c < s; c += nw) {
+            const int j = idx[c];
+            const TA d = dl[c];
+            const int64_t k0 = a.sp_colptr[j], k1 = a.sp_colptr[j + 1];
+            for (int64_t k = k0 + lane; k < k1; k += 32) {
+                const TA v = sizeof(TS) == 8 ? (TA)((const double *)vs)[k] : (TA)sp_val<TS>(vs, k);
+                atomicAdd(a.dres + a.sp_rowidx[k], (double)(v * d));
+            }
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && a.e) *a.t = t;
+}
+
+template <class TS, class TA>
+static cudaError_t sp_chain_impl(const ChainArgs &a, cudaStream_t st) {
+    const int smax = BlockLayout(a.n, a.p).smax();
+    const size_t smem = (((size_t)smax * sizeof(int) + 15) & ~(size_t)15) +
+                        2 * (size_t)smax * sizeof(TA) + 16 + 32 * sizeof(double) + 16;
+    auto kern = k_sp_chain<TS, TA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<1, kSpThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_chain(int store, const ChainArgs &a, cudaStream_t st) {
+    if (store == ST_F64) return sp_chain_impl<double, double>(a, st);
+    if (store == ST_F32) return sp_chain_impl<float, float>(a, st);
+    return sp_chain_impl<__nv_bfloat16, float>(a, st);
+}
+
+// ---------------------------------------------------------------- FP64 refresh
+__global__ void k_sp_fill(int m, const double *b, double sign, double *r) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        r[i] = b ? sign * b[i] : 0.0;
+}
+// r += A[:, j] w_j for every j with w_j != 0 (w = z, or x - z for the anchor);
+// values: FP64 (refresh) or the storage copy (anchor)
+template <class TV>
+__global__ void k_sp_scatter(int n, const int64_t *colptr, const int *rowidx, const TV *vals,
+                             const double *w1, const double *w2, double *r) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += warps) {
+        const double wj = w2 ? w1[j] - w2[j] : w1[j];
+        if (wj == 0.0) continue;
+        for (int64_t k = colptr[j] + lane; k < colptr[j + 1]; k += 32) {
+            double v;
+            if constexpr (sizeof(TV) == 8) v = vals[k];
+            else v = (double)to_f(vals[k]);
+            atomicAdd(r + rowidx[k], v * wj);
+        }
+    }
+}
+// g_j = A[:, j]^T r + c_j, one warp per column
+__global__ void k_sp_gemvt(int n, const int64_t *colptr, const int *rowidx, const double *vals,
+                           const double *r, const double *c, double *g) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += warps) {
+        double acc = 0.0;
+        for (int64_t k = colptr[j] + lane; k < colptr[j + 1]; k += 32) acc += vals[k] * r[rowidx[k]];
+        acc = warp_sum(acc);
+        if (lane == 0) g[j] = acc + (c ? c[j] : 0.0);
+    }
+}
+// ||A_j||^2
+__global__ void k_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += warps) {
+        double acc = 0.0;
+        for (int64_t k = colptr[j] + lane; k < colptr[j + 1]; k += 32) acc += vals[k] * vals[k];
+        acc = warp_sum(acc);
+        if (lane == 0) out[j] = acc;
+    }
+}
+
+static int sp_grid(int n) { return std::max(1, std::min(4096, (n + 7) / 8)); }
+
+cudaError_t launch_sp_resid_f64(int m, int n, const int64_t *colptr, const int *rowidx,
+                                const double *vals, const double *z, const double *b, double *r,
+                                cudaStream_t st) {
+    k_sp_fill<<<std::max(1, std::min(2048, (m + 255) / 256)), 256, 0, st>>>(m, b, -1.0, r);
+    k_sp_scatter<double><<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, vals, z, nullptr, r);
+    return cudaGetLastError();
+}
+cudaError_t launch_sp_gemvt_f64(int n, const int64_t *colptr, const int *rowidx,
+                                const double *vals, const double *r, const double *c, double *g,
+                                cudaStream_t st) {
+    k_sp_gemvt<<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, vals, r, c, g);
+    return cudaGetLastError();
+}
+cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, const int *rowidx,
+                             const void *vals, const double *x, const double *z, double *dres,
+                             cudaStream_t st) {
+    k_sp_fill<<<std::max(1, std::min(2048, (m + 255) / 256)), 256, 0, st>>>(m, nullptr, 0.0, dres);
+    if (store == ST_F64)
+        k_sp_scatter<double><<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, (const double *)vals,
+                                                         x, z, dres);
+    else if (store == ST_F32)
+        k_sp_scatter<float><<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, (const float *)vals, x,
+                                                        z, dres);
+    else
+        k_sp_scatter<__nv_bfloat16><<<sp_grid(n), 256, 0, st>>>(
+            n, colptr, rowidx, (const __nv_bfloat16 *)vals, x, z, dres);
+    return cudaGetLastError();
+}
+cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,
+                            cudaStream_t st) {
+    k_sp_colsq<<<sp_grid(n), 256, 0, st>>>(n, colptr, vals, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rac

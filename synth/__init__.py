@@ -15,4 +15,5 @@ from .workloads import (  # noqa: F401
     warmstart_family,
     path_instance,
     small_instance,
+    sparse_en_instance,
 )

@@ -238,3 +238,37 @@ def small_instance(seed: int, m: int, n: int, num_blocks: int, phi: str = "l1l2"
     return Instance("small", A, b, phi, lam1=lam_frac * lam_max if phi == "l1l2" else 0.0,
                     lam2=lam2, lo=lo, hi=hi, c=c, E=E, d=d, num_blocks=num_blocks,
                     beta=beta, gamma=gamma, seed=seed, x_true=x_true)
+
+
+def sparse_en_instance(seed: int = 0, m: int = 2000, n: int = 20000, density: float = 0.01,
+                       nnz_frac: float = 0.01, noise: float = 0.01, lam_frac: float = 0.1,
+                       lam2: float = 0.0, block: int = 100,
+                       num_blocks: Optional[int] = None) -> Instance:
+    """Sparse LASSO / Elastic-Net design (Sec. 3.1, Table 3: X 40000 x 4M at
+    99.8% sparsity, here scaled): every column holds about density * m N(0,1)
+    entries at uniformly random rows (coinciding rows summed), scaled to unit
+    norm; x_true nnz_frac nonzero N(0,1); b = A x_true + noise; lambda1 =
+    lam_frac ||A^T b||_inf.  A is a scipy.sparse CSC matrix."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    per = max(1, int(round(density * m)))
+    rows = rng.integers(0, m, size=(n, per), dtype=np.int64).ravel()
+    cols = np.repeat(np.arange(n, dtype=np.int64), per)
+    vals = rng.standard_normal(n * per)
+    A = sp.csc_matrix((vals, (rows, cols)), shape=(m, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    nrm = np.sqrt(np.asarray(A.multiply(A).sum(axis=0)).ravel())
+    nrm[nrm == 0.0] = 1.0
+    A = sp.csc_matrix(A @ sp.diags(1.0 / nrm))
+    A.sort_indices()
+    k = max(1, int(round(nnz_frac * n)))
+    support = rng.choice(n, size=k, replace=False)
+    x_true = np.zeros(n)
+    x_true[support] = rng.standard_normal(k)
+    b = A @ x_true + noise * rng.standard_normal(m)
+    lam_max = float(np.abs(A.T @ b).max())
+    p = num_blocks if num_blocks is not None else max(1, (n + block - 1) // block)
+    return Instance("sparse_en", A, b, "l1l2", lam1=lam_frac * lam_max, lam2=lam2,
+                    num_blocks=p, beta=1.0, gamma=1.0, seed=seed, x_true=x_true,
+                    meta={"lambda_max": lam_max, "density": density})

@@ -101,4 +101,17 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     o.assembly = 0
     assert h.value is None
     assert lib.rac_assembly(0, 1, 0, 0, 1, None, None, None) == L.RAC_ERR_ARG
+    # sparse data: only the residual form, and not together with a dense A
+    colptr = np.array([0, 1, 2, 2], dtype=np.int64)
+    rowidx = np.array([0, 3], dtype=np.int32)
+    vals = np.array([1.0, 2.0])
+    ps = L.RacProblem()
+    ps.m, ps.n, ps.nnz = 4, 3, 2
+    ps.colptr, ps.rowidx, ps.vals = colptr.ctypes.data, rowidx.ctypes.data, vals.ctypes.data
+    o.form = 1   # RAC_FORM_GRAM
+    assert lib.rac_admm_setup(ctypes.byref(ps), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
+    o.form = 0
+    ps.A, ps.lda = A.ctypes.data, 4
+    assert lib.rac_admm_setup(ctypes.byref(ps), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
+    assert h.value is None
     assert lib.rac_status_string(4).decode() == "block matrix not positive definite"

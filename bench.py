@@ -236,6 +236,40 @@ def path_leg(dev, flush, st, peaks, sms):
     return out
 
 
+SPARSE_WORKLOAD = dict(name="sparse_en_20000x100000_d0.005", m=20000, n=100000, density=0.005,
+                       block=100, tol=1e-6, refresh_every=10)
+
+
+def sparse_leg(flush, st):
+    """Sparse Elastic-Net (Sec. 3.1, Table 3's regime, scaled): A 20000 x 100000
+    with 0.5% N(0,1) entries per column at random rows, unit-norm columns,
+    x_true 1% nonzero, lambda1 = 0.1 ||A^T b||_inf, lambda2 = 0.1, blocks of
+    100, residual form on compressed columns; time to KKT <= 1e-6 from the
+    host CSC (setup included) in BF16 and FP32 storage and on the plain FP64
+    path."""
+    import synth
+    from paper_1907_01995_gb300 import api
+    w = SPARSE_WORKLOAD
+    inst = synth.sparse_en_instance(0, m=w["m"], n=w["n"], density=w["density"],
+                                    nnz_frac=0.01, lam_frac=0.1, lam2=0.1, block=w["block"])
+    out = {"workload": w["name"], "m": w["m"], "n": w["n"], "nnz": int(inst.A.nnz),
+           "p": inst.num_blocks, "tol": w["tol"], "lambda1": "0.1*||A^T b||_inf", "lambda2": 0.1}
+
+    def solve(storage):
+        with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=inst.lam1, lambda2=0.1,
+                        num_blocks=inst.num_blocks, tol=w["tol"], max_sweeps=2000,
+                        refresh_every=w["refresh_every"], storage=storage) as h:
+            return h.solve()[1]
+
+    for storage in ("bf16", "fp32", "fp64"):
+        ms, info = _timed_call(lambda: solve(storage), flush, st)
+        out[storage] = {"time_ms": ms, "sweeps": info["sweeps"], "kkt": info["kkt"],
+                        "status": info["status"], "form": info["form"],
+                        "block_updates_per_s": info["block_updates"] / (ms / 1000.0)}
+    out["speedup_bf16_vs_fp64_plain"] = out["fp64"]["time_ms"] / out["bf16"]["time_ms"]
+    return out
+
+
 def path_once(k):
     """K batched BF16 solves of the 64-point path (profiling entry)."""
     import torch
@@ -668,6 +702,10 @@ def main():
             extra["lasso_path_20000x5000_64"] = path_leg(dev, flush, st, peaks, sms)
         except Exception as ex:
             extra["lasso_path_20000x5000_64"] = {"failed": str(ex)[:300]}
+        try:
+            extra["sparse_en_20000x100000"] = sparse_leg(flush, st)
+        except Exception as ex:
+            extra["sparse_en_20000x100000"] = {"failed": str(ex)[:300]}
         try:
             extra["svm_batch_256"] = svm_batch_times(
                 256, dev, [("bf16", "rp"), ("bf16", "rac"), ("fp32", "rp"), ("fp64", "rp"),

@@ -186,6 +186,11 @@ typedef struct {
     double t_loop_ms;       /* rac_admm_batch: device time from the first sweep to the end of
                                the last refresh (all periods, checks between them included),
                                by CUDA events on the batch's stream; 0 elsewhere */
+    double obj;             /* rac_admm_solve (and each point of a sequential path): the
+                               objective of the returned z in FP64 with the exact data,
+                               1/2 ||A z - b||^2 + c^T z + sum_j phi(z_j) (H form:
+                               1/2 z^T H z + c^T z + sum_j phi(z_j)); the box indicator counts
+                               0 (z is in the box).  0 in rac_admm_batch and the batched path. */
 } rac_info;
 
 typedef struct rac_handle rac_handle;

@@ -51,7 +51,7 @@ class RacInfo(ctypes.Structure):
                 ("kernel_launches", c_int64), ("setup_launches", c_int64),
                 ("t_assembly_ms", c_double), ("t_factor_ms", c_double), ("t_chain_ms", c_double),
                 ("t_prox_ms", c_double), ("t_refresh_ms", c_double), ("chain_launches", c_int64),
-                ("warm_start_rejected", c_int32), ("t_loop_ms", c_double)]
+                ("warm_start_rejected", c_int32), ("t_loop_ms", c_double), ("obj", c_double)]
 
 
 P = ctypes.POINTER

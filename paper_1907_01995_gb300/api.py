@@ -143,7 +143,8 @@ def _info_dict(info: L.RacInfo) -> dict:
             "t_assembly_ms": info.t_assembly_ms, "t_factor_ms": info.t_factor_ms,
             "t_chain_ms": info.t_chain_ms, "t_prox_ms": info.t_prox_ms,
             "t_refresh_ms": info.t_refresh_ms, "chain_launches": info.chain_launches,
-            "warm_start_rejected": info.warm_start_rejected, "t_loop_ms": info.t_loop_ms}
+            "warm_start_rejected": info.warm_start_rejected, "t_loop_ms": info.t_loop_ms,
+            "obj": info.obj}
 
 
 class Handle:

@@ -984,8 +984,13 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
     if (x_out) {
         RAC_CK(cudaMemcpyAsync(x_out, h->z, (size_t)h->n * sizeof(double), cudaMemcpyDefault, h->st));
     }
-    double mu = 0.0;
+    double mu = 0.0, obj = 0.0;
     if (h->k) RAC_CK(cudaMemcpyAsync(&mu, h->mu, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    // objective of z from the last refresh (r = A z - b and g = grad f(z) are current)
+    RAC_CK(launch_objective(h->m, h->n, (h->has_A || h->sparse) ? h->rbuf : nullptr, h->z, h->c64,
+                            h->gz, h->phi, h->lam1, h->lam2, h->lam_dev, h->kpart, h->st));
+    h->nlaunch += 1;
+    RAC_CK(cudaMemcpyAsync(&obj, h->kpart, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     RAC_CK(cudaStreamSynchronize(h->st));
     if (info) {
         info->sweeps = done;
@@ -1006,6 +1011,8 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
         info->t_refresh_ms = h->t_ref;
         info->chain_launches = h->chain_launches;
         info->warm_start_rejected = rejected;
+        info->t_loop_ms = 0.0;
+        info->obj = obj;
     }
     return status;
 }

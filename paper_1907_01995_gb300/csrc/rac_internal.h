@@ -233,6 +233,10 @@ cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z
                        double hi, DevStats *stats, double *part, cudaStream_t st,
                        const double *lam_dev = nullptr);
 int kkt_part_doubles();
+// objective of z from the last exact refresh (r = A z - b, or NULL in the H form with g = H z + c)
+cudaError_t launch_objective(int m, int n, const double *r, const double *z, const double *c,
+                             const double *g, int phi, double lam1, double lam2,
+                             const double *lam_dev, double *out, cudaStream_t st);
 // anchor reset in the storage type: g = gz + G~ (x - z)  or  dres = A~ (x - z);
 // dxz: n floats of scratch (FP32/BF16 storage)
 cudaError_t launch_gram_anchor(int store, int n, const void *G, const double *gz,

@@ -1517,6 +1517,38 @@ cudaError_t launch_kkt(int n, const double *gz, const double *x, const double *z
 }
 int kkt_part_doubles() { return 6 * kKktParts; }
 
+// Objective of z from the last exact refresh (one CTA, fixed order):
+// data form 1/2 ||r||^2 + c^T z + phi(z) with r = A z - b; H form
+// 1/2 z^T (g - c) + c^T z + phi(z) with g = H z + c.
+__global__ void __launch_bounds__(1024) k_objective(int m, int n, const double *r, const double *z,
+                                                    const double *c, const double *g, int phi,
+                                                    double lam1, double lam2, const double *lam_dev,
+                                                    double *out) {
+    __shared__ double red[32];
+    if (lam_dev) {
+        lam1 = lam_dev[0];
+        lam2 = lam_dev[1];
+    }
+    double acc = 0.0;
+    if (r) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) acc += 0.5 * r[i] * r[i];
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double zj = z[j], cj = c ? c[j] : 0.0;
+        if (!r) acc += 0.5 * zj * (g[j] - cj);
+        acc += cj * zj;
+        if (phi == RAC_PHI_L1L2) acc += lam1 * fabs(zj) + 0.5 * lam2 * zj * zj;
+    }
+    acc = block_sum<double>(acc, red);
+    if (threadIdx.x == 0) *out = acc;
+}
+cudaError_t launch_objective(int m, int n, const double *r, const double *z, const double *c,
+                             const double *g, int phi, double lam1, double lam2,
+                             const double *lam_dev, double *out, cudaStream_t st) {
+    k_objective<<<1, 1024, 0, st>>>(m, n, r, z, c, g, phi, lam1, lam2, lam_dev, out);
+    return cudaGetLastError();
+}
+
 // Statistics of the gradient at z = 0 for setup: the KKT scale max|g0| and
 // the unscaled stationarity of z = 0 (the cold start a warm start must beat).
 __global__ void __launch_bounds__(1024) k_kkt_zero(int n, const double *g0, int phi, double lam1,

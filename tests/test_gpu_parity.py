@@ -179,6 +179,9 @@ def test_lasso_config_converged(lasso_ref, storage, form, tol, bound):
     assert np.array_equal(z != 0, ref != 0)
     P = O.problem_from_instance(inst)
     assert O.kkt(P, z)["kkt"] <= tol * 1.01 + 1e-15
+    # rac_info.obj: 1/2 ||A z - b||^2 + lambda1 ||z||_1 (the oracle drops the constant 1/2 ||b||^2)
+    ref_obj = P.objective(z) + 0.5 * float(inst.b @ inst.b)
+    assert abs(info["obj"] - ref_obj) <= 1e-12 * abs(ref_obj)
 
 
 def test_svm_small_converged_matches_smo():

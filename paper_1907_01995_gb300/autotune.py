@@ -95,3 +95,80 @@ def choose(A, b, common: dict, key: str, device=None, candidates=None, grids=Non
         except OSError:
             pass
     return res
+
+
+# ---------------------------------------------------------------- batched form
+BATCH_CANDIDATES = [(32, "rac", "bf16"), (64, "rac", "bf16"), (128, "rac", "bf16"),
+                    (32, "rp", "bf16"), (64, "rp", "bf16"), (128, "rp", "bf16"),
+                    (64, "rp", "fp32")]
+
+
+def batch_sample(work, count):
+    """Indices of `count` instances spread over the work quantiles (sorted by
+    work, evenly spaced ranks), so that the sample keeps the batch's mix of
+    small and large instances."""
+    order = sorted(range(len(work)), key=lambda i: (work[i], i))
+    if count >= len(order):
+        return order
+    return sorted({order[int(round(k * (len(order) - 1) / (count - 1)))] for k in range(count)})
+
+
+def choose_batch(probs, common: dict, key: str, device=None, candidates=None, sample=8,
+                 budget_s=2.0, use_cache: bool = True) -> dict:
+    """Block size, assembly (RAC or RP) and storage for rac_admm_batch on this
+    family.  Every candidate gets the same device-time budget on the same
+    stratified sample of the problems (batch_sample): a 30-sweep run measures
+    its time per sweep, then it runs as many sweeps as the budget buys, and
+    it is scored by the geometric mean of the sample's KKT measures at the
+    end (so a candidate with cheaper sweeps, or with more progress per sweep,
+    wins).  Time to a fixed tolerance cannot rank these duals at full size:
+    the split iteration needs more than 10^4 sweeps to reach KKT 1e-3 on the
+    largest ones.  Returns {"block", "assembly", "storage", "score",
+    "table"}; cached per (GPU, library build, key) like choose()."""
+    import math
+    candidates = candidates or BATCH_CANDIDATES
+    ck = "%s|%s|batch|%s" % (_gpu_name(device), _build_id(), key)
+    path = _cache_path()
+    cache = {}
+    if use_cache:
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if ck in cache:
+            return cache[ck]
+    work = [int(p["A"].shape[0]) * int(p["A"].shape[1]) for p in probs]
+    pick = batch_sample(work, sample)
+    sub = [probs[i] for i in pick]
+    table = []
+    for block, assembly, storage in candidates:
+        kw = dict(common)
+        kw.update(num_blocks=-block, assembly=assembly, storage=storage, tol=0.0)
+        try:
+            _, probe = api.batch(sub, max_sweeps=30, **kw)
+            ms_sweep = probe[0]["t_loop_ms"] / 30.0
+            sweeps = int(min(20000, max(30, budget_s * 1000.0 / max(ms_sweep, 1e-3))))
+            sweeps -= sweeps % int(kw.get("refresh_every", 10))
+            _, infos = api.batch(sub, max_sweeps=max(sweeps, 30), **kw)
+        except _lib.RacError:
+            continue
+        kkts = [max(i["kkt"], 1e-300) for i in infos]
+        score = math.exp(sum(math.log(k) for k in kkts) / len(kkts))
+        table.append({"block": block, "assembly": assembly, "storage": storage,
+                      "ms_per_sweep": ms_sweep, "sweeps": infos[0]["sweeps"], "score": score,
+                      "worst_kkt": max(kkts)})
+    if not table:
+        raise RuntimeError("no batch autotuner candidate ran")
+    best = min(table, key=lambda r: r["score"])
+    res = {k: best[k] for k in ("block", "assembly", "storage", "score", "ms_per_sweep")}
+    res.update({"table": table, "sample": pick, "budget_s": budget_s})
+    if use_cache:
+        cache[ck] = res
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+    return res

@@ -92,9 +92,13 @@ typedef struct {
     const double *b;        /* m, or NULL (= 0) */
     const double *H;        /* n x n symmetric PSD (column-major), or NULL */
     const double *c;        /* n, or NULL (= 0): linear term added to the smooth part */
-    const double *E;        /* 1 x n coupling row, or NULL (k = 0) */
-    const double *d;        /* 1, right-hand side of E x = d (NULL = 0) */
-    int32_t k;              /* number of coupling rows: 0 or 1 */
+    const double *E;        /* k x n coupling rows, row-major, or NULL (k = 0) */
+    const double *d;        /* k, right-hand side of E x = d (NULL = 0) */
+    int32_t k;              /* number of coupling rows, 0 .. 64.  k >= 2 (the general
+                               constraint block of eq. lcqp, Sec. 2) runs the Gram form with
+                               beta E^T E folded into the Gram matrix and the multipliers in the
+                               linear term (same iterates); RESIDUAL form, sparse A and
+                               rac_admm_batch take k <= 1 */
     int32_t phi;            /* rac_phi */
     double lambda1, lambda2;/* l1l2 weights (>= 0) */
     double lo, hi;          /* box bounds (lo < hi) */
@@ -172,7 +176,7 @@ typedef struct {
     int64_t block_updates;  /* sweeps * p */
     double kkt;             /* KKT of the returned z (see above) */
     double primal_res;      /* ||x - z||_inf */
-    double mu;              /* coupling multiplier (0 when k = 0) */
+    double mu;              /* coupling multiplier (the first one when k >= 2; 0 when k = 0) */
     double seconds;         /* wall time of the call */
     int32_t status;         /* rac_status of this problem */
     char form[32];          /* e.g. "gram/fp32" */
@@ -232,7 +236,8 @@ rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *info);
  * sweep counter to 0. */
 rac_status rac_admm_reset(rac_handle *h, const double *x0, const double *xi0);
 
-/* Copy the current iterates (each n; NULL to skip) and mu (1) out. */
+/* Copy the current iterates (each n; NULL to skip) and the multipliers mu
+ * (max(1, k) values) out. */
 rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, double *xi, double *mu);
 
 /* Solve `count` independent problems in one persistent launch (Sec. 3.2's

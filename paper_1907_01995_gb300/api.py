@@ -100,9 +100,11 @@ def make_problem(keep: _Keep, A=None, b=None, *, H=None, c=None, E=None, d=None,
         raise ValueError("need A or H")
     pr.c = keep.vec(c, pr.n)
     if E is not None:
-        pr.E = keep.vec(E, pr.n)
-        pr.d = keep.vec(np.zeros(1) if d is None else d, 1)
-        pr.k = 1
+        Ek = E if _is_tensor(E) else np.asarray(E, dtype=np.float64)
+        k = 1 if Ek.ndim == 1 else int(Ek.shape[0])
+        pr.E = keep.vec(Ek, k * pr.n)        # k x n row-major
+        pr.d = keep.vec(np.zeros(k) if d is None else d, k)
+        pr.k = k
     pr.phi = L.PHI[phi]
     pr.lambda1, pr.lambda2, pr.lo, pr.hi = float(lambda1), float(lambda2), float(lo), float(hi)
     return pr
@@ -193,12 +195,14 @@ class Handle:
                 "rac_admm_reset")
 
     def state(self):
+        """Current iterates; "mu" is the multiplier (k = 1) or the array of k."""
         x, z, xi = (np.empty(self.n) for _ in range(3))
-        mu = np.zeros(1)
+        k = max(1, int(self.problem.k))
+        mu = np.zeros(k)
         L.check(self._lib.rac_admm_get_state(self._h, x.ctypes.data, z.ctypes.data,
                                              xi.ctypes.data, mu.ctypes.data),
                 "rac_admm_get_state")
-        return {"x": x, "z": z, "xi": xi, "mu": mu[0]}
+        return {"x": x, "z": z, "xi": xi, "mu": mu[0] if k == 1 else mu}
 
     def checkpoint(self) -> bytes:
         n = ctypes.c_size_t(0)

@@ -131,6 +131,9 @@ struct rac_handle {
     void *Wfix = nullptr;
     // sparse A (compressed columns): FP64 values for the refresh, storage copy
     // for the sweeps; sp_emax bounds the entries of one block's columns
+    // k >= 2 coupling rows folded into the Gram form (rac_coupling.cu)
+    bool fold = false;
+    double *E64k = nullptr, *dk = nullptr, *vbuf = nullptr, *fbuf = nullptr;
     bool sparse = false;
     int64_t nnz = 0, sp_emax = 0;
     int64_t *sp_colptr = nullptr;
@@ -230,8 +233,20 @@ static rac_status enqueue_refresh(rac_handle *h) {
     } else {
         RAC_CK(launch_symv_f64(h->n, h->H64, h->z, h->c64, h->gz, st));
     }
-    RAC_CK(launch_kkt(h->n, h->gz, h->x, h->z, h->e64, h->d, h->k ? h->mu : nullptr, h->phi,
-                      h->lam1, h->lam2, h->lo, h->hi, h->stats, h->kpart, st, h->lam_dev));
+    if (h->fold) {
+        // KKT on v = grad f(z) - E^T mu; gz becomes the folded gradient for the anchor
+        RAC_CK(launch_couple_refresh(h->n, h->k, h->E64k, h->dk, h->z, h->mu, h->beta, h->gz,
+                                     h->vbuf, h->fbuf, st));
+        RAC_CK(launch_kkt(h->n, h->vbuf, h->x, h->z, nullptr, 0.0, nullptr, h->phi, h->lam1,
+                          h->lam2, h->lo, h->hi, h->stats, h->kpart, st, h->lam_dev));
+        RAC_CK(cudaMemcpyAsync(&h->stats->ez_minus_d, h->fbuf, sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+        h->nlaunch += 1;
+    } else {
+        RAC_CK(launch_kkt(h->n, h->gz, h->x, h->z, h->e64, h->d, h->k ? h->mu : nullptr,
+                          h->phi, h->lam1, h->lam2, h->lo, h->hi, h->stats, h->kpart, st,
+                          h->lam_dev));
+    }
     if (h->gram) {
         RAC_CK(launch_gram_anchor(h->store, h->n, h->G, h->gz, h->x, h->z, h->dxz, h->g, st));
     } else if (h->sparse) {
@@ -242,7 +257,7 @@ static rac_status enqueue_refresh(rac_handle *h) {
         RAC_CK(cudaMemcpyAsync(h->ga, h->gz, h->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         RAC_CK(launch_slab_anchor(h->store, h->n, h->nslab, h->R, h->As, h->x, h->z, h->dres, st));
     }
-    if (h->k)
+    if (h->k == 1)
         RAC_CK(cudaMemcpyAsync(h->t, &h->stats->ex_minus_d, sizeof(double),
                                cudaMemcpyDeviceToDevice, st));
     return RAC_OK;
@@ -272,7 +287,7 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.dx = h->dx;
     a.e = h->e64;
     a.t = h->t;
-    a.mu = h->k ? h->mu : nullptr;
+    a.mu = h->k == 1 ? h->mu : nullptr;
     a.beta = h->beta;
     a.gamma = h->gamma;
     a.bar = h->bar;
@@ -285,7 +300,7 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.P = h->lookahead ? (const void *)((char *)h->Pbuf + (size_t)slot * h->pstride) : nullptr;
     a.gnext = h->gnext;
     a.sperm = h->sperm;
-    a.eperm = h->k ? h->eperm : nullptr;
+    a.eperm = h->k == 1 ? h->eperm : nullptr;
     a.perm_in_smem = h->perm_in_smem;
     a.p_rows = h->cluster ? 1 : 0;
     a.dbg_exit_cta = h->dbg_exit_cta;
@@ -310,8 +325,8 @@ static ProxArgs prox_args(const rac_handle *h) {
     pa.g = h->gram ? h->g : nullptr;
     pa.gdef = h->gdef;
     pa.gnext = h->gram ? h->gnext : nullptr;
-    pa.mu = h->k ? h->mu : nullptr;
-    pa.t = h->k ? h->t : nullptr;
+    pa.mu = h->k == 1 ? h->mu : nullptr;
+    pa.t = h->k == 1 ? h->t : nullptr;
     pa.phi = h->phi;
     pa.lam1 = h->lam1;
     pa.lam2 = h->lam2;
@@ -387,7 +402,7 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         ChainArgs a = chain_args(h, s);
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
         if (h->lookahead)
-            RAC_CK(launch_prepare(h->n, a.perm, h->x, h->z, h->xi, h->k ? h->e64 : nullptr,
+            RAC_CK(launch_prepare(h->n, a.perm, h->x, h->z, h->xi, h->k == 1 ? h->e64 : nullptr,
                                   h->gamma, h->sperm, h->eperm, st));
         if (s >= pre_in && !h->rp) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
@@ -406,6 +421,11 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         if (pf) RAC_CK(cudaEventRecord(ev[3], st));
         if (!h->cluster) {
             RAC_CK(launch_prox(prox_args(h), st));
+            h->nlaunch += 1;
+        }
+        if (h->fold) {   // mu ascent of the k rows and the gradient shift it causes
+            RAC_CK(launch_couple_ascent(h->n, h->k, h->E64k, h->dk, h->x, h->beta, h->mu, h->g,
+                                        st));
             h->nlaunch += 1;
         }
         if (pf) RAC_CK(cudaEventRecord(ev[4], st));
@@ -533,8 +553,8 @@ static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) 
     } else {
         RAC_CK(cudaMemsetAsync(h->xi, 0, nb, st));
     }
-    RAC_CK(cudaMemsetAsync(h->mu, 0, sizeof(double), st));
-    RAC_CK(cudaMemsetAsync(h->t, 0, sizeof(double), st));
+    RAC_CK(cudaMemsetAsync(h->mu, 0, std::max(1, h->k) * sizeof(double), st));
+    RAC_CK(cudaMemsetAsync(h->t, 0, std::max(1, h->k) * sizeof(double), st));
     RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     h->sweep = 0;
     h->pre = 0;   // a pre-launched period head belongs to the old sweep count
@@ -565,6 +585,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->hi = pr->hi;
     h->has_A = pr->A != nullptr;
     h->sparse = pr->vals != nullptr;
+    h->fold = pr->k >= 2;
     h->nnz = h->sparse ? pr->nnz : 0;
     h->p = o->num_blocks;
     h->beta = o->beta;
@@ -581,8 +602,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->dbg_exit_cta = o->debug_exit_cta > 0 ? o->debug_exit_cta - 1 : -1;
     h->path_mode = o->path;
     h->rp = o->assembly == 1 ? 1 : 0;
-    h->gram = !h->sparse &&
-              (!h->has_A || o->form == RAC_FORM_GRAM || (o->form == RAC_FORM_AUTO && h->n <= h->m));
+    h->gram = !h->sparse && (!h->has_A || h->fold || o->form == RAC_FORM_GRAM ||
+                             (o->form == RAC_FORM_AUTO && h->n <= h->m));
     {
         const size_t nfev = std::max<size_t>(1 + (size_t)h->refresh_every, 6);
         const size_t npev = h->profile ? 3 + 5 * (size_t)h->refresh_every : 0;
@@ -668,13 +689,24 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_ST(h->alloc(&h->c64, n));
         RAC_ST(copy_in(h->c64, pr->c, n, st));
     }
-    if (h->k) {
+    if (h->k == 1) {
         RAC_ST(h->alloc(&h->e64, n));
         RAC_ST(copy_in(h->e64, pr->E, n, st));
         if (pr->d) {
             RAC_CK(cudaMemcpyAsync(&h->d, pr->d, sizeof(double), cudaMemcpyDefault, st));
             RAC_CK(cudaStreamSynchronize(st));
         }
+    } else if (h->fold) {
+        RAC_ST(h->alloc(&h->E64k, (size_t)h->k * n));
+        RAC_ST(copy_in(h->E64k, pr->E, (size_t)h->k * n, st));
+        RAC_ST(h->alloc(&h->dk, h->k));
+        if (pr->d) {
+            RAC_ST(copy_in(h->dk, pr->d, h->k, st));
+        } else {
+            RAC_CK(cudaMemsetAsync(h->dk, 0, h->k * sizeof(double), st));
+        }
+        RAC_ST(h->alloc(&h->vbuf, n));
+        RAC_ST(h->alloc(&h->fbuf, 1));
     }
     // work buffers
     RAC_ST(h->alloc(&h->x, n));
@@ -682,8 +714,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(h->alloc(&h->xi, n));
     RAC_ST(h->alloc(&h->dx, n));
     RAC_ST(h->alloc(&h->gz, n));
-    RAC_ST(h->alloc(&h->mu, 1));
-    RAC_ST(h->alloc(&h->t, 1));
+    RAC_ST(h->alloc(&h->mu, std::max(1, h->k)));
+    RAC_ST(h->alloc(&h->t, std::max(1, h->k)));
     RAC_ST(h->alloc(&h->err, 1));
     RAC_ST(h->alloc(&h->stats, 1));
     RAC_ST(h->alloc(&h->bar, 1));
@@ -774,6 +806,10 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         } else {
             RAC_CK(launch_sym_convert(h->store, n, h->H64, h->G, st));
         }
+        if (h->fold) {   // the coupling rows' beta E^T E, once
+            RAC_CK(launch_fold_gram(h->store, n, h->k, h->E64k, h->beta, h->G, st));
+            h->nlaunch += 1;
+        }
         RAC_ST(h->alloc(&h->g, n));
         RAC_ST(h->alloc(&h->gdef, n));
         RAC_ST(h->alloc(&h->gnext, n));
@@ -850,7 +886,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
                      ~(size_t)255;
         RAC_ST(h->alloc_bytes((void **)&h->Pbuf, (size_t)h->refresh_every * h->pstride));
         RAC_ST(h->alloc(&h->sperm, n));
-        if (h->k) RAC_ST(h->alloc(&h->eperm, n));
+        if (h->k == 1) RAC_ST(h->alloc(&h->eperm, n));
     }
     if (!h->gram && !h->sparse) {
         RAC_ST(h->alloc_bytes((void **)&h->cpart, (size_t)2 * h->grid * lay.smax() * ta));
@@ -912,7 +948,9 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
         return RAC_ERR_ARG;
     if (!pr->A && !pr->H && !sparse) return RAC_ERR_ARG;
     if (pr->A && (pr->m <= 0 || pr->lda < pr->m || pr->m > (int64_t)1 << 30)) return RAC_ERR_ARG;
-    if (pr->k < 0 || pr->k > 1 || (pr->k == 1 && !pr->E)) return RAC_ERR_ARG;
+    if (pr->k < 0 || pr->k > couple_max_rows() || (pr->k >= 1 && !pr->E)) return RAC_ERR_ARG;
+    // k >= 2 rows are folded into the Gram form
+    if (pr->k >= 2 && (pr->vals || o->form == RAC_FORM_RESIDUAL)) return RAC_ERR_ARG;
     if (pr->phi < RAC_PHI_NONE || pr->phi > RAC_PHI_BOX) return RAC_ERR_ARG;
     if (pr->phi == RAC_PHI_L1L2 && (pr->lambda1 < 0 || pr->lambda2 < 0)) return RAC_ERR_ARG;
     if (pr->phi == RAC_PHI_BOX && !(pr->lo < pr->hi)) return RAC_ERR_ARG;
@@ -1032,7 +1070,9 @@ extern "C" rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, do
     if (x) RAC_CK(cudaMemcpyAsync(x, h->x, nb, cudaMemcpyDefault, h->st));
     if (z) RAC_CK(cudaMemcpyAsync(z, h->z, nb, cudaMemcpyDefault, h->st));
     if (xi) RAC_CK(cudaMemcpyAsync(xi, h->xi, nb, cudaMemcpyDefault, h->st));
-    if (mu) RAC_CK(cudaMemcpyAsync(mu, h->mu, sizeof(double), cudaMemcpyDefault, h->st));
+    if (mu)
+        RAC_CK(cudaMemcpyAsync(mu, h->mu, std::max(1, h->k) * sizeof(double), cudaMemcpyDefault,
+                               h->st));
     RAC_CK(cudaStreamSynchronize(h->st));
     return RAC_OK;
 }
@@ -1303,7 +1343,7 @@ struct CkptHeader {
 
 extern "C" rac_status rac_admm_checkpoint(rac_handle *h, void *buf, size_t *len) {
     if (!h || !len) return RAC_ERR_ARG;
-    size_t need = sizeof(CkptHeader) + (3 * (size_t)h->n + 1) * sizeof(double);
+    size_t need = sizeof(CkptHeader) + (3 * (size_t)h->n + std::max(1, h->k)) * sizeof(double);
     if (!buf) {
         *len = need;
         return RAC_OK;
@@ -1326,7 +1366,8 @@ extern "C" rac_status rac_admm_checkpoint(rac_handle *h, void *buf, size_t *len)
     RAC_CK(cudaMemcpyAsync(body, h->x, nb, cudaMemcpyDefault, h->st));
     RAC_CK(cudaMemcpyAsync(body + h->n, h->z, nb, cudaMemcpyDefault, h->st));
     RAC_CK(cudaMemcpyAsync(body + 2 * (size_t)h->n, h->xi, nb, cudaMemcpyDefault, h->st));
-    RAC_CK(cudaMemcpyAsync(body + 3 * (size_t)h->n, h->mu, sizeof(double), cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(body + 3 * (size_t)h->n, h->mu, std::max(1, h->k) * sizeof(double),
+                           cudaMemcpyDefault, h->st));
     RAC_CK(cudaStreamSynchronize(h->st));
     *len = need;
     return RAC_OK;
@@ -1334,7 +1375,7 @@ extern "C" rac_status rac_admm_checkpoint(rac_handle *h, void *buf, size_t *len)
 
 extern "C" rac_status rac_admm_restore(rac_handle *h, const void *buf, size_t len) {
     if (!h || !buf) return RAC_ERR_ARG;
-    size_t need = sizeof(CkptHeader) + (3 * (size_t)h->n + 1) * sizeof(double);
+    size_t need = sizeof(CkptHeader) + (3 * (size_t)h->n + std::max(1, h->k)) * sizeof(double);
     if (len < need) return RAC_ERR_STATE;
     CkptHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
@@ -1348,7 +1389,8 @@ extern "C" rac_status rac_admm_restore(rac_handle *h, const void *buf, size_t le
     RAC_CK(cudaMemcpyAsync(h->x, body, nb, cudaMemcpyDefault, h->st));
     RAC_CK(cudaMemcpyAsync(h->z, body + h->n, nb, cudaMemcpyDefault, h->st));
     RAC_CK(cudaMemcpyAsync(h->xi, body + 2 * (size_t)h->n, nb, cudaMemcpyDefault, h->st));
-    RAC_CK(cudaMemcpyAsync(h->mu, body + 3 * (size_t)h->n, sizeof(double), cudaMemcpyDefault, h->st));
+    RAC_CK(cudaMemcpyAsync(h->mu, body + 3 * (size_t)h->n, std::max(1, h->k) * sizeof(double),
+                           cudaMemcpyDefault, h->st));
     RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
     h->sweep = hd.sweep;
     h->pre = 0;

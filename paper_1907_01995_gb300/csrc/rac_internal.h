@@ -174,6 +174,18 @@ bool path_shape(int store, int n, int p, int L, PathShape *out);
 cudaError_t launch_path_chain(int store, const PathArgs &a, const PathShape &sh,
                               cudaStream_t st);
 
+// k >= 2 coupling rows folded into the Gram form (rac_coupling.cu): G += beta E^T E,
+// the per-sweep multiplier ascent with its gradient shift, and the refresh's
+// unfolded KKT gradient v, folded anchor gradient and feasibility
+cudaError_t launch_fold_gram(int store, int n, int k, const double *E, double beta, void *G,
+                             cudaStream_t st);
+cudaError_t launch_couple_ascent(int n, int k, const double *E, const double *d, const double *x,
+                                 double beta, double *mu, double *g, cudaStream_t st);
+cudaError_t launch_couple_refresh(int n, int k, const double *E, const double *d, const double *z,
+                                  const double *mu, double beta, double *gz, double *v,
+                                  double *feas, cudaStream_t st);
+int couple_max_rows();
+
 // the blocked sweep-operator inverse alone, in place of raw block Grams in Wout
 // (store: ST_F64 for an FP64 compute type, else FP32)
 cudaError_t launch_big_inverse(int store, const ChainArgs &a, void *Wout, void *Pan,

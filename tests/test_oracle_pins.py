@@ -214,6 +214,30 @@ def test_split_sweep_equals_paper_linear_map(coupling):
     assert np.allclose(got, expect, rtol=1e-11, atol=1e-11)
 
 
+def test_split_sweep_with_three_coupling_rows_equals_paper_linear_map():
+    """The split sweep with k = 3 coupling rows (the general eq. lcqp
+    constraint block) equals the paper's linear map of the lifted problem
+    (Sec. 2), as the one-row case above."""
+    inst = synth.small_instance(8, 25, 13, 4, phi="l1l2", beta=0.8, gamma=0.8, lam2=0.3)
+    inst.lam1 = 0.0
+    rng = np.random.default_rng(5)
+    inst.E = rng.normal(size=(3, 13))
+    inst.d = rng.normal(size=3)
+    P = O.problem_from_instance(inst)
+    beta = 0.8
+    st = O.State(x=rng.normal(size=13), z=rng.normal(size=13), xi=rng.normal(size=13),
+                 mu=rng.normal(size=3))
+    blocks = O.random_assembly(13, 4, seed=3, sweep=2)
+    Hw, cw, Aw, bw = _lifted(P, beta)
+    sigma = [np.asarray(S) for S in blocks] + [np.arange(13, 26)]
+    M, off = O.linear_map(Hw, cw, Aw, bw, beta, sigma)
+    zk = np.concatenate([st.x, st.z, st.xi, st.mu])
+    expect = M @ zk + off
+    O.sweep(P, st, 4, 3, beta, beta, blocks=blocks)
+    got = np.concatenate([st.x, st.z, st.xi, st.mu])
+    assert np.allclose(got, expect, rtol=1e-11, atol=1e-11)
+
+
 def test_lcqp_sweep_equals_paper_linear_map():
     rng = np.random.default_rng(4)
     n, mm = 9, 3

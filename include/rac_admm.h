@@ -320,6 +320,19 @@ rac_status rac_assembly(int64_t n, int32_t num_blocks, uint64_t seed, int64_t sw
 rac_status rac_gram(int64_t m, int64_t n, const double *A, int64_t lda, int32_t storage,
                     void *G_out, void *stream);
 
+/* Gaussian-kernel matrix of the non-linear C-SVC dual (Sec. 3.2, eq. svm,
+ * with the Gaussian kernel K(x_i, x_j) = exp(-||x_i - x_j||^2 / (2 sigma^2))
+ * the paper uses for Table 8): Q_out[i, j] = y_i y_j K(x_i, x_j), FP64,
+ * N x N (symmetric, so row- and column-major agree).  X is d x N
+ * column-major (sample i = column i, leading dimension ldx >= d), y holds N
+ * labels; all three are device pointers.  The dual min 1/2 a^T Q a - e^T a,
+ * y^T a = 0, 0 <= a <= C is then the H-form problem (H = Q, c = -e, E = y^T,
+ * box [0, C]) of rac_admm_setup.  Squared distances are summed directly in
+ * FP64.  Returns RAC_ERR_ARG for N < 1, d < 1, ldx < d, sigma <= 0 or a NULL
+ * pointer; the call returns after the work on `stream` has finished. */
+rac_status rac_rbf_gram(int64_t N, int64_t d, const double *X, int64_t ldx, const double *y,
+                        double sigma, double *Q_out, void *stream);
+
 /* Random assembly that allocates nothing.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory,
  * such as programs whose device memory is wholly owned by their own

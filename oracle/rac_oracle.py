@@ -759,3 +759,16 @@ def svm_ipm(Z, y, C, tol=1e-11, max_iter=200, snap=1e-5):
     lo = (a < lam) & (a <= snap * C)
     hi = (C - a < nu) & (C - a <= snap * C)
     return np.where(lo, 0.0, np.where(hi, C, a))
+
+
+
+def rbf_svm_matrix(X, y, sigma):
+    """Q_ij = y_i y_j exp(-||x_i - x_j||^2 / (2 sigma^2)), the Gaussian-kernel
+    C-SVC dual matrix (Sec. 3.2, eq. svm; the kernel of Table 8), in FP64
+    from the plain definition: squared distances from coordinate
+    differences."""
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    diff = X[:, None, :] - X[None, :, :]
+    D = (diff * diff).sum(axis=2)
+    return (y[:, None] * y[None, :]) * np.exp(-D / (2.0 * sigma * sigma))

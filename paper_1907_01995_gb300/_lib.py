@@ -73,6 +73,8 @@ SIGNATURES = [
     ("rac_assembly", c_int32, [c_int64, c_int32, c_uint64, c_int64, c_int32, c_void_p, c_void_p,
                                c_void_p]),
     ("rac_gram", c_int32, [c_int64, c_int64, c_void_p, c_int64, c_int32, c_void_p, c_void_p]),
+    ("rac_rbf_gram", c_int32, [c_int64, c_int64, c_void_p, c_int64, c_void_p, c_double,
+                               c_void_p, c_void_p]),
     ("rac_assembly_noalloc", c_int32, [c_int64, c_int32, c_uint64, c_int64, c_int32, c_void_p,
                                        c_void_p, c_void_p]),
     ("rac_ws_num_params", c_int64, []),

@@ -290,3 +290,18 @@ def assembly(n: int, num_blocks: int, seed: int, sweep0: int, nsweeps: int, stre
 def trim_pool():
     """Return the cached, unused device memory of closed handles to the driver."""
     L.check(L.load().rac_trim_pool(), "rac_trim_pool")
+
+
+def rbf_svm_matrix(X, y, sigma: float, stream=None):
+    """Q = diag(y) K diag(y) with the Gaussian kernel K_ij = exp(-||x_i -
+    x_j||^2 / (2 sigma^2)) on the GPU (rac_rbf_gram).  X: N x d samples (host
+    or device), y: N labels.  Returns Q as an N x N float64 CUDA tensor, the
+    H of the C-SVC dual (with c = -1, E = y, box [0, C])."""
+    Xt = torch.as_tensor(X, dtype=torch.float64, device="cuda").contiguous()  # N x d row-major
+    yt = torch.as_tensor(y, dtype=torch.float64, device="cuda").contiguous()
+    N, d = int(Xt.shape[0]), int(Xt.shape[1])
+    Q = torch.empty((N, N), dtype=torch.float64, device="cuda")
+    # row-major N x d is column-major d x N with leading dimension d
+    L.check(L.load().rac_rbf_gram(N, d, Xt.data_ptr(), d, yt.data_ptr(), float(sigma),
+                                  Q.data_ptr(), _stream_handle(stream)), "rac_rbf_gram")
+    return Q

@@ -1407,6 +1407,18 @@ extern "C" void rac_admm_destroy(rac_handle *h) {
 }
 
 // ---------------------------------------------------------------- components
+extern "C" rac_status rac_rbf_gram(int64_t N, int64_t d, const double *X, int64_t ldx,
+                                   const double *y, double sigma, double *Q_out, void *stream) {
+    if (N < 1 || N > (int64_t)1 << 20 || d < 1 || d > (int64_t)1 << 30 || ldx < d ||
+        !(sigma > 0) || !X || !y || !Q_out)
+        return RAC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    RAC_CK(launch_rbf_gram((int)N, (int)d, X, ldx, y, sigma, Q_out, st));
+    RAC_CK(cudaStreamSynchronize(st));
+    return RAC_OK;
+}
+
 extern "C" rac_status rac_assembly(int64_t n, int32_t p, uint64_t seed, int64_t sweep0,
                                    int32_t nsweeps, int32_t *perm_out, int32_t *blk_out,
                                    void *stream) {

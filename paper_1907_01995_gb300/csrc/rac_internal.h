@@ -186,6 +186,10 @@ cudaError_t launch_couple_refresh(int n, int k, const double *E, const double *d
                                   double *feas, cudaStream_t st);
 int couple_max_rows();
 
+// Gaussian-kernel SVM matrix Q = diag(y) K diag(y) in FP64 (rac_rbf.cu)
+cudaError_t launch_rbf_gram(int N, int d, const double *X, int64_t ldx, const double *y,
+                            double sigma, double *Q, cudaStream_t st);
+
 // the blocked sweep-operator inverse alone, in place of raw block Grams in Wout
 // (store: ST_F64 for an FP64 compute type, else FP32)
 cudaError_t launch_big_inverse(int store, const ChainArgs &a, void *Wout, void *Pan,

@@ -49,3 +49,23 @@ def check(inst, a, a_ref, C=1.0):
     fl = 1e-12 * max(1.0, abs(obj_r))
     return gap, b1 + b2 + fl, wdist, np.sqrt(2 * b1) + np.sqrt(2 * b2) + 1e-12 * max(
         1.0, float(np.linalg.norm(w_r)))
+
+
+def check_q(Q, y, a, a_ref, C=1.0):
+    """check() for a dual given by its matrix Q (a kernel SVM): the same
+    bounds, with ||w - w*||^2 = (a - a*)^T Q (a - a*) in feature space.
+    Returns (gap, gap_bound, wdist, w_bound)."""
+    def pt(v):
+        P = O.Problem(H=Q, q=-np.ones(len(v)), phi="box", lo=0.0, hi=C,
+                      E=np.asarray(y, dtype=np.float64).reshape(1, -1), d=np.zeros(1))
+        mu = O.kkt(P, v)["mu"]
+        r = O._stationarity_vec(P, v, P.grad(v), mu)
+        return 0.5 * float(v @ Q @ v) - float(v.sum()), C * float(r.sum()), abs(float(y @ v)), mu
+    obj, rs, eps, mu = pt(a)
+    obj_r, rs_r, eps_r, mu_r = pt(a_ref)
+    ms = 2.0 * max(abs(mu), abs(mu_r))
+    b1, b2 = rs + ms * eps, rs_r + ms * eps_r
+    dlt = a - a_ref
+    wdist = float(np.sqrt(max(0.0, float(dlt @ Q @ dlt))))
+    fl = 1e-12 * max(1.0, abs(obj_r))
+    return abs(obj - obj_r), b1 + b2 + fl, wdist, np.sqrt(2 * b1) + np.sqrt(2 * b2) + 1e-9

@@ -551,3 +551,20 @@ def test_interior_point_svm_matches_enumeration_and_smo(seed):
     gap, gap_bound, wdist, w_bound = svm_gap.check(med, a_ipm, a_smo)
     assert gap <= gap_bound and wdist <= w_bound
     assert gap_bound < 1e-5
+
+
+def test_rbf_matrix_definition():
+    """The Gaussian-kernel dual matrix against a plain double loop; unit
+    diagonal, symmetric, positive semidefinite, and y y^T as sigma grows."""
+    import math
+    rng = np.random.default_rng(11)
+    X = rng.normal(size=(9, 3))
+    y = rng.choice([-1.0, 1.0], size=9)
+    Q = O.rbf_svm_matrix(X, y, 0.7)
+    for i in range(9):
+        for j in range(9):
+            d2 = sum((X[i, k] - X[j, k]) ** 2 for k in range(3))
+            assert abs(Q[i, j] - y[i] * y[j] * math.exp(-d2 / (2 * 0.49))) < 1e-15
+    assert np.allclose(np.diag(Q), 1.0) and np.array_equal(Q, Q.T)
+    assert np.linalg.eigvalsh(Q).min() > -1e-12
+    assert np.abs(O.rbf_svm_matrix(X, y, 1e6) - np.outer(y, y)).max() < 1e-10

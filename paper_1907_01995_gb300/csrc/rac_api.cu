@@ -140,6 +140,8 @@ struct rac_handle {
     int *sp_rowidx = nullptr;
     double *sp_vals64 = nullptr;
     void *sp_vals = nullptr;
+    void *sp_stage = nullptr;       // per slot: the blocks' staged columns (or NULL)
+    size_t sp_sb = 0, sp_slot = 0;  // bytes per block region, per slot
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -307,6 +309,8 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.sp_colptr = h->sp_colptr;
     a.sp_rowidx = h->sp_rowidx;
     a.sp_vals = h->sp_vals;
+    a.sp_stage = h->sp_stage ? (char *)h->sp_stage + (size_t)slot * h->sp_slot : nullptr;
+    a.sp_stage_bytes = h->sp_sb;
     return a;
 }
 
@@ -408,7 +412,7 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         if (h->sparse) {
-            RAC_CK(launch_sp_chain(h->store, a, st));
+            RAC_CK(launch_sp_chain(h->store, a, h->sp_emax, st));
         } else if (h->big) {
             RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
         } else if (h->cluster) {
@@ -870,7 +874,15 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_ST(h->alloc_bytes((void **)&h->Pbuf, (size_t)h->refresh_every * h->pstride));
     }
     if (h->sparse) {
-        // one-CTA chain; the blocked inverse needs its pivot panels per slot
+        // one-CTA chain; the blocked inverse needs its pivot panels per slot.
+        // The chain stages each block's columns in shared memory (a block
+        // ahead) where two regions fit and the factor writes them per sweep
+        // (not for RP, whose factors are computed once)
+        if (!h->rp && sp_can_stage(h->store, lay.smax(), h->sp_emax)) {
+            h->sp_sb = sp_stage_bytes(h->store, lay.smax(), h->sp_emax);
+            h->sp_slot = (size_t)h->p * h->sp_sb;
+            RAC_ST(h->alloc_bytes(&h->sp_stage, (size_t)h->refresh_every * h->sp_slot));
+        }
         h->stage = 0;
         gmax = 1;
         h->pstride = (big_panel_bytes(h->store, h->p, lay.smax()) + 255) & ~(size_t)255;

@@ -98,6 +98,8 @@ struct ChainArgs {
     const int64_t *sp_colptr;
     const int *sp_rowidx;
     const void *sp_vals;    // storage-type values
+    void *sp_stage;         // this sweep slot's staging regions (one per block position), or NULL
+    size_t sp_stage_bytes;  // bytes of one block's region
     int dbg_exit_cta;       // k_chain_res: this CTA returns at its start (-1: none), so the
                             // others' bounded barrier waits run out (failure-path testing)
     int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
@@ -203,7 +205,9 @@ cudaError_t launch_sp_convert(int store, int64_t nnz, const double *v64, void *v
 cudaError_t launch_sp_factor(int store, const ChainArgs &a, void *Wout, void *Pan, int64_t emax,
                              cudaStream_t st);
 int64_t sp_max_entries(int store, int smax);
-cudaError_t launch_sp_chain(int store, const ChainArgs &a, cudaStream_t st);
+cudaError_t launch_sp_chain(int store, const ChainArgs &a, int64_t emax, cudaStream_t st);
+size_t sp_stage_bytes(int store, int smax, int64_t emax);
+bool sp_can_stage(int store, int smax, int64_t emax);
 cudaError_t launch_sp_resid_f64(int m, int n, const int64_t *colptr, const int *rowidx,
                                 const double *vals, const double *z, const double *b, double *r,
                                 cudaStream_t st);

@@ -17,6 +17,9 @@
 //                 d += A~_S dx by FP64 atomic adds (rows shared by two
 //                 columns of a block are added in no fixed order, so sparse
 //                 runs are reproducible to rounding, not bit for bit)
+//   k_sp_chain_staged  the same chain with each block's columns, starts, rows
+//                 and values (written by k_sp_gram per sweep) brought into
+//                 shared memory by one bulk copy a block ahead
 //   k_sp_*_f64    the exact FP64 refresh: r = A z - b (sparse z, atomic
 //                 scatter), g = A^T r + c (a warp per column), and the
 //                 anchor d = A~ (x - z)
@@ -89,6 +92,21 @@ template <class TA> size_t sp_gram_smem(int smax, int64_t emax) {
            (size_t)emax * sizeof(TA) + 16;
 }
 
+// One block's region of the per-slot staging buffer that k_sp_gram writes and
+// k_sp_chain_staged copies into shared memory with one bulk copy: the block's
+// columns (s ints), their entry starts (s + 1), rows and storage values.
+struct SpStage {
+    size_t cols, starts, rows, vals, bytes;
+    __host__ __device__ SpStage(int smax, int64_t emax, size_t ts) {
+        auto pad = [](size_t v) { return (v + 15) & ~(size_t)15; };
+        cols = 0;
+        starts = pad((size_t)smax * 4);
+        rows = starts + pad((size_t)(smax + 1) * 4);
+        vals = rows + pad((size_t)emax * 4);
+        bytes = vals + pad((size_t)emax * ts);
+    }
+};
+
 template <class TS, class TA>
 __global__ void __launch_bounds__(256) k_sp_gram(ChainArgs a, TA *Wout, int64_t emax) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -115,15 +133,27 @@ __global__ void __launch_bounds__(256) k_sp_gram(ChainArgs a, TA *Wout, int64_t 
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // the block's region of the chain's staging buffer (when it stages)
+    unsigned char *stg = a.sp_stage ? (unsigned char *)a.sp_stage + (size_t)b * a.sp_stage_bytes
+                                    : nullptr;
+    const SpStage L(smax, emax, sizeof(TS));
     for (int c = warp; c < s; c += nw) {
         const int j = a.perm[off + c];
         const int64_t k0 = a.sp_colptr[j], len = a.sp_colptr[j + 1] - k0;
         for (int t = lane; t < len; t += 32) {
-            rows[start[c] + t] = a.sp_rowidx[k0 + t];
+            const int row = a.sp_rowidx[k0 + t];
+            rows[start[c] + t] = row;
             if constexpr (sizeof(TS) == 8) vals[start[c] + t] = (TA)vs[k0 + t];
             else vals[start[c] + t] = (TA)sp_val<TS>(vs, k0 + t);
+            if (stg) {
+                ((int *)(stg + L.rows))[start[c] + t] = row;
+                ((TS *)(stg + L.vals))[start[c] + t] = vs[k0 + t];
+            }
         }
+        if (stg && lane == 0) ((int *)(stg + L.cols))[c] = j;
     }
+    if (stg)
+        for (int c = threadIdx.x; c <= s; c += blockDim.x) ((int *)(stg + L.starts))[c] = start[c];
     __syncthreads();
     // pairs (u, v), u >= v, by a running index over the lower triangle
     TA *K = Wout + lay.factor_offset(b);
@@ -251,6 +281,145 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain(ChainArgs a) {
     if (threadIdx.x == 0 && a.e) *a.t = t;
 }
 
+// The same chain with each block's columns, entry starts, rows and values
+// brought into shared memory by one bulk copy on an mbarrier, a block ahead
+// (two buffers): a step then waits only on its gathers from d and its
+// scatter.  The waits are bounded; after one expires the kernel records
+// RAC_ERR_TIMEOUT, stops touching memory by the staged indices, waits
+// (bounded) for the copy in flight and returns.
+template <class TS, class TA>
+__global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, int64_t emax) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    BlockLayout lay(a.n, a.p);
+    const int smax = lay.smax();
+    const SpStage L(smax, emax, sizeof(TS));
+    const size_t sb = a.sp_stage_bytes;
+    unsigned char *buf = sm;                                     // [2][sb]
+    uint64_t *bars = (uint64_t *)(sm + 2 * sb);                 // 2
+    TA *rhs = (TA *)(((uintptr_t)(bars + 2) + 15) & ~(uintptr_t)15);
+    TA *dl = rhs + smax;
+    double *dred = (double *)(((uintptr_t)(dl + smax) + 15) & ~(uintptr_t)15);   // 32
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const TA *Wall = (const TA *)a.W;
+    const unsigned char *stage = (const unsigned char *)a.sp_stage;
+    const double gamma = a.gamma, beta = a.beta;
+    const double mu = a.mu ? *a.mu : 0.0;
+    double t = a.e ? *a.t : 0.0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+        s_ok = 1;
+        mbar_expect_tx(&bars[0], (uint32_t)sb);
+        bulk_g2s_chunks(buf, stage, sb, &bars[0]);
+    }
+    __syncthreads();
+    int pending = 0;   // buffer whose copy is in flight (thread 0)
+    for (int i = 0; i < a.p; ++i) {
+        const int s = lay.size(i);
+        unsigned char *cur = buf + (size_t)(i & 1) * sb;
+        if (threadIdx.x == 0) {
+            if (s_ok && !mbar_wait(&bars[i & 1], (uint32_t)((i >> 1) & 1), a.err,
+                                   kBarrierTimeoutNs))
+                s_ok = 0;
+            if (s_ok && i + 1 < a.p) {
+                // the other buffer was last read in step i - 1 (the barrier
+                // that ended it orders those reads before this copy)
+                fence_proxy_async_smem();
+                mbar_expect_tx(&bars[(i + 1) & 1], (uint32_t)sb);
+                bulk_g2s_chunks(buf + (size_t)((i + 1) & 1) * sb, stage + (size_t)(i + 1) * sb,
+                                sb, &bars[(i + 1) & 1]);
+                pending = (i + 1) & 1;
+            } else {
+                pending = -1;
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;   // uniform: read after the barrier
+        const int *cols = (const int *)(cur + L.cols);
+        const int *starts = (const int *)(cur + L.starts);
+        const int *rows = (const int *)(cur + L.rows);
+        const TS *vals = (const TS *)(cur + L.vals);
+        // (staged indices are clamped to their ranges: the factor writes every
+        // region before this launch, but nothing here may address outside d)
+        for (int c = warp; c < s; c += nw) {
+            const int j = min(max(cols[c], 0), a.n - 1);
+            const int e0 = max(starts[c], 0), e1 = min(starts[c + 1], (int)emax);
+            TA acc = 0;
+            for (int e = e0 + lane; e < e1; e += 32) {
+                TA v;
+                if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
+                else v = (TA)to_f(vals[e]);
+                acc += v * (TA)__ldcg(a.dres + min(max(rows[e], 0), a.m - 1));
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                double r = a.ga[j] + (double)acc - a.xi[j] + gamma * (a.x[j] - a.z[j]);
+                if (a.e) r += a.e[j] * (beta * t - mu);
+                rhs[c] = (TA)r;
+            }
+        }
+        __syncthreads();
+        block_solve_kinv<TA>(Wall + lay.factor_offset(i), s, rhs, dl);   // dl = -K^{-1} rhs
+        if (a.e) {
+            double loc = 0.0;
+            for (int q = threadIdx.x; q < s; q += blockDim.x)
+                loc += a.e[min(max(cols[q], 0), a.n - 1)] * (double)dl[q];
+            t += block_sum<double>(loc, dred);
+        }
+        for (int q = threadIdx.x; q < s; q += blockDim.x)
+            a.dx[min(max(cols[q], 0), a.n - 1)] = (double)dl[q];
+        for (int c = warp; c < s; c += nw) {
+            const TA d = dl[c];
+            const int e0 = max(starts[c], 0), e1 = min(starts[c + 1], (int)emax);
+            for (int e = e0 + lane; e < e1; e += 32) {
+                TA v;
+                if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
+                else v = (TA)to_f(vals[e]);
+                atomicAdd(a.dres + min(max(rows[e], 0), a.m - 1), (double)(v * d));
+            }
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+    // a copy may still be in flight after an expired wait: wait for it (bounded)
+    if (threadIdx.x == 0 && !s_ok && pending >= 0)
+        mbar_wait(&bars[pending], 0u, a.err, kBarrierTimeoutNs);
+    if (threadIdx.x == 0 && a.e) *a.t = t;
+}
+
+template <class TS, class TA>
+static size_t sp_staged_smem(int smax, size_t sb) {
+    return 2 * sb + 16 + 16 + 2 * (size_t)smax * sizeof(TA) + 16 + 32 * sizeof(double) + 16;
+}
+
+// bytes of one block's staging region, and whether the staged chain fits
+size_t sp_stage_bytes(int store, int smax, int64_t emax) {
+    return SpStage(smax, emax, store == ST_F64 ? 8 : (store == ST_F32 ? 4 : 2)).bytes;
+}
+bool sp_can_stage(int store, int smax, int64_t emax) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t sb = sp_stage_bytes(store, smax, emax);
+    const size_t need = store == ST_F64 ? sp_staged_smem<double, double>(smax, sb)
+                                        : sp_staged_smem<float, float>(smax, sb);
+    return need <= (size_t)optin;
+}
+
+template <class TS, class TA>
+static cudaError_t sp_chain_staged_impl(const ChainArgs &a, int64_t emax, cudaStream_t st) {
+    const int smax = BlockLayout(a.n, a.p).smax();
+    const size_t smem = sp_staged_smem<TS, TA>(smax, a.sp_stage_bytes);
+    auto kern = k_sp_chain_staged<TS, TA>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<1, kSpThreads, smem, st>>>(a, emax);
+    return cudaGetLastError();
+}
+
 template <class TS, class TA>
 static cudaError_t sp_chain_impl(const ChainArgs &a, cudaStream_t st) {
     const int smax = BlockLayout(a.n, a.p).smax();
@@ -264,7 +433,12 @@ static cudaError_t sp_chain_impl(const ChainArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_sp_chain(int store, const ChainArgs &a, cudaStream_t st) {
+cudaError_t launch_sp_chain(int store, const ChainArgs &a, int64_t emax, cudaStream_t st) {
+    if (a.sp_stage) {
+        if (store == ST_F64) return sp_chain_staged_impl<double, double>(a, emax, st);
+        if (store == ST_F32) return sp_chain_staged_impl<float, float>(a, emax, st);
+        return sp_chain_staged_impl<__nv_bfloat16, float>(a, emax, st);
+    }
     if (store == ST_F64) return sp_chain_impl<double, double>(a, st);
     if (store == ST_F32) return sp_chain_impl<float, float>(a, st);
     return sp_chain_impl<__nv_bfloat16, float>(a, st);

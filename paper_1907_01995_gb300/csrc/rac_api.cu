@@ -142,6 +142,7 @@ struct rac_handle {
     void *sp_vals = nullptr;
     void *sp_stage = nullptr;       // per slot: the blocks' staged columns (or NULL)
     size_t sp_sb = 0, sp_slot = 0;  // bytes per block region, per slot
+    int sp_nbuf = 0;                // shared-memory buffers of the staged chain
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -412,7 +413,7 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         if (h->sparse) {
-            RAC_CK(launch_sp_chain(h->store, a, h->sp_emax, st));
+            RAC_CK(launch_sp_chain(h->store, a, h->sp_emax, h->sp_nbuf, st));
         } else if (h->big) {
             RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
         } else if (h->cluster) {
@@ -878,7 +879,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         // The chain stages each block's columns in shared memory (a block
         // ahead) where two regions fit and the factor writes them per sweep
         // (not for RP, whose factors are computed once)
-        if (!h->rp && sp_can_stage(h->store, lay.smax(), h->sp_emax)) {
+        h->sp_nbuf = h->rp ? 0 : sp_stage_buffers(h->store, lay.smax(), h->sp_emax);
+        if (h->sp_nbuf > 0) {
             h->sp_sb = sp_stage_bytes(h->store, lay.smax(), h->sp_emax);
             h->sp_slot = (size_t)h->p * h->sp_sb;
             RAC_ST(h->alloc_bytes(&h->sp_stage, (size_t)h->refresh_every * h->sp_slot));

@@ -205,9 +205,10 @@ cudaError_t launch_sp_convert(int store, int64_t nnz, const double *v64, void *v
 cudaError_t launch_sp_factor(int store, const ChainArgs &a, void *Wout, void *Pan, int64_t emax,
                              cudaStream_t st);
 int64_t sp_max_entries(int store, int smax);
-cudaError_t launch_sp_chain(int store, const ChainArgs &a, int64_t emax, cudaStream_t st);
+cudaError_t launch_sp_chain(int store, const ChainArgs &a, int64_t emax, int nbuf,
+                            cudaStream_t st);
 size_t sp_stage_bytes(int store, int smax, int64_t emax);
-bool sp_can_stage(int store, int smax, int64_t emax);
+int sp_stage_buffers(int store, int smax, int64_t emax);
 cudaError_t launch_sp_resid_f64(int m, int n, const int64_t *colptr, const int *rowidx,
                                 const double *vals, const double *z, const double *b, double *r,
                                 cudaStream_t st);

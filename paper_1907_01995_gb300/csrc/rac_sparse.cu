@@ -96,14 +96,15 @@ template <class TA> size_t sp_gram_smem(int smax, int64_t emax) {
 // k_sp_chain_staged copies into shared memory with one bulk copy: the block's
 // columns (s ints), their entry starts (s + 1), rows and storage values.
 struct SpStage {
-    size_t cols, starts, rows, vals, bytes;
+    size_t cols, starts, rows, vals, ecol, bytes;
     __host__ __device__ SpStage(int smax, int64_t emax, size_t ts) {
         auto pad = [](size_t v) { return (v + 15) & ~(size_t)15; };
         cols = 0;
         starts = pad((size_t)smax * 4);
         rows = starts + pad((size_t)(smax + 1) * 4);
         vals = rows + pad((size_t)emax * 4);
-        bytes = vals + pad((size_t)emax * ts);
+        ecol = vals + pad((size_t)emax * ts);          // column (in the block) of each entry
+        bytes = ecol + pad((size_t)emax * 2);
     }
 };
 
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(256) k_sp_gram(ChainArgs a, TA *Wout, int64_t 
             if (stg) {
                 ((int *)(stg + L.rows))[start[c] + t] = row;
                 ((TS *)(stg + L.vals))[start[c] + t] = vs[k0 + t];
+                ((unsigned short *)(stg + L.ecol))[start[c] + t] = (unsigned short)c;
             }
         }
         if (stg && lane == 0) ((int *)(stg + L.cols))[c] = j;
@@ -288,15 +290,17 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain(ChainArgs a) {
 // RAC_ERR_TIMEOUT, stops touching memory by the staged indices, waits
 // (bounded) for the copy in flight and returns.
 template <class TS, class TA>
-__global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, int64_t emax) {
+__global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, int64_t emax,
+                                                                   int nbuf) {
     extern __shared__ __align__(128) unsigned char sm[];
     BlockLayout lay(a.n, a.p);
     const int smax = lay.smax();
     const SpStage L(smax, emax, sizeof(TS));
     const size_t sb = a.sp_stage_bytes;
-    unsigned char *buf = sm;                                     // [2][sb]
-    uint64_t *bars = (uint64_t *)(sm + 2 * sb);                 // 2
-    TA *rhs = (TA *)(((uintptr_t)(bars + 2) + 15) & ~(uintptr_t)15);
+    unsigned char *buf = sm;                                     // [nbuf][sb]
+    uint64_t *bars = (uint64_t *)(sm + (size_t)nbuf * sb);      // 2
+    TA *prod = (TA *)(((uintptr_t)(bars + 2) + 15) & ~(uintptr_t)15);   // [emax]
+    TA *rhs = prod + ((emax + 3) & ~(int64_t)3);
     TA *dl = rhs + smax;
     double *dred = (double *)(((uintptr_t)(dl + smax) + 15) & ~(uintptr_t)15);   // 32
     __shared__ int s_ok;
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, 
     const double gamma = a.gamma, beta = a.beta;
     const double mu = a.mu ? *a.mu : 0.0;
     double t = a.e ? *a.t : 0.0;
+    const int m1 = a.m - 1, n1 = a.n - 1;
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -315,15 +320,17 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, 
         bulk_g2s_chunks(buf, stage, sb, &bars[0]);
     }
     __syncthreads();
-    int pending = 0;   // buffer whose copy is in flight (thread 0)
+    int pending = 0;   // barrier whose copy is in flight (thread 0), -1: none
     for (int i = 0; i < a.p; ++i) {
         const int s = lay.size(i);
-        unsigned char *cur = buf + (size_t)(i & 1) * sb;
+        const int bi = nbuf == 2 ? (i & 1) : 0;
+        unsigned char *cur = buf + (size_t)bi * sb;
         if (threadIdx.x == 0) {
-            if (s_ok && !mbar_wait(&bars[i & 1], (uint32_t)((i >> 1) & 1), a.err,
-                                   kBarrierTimeoutNs))
-                s_ok = 0;
-            if (s_ok && i + 1 < a.p) {
+            const uint32_t par = nbuf == 2 ? (uint32_t)((i >> 1) & 1) : (uint32_t)(i & 1);
+            const int wb = nbuf == 2 ? (i & 1) : 0;
+            if (s_ok && !mbar_wait(&bars[wb], par, a.err, kBarrierTimeoutNs)) s_ok = 0;
+            pending = -1;
+            if (s_ok && nbuf == 2 && i + 1 < a.p) {
                 // the other buffer was last read in step i - 1 (the barrier
                 // that ended it orders those reads before this copy)
                 fence_proxy_async_smem();
@@ -331,57 +338,82 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, 
                 bulk_g2s_chunks(buf + (size_t)((i + 1) & 1) * sb, stage + (size_t)(i + 1) * sb,
                                 sb, &bars[(i + 1) & 1]);
                 pending = (i + 1) & 1;
-            } else {
-                pending = -1;
             }
         }
         __syncthreads();
         if (!s_ok) break;   // uniform: read after the barrier
+        // (staged indices are clamped to their ranges: the factor writes every
+        // region before this launch, but nothing here may address outside d)
         const int *cols = (const int *)(cur + L.cols);
         const int *starts = (const int *)(cur + L.starts);
         const int *rows = (const int *)(cur + L.rows);
         const TS *vals = (const TS *)(cur + L.vals);
-        // (staged indices are clamped to their ranges: the factor writes every
-        // region before this launch, but nothing here may address outside d)
+        const unsigned short *ecol = (const unsigned short *)(cur + L.ecol);
+        const int E = min(max(starts[s], 0), (int)emax);
+        // gather: one product per entry (all loads independent), then a warp per column
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            TA v;
+            if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
+            else v = (TA)to_f(vals[e]);
+            prod[e] = v * (TA)__ldcg(a.dres + min(max(rows[e], 0), m1));
+        }
+        __syncthreads();
         for (int c = warp; c < s; c += nw) {
-            const int j = min(max(cols[c], 0), a.n - 1);
-            const int e0 = max(starts[c], 0), e1 = min(starts[c + 1], (int)emax);
+            const int e0 = max(starts[c], 0), e1 = min(starts[c + 1], E);
             TA acc = 0;
-            for (int e = e0 + lane; e < e1; e += 32) {
-                TA v;
-                if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
-                else v = (TA)to_f(vals[e]);
-                acc += v * (TA)__ldcg(a.dres + min(max(rows[e], 0), a.m - 1));
-            }
+            for (int e = e0 + lane; e < e1; e += 32) acc += prod[e];
             acc = warp_sum(acc);
             if (lane == 0) {
+                const int j = min(max(cols[c], 0), n1);
                 double r = a.ga[j] + (double)acc - a.xi[j] + gamma * (a.x[j] - a.z[j]);
                 if (a.e) r += a.e[j] * (beta * t - mu);
                 rhs[c] = (TA)r;
             }
         }
         __syncthreads();
-        block_solve_kinv<TA>(Wall + lay.factor_offset(i), s, rhs, dl);   // dl = -K^{-1} rhs
+        // dl = -K^{-1} rhs: 8 threads per row, each a contiguous part of the row
+        {
+            const TA *Ki = Wall + lay.factor_offset(i);
+            const int part = (s + 7) / 8;
+            for (int base = 0; base < s; base += kSpThreads / 8) {
+                const int r = base + (int)(threadIdx.x >> 3), g = threadIdx.x & 7;
+                TA acc = 0;
+                if (r < s) {
+                    const int c0 = g * part, c1 = min(s, c0 + part);
+                    const TA *kr = Ki + (size_t)r * s;
+                    for (int c = c0; c < c1; ++c) acc += kr[c] * rhs[c];
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+                if (r < s && g == 0) dl[r] = -acc;
+            }
+        }
+        __syncthreads();
         if (a.e) {
             double loc = 0.0;
             for (int q = threadIdx.x; q < s; q += blockDim.x)
-                loc += a.e[min(max(cols[q], 0), a.n - 1)] * (double)dl[q];
+                loc += a.e[min(max(cols[q], 0), n1)] * (double)dl[q];
             t += block_sum<double>(loc, dred);
         }
         for (int q = threadIdx.x; q < s; q += blockDim.x)
-            a.dx[min(max(cols[q], 0), a.n - 1)] = (double)dl[q];
-        for (int c = warp; c < s; c += nw) {
-            const TA d = dl[c];
-            const int e0 = max(starts[c], 0), e1 = min(starts[c + 1], (int)emax);
-            for (int e = e0 + lane; e < e1; e += 32) {
-                TA v;
-                if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
-                else v = (TA)to_f(vals[e]);
-                atomicAdd(a.dres + min(max(rows[e], 0), a.m - 1), (double)(v * d));
-            }
+            a.dx[min(max(cols[q], 0), n1)] = (double)dl[q];
+        // scatter d += A~_S dl, one entry per thread
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            TA v;
+            if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
+            else v = (TA)to_f(vals[e]);
+            atomicAdd(a.dres + min(max(rows[e], 0), m1), (double)(v * dl[min((int)ecol[e], s - 1)]));
         }
         __threadfence_block();
         __syncthreads();
+        if (nbuf == 1 && i + 1 < a.p && threadIdx.x == 0 && s_ok) {
+            // one buffer: the next block's copy starts after this step's reads
+            fence_proxy_async_smem();
+            mbar_expect_tx(&bars[0], (uint32_t)sb);
+            bulk_g2s_chunks(buf, stage + (size_t)(i + 1) * sb, sb, &bars[0]);
+            pending = 0;
+        }
     }
     // a copy may still be in flight after an expired wait: wait for it (bounded)
     if (threadIdx.x == 0 && !s_ok && pending >= 0)
@@ -389,34 +421,42 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, 
     if (threadIdx.x == 0 && a.e) *a.t = t;
 }
 
-template <class TS, class TA>
-static size_t sp_staged_smem(int smax, size_t sb) {
-    return 2 * sb + 16 + 16 + 2 * (size_t)smax * sizeof(TA) + 16 + 32 * sizeof(double) + 16;
+template <class TA>
+static size_t sp_staged_smem(int smax, int64_t emax, size_t sb, int nbuf) {
+    return (size_t)nbuf * sb + 16 + 16 + ((size_t)((emax + 3) & ~(int64_t)3) + 2 * smax) * sizeof(TA) +
+           16 + 32 * sizeof(double) + 16;
 }
 
 // bytes of one block's staging region, and whether the staged chain fits
 size_t sp_stage_bytes(int store, int smax, int64_t emax) {
     return SpStage(smax, emax, store == ST_F64 ? 8 : (store == ST_F32 ? 4 : 2)).bytes;
 }
-bool sp_can_stage(int store, int smax, int64_t emax) {
+// buffers of the staged chain that fit (2: the next block's copy overlaps the
+// step; 1: it follows it), 0: none (the chain reads the columns in place)
+int sp_stage_buffers(int store, int smax, int64_t emax) {
+    if (smax > 65535) return 0;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t sb = sp_stage_bytes(store, smax, emax);
-    const size_t need = store == ST_F64 ? sp_staged_smem<double, double>(smax, sb)
-                                        : sp_staged_smem<float, float>(smax, sb);
-    return need <= (size_t)optin;
+    for (int nbuf = 2; nbuf >= 1; --nbuf) {
+        const size_t need = store == ST_F64 ? sp_staged_smem<double>(smax, emax, sb, nbuf)
+                                            : sp_staged_smem<float>(smax, emax, sb, nbuf);
+        if (need <= (size_t)optin) return nbuf;
+    }
+    return 0;
 }
 
 template <class TS, class TA>
-static cudaError_t sp_chain_staged_impl(const ChainArgs &a, int64_t emax, cudaStream_t st) {
+static cudaError_t sp_chain_staged_impl(const ChainArgs &a, int64_t emax, int nbuf,
+                                        cudaStream_t st) {
     const int smax = BlockLayout(a.n, a.p).smax();
-    const size_t smem = sp_staged_smem<TS, TA>(smax, a.sp_stage_bytes);
+    const size_t smem = sp_staged_smem<TA>(smax, emax, a.sp_stage_bytes, nbuf);
     auto kern = k_sp_chain_staged<TS, TA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<1, kSpThreads, smem, st>>>(a, emax);
+    kern<<<1, kSpThreads, smem, st>>>(a, emax, nbuf);
     return cudaGetLastError();
 }
 
@@ -433,11 +473,12 @@ static cudaError_t sp_chain_impl(const ChainArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_sp_chain(int store, const ChainArgs &a, int64_t emax, cudaStream_t st) {
-    if (a.sp_stage) {
-        if (store == ST_F64) return sp_chain_staged_impl<double, double>(a, emax, st);
-        if (store == ST_F32) return sp_chain_staged_impl<float, float>(a, emax, st);
-        return sp_chain_staged_impl<__nv_bfloat16, float>(a, emax, st);
+cudaError_t launch_sp_chain(int store, const ChainArgs &a, int64_t emax, int nbuf,
+                            cudaStream_t st) {
+    if (a.sp_stage && nbuf > 0) {
+        if (store == ST_F64) return sp_chain_staged_impl<double, double>(a, emax, nbuf, st);
+        if (store == ST_F32) return sp_chain_staged_impl<float, float>(a, emax, nbuf, st);
+        return sp_chain_staged_impl<__nv_bfloat16, float>(a, emax, nbuf, st);
     }
     if (store == ST_F64) return sp_chain_impl<double, double>(a, st);
     if (store == ST_F32) return sp_chain_impl<float, float>(a, st);

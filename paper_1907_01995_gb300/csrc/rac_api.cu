@@ -823,7 +823,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         RAC_ST(h->alloc_bytes(&h->sp_vals, (size_t)std::max<int64_t>(h->nnz, 1) * sb));
         if (h->nnz > 0) RAC_CK(launch_sp_convert(h->store, h->nnz, h->sp_vals64, h->sp_vals, st));
         RAC_ST(h->alloc(&h->ga, n));
-        RAC_ST(h->alloc(&h->dres, m));
+        RAC_ST(h->alloc(&h->dres, m));   // m values of the chain's accumulation type
     } else {
         h->R = slab_rows(h->store);
         h->nslab = (m + h->R - 1) / h->R;

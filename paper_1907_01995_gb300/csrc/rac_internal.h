@@ -216,7 +216,7 @@ cudaError_t launch_sp_gemvt_f64(int n, const int64_t *colptr, const int *rowidx,
                                 const double *vals, const double *r, const double *c, double *g,
                                 cudaStream_t st);
 cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, const int *rowidx,
-                             const void *vals, const double *x, const double *z, double *dres,
+                             const void *vals, const double *x, const double *z, void *dres,
                              cudaStream_t st);
 cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,
                             cudaStream_t st);

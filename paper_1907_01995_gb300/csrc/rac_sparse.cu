@@ -14,15 +14,19 @@
 //                 sweep operator, which adds gamma I + beta e e^T)
 //   k_sp_chain    the cyclic pass over the blocks on one CTA: a warp per
 //                 column for A_S^T d (gathers from d), K_S^{-1} rhs, and
-//                 d += A~_S dx by FP64 atomic adds (rows shared by two
-//                 columns of a block are added in no fixed order, so sparse
-//                 runs are reproducible to rounding, not bit for bit)
+//                 d += A~_S dx by atomic adds (rows shared by two columns
+//                 of a block are added in no fixed order, so sparse runs
+//                 are reproducible to rounding, not bit for bit).  d is held
+//                 in the accumulation type (FP32 for FP32/BF16 storage): it
+//                 is rebuilt by every anchor reset, so its rounding moves
+//                 the iterates between refreshes but not the fixed point,
+//                 and the chain does no FP64 conversion per entry
 //   k_sp_chain_staged  the same chain with each block's columns, starts, rows
 //                 and values (written by k_sp_gram per sweep) brought into
 //                 shared memory by one bulk copy a block ahead
 //   k_sp_*_f64    the exact FP64 refresh: r = A z - b (sparse z, atomic
 //                 scatter), g = A^T r + c (a warp per column), and the
-//                 anchor d = A~ (x - z)
+//                 anchor d = A~ (x - z) (in d's type)
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -236,6 +240,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain(ChainArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const TS *vs = (const TS *)a.sp_vals;
     const TA *Wall = (const TA *)a.W;
+    TA *dr = (TA *)a.dres;   // d = A~ (x - x_anchor), in the accumulation type
     const double gamma = a.gamma, beta = a.beta;
     const double mu = a.mu ? *a.mu : 0.0;
     double t = a.e ? *a.t : 0.0;
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain(ChainArgs a) {
             TA acc = 0;
             for (int64_t k = k0 + lane; k < k1; k += 32) {
                 const TA v = sizeof(TS) == 8 ? (TA)((const double *)vs)[k] : (TA)sp_val<TS>(vs, k);
-                acc += v * (TA)__ldcg(a.dres + a.sp_rowidx[k]);
+                acc += v * __ldcg(dr + a.sp_rowidx[k]);
             }
             acc = warp_sum(acc);
             if (lane == 0) {
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain(ChainArgs a) {
             const int64_t k0 = a.sp_colptr[j], k1 = a.sp_colptr[j + 1];
             for (int64_t k = k0 + lane; k < k1; k += 32) {
                 const TA v = sizeof(TS) == 8 ? (TA)((const double *)vs)[k] : (TA)sp_val<TS>(vs, k);
-                atomicAdd(a.dres + a.sp_rowidx[k], (double)(v * d));
+                atomicAdd(dr + a.sp_rowidx[k], v * d);
             }
         }
         __threadfence_block();
@@ -306,6 +311,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, 
     __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const TA *Wall = (const TA *)a.W;
+    TA *dr = (TA *)a.dres;   // d = A~ (x - x_anchor), in the accumulation type
     const unsigned char *stage = (const unsigned char *)a.sp_stage;
     const double gamma = a.gamma, beta = a.beta;
     const double mu = a.mu ? *a.mu : 0.0;
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, 
             TA v;
             if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
             else v = (TA)to_f(vals[e]);
-            prod[e] = v * (TA)__ldcg(a.dres + min(max(rows[e], 0), m1));
+            prod[e] = v * __ldcg(dr + min(max(rows[e], 0), m1));
         }
         __syncthreads();
         for (int c = warp; c < s; c += nw) {
@@ -403,7 +409,7 @@ __global__ void __launch_bounds__(kSpThreads, 1) k_sp_chain_staged(ChainArgs a, 
             TA v;
             if constexpr (sizeof(TS) == 8) v = (TA)vals[e];
             else v = (TA)to_f(vals[e]);
-            atomicAdd(a.dres + min(max(rows[e], 0), m1), (double)(v * dl[min((int)ecol[e], s - 1)]));
+            atomicAdd(dr + min(max(rows[e], 0), m1), v * dl[min((int)ecol[e], s - 1)]);
         }
         __threadfence_block();
         __syncthreads();
@@ -492,9 +498,9 @@ __global__ void k_sp_fill(int m, const double *b, double sign, double *r) {
 }
 // r += A[:, j] w_j for every j with w_j != 0 (w = z, or x - z for the anchor);
 // values: FP64 (refresh) or the storage copy (anchor)
-template <class TV>
+template <class TV, class TR>
 __global__ void k_sp_scatter(int n, const int64_t *colptr, const int *rowidx, const TV *vals,
-                             const double *w1, const double *w2, double *r) {
+                             const double *w1, const double *w2, TR *r) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += warps) {
@@ -504,7 +510,7 @@ __global__ void k_sp_scatter(int n, const int64_t *colptr, const int *rowidx, co
             double v;
             if constexpr (sizeof(TV) == 8) v = vals[k];
             else v = (double)to_f(vals[k]);
-            atomicAdd(r + rowidx[k], v * wj);
+            atomicAdd(r + rowidx[k], (TR)(v * wj));
         }
     }
 }
@@ -538,7 +544,7 @@ cudaError_t launch_sp_resid_f64(int m, int n, const int64_t *colptr, const int *
                                 const double *vals, const double *z, const double *b, double *r,
                                 cudaStream_t st) {
     k_sp_fill<<<std::max(1, std::min(2048, (m + 255) / 256)), 256, 0, st>>>(m, b, -1.0, r);
-    k_sp_scatter<double><<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, vals, z, nullptr, r);
+    k_sp_scatter<double, double><<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, vals, z, nullptr, r);
     return cudaGetLastError();
 }
 cudaError_t launch_sp_gemvt_f64(int n, const int64_t *colptr, const int *rowidx,
@@ -548,18 +554,21 @@ cudaError_t launch_sp_gemvt_f64(int n, const int64_t *colptr, const int *rowidx,
     return cudaGetLastError();
 }
 cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, const int *rowidx,
-                             const void *vals, const double *x, const double *z, double *dres,
+                             const void *vals, const double *x, const double *z, void *dres,
                              cudaStream_t st) {
-    k_sp_fill<<<std::max(1, std::min(2048, (m + 255) / 256)), 256, 0, st>>>(m, nullptr, 0.0, dres);
+    // d is held in the chain's accumulation type: FP64 for FP64 storage, else FP32
+    const size_t td = store == ST_F64 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaMemsetAsync(dres, 0, (size_t)m * td, st);
+    if (e != cudaSuccess) return e;
     if (store == ST_F64)
-        k_sp_scatter<double><<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, (const double *)vals,
-                                                         x, z, dres);
+        k_sp_scatter<double, double><<<sp_grid(n), 256, 0, st>>>(
+            n, colptr, rowidx, (const double *)vals, x, z, (double *)dres);
     else if (store == ST_F32)
-        k_sp_scatter<float><<<sp_grid(n), 256, 0, st>>>(n, colptr, rowidx, (const float *)vals, x,
-                                                        z, dres);
+        k_sp_scatter<float, float><<<sp_grid(n), 256, 0, st>>>(
+            n, colptr, rowidx, (const float *)vals, x, z, (float *)dres);
     else
-        k_sp_scatter<__nv_bfloat16><<<sp_grid(n), 256, 0, st>>>(
-            n, colptr, rowidx, (const __nv_bfloat16 *)vals, x, z, dres);
+        k_sp_scatter<__nv_bfloat16, float><<<sp_grid(n), 256, 0, st>>>(
+            n, colptr, rowidx, (const __nv_bfloat16 *)vals, x, z, (float *)dres);
     return cudaGetLastError();
 }
 cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,

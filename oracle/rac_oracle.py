@@ -15,7 +15,8 @@ What is here, each piece written from the paper's text:
   [sigma_1, ..., sigma_p]), and the RP-MBADMM variant of Sec. 1 (a fixed
   partition visited in a random order).
 * The block argmin of the augmented Lagrangian (Sec. 1, eq. lagrangian and
-  eq. RAC-ADDM) in the split form the paper uses for the Elastic-Net
+  eq. RAC-ADDM), literally with the box kept in the block (an exact
+  bound-constrained QP per block, for phi = box), and in the split form the paper uses for the Elastic-Net
   (Sec. 3.1: x - z = 0 with penalty gamma and dual xi; x partitioned into RAC
   blocks, z solved as one block in closed form), with an optional single
   coupling row E x = d (penalty beta, dual mu) for the SVM dual (Sec. 3.2,
@@ -299,14 +300,114 @@ def block_argmin(P: Problem, st: State, S: np.ndarray, beta: float, gamma: float
     x[S] = x[S] - cho_solve(cf, grad)
 
 
+# ---------------------------------------------------------------------------
+# The box kept inside the block.  Eq. RAC-ADDM restricts each block argmin to
+# x_i in X_i; for the SVM dual (Sec. 3.2, eq. svm) X = [0, C]^n.  Read
+# literally, a block step is then the bound-constrained quadratic
+#   min { 1/2 d^T K d + r^T d : l <= d <= u },  d = x_S^new - x_S,
+# with K = H_SS + beta E_S^T E_S (+ gamma I, an optional proximal term
+# gamma/2 ||x_S - x_S^k||^2; gamma = 0 is the paper's step), r the gradient
+# of the augmented Lagrangian at x restricted to S, l = lo - x_S <= 0 and
+# u = hi - x_S >= 0.  There is no z-block and no xi in this reading.
+# ---------------------------------------------------------------------------
+def box_qp(K, r, l, u, tol=None, max_iter=None):
+    """Exact minimiser of 1/2 d^T K d + r^T d over l <= d <= u (K symmetric
+    positive definite, l <= 0 <= u) by the primal active-set method for convex
+    QP (Nocedal and Wright, Numerical Optimization, Ch. 16, "active-set
+    methods"), specialised to bounds: start at the feasible d = 0 with the
+    bounds that hold there active; take the minimiser over the current face
+    (a linear solve with the free rows and columns of K) as far as the first
+    bound it would cross, which becomes active; at a face minimiser release
+    the active bound whose multiplier (the gradient there) has the wrong sign
+    by the most, or stop when none has.  Returns (d, state): state 0 free,
+    1 at l, 2 at u; d equals l or u exactly where a bound is active."""
+    K = np.asarray(K, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    l = np.asarray(l, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    s = r.shape[0]
+    if tol is None:
+        tol = 1e-13 * max(1.0, float(np.abs(r).max()) if s else 1.0)
+    if max_iter is None:
+        max_iter = 10 * s + 20
+    d = np.zeros(s)
+    state = np.zeros(s, dtype=np.int64)
+    state[l == 0.0] = 1
+    state[(u == 0.0) & (l < 0.0)] = 2
+    for _ in range(max_iter):
+        F = np.nonzero(state == 0)[0]
+        g = K @ d + r
+        step = np.zeros(s)
+        if len(F):
+            step[F] = np.linalg.solve(K[np.ix_(F, F)], -g[F])
+        alpha, hit = 1.0, -1
+        for j in F:
+            if step[j] < 0.0 and d[j] + step[j] < l[j]:
+                a = (l[j] - d[j]) / step[j]
+            elif step[j] > 0.0 and d[j] + step[j] > u[j]:
+                a = (u[j] - d[j]) / step[j]
+            else:
+                continue
+            if a < alpha:
+                alpha, hit = a, j
+        d = d + alpha * step
+        if hit >= 0:
+            state[hit] = 1 if step[hit] < 0.0 else 2
+            d[hit] = l[hit] if state[hit] == 1 else u[hit]
+            continue
+        g = K @ d + r
+        viol = np.zeros(s)
+        movable = u > l
+        viol[(state == 1) & movable] = -g[(state == 1) & movable]
+        viol[(state == 2) & movable] = g[(state == 2) & movable]
+        j = int(np.argmax(viol)) if s else 0
+        if s == 0 or viol[j] <= tol:
+            d[state == 1] = l[state == 1]
+            d[state == 2] = u[state == 2]
+            return d, state
+        state[j] = 0
+    raise RuntimeError("box_qp: no convergence in %d iterations" % max_iter)
+
+
+def block_argmin_box(P: Problem, st: State, S: np.ndarray, beta: float, gamma: float):
+    """x_S <- argmin { L(x_S; others fixed) + gamma/2 ||x_S - x_S^k||^2 :
+    lo <= x_S <= hi } (eq. RAC-ADDM with the box of eq. svm kept in the
+    block); coordinates ending on a bound take its value exactly."""
+    x = st.x
+    grad = P.H[S, :] @ x + P.q[S]
+    K = P.H[np.ix_(S, S)] + gamma * np.eye(len(S))
+    if P.E is not None:
+        ES = P.E[:, S]
+        grad = grad + ES.T @ (beta * (P.E @ x - P.d) - st.mu)
+        K = K + beta * ES.T @ ES
+    d, state = box_qp(K, grad, P.lo - x[S], P.hi - x[S])
+    xs = x[S] + d
+    xs[state == 1] = P.lo
+    xs[state == 2] = P.hi
+    x[S] = xs
+
+
 def sweep(P: Problem, st: State, p: int, seed: int, beta: float, gamma: float,
-          blocks: Optional[List[np.ndarray]] = None, rp: bool = False) -> State:
+          blocks: Optional[List[np.ndarray]] = None, rp: bool = False,
+          box_qp: bool = False) -> State:
     """One RAC-MBADMM iteration (eq. RAC-ADDM) in the split form of Sec. 3.1:
     random assembly, cyclic block argmins over the x-blocks, the z-block in
     closed form, then the multiplier ascent on both constraints.  rp=True is
-    the RP-MBADMM iteration (Sec. 1): the fixed partition in a random order."""
+    the RP-MBADMM iteration (Sec. 1): the fixed partition in a random order.
+    box_qp=True (phi = box only) keeps the box in the block argmins instead
+    of the split: gamma is then the proximal weight, z = x and xi stays 0."""
     if blocks is None:
         blocks = (rp_assembly if rp else random_assembly)(P.n, p, seed, st.sweep)
+    if box_qp:
+        if P.phi != "box":
+            raise ValueError("box_qp needs phi = box")
+        for S in blocks:
+            block_argmin_box(P, st, S, beta, gamma)
+        st.z = st.x.copy()
+        if P.E is not None:
+            st.mu = st.mu - beta * (P.E @ st.x - P.d)
+        st.sweep += 1
+        return st
     for S in blocks:
         block_argmin(P, st, S, beta, gamma)
     st.z = z_block(P, st.x, st.xi, gamma)
@@ -379,14 +480,15 @@ def kkt(P: Problem, z: np.ndarray, mu=None) -> dict:
 
 def solve(P: Problem, p: int, seed: int = 0, beta: float = 1.0, gamma: float = 1.0,
           tol: float = 1e-6, max_sweeps: int = 1000, check_every: int = 1,
-          x0=None, xi0=None, record: bool = False, rp: bool = False):
+          x0=None, xi0=None, record: bool = False, rp: bool = False,
+          box_qp: bool = False):
     """Run sweeps from the initial state until KKT(z) <= tol or max_sweeps.
     Returns (state, info)."""
     st = initial_state(P, x0, xi0)
     hist = []
     k_val = kkt(P, st.z, st.mu if P.E is not None else None)["kkt"]
     while st.sweep < max_sweeps:
-        sweep(P, st, p, seed, beta, gamma, rp=rp)
+        sweep(P, st, p, seed, beta, gamma, rp=rp, box_qp=box_qp)
         if record:
             hist.append(st.copy())
         if st.sweep % check_every == 0 or st.sweep == max_sweeps:

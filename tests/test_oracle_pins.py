@@ -568,3 +568,138 @@ def test_rbf_matrix_definition():
     assert np.allclose(np.diag(Q), 1.0) and np.array_equal(Q, Q.T)
     assert np.linalg.eigvalsh(Q).min() > -1e-12
     assert np.abs(O.rbf_svm_matrix(X, y, 1e6) - np.outer(y, y)).max() < 1e-10
+
+
+# --------------------------------------------------------------------------
+# The box kept inside the block (eq. RAC-ADDM with x_i in X_i; eq. svm)
+# --------------------------------------------------------------------------
+def _box_enum(K, r, l, u):
+    """Every pattern in {free, at l, at u}^s: the free rows solve K_FF d_F =
+    -(r + K_FW d_W)_F; keep the feasible pattern whose bound multipliers have
+    the right signs (the unique KKT point of a strictly convex box QP)."""
+    s = len(r)
+    found = []
+    for pat in itertools.product((0, 1, 2), repeat=s):
+        pat = np.array(pat)
+        if np.any((pat == 1) & ~np.isfinite(l)) or np.any((pat == 2) & ~np.isfinite(u)):
+            continue
+        d = np.zeros(s)
+        d[pat == 1] = l[pat == 1]
+        d[pat == 2] = u[pat == 2]
+        F = np.nonzero(pat == 0)[0]
+        if len(F):
+            W = np.nonzero(pat != 0)[0]
+            rhs = -(r[F] + K[np.ix_(F, W)] @ d[W])
+            d[F] = np.linalg.solve(K[np.ix_(F, F)], rhs)
+        sc = 1e-9 * max(1.0, np.abs(r).max())
+        if np.any(d < l - sc) or np.any(d > u + sc):
+            continue
+        g = K @ d + r
+        if np.any(g[pat == 1] < -sc) or np.any(g[pat == 2] > sc):
+            continue
+        found.append(d)
+    assert found, "no KKT pattern"
+    for d in found[1:]:
+        assert np.abs(d - found[0]).max() < 1e-8
+    return found[0]
+
+
+def _box_case(rng, s, cond):
+    Qm, _ = np.linalg.qr(rng.normal(size=(s, s)))
+    ev = np.geomspace(1.0, cond, s)
+    K = (Qm * ev) @ Qm.T
+    r = rng.normal(size=s) * 3.0
+    l = -rng.uniform(0.0, 1.5, s)
+    u = rng.uniform(0.0, 1.5, s)
+    l[rng.random(s) < 0.25] = 0.0          # starts on a lower bound
+    u[rng.random(s) < 0.15] = 0.0          # starts on an upper bound
+    u[rng.random(s) < 0.15] = np.inf       # one-sided
+    if s > 2:
+        l[1] = u[1] = 0.0                  # a fixed coordinate
+    return K, r, l, u
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_box_qp_matches_enumeration(seed):
+    rng = np.random.default_rng(100 + seed)
+    s = 1 + seed % 6
+    K, r, l, u = _box_case(rng, s, 10.0 ** (seed % 4 + 1))
+    d, state = O.box_qp(K, r, l, u)
+    ref = _box_enum(K, r, l, u)
+    assert np.abs(d - ref).max() <= 1e-10 * max(1.0, np.abs(ref[np.isfinite(ref)]).max())
+    assert np.array_equal(d[state == 1], l[state == 1])
+    assert np.array_equal(d[state == 2], u[state == 2])
+
+
+def test_box_qp_diagonal_is_clipped_newton_step():
+    rng = np.random.default_rng(5)
+    k = rng.uniform(0.5, 4.0, 30)
+    r = rng.normal(size=30)
+    l, u = -rng.uniform(0, 1, 30), rng.uniform(0, 1, 30)
+    d, _ = O.box_qp(np.diag(k), r, l, u)
+    assert np.abs(d - np.clip(-r / k, l, u)).max() < 1e-15
+
+
+def test_box_qp_kkt_at_size_and_clipping_is_not_enough():
+    """s = 80, condition 1e4: the optimality conditions of a box QP hold to
+    rounding; the clipped unconstrained minimiser (a plausible shortcut)
+    violates them on the same instance."""
+    rng = np.random.default_rng(9)
+    K, r, l, u = _box_case(rng, 80, 1e4)
+    d, state = O.box_qp(K, r, l, u)
+    g = K @ d + r
+    sc = 1e-10 * max(1.0, np.abs(r).max())
+    assert np.all(d >= l) and np.all(d <= u)
+    assert np.abs(g[state == 0]).max() <= sc
+    movable = u > l
+    assert np.all(g[(state == 1) & movable] >= -sc)
+    assert np.all(g[(state == 2) & movable] <= sc)
+    dc = np.clip(np.linalg.solve(K, -r), l, u)
+    gc = K @ dc + r
+    inside = (dc > l) & (dc < u)
+    assert np.abs(gc[inside]).max() > 1e-3
+
+
+def test_box_sweep_with_unit_blocks_is_projected_coordinate_descent():
+    """Blocks of one coordinate: the literal box step is the clipped exact
+    line minimisation along that coordinate, taken in the assembled order."""
+    rng = np.random.default_rng(3)
+    n = 12
+    B = rng.normal(size=(20, n))
+    H = B.T @ B
+    q = rng.normal(size=n)
+    e = rng.choice([-1.0, 1.0], size=(1, n))
+    P = O.Problem(H=H, q=q, phi="box", lo=0.0, hi=0.8, E=e, d=np.zeros(1))
+    st = O.initial_state(P)
+    x, mu = np.zeros(n), np.zeros(1)
+    beta, gamma = 0.7, 0.3
+    for k in range(6):
+        order = np.concatenate(O.random_assembly(n, n, 4, k))
+        O.sweep(P, st, n, 4, beta, gamma, box_qp=True)
+        for j in order:
+            g = H[j] @ x + q[j] + e[0, j] * (beta * (e[0] @ x) - mu[0])
+            x[j] = min(max(x[j] - g / (H[j, j] + beta + gamma), 0.0), 0.8)
+        mu = mu - beta * (e[0] @ x)
+        assert np.abs(st.x - x).max() < 1e-13
+        assert np.array_equal(st.z, st.x) and not st.xi.any()
+        assert abs(st.mu[0] - mu[0]) < 1e-13
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.5])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_box_sweep_svm_converges_to_enumeration(seed, gamma):
+    """Gaussian-kernel C-SVC dual (eq. svm, Sec. 3.2): the literal box-block
+    iteration converges to the enumerated optimum; every iterate is in the box."""
+    rng = np.random.default_rng(40 + seed)
+    X = rng.normal(size=(7, 2))
+    y = np.where(X[:, 0] + 0.3 * rng.normal(size=7) > 0, 1.0, -1.0)
+    C = 1.0
+    Q = O.rbf_svm_matrix(X, y, 1.0)
+    P = O.Problem(H=Q, q=-np.ones(7), phi="box", lo=0.0, hi=C, E=y[None, :], d=np.zeros(1))
+    a_enum, _ = O.enum_svm(Q, y, C)
+    st = O.initial_state(P)
+    for _ in range(3000):
+        O.sweep(P, st, 3, seed, 0.3, gamma, box_qp=True)
+        assert np.all(st.x >= 0.0) and np.all(st.x <= C)
+    assert np.abs(st.x - a_enum).max() < 1e-8
+    assert O.kkt(P, st.x, mu=st.mu)["kkt"] < 1e-9

@@ -163,6 +163,23 @@ typedef struct {
                                it applies, else sequential), 1 = sequential warm-started loop,
                                2 = batched (RAC_ERR_ARG where it does not apply); see
                                rac_admm_path */
+    int32_t box_qp;         /* phi = RAC_PHI_BOX: how the box enters the block argmins of
+                               eq. RAC-ADDM ("x_i in X_i").  0 = the split x - z = 0 with the box
+                               in the z-block (the pattern of Sec. 3.1).  1 = the box kept inside
+                               every block argmin: each block step solves
+                                 min 1/2 d^T K_S d + r^T d,  lo - x_S <= d <= hi - x_S,
+                                 K_S = H_SS + beta e_S e_S^T + box_prox I,
+                               exactly (primal active-set method with the sweep operator); z = x
+                               and xi = 0 throughout, a warm start x0 is projected onto the box
+                               and xi0 is ignored, and each sweep's block matrices are formed
+                               after the previous sweep (they depend on x).  Needs the Gram form
+                               (H given, or A with the form not RAC_FORM_RESIDUAL), k <= 1, the
+                               RAC assembly and blocks of at most 128 coordinates, else
+                               RAC_ERR_ARG.  Ignored (must be 0) for rac_admm_batch. */
+    double box_prox;        /* box_qp = 1: weight of the proximal term box_prox/2 ||x_S - x_S^k||^2
+                               of each block problem, >= 0 (gamma is unused in that mode).  0 is
+                               the literal block argmin; H_SS + beta e_S e_S^T must then be
+                               positive definite, else the solve returns RAC_ERR_NOT_PD. */
 } rac_options;
 
 /* KKT measure used for the stop test, evaluated in FP64 on z with the exact
@@ -195,6 +212,11 @@ typedef struct {
                                1/2 ||A z - b||^2 + c^T z + sum_j phi(z_j) (H form:
                                1/2 z^T H z + c^T z + sum_j phi(z_j)); the box indicator counts
                                0 (z is in the box).  0 in rac_admm_batch and the batched path. */
+    int64_t box_iters;      /* box_qp = 1: active-set iterations of all block steps of this call
+                               (a step that changes no bound takes one); 0 otherwise */
+    int64_t box_capped;     /* box_qp = 1: block steps that reached the iteration cap
+                               (4 s_max + 16) before the optimality test held; such a step is
+                               still feasible.  0 otherwise */
 } rac_info;
 
 typedef struct rac_handle rac_handle;

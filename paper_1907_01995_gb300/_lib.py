@@ -41,7 +41,8 @@ class RacOptions(ctypes.Structure):
                 ("seed", c_uint64), ("storage", c_int32), ("form", c_int32), ("grid", c_int32),
                 ("x0", c_void_p), ("xi0", c_void_p), ("stream", c_void_p), ("profile", c_int32),
                 ("xi0_from_grad", c_int32), ("ws_fallback", c_int32), ("chain", c_int32),
-                ("assembly", c_int32), ("debug_exit_cta", c_int32), ("path", c_int32)]
+                ("assembly", c_int32), ("debug_exit_cta", c_int32), ("path", c_int32),
+                ("box_qp", c_int32), ("box_prox", c_double)]
 
 
 class RacInfo(ctypes.Structure):
@@ -51,7 +52,8 @@ class RacInfo(ctypes.Structure):
                 ("kernel_launches", c_int64), ("setup_launches", c_int64),
                 ("t_assembly_ms", c_double), ("t_factor_ms", c_double), ("t_chain_ms", c_double),
                 ("t_prox_ms", c_double), ("t_refresh_ms", c_double), ("chain_launches", c_int64),
-                ("warm_start_rejected", c_int32), ("t_loop_ms", c_double), ("obj", c_double)]
+                ("warm_start_rejected", c_int32), ("t_loop_ms", c_double), ("obj", c_double),
+                ("box_iters", c_int64), ("box_capped", c_int64)]
 
 
 P = ctypes.POINTER

@@ -114,7 +114,7 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
                  max_sweeps=1000, refresh_every=10, seed=0, storage="fp64", form="auto",
                  grid=0, x0=None, xi0=None, stream=None, profile=False, xi0_from_grad=False,
                  ws_fallback=False, chain="auto", assembly="rac",
-                 debug_exit_cta=0, path="auto") -> L.RacOptions:
+                 debug_exit_cta=0, path="auto", box_qp=False, box_prox=0.0) -> L.RacOptions:
     o = L.RacOptions()
     L.load().rac_options_default(ctypes.byref(o))
     o.num_blocks = int(num_blocks)
@@ -134,6 +134,8 @@ def make_options(keep: _Keep, n: int, *, num_blocks=1, beta=1.0, gamma=0.0, tol=
     o.assembly = L.ASSEMBLY[assembly]
     o.debug_exit_cta = int(debug_exit_cta)
     o.path = L.PATH[path]
+    o.box_qp = 1 if box_qp else 0
+    o.box_prox = float(box_prox)
     return o
 
 
@@ -146,7 +148,7 @@ def _info_dict(info: L.RacInfo) -> dict:
             "t_chain_ms": info.t_chain_ms, "t_prox_ms": info.t_prox_ms,
             "t_refresh_ms": info.t_refresh_ms, "chain_launches": info.chain_launches,
             "warm_start_rejected": info.warm_start_rejected, "t_loop_ms": info.t_loop_ms,
-            "obj": info.obj}
+            "obj": info.obj, "box_iters": info.box_iters, "box_capped": info.box_capped}
 
 
 class Handle:

@@ -129,6 +129,10 @@ struct rac_handle {
     int rp = 0;
     int *order = nullptr;
     void *Wfix = nullptr;
+    // the box kept inside the block argmins (rac_options.box_qp): per-sweep
+    // factors after the previous sweep, exact box-QP block steps
+    int boxqp = 0;
+    unsigned long long *box_ctr = nullptr;   // [0] active-set iterations, [1] capped steps
     // sparse A (compressed columns): FP64 values for the refresh, storage copy
     // for the sweeps; sp_emax bounds the entries of one block's columns
     // k >= 2 coupling rows folded into the Gram form (rac_coupling.cu)
@@ -266,6 +270,8 @@ static rac_status enqueue_refresh(rac_handle *h) {
     return RAC_OK;
 }
 
+static ProxArgs prox_args(const rac_handle *h);
+
 static ChainArgs chain_args(rac_handle *h, int slot) {
     ChainArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -312,6 +318,8 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.sp_vals = h->sp_vals;
     a.sp_stage = h->sp_stage ? (char *)h->sp_stage + (size_t)slot * h->sp_slot : nullptr;
     a.sp_stage_bytes = h->sp_sb;
+    a.box_ctr = h->box_ctr;
+    if (h->boxqp) a.prox = prox_args(h);   // the box chain reads lo and hi there
     return a;
 }
 
@@ -340,6 +348,7 @@ static ProxArgs prox_args(const rac_handle *h) {
     pa.beta = h->beta;
     pa.gamma = h->gamma;
     pa.lam_dev = h->lam_dev;
+    pa.clamp_x = h->boxqp;
     return pa;
 }
 
@@ -347,7 +356,10 @@ static ProxArgs prox_args(const rac_handle *h) {
 static rac_status enqueue_factor(rac_handle *h, int s, cudaStream_t sf) {
     ChainArgs a = chain_args(h, s);
     int kinv = 1;
-    if (h->sparse) {
+    if (h->boxqp) {
+        RAC_CK(launch_box_factor(h->store, a, const_cast<void *>(a.W), h->lo, h->hi, sf));
+        h->nlaunch += 1;
+    } else if (h->sparse) {
         RAC_CK(launch_sp_factor(h->store, a, const_cast<void *>(a.W),
                                 (char *)h->Pbuf + (size_t)s * h->pstride, h->sp_emax, sf));
         h->nlaunch += big_factor_launches(BlockLayout(h->n, h->p).smax(), h->store);
@@ -391,11 +403,13 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
     if (pf) RAC_CK(cudaEventRecord(h->pev[1], st));
     RAC_CK(cudaEventRecord(h->fev[0], st));      // fork: factors wait for the assembly
     // fork only the streams that receive work, so every forked stream rejoins
-    const int nfac = h->rp ? 0 : nb - pre_in;
+    // (box mode: a sweep's factors depend on the previous sweep's x, so each
+    // runs on this stream right before its chain)
+    const int nfac = (h->rp || h->boxqp) ? 0 : nb - pre_in;
     for (int q = 0; q < std::min(nfac, (int)rac_handle::kFactorStreams); ++q)
         RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[0], 0));
     h->nlaunch += (h->rp ? 0 : 1 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;   // + prox below
-    for (int s = pre_in; s < nb && !h->rp; ++s) {
+    for (int s = pre_in; s < nb && !h->rp && !h->boxqp; ++s) {
         cudaStream_t sf = h->sfs[(s - pre_in) % rac_handle::kFactorStreams];
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
         if (pf) RAC_CK(cudaEventRecord(ev[0], sf));
@@ -409,10 +423,17 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         if (h->lookahead)
             RAC_CK(launch_prepare(h->n, a.perm, h->x, h->z, h->xi, h->k == 1 ? h->e64 : nullptr,
                                   h->gamma, h->sperm, h->eperm, st));
-        if (s >= pre_in && !h->rp) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
+        if (s >= pre_in && !h->rp && !h->boxqp) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
+        if (h->boxqp) {
+            if (pf) RAC_CK(cudaEventRecord(ev[0], st));
+            RAC_ST(enqueue_factor(h, s, st));
+            if (pf) RAC_CK(cudaEventRecord(ev[1], st));
+        }
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
-        if (h->sparse) {
+        if (h->boxqp) {
+            RAC_CK(launch_box_chain(h->store, a, h->grid, st));
+        } else if (h->sparse) {
             RAC_CK(launch_sp_chain(h->store, a, h->sp_emax, h->sp_nbuf, st));
         } else if (h->big) {
             RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
@@ -558,6 +579,10 @@ static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) 
     } else {
         RAC_CK(cudaMemsetAsync(h->xi, 0, nb, st));
     }
+    if (h->boxqp) {   // box kept in the blocks: x in the box, z = x, xi = 0
+        RAC_CK(launch_box_project(h->n, h->lo, h->hi, h->x, h->z, h->xi, st));
+        h->nlaunch += 1;
+    }
     RAC_CK(cudaMemsetAsync(h->mu, 0, std::max(1, h->k) * sizeof(double), st));
     RAC_CK(cudaMemsetAsync(h->t, 0, std::max(1, h->k) * sizeof(double), st));
     RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
@@ -607,7 +632,9 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     h->dbg_exit_cta = o->debug_exit_cta > 0 ? o->debug_exit_cta - 1 : -1;
     h->path_mode = o->path;
     h->rp = o->assembly == 1 ? 1 : 0;
-    h->gram = !h->sparse && (!h->has_A || h->fold || o->form == RAC_FORM_GRAM ||
+    h->boxqp = o->box_qp == 1 ? 1 : 0;
+    if (h->boxqp) h->gamma = o->box_prox;   // the proximal weight; there is no split
+    h->gram = !h->sparse && (!h->has_A || h->fold || h->boxqp || o->form == RAC_FORM_GRAM ||
                              (o->form == RAC_FORM_AUTO && h->n <= h->m));
     {
         const size_t nfev = std::max<size_t>(1 + (size_t)h->refresh_every, 6);
@@ -772,7 +799,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
             RAC_CK(cudaMemcpyAsync(h->ss->h_aux, h->kpart, 2 * sizeof(double),
                                    cudaMemcpyDeviceToHost, st));
         }
-        if (o->gamma < 0) {
+        if (o->gamma < 0 && !h->boxqp) {
             // curvature-scaled split penalty |gamma| * trace(H) / n
             double tr = 0.0;
             if (h->has_A || h->sparse) {
@@ -865,6 +892,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         h->stage = chain_can_stage(h->store, lay.smax(), 0, 0) ? 1 : 0;
         gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, 0, 0, 0, &smem);
     }
+    if (h->boxqp) {
+        // its own chain: no lookahead, cluster or K^{-1} staging
+        h->lookahead = h->cluster = h->stage = h->stage_p = h->perm_in_smem = 0;
+        gmax = box_chain_max_grid(h->store, lay.smax());
+        RAC_ST(h->alloc_bytes((void **)&h->box_ctr, 2 * sizeof(unsigned long long)));
+    }
     if (h->big) {
         h->stage = 0;
         gmax = big_chain_max_grid(h->store);
@@ -937,11 +970,11 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         h->nlaunch += 1;
         RAC_CK(cudaStreamSynchronize(st));   // the pageable identity order is consumed
     }
-    std::snprintf(h->form, sizeof(h->form), "%s/%s%s%s",
+    std::snprintf(h->form, sizeof(h->form), "%s/%s%s%s%s",
                   h->gram ? "gram" : (h->sparse ? "sparse" : "residual"),
                   h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
                   h->cluster ? (h->cluster == 16 ? "/cluster16" : "/cluster8") : "",
-                  h->rp ? "/rp" : "");
+                  h->rp ? "/rp" : "", h->boxqp ? "/boxqp" : "");
     RAC_ST(set_state(h, o->x0, o->xi0));
     RAC_CK(cudaStreamSynchronize(st));
     h->kkt_scale = std::max(1.0, h->ss->h_aux[0]);
@@ -976,6 +1009,12 @@ extern "C" rac_status rac_admm_setup(const rac_problem *pr, const rac_options *o
     // RP on the handle: equal blocks (the chains index blocks by position)
     if (o->assembly == 1 && pr->n % o->num_blocks != 0) return RAC_ERR_ARG;
     if (o->path < 0 || o->path > 2) return RAC_ERR_ARG;
+    if (o->box_qp < 0 || o->box_qp > 1) return RAC_ERR_ARG;
+    if (o->box_qp == 1 &&
+        (pr->phi != RAC_PHI_BOX || sparse || pr->k > 1 || o->assembly != 0 ||
+         o->form == RAC_FORM_RESIDUAL || !(o->box_prox >= 0) || !std::isfinite(o->box_prox) ||
+         (pr->n + o->num_blocks - 1) / o->num_blocks > box_max_block()))
+        return RAC_ERR_ARG;
     if (o->form == RAC_FORM_RESIDUAL && !pr->A && !sparse) return RAC_ERR_ARG;
     int64_t smax = (pr->n + o->num_blocks - 1) / o->num_blocks;
     if (smax > 4096) return RAC_ERR_ARG;
@@ -998,6 +1037,7 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
     h->nlaunch = 0;
     h->t_asm = h->t_fac = h->t_chain = h->t_prox = h->t_ref = 0.0;
     h->chain_launches = 0;
+    if (h->box_ctr) RAC_CK(cudaMemsetAsync(h->box_ctr, 0, 2 * sizeof(unsigned long long), h->st));
     HostStats hs;
     int dev_err = 0;
     RAC_ST(read_stats(h, &hs, &dev_err));
@@ -1014,7 +1054,7 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
         if (h->pre > 0 && pre_in == 0) h->pre = 0;   // stale: recompute everything
         const int left = h->max_sweeps - done - nb;
         const int next_nb =
-            (h->profile || h->rp || left <= 0) ? 0 : std::min(h->refresh_every, left);
+            (h->profile || h->rp || h->boxqp || left <= 0) ? 0 : std::min(h->refresh_every, left);
         RAC_ST(run_period(h, nb, pre_in, next_nb));
         h->pre = std::min(next_nb, (int)rac_handle::kFactorStreams);
         h->pre_nb = next_nb;
@@ -1043,6 +1083,9 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
                             h->gz, h->phi, h->lam1, h->lam2, h->lam_dev, h->kpart, h->st));
     h->nlaunch += 1;
     RAC_CK(cudaMemcpyAsync(&obj, h->kpart, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    unsigned long long box_ctr[2] = {0, 0};
+    if (h->box_ctr)
+        RAC_CK(cudaMemcpyAsync(box_ctr, h->box_ctr, sizeof(box_ctr), cudaMemcpyDeviceToHost, h->st));
     RAC_CK(cudaStreamSynchronize(h->st));
     if (info) {
         info->sweeps = done;
@@ -1065,6 +1108,8 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
         info->warm_start_rejected = rejected;
         info->t_loop_ms = 0.0;
         info->obj = obj;
+        info->box_iters = (int64_t)box_ctr[0];
+        info->box_capped = (int64_t)box_ctr[1];
     }
     return status;
 }

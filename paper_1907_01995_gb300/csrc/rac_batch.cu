@@ -1403,6 +1403,7 @@ extern "C" rac_status rac_admm_batch(int32_t count, const rac_problem *probs, co
     if (o->storage < RAC_FP64 || o->storage > RAC_BF16 || !(o->tol >= 0) || o->max_sweeps < 0)
         return RAC_ERR_ARG;
     if (o->assembly < 0 || o->assembly > 1) return RAC_ERR_ARG;
+    if (o->box_qp != 0) return RAC_ERR_ARG;   // the batch keeps the split form
     auto t0 = std::chrono::steady_clock::now();
     (void)cudaGetLastError();
     BatchRun B;

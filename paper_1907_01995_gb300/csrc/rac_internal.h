@@ -58,6 +58,7 @@ struct ProxArgs {
     int phi;
     double lam1, lam2, lo, hi, beta, gamma;
     const double *lam_dev;  // if set: (lambda1, lambda2) read from device memory
+    int clamp_x;            // box kept in the blocks: x <- clamp(x + dx, lo, hi), z = x, xi kept
 };
 
 // Arguments of the persistent sweep kernels (one instance, one rhs column).
@@ -103,7 +104,8 @@ struct ChainArgs {
     int dbg_exit_cta;       // k_chain_res: this CTA returns at its start (-1: none), so the
                             // others' bounded barrier waits run out (failure-path testing)
     int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
-    ProxArgs prox;          //   ... with these arguments
+    ProxArgs prox;          //   ... with these arguments (the box chain reads lo, hi here)
+    unsigned long long *box_ctr;  // box chain: [0] active-set iterations, [1] capped solves
 };
 
 
@@ -220,6 +222,17 @@ cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, con
                              cudaStream_t st);
 cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,
                             cudaStream_t st);
+
+// The box kept inside the block argmins (rac_boxqp.cu): per sweep, the block
+// matrices swept on their free sets (after the previous sweep), the chain of
+// exact bound-constrained block steps, and the projection of a warm start.
+cudaError_t launch_box_factor(int store, const ChainArgs &a, void *Wout, double lo, double hi,
+                              cudaStream_t st);
+cudaError_t launch_box_chain(int store, const ChainArgs &a, int grid, cudaStream_t st);
+int box_chain_max_grid(int store, int smax);
+int box_max_block();
+cudaError_t launch_box_project(int n, double lo, double hi, double *x, double *z, double *xi,
+                               cudaStream_t st);
 
 // RP-MBADMM on the single-problem handle (equal blocks s = n / p): expand the
 // block orders (nsweeps x p) into permutations / block positions, and gather

@@ -1267,11 +1267,19 @@ __global__ void k_prox(ProxArgs a) {
             a.g[j] += a.gdef[j] + (a.gnext ? a.gnext[j] : 0.0);
             if (a.gnext) a.gnext[j] = 0.0;
         }
-        double xi = a.xi[j];
-        double z = prox_z(a.phi, x, xi, a.gamma, a.lam1, a.lam2, a.lo, a.hi);
-        a.x[j] = x;
-        a.z[j] = z;
-        a.xi[j] = xi - a.gamma * (x - z);
+        if (a.clamp_x) {
+            // box kept in the blocks: an infinite increment lands on the bound
+            // exactly; NaN stays NaN
+            x = x < a.lo ? a.lo : (x > a.hi ? a.hi : x);
+            a.x[j] = x;
+            a.z[j] = x;
+        } else {
+            double xi = a.xi[j];
+            double z = prox_z(a.phi, x, xi, a.gamma, a.lam1, a.lam2, a.lo, a.hi);
+            a.x[j] = x;
+            a.z[j] = z;
+            a.xi[j] = xi - a.gamma * (x - z);
+        }
     }
     if (j == 0 && a.mu && a.t) *a.mu = *a.mu - a.beta * (*a.t);
 }

@@ -115,3 +115,38 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.rac_admm_setup(ctypes.byref(ps), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
     assert h.value is None
     assert lib.rac_status_string(4).decode() == "block matrix not positive definite"
+
+
+def test_box_qp_mode_arguments_rejected_without_gpu(lib):
+    """The box kept in the block argmins needs phi = box, the Gram form, k <= 1,
+    the RAC assembly, blocks of at most 128 coordinates and box_prox >= 0;
+    the batch does not take it."""
+    import numpy as np
+    from paper_1907_01995_gb300 import _lib as L
+    n = 300
+    H = np.eye(n)
+    pr = L.RacProblem()
+    pr.m, pr.n, pr.H = n, n, H.ctypes.data
+    pr.phi, pr.lo, pr.hi = 2, 0.0, 1.0
+    o = L.RacOptions()
+    assert lib.rac_options_default(ctypes.byref(o)) == 0
+    h = ctypes.c_void_p()
+    o.box_qp, o.num_blocks = 1, 2              # blocks of 150 > 128
+    assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
+    o.num_blocks = 3
+    for field, bad in (("box_qp", 2), ("box_prox", -1.0), ("box_prox", float("nan")),
+                       ("assembly", 1), ("form", 2)):
+        old = getattr(o, field)
+        setattr(o, field, bad)
+        assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG, field
+        setattr(o, field, old)
+    pr.phi = 1                                 # not a box
+    assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
+    pr.phi = 2
+    E = np.ones((2, n))
+    pr.E, pr.k, pr.d = E.ctypes.data, 2, np.zeros(2).ctypes.data   # k = 2 rows
+    assert lib.rac_admm_setup(ctypes.byref(pr), ctypes.byref(o), ctypes.byref(h)) == L.RAC_ERR_ARG
+    pr.k = 0
+    xo = (ctypes.c_void_p * 1)(None)
+    assert lib.rac_admm_batch(1, ctypes.byref(pr), ctypes.byref(o), xo, None) == L.RAC_ERR_ARG
+    assert h.value is None

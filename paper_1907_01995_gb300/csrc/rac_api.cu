@@ -132,6 +132,7 @@ struct rac_handle {
     // the box kept inside the block argmins (rac_options.box_qp): per-sweep
     // factors after the previous sweep, exact box-QP block steps
     int boxqp = 0;
+    BoxShape bshape = {};
     unsigned long long *box_ctr = nullptr;   // [0] active-set iterations, [1] capped steps
     // sparse A (compressed columns): FP64 values for the refresh, storage copy
     // for the sweeps; sp_emax bounds the entries of one block's columns
@@ -319,7 +320,13 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.sp_stage = h->sp_stage ? (char *)h->sp_stage + (size_t)slot * h->sp_slot : nullptr;
     a.sp_stage_bytes = h->sp_sb;
     a.box_ctr = h->box_ctr;
-    if (h->boxqp) a.prox = prox_args(h);   // the box chain reads lo and hi there
+    if (h->boxqp) {
+        a.prox = prox_args(h);   // the box chain reads lo and hi there
+        a.box_ld = h->bshape.ld;
+        a.box_tiles = h->bshape.tiles;
+        a.box_nbuf = h->bshape.nbuf;
+        a.box_gpre = h->bshape.gpre;
+    }
     return a;
 }
 
@@ -862,6 +869,9 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     BlockLayout lay(n, h->p);
     const size_t ta = h->store == ST_F64 ? 8 : 4;
     h->wstride = (lay.factor_total() * ta + 255) & ~(size_t)255;
+    if (h->boxqp)   // box mode: block i at i * smax * ld (row stride ld)
+        h->wstride = ((size_t)h->p * lay.smax() * box_ld_of(h->store, lay.smax()) * ta + 255) &
+                     ~(size_t)255;
     RAC_ST(h->alloc_bytes((void **)&h->W, (size_t)h->refresh_every * h->wstride));
     h->kinv = factor_uses_kinv(lay.smax()) ? 1 : 0;
     h->big = (!h->gram && !h->kinv && !h->sparse) ? 1 : 0;
@@ -893,9 +903,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         gmax = chain_max_grid(h->store, h->gram, lay.smax(), h->stage, 0, 0, 0, &smem);
     }
     if (h->boxqp) {
-        // its own chain: no lookahead, cluster or K^{-1} staging
+        // its own chain: no lookahead, cluster or K^{-1} staging; one CTA per
+        // SM at most, each with its column tiles of G
         h->lookahead = h->cluster = h->stage = h->stage_p = h->perm_in_smem = 0;
-        gmax = box_chain_max_grid(h->store, lay.smax());
+        const int bwant = o->grid > 0 ? o->grid : sms;
+        if (!box_shape(h->store, n, h->p, bwant, &h->bshape)) return RAC_ERR_ARG;
+        gmax = h->bshape.grid;
         RAC_ST(h->alloc_bytes((void **)&h->box_ctr, 2 * sizeof(unsigned long long)));
     }
     if (h->big) {
@@ -928,6 +941,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     if (o->grid > 0) want = o->grid;
     if (h->lookahead) want = std::max(want, lookahead_min_grid(n));
     h->grid = std::max(1, std::min(want, gmax));
+    if (h->boxqp) h->grid = h->bshape.grid;   // its tiles per CTA were sized for this grid
     if (h->lookahead) {
         h->pstride = ((size_t)h->p * BlockLayout::pad4((size_t)lay.smax() * lay.smax()) * ta + 255) &
                      ~(size_t)255;

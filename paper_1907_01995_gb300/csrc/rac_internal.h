@@ -106,6 +106,17 @@ struct ChainArgs {
     int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
     ProxArgs prox;          //   ... with these arguments (the box chain reads lo, hi here)
     unsigned long long *box_ctr;  // box chain: [0] active-set iterations, [1] capped solves
+    int box_ld;             // box mode: row stride of the block matrices (W holds block i
+                            //   at i * smax * box_ld)
+    int box_tiles;          // box chain: column tiles of 32 per CTA (upper bound)
+    int box_nbuf;           // box chain: shared-memory buffers of M (and G tiles): 1 or 2
+    int box_gpre;           // box chain: 1 = this CTA's G tiles staged in shared memory
+};
+
+// Configuration of the box chain (rac_boxqp.cu).
+struct BoxShape {
+    int ld, tiles, nbuf, gpre, grid;
+    size_t smem;
 };
 
 
@@ -229,8 +240,9 @@ cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, do
 cudaError_t launch_box_factor(int store, const ChainArgs &a, void *Wout, double lo, double hi,
                               cudaStream_t st);
 cudaError_t launch_box_chain(int store, const ChainArgs &a, int grid, cudaStream_t st);
-int box_chain_max_grid(int store, int smax);
+bool box_shape(int store, int n, int p, int want, BoxShape *out);
 int box_max_block();
+int box_ld_of(int store, int smax);
 cudaError_t launch_box_project(int n, double lo, double hi, double *x, double *z, double *xi,
                                cudaStream_t st);
 

@@ -28,7 +28,8 @@
 //   k_chain_box   the cyclic pass over the blocks (a grid chain with bounded
 //                 barriers): every CTA runs the same solve (identical inputs
 //                 and reduction order, so identical steps), then adds
-//                 G[:, S] d to its column tiles of g.  The next block's M and
+//                 G[:, S] d to its column tiles of g, which it keeps in
+//                 shared memory.  The next block's M and
 //                 this CTA's G tiles of the next block are copied into shared
 //                 memory (cp.async) while the current block is solved.  A
 //                 coordinate that ends on a bound gets an infinite increment,
@@ -170,17 +171,87 @@ __device__ __forceinline__ bool sweep_rows(TA *M, int ld, int s, int k, bool uns
     return true;
 }
 
+// The same pivot step fused with the product of the next iteration: thread t
+// also publishes rnext (its entry of the next face gradient) and returns in
+// *v its row of the updated M against that vector, in the one pass that
+// updates the row.  The row's column k is replaced after the bulk pass, so
+// its term is corrected by (final - bulk) rf_k.
+template <class TA, bool NAMED>
+__device__ __forceinline__ bool sweep_rows_dot(TA *M, int ld, int s, int k, bool unsweep, TA *colb,
+                                               TA *rf, TA rnext, int *err, int t, TA *v) {
+    using V = Vec<TA>;
+    gbar<NAMED>();   // earlier readers of colb and rf are done
+    TA cq = TA(0);
+    if (t < s) {
+        cq = M[(size_t)t * ld + k];
+        colb[t] = cq;
+        rf[t] = rnext;
+    }
+    gbar<NAMED>();
+    const TA d = colb[k];
+    const bool ok = (unsweep ? d < TA(0) : d > TA(0)) && isfinite((double)d);
+    if (!ok) {
+        if (t == 0) set_err(err, RAC_ERR_NOT_PD);
+        *v = t < s ? row_dot<TA>(M + (size_t)t * ld, rf, ld) : TA(0);
+        return false;
+    }
+    const TA inv = TA(1) / d;
+    const TA sg = unsweep ? TA(-1) : TA(1);
+    TA acc[V::W] = {};
+    TA tot = TA(0);
+    if (t < s) {
+        TA *row = M + (size_t)t * ld;
+        typename V::T *rv = (typename V::T *)row;
+        const typename V::T *cv = (const typename V::T *)colb;
+        const typename V::T *wv = (const typename V::T *)rf;
+        const bool pivot_row = t == k;
+#pragma unroll 2
+        for (int c = 0; c < ld / V::W; ++c) {
+            typename V::T a = rv[c];
+            const typename V::T b = cv[c], w = wv[c];
+#pragma unroll
+            for (int u = 0; u < V::W; ++u) {
+                const TA m = pivot_row ? sg * V::get(b, u) * inv
+                                       : V::get(a, u) - (cq * V::get(b, u)) * inv;
+                V::set(a, u, m);
+                acc[u] += m * V::get(w, u);
+            }
+            rv[c] = a;
+        }
+        const TA bulk = row[k], fin = pivot_row ? -inv : sg * cq * inv;
+        row[k] = fin;
+#pragma unroll
+        for (int u = 0; u < V::W; ++u) tot += acc[u];
+        tot += (fin - bulk) * rf[k];
+    }
+    *v = tot;
+    return true;
+}
+
 // The smallest (value, index) pair over the solve group, ties to the smaller
 // index; every thread of the group receives it.  sv, si: one slot per warp.
+// Within a warp the indices grow with the lane (each thread offers its own
+// coordinate or INT_MAX), so the first lane holding the minimum value holds
+// the pair.  FP32 values are mapped to order-preserving unsigned keys and
+// reduced in one instruction; FP64 values by a butterfly of shuffles.
 template <class TA, bool NAMED>
 __device__ __forceinline__ void group_argmin(TA &v, int &i, TA *sv, int *si) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        const TA v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (v2 < v || (v2 == v && i2 < i)) {
-            v = v2;
-            i = i2;
+    if constexpr (sizeof(TA) == 4) {
+        const unsigned b = __float_as_uint(v);
+        const unsigned key = b ^ ((b >> 31) ? 0xffffffffu : 0x80000000u);
+        const unsigned m = __reduce_min_sync(0xffffffffu, key);
+        const int src = __ffs(__ballot_sync(0xffffffffu, key == m)) - 1;
+        v = __shfl_sync(0xffffffffu, v, src);
+        i = __shfl_sync(0xffffffffu, i, src);
+    } else {
+        for (int o = 16; o > 0; o >>= 1) {
+            const TA v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+            if (v2 < v || (v2 == v && i2 < i)) {
+                v = v2;
+                i = i2;
+            }
         }
     }
     if (lane == 0) {
@@ -240,11 +311,12 @@ __device__ __forceinline__ int box_solve(TA *M, int ld, int s, BoxLane<TA> &L, T
     const bool movable = t < s && L.bu > L.bl;
     int it = 0;
     bool done = false;
+    // the first face step; later ones come out of the fused pivot steps
+    if (t < s) rf[t] = L.st == kFree ? L.r : TA(0);
+    gbar<NAMED>();
+    TA v = t < s ? row_dot<TA>(M + (size_t)t * ld, rf, ld) : TA(0);
     while (it < cap) {
         ++it;
-        if (t < s) rf[t] = L.st == kFree ? L.r : TA(0);
-        gbar<NAMED>();
-        const TA v = t < s ? row_dot<TA>(M + (size_t)t * ld, rf, ld) : TA(0);
         // ratio test: the first bound the face step crosses
         TA a = TA(INFINITY);
         int ja = INT_MAX;
@@ -268,33 +340,39 @@ __device__ __forceinline__ int box_solve(TA *M, int ld, int s, BoxLane<TA> &L, T
                 L.r -= alpha * v;
             }
         }
+        int k;
+        bool uns;
         if (blocked) {
             if (t == ja) {
                 const bool low = v < TA(0);
                 L.st = low ? kAtLo : kAtHi;
                 L.d = low ? L.bl : L.bu;
             }
-            sweep_rows<TA, NAMED>(M, ld, s, ja, true, colb, err, t);
-            continue;
-        }
-        // at the face minimiser: the most violated multiplier of a movable
-        // fixed coordinate (at lo it must be >= 0, at hi <= 0)
-        TA nv = TA(INFINITY);
-        int jv = INT_MAX;
-        if (movable && L.st != kFree) {
-            const TA viol = L.st == kAtLo ? -L.r : L.r;
-            if (viol > tau) {
-                nv = -viol;
-                jv = t;
+            k = ja;
+            uns = true;
+        } else {
+            // at the face minimiser: the most violated multiplier of a
+            // movable fixed coordinate (at lo it must be >= 0, at hi <= 0)
+            TA nv = TA(INFINITY);
+            int jv = INT_MAX;
+            if (movable && L.st != kFree) {
+                const TA viol = L.st == kAtLo ? -L.r : L.r;
+                if (viol > tau) {
+                    nv = -viol;
+                    jv = t;
+                }
             }
+            group_argmin<TA, NAMED>(nv, jv, svB, siB);
+            if (!(nv < TA(INFINITY))) {
+                done = true;
+                break;
+            }
+            if (t == jv) L.st = kFree;
+            k = jv;
+            uns = false;
         }
-        group_argmin<TA, NAMED>(nv, jv, svB, siB);
-        if (!(nv < TA(INFINITY))) {
-            done = true;
-            break;
-        }
-        if (t == jv) L.st = kFree;
-        sweep_rows<TA, NAMED>(M, ld, s, jv, false, colb, err, t);
+        sweep_rows_dot<TA, NAMED>(M, ld, s, k, uns, colb, rf,
+                                  (t < s && L.st == kFree) ? L.r : TA(0), err, t, &v);
     }
     *capped = !done;
     return it;
@@ -375,7 +453,7 @@ cudaError_t launch_box_factor(int store, const ChainArgs &a, void *Wout, double 
 // nbuf buffers of this CTA's G tiles (tiles x smax x 32 storage values), then
 // the broadcast vectors, the step, the tile partials and the reductions.
 struct BoxSmem {
-    size_t M, G, rf, colb, dsh, wred, slots, idx, total;
+    size_t M, G, rf, colb, dsh, wred, slots, idx, gs, bk, xs, total;
     __host__ __device__ BoxSmem(int smax, int ld, int ta, int ts, int tiles, int nbuf, int gpre,
                                 int nw) {
         auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
@@ -385,9 +463,12 @@ struct BoxSmem {
         colb = al(rf + (size_t)ld * ta);
         dsh = al(colb + (size_t)ld * ta);
         wred = al(dsh + (size_t)smax * ta);
-        slots = al(wred + (size_t)kBoxMaxTiles * nw * 32 * ta);
+        slots = al(wred + (size_t)(tiles < kBoxMaxTiles ? tiles : kBoxMaxTiles) * nw * 32 * ta);
         idx = al(slots + 2 * 4 * (size_t)ta + 2 * 4 * sizeof(int) + 4 * sizeof(double) + 16);
-        total = al(idx + 2 * (size_t)smax * sizeof(int)) + 16;
+        gs = al(idx + 2 * (size_t)smax * sizeof(int));            // this CTA's g (tiles x 32)
+        bk = al(gs + (size_t)tiles * 32 * sizeof(double));        // and their block ids
+        xs = al(bk + (size_t)tiles * 32 * sizeof(int));           // x of the block, two buffers
+        total = al(xs + 2 * (size_t)smax * sizeof(double)) + 16;
     }
 };
 
@@ -436,6 +517,9 @@ __global__ void __launch_bounds__(kBoxThreads, 1) k_chain_box(ChainArgs a) {
     int *siA = (int *)(svB + 4), *siB = siA + 4;
     double *sd = (double *)(((uintptr_t)(siB + 4) + 15) & ~(uintptr_t)15);
     int *idxb = (int *)(sm + S.idx);
+    double *gs = (double *)(sm + S.gs);
+    int *bk = (int *)(sm + S.bk);
+    double *xsb = (double *)(sm + S.xs);
     __shared__ int s_flag;
     const bool solver = t < kBoxGroup;
     const TS *G = (const TS *)a.G;
@@ -447,10 +531,21 @@ __global__ void __launch_bounds__(kBoxThreads, 1) k_chain_box(ChainArgs a) {
     unsigned gen = 0;
     const int cap = 4 * smax + 16;
     long long iters = 0, ncap = 0;
-    int mytiles = 0;   // column tiles of this CTA
+    int mytiles = 0;   // column tiles of this CTA (at most box_tiles, checked at launch)
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) ++mytiles;
-    // block 0: indices, then its copies
-    for (int q = t; q < lay.size(0); q += blockDim.x) idxb[q] = a.perm[lay.offset(0) + q];
+    // this CTA's columns of g and their block ids stay in shared memory: the
+    // CTA is their only writer during the pass
+    for (int e = t; e < mytiles * 32; e += blockDim.x) {
+        const int c = (blockIdx.x + (e >> 5) * gridDim.x) * 32 + (e & 31);
+        gs[e] = c < n ? a.g[c] : 0.0;
+        bk[e] = c < n ? a.blk[c] : -1;
+    }
+    // block 0: indices and x, then its copies
+    for (int q = t; q < lay.size(0); q += blockDim.x) {
+        const int j = a.perm[lay.offset(0) + q];
+        idxb[q] = j;
+        xsb[q] = a.x[j];
+    }
     __syncthreads();
     box_issue<TS, TA>(a, lay, 0, 0, Mb, Gb, idxb, nbuf == 1);
     for (int i = 0; i < a.p; ++i) {
@@ -463,9 +558,14 @@ __global__ void __launch_bounds__(kBoxThreads, 1) k_chain_box(ChainArgs a) {
             box_issue<TS, TA>(a, lay, i, 0, Mb, Gb, idx, true);
         }
         if (nbuf == 2 && !solver && i + 1 < a.p) {
+            // the next block's indices and x (x changes only after the pass)
             int *nidx = idxb + (size_t)((i + 1) & 1) * smax;
-            for (int q = t - kBoxGroup; q < lay.size(i + 1); q += blockDim.x - kBoxGroup)
-                nidx[q] = a.perm[lay.offset(i + 1) + q];
+            double *nx = xsb + (size_t)((i + 1) & 1) * smax;
+            for (int q = t - kBoxGroup; q < lay.size(i + 1); q += blockDim.x - kBoxGroup) {
+                const int jn = a.perm[lay.offset(i + 1) + q];
+                nidx[q] = jn;
+                nx[q] = a.x[jn];
+            }
         }
         // this block's gradient and bounds, one coordinate per solve thread
         BoxLane<TA> L;
@@ -475,7 +575,7 @@ __global__ void __launch_bounds__(kBoxThreads, 1) k_chain_box(ChainArgs a) {
         if (solver) {
             if (t < s) {
                 j = idx[t];
-                const double xj = a.x[j];
+                const double xj = nbuf == 2 ? xsb[(size_t)bi * smax + t] : a.x[j];
                 double rr = __ldcg(a.g + j);
                 if (a.e) rr += a.e[j] * (beta * tc - mu);
                 L.r = (TA)rr;
@@ -541,12 +641,17 @@ __global__ void __launch_bounds__(kBoxThreads, 1) k_chain_box(ChainArgs a) {
             }
             __syncthreads();
             if (warp < tcount) {
+                const int e = (k0 + warp) * 32 + lane;
                 const int c = (blockIdx.x + (k0 + warp) * gridDim.x) * 32 + lane;
                 TA tot = 0;
                 for (int w = 0; w < nw; ++w) tot += wred[((size_t)warp * nw + w) * 32 + lane];
                 if (c < n) {
-                    if (a.blk[c] == i) a.gdef[c] = (double)tot;
-                    else a.g[c] = __ldcg(a.g + c) + (double)tot;
+                    if (bk[e] == i) {
+                        a.gdef[c] = (double)tot;
+                    } else {
+                        gs[e] += (double)tot;
+                        a.g[c] = gs[e];
+                    }
                 }
             }
             __syncthreads();
@@ -592,8 +697,8 @@ cudaError_t launch_box_chain(int store, const ChainArgs &a, int grid, cudaStream
     BlockLayout lay(a.n, a.p);
     if (lay.smax() > kBoxMaxBlock || a.box_nbuf < 1 || a.box_nbuf > 2 || grid < 1)
         return cudaErrorInvalidValue;
-    // the staged G tiles of a CTA must fit the buffers sized for them
-    if (a.box_gpre && ((a.n + 31) / 32 + grid - 1) / grid > a.box_tiles) return cudaErrorInvalidValue;
+    // a CTA's columns (and, staged, its G tiles) must fit the buffers sized for them
+    if (((a.n + 31) / 32 + grid - 1) / grid > a.box_tiles) return cudaErrorInvalidValue;
     if (store == ST_F64) return box_chain_impl<double, double>(a, grid, st);
     if (store == ST_F32) return box_chain_impl<float, float>(a, grid, st);
     return box_chain_impl<__nv_bfloat16, float>(a, grid, st);

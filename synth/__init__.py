@@ -16,4 +16,5 @@ from .workloads import (  # noqa: F401
     path_instance,
     small_instance,
     sparse_en_instance,
+    rbf_svm_data,
 )

@@ -272,3 +272,15 @@ def sparse_en_instance(seed: int = 0, m: int = 2000, n: int = 20000, density: fl
     return Instance("sparse_en", A, b, "l1l2", lam1=lam_frac * lam_max, lam2=lam2,
                     num_blocks=p, beta=1.0, gamma=1.0, seed=seed, x_true=x_true,
                     meta={"lambda_max": lam_max, "density": density})
+
+
+def rbf_svm_data(seed: int = 0, N: int = 20000, d: int = 8, noise: float = 0.5):
+    """Features and labels for a Gaussian-kernel C-SVC (Sec. 3.2, Table 8's
+    non-linear SVMs): x_i ~ N(0, I_d), y_i = sign(||x_i||^2 - d + noise * eps_i),
+    a spherical class boundary that a linear kernel cannot separate.  Stands
+    in for the LIBSVM data sets of Table 8, which are not available here.
+    Returns (X, y), X of shape (N, d)."""
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(N, d))
+    y = np.where((X ** 2).sum(1) + noise * rng.normal(size=N) > d, 1.0, -1.0)
+    return X, y

@@ -55,6 +55,12 @@ def parse():
     ap.add_argument("--path-once", type=int, default=0, metavar="K",
                     help="run K batched BF16 solves of the 64-point regularisation path "
                          "20000x5000 and exit (no timing; a fixed command to profile)")
+    ap.add_argument("--rbf-once", type=int, default=0, metavar="SWEEPS",
+                    help="profiling entry: the Gaussian-kernel SVM workload with the box kept "
+                         "in the blocks (BF16), SWEEPS sweeps once, then exit")
+    ap.add_argument("--rbf-n", type=int, default=0, metavar="N",
+                    help="with --rbf-once: N samples instead of the workload's (a smaller "
+                         "case for profiling)")
     ap.add_argument("--svm-batch", type=int, default=0, metavar="COUNT",
                     help="time the batched soft-margin SVM dual workload (COUNT uneven "
                          "instances, N in [500, 20000], d in [20, 1000], blocks of 64) per "
@@ -274,7 +280,7 @@ RBF_WORKLOAD = dict(name="rbf_svm_20000x8_s100", N=20000, d=8, sigma=1.0, C=1.0,
                     tol=1e-6, refresh_every=10, split_sweeps=600)
 
 
-def rbf_svm_leg(flush, st):
+def rbf_svm_leg(flush, st, peaks):
     """Gaussian-kernel C-SVC dual (Sec. 3.2, eq. svm; Table 8's kernel and
     block size s = 100, beta = 0.1 p): 20000 samples of 8 features with a
     spherical class boundary, sigma = 1, C = 1.  Q = diag(y) K diag(y) is
@@ -283,8 +289,10 @@ def rbf_svm_leg(flush, st):
     form (box in the z-block) is run for a bounded number of sweeps on the
     same Q for comparison.  Times are from the device-resident Q (its build
     is reported separately)."""
-    import synth
+    import numpy as np
     import torch
+
+    import synth
     from paper_1907_01995_gb300 import api
     w = RBF_WORKLOAD
     X, y = synth.rbf_svm_data(0, w["N"], w["d"])
@@ -309,6 +317,32 @@ def rbf_svm_leg(flush, st):
                                    max(1, info["block_updates"]),
                                    "box_capped": info["box_capped"],
                                    "ms_per_sweep": ms / max(1, info["sweeps"])}
+    # the chain's roofline: one launch per sweep reads G once (n^2 storage values)
+    # and each block's M (s x ld FP32); time per launch from CUDA events
+    with api.Handle(H=Q, c=-np.ones(N), E=y, d=np.zeros(1), phi="box", lo=0.0, hi=w["C"],
+                    num_blocks=p, beta=0.1 * p, tol=0.0, max_sweeps=20,
+                    refresh_every=w["refresh_every"], storage="bf16", box_qp=True,
+                    profile=True) as h:
+        info = h.solve()[1]
+    ms_chain = info["t_chain_ms"] / max(1, info["chain_launches"])
+    ld = ((w["block"] + 3) // 4 + (1 - ((w["block"] + 3) // 4) % 2)) * 4
+    alg = N * N * 2 + N * ld * 4
+    peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = None
+    try:
+        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        t = tj.get("box_chain/bf16/gram")
+        src = open(os.path.join(ROOT, t["source"]), "rb").read()
+        if t.get("source_sha256") == hashlib.sha256(src).hexdigest():
+            traffic = t["bytes_per_launch"] * (N / t["n_captured"]) ** 2
+    except Exception:
+        traffic = None
+    ach = alg / (ms_chain * 1e-3) / 1e9
+    out["roofline_chain"] = {"bound": "hbm", "kernel": "k_chain_box", "ms_per_launch": ms_chain,
+                             "achieved": ach, "peak": peak, "unit": "GB/s",
+                             "frac": ach / peak if peak else None, "traffic": traffic,
+                             "algorithmic_bytes": alg,
+                             "note": "latency-bound sequential chain; peak of measured"}
     ms, info = _timed_call(lambda: solve("bf16", False, w["split_sweeps"]), flush, st)
     out["split_bf16"] = {"time_ms": ms, "sweeps": info["sweeps"], "kkt": info["kkt"],
                          "status": info["status"], "obj": info["obj"],
@@ -316,6 +350,29 @@ def rbf_svm_leg(flush, st):
     del Q
     torch.cuda.empty_cache()
     return out
+
+
+def rbf_once(sweeps, n_override=0):
+    """One BF16 box-mode solve of the Gaussian-kernel SVM workload for a fixed
+    number of sweeps (profiling entry)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    w = RBF_WORKLOAD
+    N = n_override if n_override > 0 else w["N"]
+    X, y = synth.rbf_svm_data(0, N, w["d"])
+    p = (N + w["block"] - 1) // w["block"]
+    Q = api.rbf_svm_matrix(X, y, w["sigma"])
+    with api.Handle(H=Q, c=-np.ones(N), E=y, d=np.zeros(1), phi="box", lo=0.0, hi=w["C"],
+                    num_blocks=p, beta=0.1 * p, tol=0.0, max_sweeps=sweeps,
+                    refresh_every=w["refresh_every"], storage="bf16", box_qp=True) as h:
+        _, info = h.solve()
+    torch.cuda.synchronize()
+    print(json.dumps({"rbf_once": sweeps, "N": N, "form": info["form"], "kkt": info["kkt"],
+                      "box_iters": info["box_iters"]}), flush=True)
+    return 0
 
 
 def path_once(k):
@@ -597,6 +654,8 @@ def main():
         return svm_batch_leg(args)
     if args.path_once:
         return path_once(args.path_once)
+    if args.rbf_once:
+        return rbf_once(args.rbf_once, args.rbf_n)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -770,7 +829,7 @@ def main():
         except Exception as ex:
             extra["sparse_en_20000x100000"] = {"failed": str(ex)[:300]}
         try:
-            extra["rbf_svm_20000"] = rbf_svm_leg(flush, st)
+            extra["rbf_svm_20000"] = rbf_svm_leg(flush, st, peaks)
         except Exception as ex:
             extra["rbf_svm_20000"] = {"failed": str(ex)[:300]}
         try:

@@ -262,8 +262,12 @@ rac_status rac_admm_reset(rac_handle *h, const double *x0, const double *xi0);
  * (max(1, k) values) out. */
 rac_status rac_admm_get_state(rac_handle *h, double *x, double *z, double *xi, double *mu);
 
-/* Solve `count` independent problems in one persistent launch (Sec. 3.2's
- * SVM duals are the intended use).  All problems share opt except that
+/* Solve `count` independent problems together (Sec. 3.2's SVM duals are the
+ * intended use).  Each refresh period of all problems runs as one captured
+ * CUDA graph of batched kernels: per sweep one factor launch (RAC; RP
+ * factors once per penalty), one chain launch with one CTA per problem
+ * (largest first; problems never wait on each other) and one z-step /
+ * ascent launch, then the exact refresh.  All problems share opt except that
  * problem i uses seed opt->seed + i and, when opt->num_blocks <= 0, blocks of
  * at most -opt->num_blocks coordinates (p_i = ceil(n_i / -num_blocks)) with
  * beta_i = 0.1 p_i (the paper's SVM rule) when opt->beta <= 0; gamma follows

@@ -260,7 +260,8 @@ def solve(A=None, b=None, **kw):
 
 def batch(problems, *, out=None, allow=(L.RAC_OK, L.RAC_ERR_NOT_CONVERGED), **opts):
     """Solve independent data-form problems (dicts of make_problem arguments)
-    in one persistent launch (rac_admm_batch).  Returns (list of z, infos);
+    together, one graph of batched kernels per refresh period
+    (rac_admm_batch).  Returns (list of z, infos);
     raises unless the call's status is in `allow` (per-problem statuses are
     in infos[i]["status"])."""
     lib = L.load()

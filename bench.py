@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--solve-once", type=int, default=0, metavar="K",
                     help="run K plain solves of the workload in the default mixed-precision "
                          "form and exit (no timing; a fixed command to profile)")
+    ap.add_argument("--en-once", type=int, default=0, metavar="K",
+                    help="run K BF16 solves of the Elastic-Net 2000x50000 (--assembly rac or "
+                         "rp) and exit (no timing; a fixed command to profile)")
     ap.add_argument("--path-once", type=int, default=0, metavar="K",
                     help="run K batched BF16 solves of the 64-point regularisation path "
                          "20000x5000 and exit (no timing; a fixed command to profile)")
@@ -379,6 +382,26 @@ def rbf_once(sweeps, n_override=0):
     return 0
 
 
+def en_once(k, assembly):
+    """K BF16 solves of the Elastic-Net 2000 x 50000 workload (profiling entry)."""
+    import torch
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    w = EN_WORKLOAD
+    inst = synth.elastic_net_instance(0)
+    A = torch.tensor(inst.A, device="cuda").t().contiguous().t()
+    b = torch.tensor(inst.b, device="cuda")
+    for _ in range(k):
+        with api.Handle(A, b, phi="l1l2", lambda1=inst.lam1, lambda2=inst.lam2,
+                        num_blocks=inst.num_blocks, tol=w["tol"], max_sweeps=2000,
+                        refresh_every=10, storage="bf16", assembly=assembly) as h:
+            _, info = h.solve()
+    torch.cuda.synchronize()
+    print(json.dumps({"en_once": k, "form": info["form"], "sweeps": info["sweeps"]}), flush=True)
+    return 0
+
+
 def path_once(k):
     """K batched BF16 solves of the 64-point path (profiling entry)."""
     import torch
@@ -658,6 +681,8 @@ def main():
         return svm_batch_leg(args)
     if args.path_once:
         return path_once(args.path_once)
+    if args.en_once:
+        return en_once(args.en_once, args.assembly)
     if args.rbf_once:
         return rbf_once(args.rbf_once, args.rbf_n)
     import numpy as np

@@ -131,6 +131,8 @@ struct rac_handle {
     void *Wfix = nullptr;
     // the box kept inside the block argmins (rac_options.box_qp): per-sweep
     // factors after the previous sweep, exact box-QP block steps
+    int rescl = 0;                  // residual form, s > 128: cluster chain of this many CTAs
+    int rescl_cached = 0;           //   ... with the block's column segments in shared memory
     int boxqp = 0;
     BoxShape bshape = {};
     unsigned long long *box_ctr = nullptr;   // [0] active-set iterations, [1] capped steps
@@ -442,6 +444,8 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
             RAC_CK(launch_box_chain(h->store, a, h->grid, st));
         } else if (h->sparse) {
             RAC_CK(launch_sp_chain(h->store, a, h->sp_emax, h->sp_nbuf, st));
+        } else if (h->big && h->rescl) {
+            RAC_CK(launch_rescl_chain(h->store, a, h->rescl, h->rescl_cached, st));
         } else if (h->big) {
             RAC_CK(launch_big_chain(h->store, a, h->grid, h->rhs_big, h->dx_big, st));
         } else if (h->cluster) {
@@ -984,10 +988,17 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         h->nlaunch += 1;
         RAC_CK(cudaStreamSynchronize(st));   // the pageable identity order is consumed
     }
+    if (h->big && o->chain != 1) {
+        // large blocks in the residual form: the one-cluster chain where it fits
+        ChainArgs a = chain_args(h, 0);
+        h->rescl = rescl_size(h->store, a, &h->rescl_cached);
+    }
     std::snprintf(h->form, sizeof(h->form), "%s/%s%s%s%s",
                   h->gram ? "gram" : (h->sparse ? "sparse" : "residual"),
                   h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
-                  h->cluster ? (h->cluster == 16 ? "/cluster16" : "/cluster8") : "",
+                  (h->cluster || h->rescl)
+                      ? ((h->cluster ? h->cluster : h->rescl) == 16 ? "/cluster16" : "/cluster8")
+                      : "",
                   h->rp ? "/rp" : "", h->boxqp ? "/boxqp" : "");
     RAC_ST(set_state(h, o->x0, o->xi0));
     RAC_CK(cudaStreamSynchronize(st));

@@ -234,6 +234,12 @@ cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, con
 cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,
                             cudaStream_t st);
 
+// Residual form, large blocks, on one thread-block cluster (rac_rescluster.cu):
+// the cluster size it runs with here (16, else 8; 0: it does not apply), and
+// the launch.
+int rescl_size(int store, const ChainArgs &a, int *cached);
+cudaError_t launch_rescl_chain(int store, const ChainArgs &a, int C, int cached, cudaStream_t st);
+
 // The box kept inside the block argmins (rac_boxqp.cu): per sweep, the block
 // matrices swept on their free sets (after the previous sweep), the chain of
 // exact bound-constrained block steps, and the projection of a warm start.

@@ -147,18 +147,43 @@ def lasso_ref():
     return inst, x
 
 
+@pytest.mark.parametrize("chain", ["auto", "grid"])
+@pytest.mark.parametrize("assembly", ["rac", "rp"])
 @pytest.mark.parametrize("storage", ["fp32", "bf16"])
-def test_big_blocks_converged(storage):
-    """Elastic-Net with n > m and 3 blocks of ~300 coordinates in FP32 / BF16
-    storage reaches the coordinate-descent solution."""
+def test_big_blocks_converged(storage, assembly, chain):
+    """Elastic-Net with n > m and 3 blocks of 300 coordinates in FP32 / BF16
+    storage reaches the coordinate-descent solution with the same support, on
+    the one-cluster residual chain (auto) and on the grid-barrier chain, under
+    RAC and RP assembly."""
     inst = synth.small_instance(21, 200, 900, 3, lam2=0.1, lam_frac=0.1)
     ref = O.cd_enet(inst.A, inst.b, inst.lam1, 0.1, tol=1e-13)
     with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=inst.lam1, lambda2=0.1, num_blocks=3,
-                    tol=1e-9, max_sweeps=20000, storage=storage, form="residual") as h:
+                    tol=1e-9, max_sweeps=20000, storage=storage, form="residual",
+                    assembly=assembly, chain=chain) as h:
         z, info = h.solve()
     assert info["status"] == 0, info
+    assert ("/cluster" in info["form"]) == (chain == "auto"), info["form"]
     assert rel(z, ref) <= (1e-5 if storage == "fp32" else 1e-3)
     assert np.array_equal(z != 0, ref != 0)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-9), ("bf16", 1e-7)])
+def test_big_blocks_coupled_box_converged_on_cluster_chain(storage, tol):
+    """Box QP with one coupling row (the SVM-dual structure of eq. svm) and
+    blocks of 226 in the residual form on the one-cluster chain.  H = A^T A has
+    rank 90 < n, so the minimiser need not be unique: the returned point is
+    certified by the oracle's KKT measure (with the solver's multiplier) and
+    the box."""
+    inst = _instance(CASES["big_blocks_coupled"], seed=3)
+    P = O.problem_from_instance(inst)
+    with _handle(inst, "residual", storage=storage, tol=tol, max_sweeps=40000,
+                 refresh_every=10) as h:
+        z, info = h.solve()
+        mu = float(np.atleast_1d(h.state()["mu"])[0])
+    assert info["status"] == 0, info
+    assert "/cluster" in info["form"], info["form"]
+    assert np.all(z >= inst.lo) and np.all(z <= inst.hi)
+    assert O.kkt(P, z, mu=mu)["kkt"] <= tol * 1.01
 
 
 @pytest.mark.parametrize("storage,form,tol,bound", [

@@ -150,6 +150,9 @@ struct rac_handle {
     void *sp_stage = nullptr;       // per slot: the blocks' staged columns (or NULL)
     size_t sp_sb = 0, sp_slot = 0;  // bytes per block region, per slot
     int sp_nbuf = 0;                // shared-memory buffers of the staged chain
+    int sp_cl = 0, sp_cl_rows = 0;  // cluster chain: CTAs and rows per CTA (0: one-CTA chain)
+    void *sp_cl_stage = nullptr;    // per slot: the blocks' owner-grouped entry records
+    size_t sp_cl_sb = 0, sp_cl_slot = 0;
     std::vector<void *> allocs;
     char form[32] = {0};
 
@@ -321,6 +324,10 @@ static ChainArgs chain_args(rac_handle *h, int slot) {
     a.sp_vals = h->sp_vals;
     a.sp_stage = h->sp_stage ? (char *)h->sp_stage + (size_t)slot * h->sp_slot : nullptr;
     a.sp_stage_bytes = h->sp_sb;
+    a.sp_cl = h->sp_cl;
+    a.sp_cl_rows = h->sp_cl_rows;
+    a.sp_cl_stage = h->sp_cl_stage ? (char *)h->sp_cl_stage + (size_t)slot * h->sp_cl_slot : nullptr;
+    a.sp_cl_bytes = h->sp_cl_sb;
     a.box_ctr = h->box_ctr;
     if (h->boxqp) {
         a.prox = prox_args(h);   // the box chain reads lo and hi there
@@ -442,6 +449,8 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         if (h->boxqp) {
             RAC_CK(launch_box_chain(h->store, a, h->grid, st));
+        } else if (h->sparse && h->sp_cl) {
+            RAC_CK(launch_spcl_chain(a, h->sp_emax, st));
         } else if (h->sparse) {
             RAC_CK(launch_sp_chain(h->store, a, h->sp_emax, h->sp_nbuf, st));
         } else if (h->big && h->rescl) {
@@ -929,7 +938,19 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         // The chain stages each block's columns in shared memory (a block
         // ahead) where two regions fit and the factor writes them per sweep
         // (not for RP, whose factors are computed once)
-        h->sp_nbuf = h->rp ? 0 : sp_stage_buffers(h->store, lay.smax(), h->sp_emax);
+        if (!h->rp && o->chain != 1) {
+            // the cluster chain where it applies (its records are staged by the
+            // factor every sweep, so not for RP, whose factors are computed once)
+            ChainArgs a0 = chain_args(h, 0);
+            h->sp_cl = spcl_size(h->store, a0);
+            if (h->sp_cl) {
+                h->sp_cl_rows = (m + h->sp_cl - 1) / h->sp_cl;
+                h->sp_cl_sb = (spcl_stage_bytes(lay.smax(), h->sp_emax, h->sp_cl) + 255) & ~(size_t)255;
+                h->sp_cl_slot = (size_t)h->p * h->sp_cl_sb;
+                RAC_ST(h->alloc_bytes(&h->sp_cl_stage, (size_t)h->refresh_every * h->sp_cl_slot));
+            }
+        }
+        h->sp_nbuf = (h->rp || h->sp_cl) ? 0 : sp_stage_buffers(h->store, lay.smax(), h->sp_emax);
         if (h->sp_nbuf > 0) {
             h->sp_sb = sp_stage_bytes(h->store, lay.smax(), h->sp_emax);
             h->sp_slot = (size_t)h->p * h->sp_sb;
@@ -996,8 +1017,10 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     std::snprintf(h->form, sizeof(h->form), "%s/%s%s%s%s",
                   h->gram ? "gram" : (h->sparse ? "sparse" : "residual"),
                   h->store == ST_F64 ? "fp64" : (h->store == ST_F32 ? "fp32" : "bf16"),
-                  (h->cluster || h->rescl)
-                      ? ((h->cluster ? h->cluster : h->rescl) == 16 ? "/cluster16" : "/cluster8")
+                  (h->cluster || h->rescl || h->sp_cl)
+                      ? ((h->cluster ? h->cluster : (h->rescl ? h->rescl : h->sp_cl)) == 16
+                             ? "/cluster16"
+                             : "/cluster8")
                       : "",
                   h->rp ? "/rp" : "", h->boxqp ? "/boxqp" : "");
     RAC_ST(set_state(h, o->x0, o->xi0));

@@ -543,4 +543,23 @@ __host__ __device__ inline int assembly_log2_buckets(int n) {
     return L;
 }
 
+
+// ---------------------------------------------------------------- sparse cluster staging
+// One block's region for the sparse chain on a cluster of C CTAs (written by
+// the block factor, read by the chain): the block's columns (s ints), the
+// start of each owner CTA's entries (C + 1 ints, each group padded to an even
+// count so that it starts on 16 bytes), and the entry records, 8 bytes each:
+// x = local row (row - owner base) | column position << 16, y = the value in
+// FP32.  Padding records are zero.
+struct SpClStage {
+    size_t cols, ostart, recs, bytes;
+    __host__ __device__ SpClStage(int smax, long long emax, int C) {
+        auto pad = [](size_t v) { return (v + 15) & ~(size_t)15; };
+        cols = 0;
+        ostart = pad((size_t)smax * 4);
+        recs = ostart + pad((size_t)(C + 1) * 4);
+        bytes = recs + pad((size_t)(emax + C) * 8);
+    }
+};
+
 }  // namespace rac

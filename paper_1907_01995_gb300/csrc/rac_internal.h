@@ -101,6 +101,14 @@ struct ChainArgs {
     const void *sp_vals;    // storage-type values
     void *sp_stage;         // this sweep slot's staging regions (one per block position), or NULL
     size_t sp_stage_bytes;  // bytes of one block's region
+    // sparse form on one cluster (rac_spcluster.cu): C CTAs owning rows
+    // [c sp_cl_rows, (c + 1) sp_cl_rows); per block position a region of
+    // sp_cl_bytes written by the factor (columns, per-owner entry offsets,
+    // 8-byte entry records), or NULL
+    int sp_cl;
+    int sp_cl_rows;
+    void *sp_cl_stage;
+    size_t sp_cl_bytes;
     int dbg_exit_cta;       // k_chain_res: this CTA returns at its start (-1: none), so the
                             // others' bounded barrier waits run out (failure-path testing)
     int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
@@ -233,6 +241,13 @@ cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, con
                              cudaStream_t st);
 cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,
                             cudaStream_t st);
+
+// Sparse form on one thread-block cluster (rac_spcluster.cu): bytes of one
+// block's staging region, the cluster size the chain runs with (0: it does
+// not apply), the launch.
+size_t spcl_stage_bytes(int smax, int64_t emax, int C);
+int spcl_size(int store, const ChainArgs &a);
+cudaError_t launch_spcl_chain(const ChainArgs &a, int64_t emax, cudaStream_t st);
 
 // Residual form, large blocks, on one thread-block cluster (rac_rescluster.cu):
 // the cluster size it runs with here (16, else 8; 0: it does not apply), and

@@ -161,6 +161,47 @@ __global__ void __launch_bounds__(256) k_sp_gram(ChainArgs a, TA *Wout, int64_t 
     if (stg)
         for (int c = threadIdx.x; c <= s; c += blockDim.x) ((int *)(stg + L.starts))[c] = start[c];
     __syncthreads();
+    if (a.sp_cl_stage) {
+        // the cluster chain's region: the block's entries grouped by the CTA
+        // that owns their row (counting pass, padded offsets, scatter)
+        __shared__ int cnt[17], cur[16];
+        const int C = a.sp_cl, rp = a.sp_cl_rows, E = start[s];
+        unsigned char *cst = (unsigned char *)a.sp_cl_stage + (size_t)b * a.sp_cl_bytes;
+        const SpClStage Lc(smax, emax, C);
+        int *ost = (int *)(cst + Lc.ostart);
+        uint2 *rec = (uint2 *)(cst + Lc.recs);
+        if ((int)threadIdx.x < C) cnt[threadIdx.x] = 0;
+        for (int c = threadIdx.x; c < s; c += blockDim.x) ((int *)(cst + Lc.cols))[c] = a.perm[off + c];
+        __syncthreads();
+        for (int e = threadIdx.x; e < E; e += blockDim.x) atomicAdd(&cnt[min(rows[e] / rp, C - 1)], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int k = 0; k < C; ++k) {
+                ost[k] = acc;
+                cur[k] = acc;
+                acc += (cnt[k] + 1) & ~1;
+            }
+            ost[C] = acc;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < C && (cnt[threadIdx.x] & 1))
+            rec[cur[threadIdx.x] + cnt[threadIdx.x]] = make_uint2(0u, 0u);   // padding record
+        __syncthreads();
+        for (int c = warp; c < s; c += nw) {
+            const int64_t k0 = a.sp_colptr[a.perm[off + c]];
+            for (int t = lane; t < start[c + 1] - start[c]; t += 32) {
+                const int row = rows[start[c] + t];
+                const int k = min(row / rp, C - 1);
+                const int pos = atomicAdd(&cur[k], 1);
+                float v;
+                if constexpr (sizeof(TS) == 8) v = (float)vs[k0 + t];
+                else v = (float)sp_val<TS>(vs, k0 + t);
+                rec[pos] = make_uint2((unsigned)(row - k * rp) | ((unsigned)c << 16), __float_as_uint(v));
+            }
+        }
+        __syncthreads();
+    }
     // pairs (u, v), u >= v, by a running index over the lower triangle
     TA *K = Wout + lay.factor_offset(b);
     const int npairs = s * (s + 1) / 2;

@@ -54,23 +54,51 @@ def test_sparse_fp64_iterates_match_oracle(name, assembly):
                 assert rel(st[key], getattr(ost, key)) <= 1e-10, (k, key)
 
 
+@pytest.mark.parametrize("chain", ["auto", "grid"])
 @pytest.mark.parametrize("storage,tol,bound", [("fp64", 1e-10, 1e-8), ("fp32", 1e-9, 1e-5),
                                                ("bf16", 1e-7, 1e-3)])
-def test_sparse_converged_matches_coordinate_descent(storage, tol, bound):
+def test_sparse_converged_matches_coordinate_descent(storage, tol, bound, chain):
+    """FP64 storage runs the one-CTA chain; FP32 / BF16 run the one-cluster
+    chain (auto) or the one-CTA chain (grid)."""
     inst = synth.sparse_en_instance(7, m=600, n=3000, density=0.02, nnz_frac=0.02,
                                     lam_frac=0.1, lam2=0.05, block=100)
     Ad = inst.A.toarray()
     ref = O.cd_enet(Ad, inst.b, inst.lam1, inst.lam2, tol=1e-13)
     with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=inst.lam1, lambda2=inst.lam2,
                     num_blocks=inst.num_blocks, tol=tol, max_sweeps=20000, refresh_every=10,
-                    storage=storage) as h:
+                    storage=storage, chain=chain) as h:
         z, info = h.solve()
     assert info["status"] == 0, info
     assert info["form"].startswith("sparse/" + storage)
+    assert ("/cluster" in info["form"]) == (chain == "auto" and storage != "fp64"), info["form"]
     assert rel(z, ref) <= bound, rel(z, ref)
     assert np.array_equal(z != 0, ref != 0)
     P = O.problem_from_data(Ad, inst.b, "l1l2", inst.lam1, inst.lam2)
     assert O.kkt(P, z)["kkt"] <= tol * 1.01 + 1e-15
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_sparse_cluster_chain_with_coupling_row_and_ragged_blocks(storage):
+    """A box QP with one coupling row on a sparse design, blocks of 61 and 60
+    (ragged), m not a multiple of the cluster's row split: the one-cluster
+    chain converges to a point the oracle's KKT measure certifies."""
+    rng = np.random.default_rng(4)
+    m, n = 1003, 2441
+    A = sp.random(m, n, density=0.03, random_state=5, format="csc")
+    A.data = rng.normal(size=A.nnz)
+    b = rng.normal(size=m)
+    e = rng.choice([-1.0, 1.0], size=n)
+    tol = 1e-9 if storage == "fp32" else 1e-7
+    with api.Handle(A, b, E=e, d=np.zeros(1), phi="box", lo=0.0, hi=0.5, num_blocks=40,
+                    beta=1.0, gamma=1.0, tol=tol, max_sweeps=40000, refresh_every=10,
+                    storage=storage) as h:
+        z, info = h.solve()
+        mu = float(np.atleast_1d(h.state()["mu"])[0])
+    assert info["status"] == 0, info
+    assert "/cluster" in info["form"], info["form"]
+    P = O.problem_from_data(A.toarray(), b, "box", lo=0.0, hi=0.5, E=e, d=np.zeros(1))
+    assert np.all(z >= 0.0) and np.all(z <= 0.5)
+    assert O.kkt(P, z, mu=mu)["kkt"] <= tol * 1.01
 
 
 def test_sparse_matches_dense_form():

@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--en-once", type=int, default=0, metavar="K",
                     help="run K BF16 solves of the Elastic-Net 2000x50000 (--assembly rac or "
                          "rp) and exit (no timing; a fixed command to profile)")
+    ap.add_argument("--ws-config5", type=int, nargs=2, default=None, metavar=("TRAIN", "TEST"),
+                    help="learned warm start at the family's stated size: train on TRAIN "
+                         "generated instances (4096 as specified), measure sweeps and time to "
+                         "KKT <= 1e-6 cold and warm on TEST held-out ones (512), print one JSON "
+                         "line and exit")
     ap.add_argument("--path-once", type=int, default=0, metavar="K",
                     help="run K batched BF16 solves of the 64-point regularisation path "
                          "20000x5000 and exit (no timing; a fixed command to profile)")
@@ -402,6 +407,101 @@ def en_once(k, assembly):
     return 0
 
 
+def _ws_instance(args):
+    """One member of the warm-start family (host, numpy): a worker's job."""
+    import synth
+    seed, kw = args
+    inst = synth.warmstart_instance(seed, **kw, block=100)
+    # sent as FP32 (half the bytes through the pool's pipe); the instance is
+    # this matrix, solved in FP64
+    import numpy as np
+    return np.asfortranarray(inst.A, dtype=np.float32), inst.b, inst.lam1, inst.lam2, inst.num_blocks
+
+
+def ws_config5(ntrain, ntest):
+    """The learned warm start (form 4) on its family at the stated size: the
+    plain solver's solutions of ntrain generated instances are the training
+    targets; the network's warm start is then compared with the cold start on
+    ntest held-out instances, both to KKT <= 1e-6 (sweeps and device time per
+    solve).  The instances are generated on the host by a process pool
+    (spawn, started before the first CUDA call) and streamed to the GPU."""
+    import multiprocessing as mp
+    import time
+
+    import numpy as np
+
+    import synth
+    fam_train = synth.warmstart_family(0, ntrain)
+    fam_test = synth.warmstart_family(100000, ntest)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        import torch
+
+        from paper_1907_01995_gb300 import api
+        from paper_1907_01995_gb300 import warmstart as ws
+        t0 = time.time()
+        Fs, Ts = [], []
+        for A, b, lam1, lam2, p in pool.imap(_ws_instance, fam_train, chunksize=4):
+            Ad = torch.tensor(A, dtype=torch.float64, device="cuda").t().contiguous().t()
+            bd = torch.tensor(b, device="cuda")
+            with api.Handle(Ad, bd, phi="l1l2", lambda1=lam1, lambda2=lam2, num_blocks=p,
+                            tol=1e-9, max_sweeps=20000, storage="bf16") as h:
+                x, _ = h.solve()
+            Fx, T, _ = ws.features(Ad, bd, lam1, lam2, torch.tensor(x, device="cuda"))
+            Fs.append(Fx)
+            Ts.append(T)
+        t_targets = time.time() - t0
+        Fx, T = torch.cat(Fs), torch.cat(Ts)
+        del Fs, Ts
+        params = ws.init_params(0)
+        tr = ws.Trainer(params, lr=3e-3)
+        t1 = time.time()
+        hist = tr.fit(Fx, T, epochs=8, batch=8192)
+        torch.cuda.synchronize()
+        t_train = time.time() - t1
+        ncoord = int(Fx.shape[0])
+        del Fx, T
+        cold, warm, tcold, twarm, rejected = [], [], [], [], 0
+        for A, b, lam1, lam2, p in pool.imap(_ws_instance, fam_test, chunksize=4):
+            Ad = torch.tensor(A, dtype=torch.float64, device="cuda").t().contiguous().t()
+            bd = torch.tensor(b, device="cuda")
+            kw = dict(phi="l1l2", lambda1=lam1, lambda2=lam2, num_blocks=p, tol=1e-6,
+                      max_sweeps=20000, refresh_every=1, storage="bf16")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            with api.Handle(Ad, bd, **kw) as h:
+                _, ic = h.solve()
+            e1.record()
+            torch.cuda.synchronize()
+            tcold.append(e0.elapsed_time(e1))
+            torch.cuda.synchronize()
+            e0.record()
+            x0 = ws.predict(Ad, bd, lam1, lam2, params)
+            with api.Handle(Ad, bd, x0=x0, xi0_from_grad=1, ws_fallback=True, **kw) as h:
+                _, iw = h.solve()
+            e1.record()
+            torch.cuda.synchronize()
+            twarm.append(e0.elapsed_time(e1))
+            if ic["status"] != 0 or iw["status"] != 0:
+                raise RuntimeError("a held-out solve missed KKT 1e-6: %s %s" % (ic, iw))
+            cold.append(ic["sweeps"])
+            warm.append(iw["sweeps"])
+            rejected += iw["warm_start_rejected"]
+    print(json.dumps({
+        "ws_config5": {"train_instances": ntrain, "test_instances": ntest,
+                       "training_coordinates": ncoord, "epochs": len(hist),
+                       "loss_first": hist[0], "loss_last": hist[-1],
+                       "targets_s": t_targets, "train_s": t_train, "tol": 1e-6,
+                       "sweeps_cold_mean": float(np.mean(cold)),
+                       "sweeps_warm_mean": float(np.mean(warm)),
+                       "ms_cold_mean": float(np.mean(tcold)), "ms_warm_mean": float(np.mean(twarm)),
+                       "sweep_gain": float(np.mean(cold) / np.mean(warm)),
+                       "time_gain": float(np.mean(tcold) / np.mean(twarm)),
+                       "warm_starts_rejected": rejected}}), flush=True)
+    return 0
+
+
 def path_once(k):
     """K batched BF16 solves of the 64-point path (profiling entry)."""
     import torch
@@ -683,6 +783,8 @@ def main():
         return path_once(args.path_once)
     if args.en_once:
         return en_once(args.en_once, args.assembly)
+    if args.ws_config5:
+        return ws_config5(*args.ws_config5)
     if args.rbf_once:
         return rbf_once(args.rbf_once, args.rbf_n)
     import numpy as np

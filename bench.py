@@ -60,6 +60,9 @@ def parse():
                          "generated instances (4096 as specified), measure sweeps and time to "
                          "KKT <= 1e-6 cold and warm on TEST held-out ones (512), print one JSON "
                          "line and exit")
+    ap.add_argument("--sparse-once", type=int, default=0, metavar="SWEEPS",
+                    help="one BF16 solve of the sparse Elastic-Net 20000x100000 workload for "
+                         "SWEEPS sweeps and exit (no timing; a fixed command to profile)")
     ap.add_argument("--path-once", type=int, default=0, metavar="K",
                     help="run K batched BF16 solves of the 64-point regularisation path "
                          "20000x5000 and exit (no timing; a fixed command to profile)")
@@ -502,6 +505,25 @@ def ws_config5(ntrain, ntest):
     return 0
 
 
+def sparse_once(sweeps):
+    """One BF16 solve of the sparse Elastic-Net workload for a fixed number of
+    sweeps (profiling entry)."""
+    import torch
+
+    import synth
+    from paper_1907_01995_gb300 import api
+    w = SPARSE_WORKLOAD
+    inst = synth.sparse_en_instance(0, m=w["m"], n=w["n"], density=w["density"],
+                                    nnz_frac=0.01, lam_frac=0.1, lam2=0.1, block=w["block"])
+    with api.Handle(inst.A, inst.b, phi="l1l2", lambda1=inst.lam1, lambda2=0.1,
+                    num_blocks=inst.num_blocks, tol=0.0, max_sweeps=sweeps,
+                    refresh_every=w["refresh_every"], storage="bf16") as h:
+        _, info = h.solve()
+    torch.cuda.synchronize()
+    print(json.dumps({"sparse_once": sweeps, "form": info["form"], "kkt": info["kkt"]}), flush=True)
+    return 0
+
+
 def path_once(k):
     """K batched BF16 solves of the 64-point path (profiling entry)."""
     import torch
@@ -785,6 +807,8 @@ def main():
         return en_once(args.en_once, args.assembly)
     if args.ws_config5:
         return ws_config5(*args.ws_config5)
+    if args.sparse_once:
+        return sparse_once(args.sparse_once)
     if args.rbf_once:
         return rbf_once(args.rbf_once, args.rbf_n)
     import numpy as np

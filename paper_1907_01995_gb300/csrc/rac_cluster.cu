@@ -490,6 +490,13 @@ template <class TS, int NK>
 static cudaError_t cluster_launch_nk(const ChainArgs &a, int C, cudaStream_t st) {
     BlockLayout lay(a.n, a.p);
     const size_t smem = ClLayout(a.n, lay.smax(), C).total;
+    // the kernel's attributes are set here, not only when its fit was checked:
+    // they belong to the kernel, and handles of other sizes may have changed them
+    auto kern = k_chain_cluster<TS, NK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kClThreads);
@@ -526,9 +533,13 @@ static int cluster_pick(int n, int smax) {
 }
 
 int cluster_chain_size(int store, int n, int smax) {
-    if (store == ST_F32) return cluster_pick<float>(n, smax);
-    if (store == ST_BF16) return cluster_pick<__nv_bfloat16>(n, smax);
-    return 0;
+    long long v = 0;
+    if (memo_get(1, store, n, smax, &v)) return (int)v;
+    int r = 0;
+    if (store == ST_F32) r = cluster_pick<float>(n, smax);
+    else if (store == ST_BF16) r = cluster_pick<__nv_bfloat16>(n, smax);
+    memo_put(1, store, n, smax, r);
+    return r;
 }
 
 template <class TS>

@@ -242,6 +242,11 @@ cudaError_t launch_sp_anchor(int store, int m, int n, const int64_t *colptr, con
 cudaError_t launch_sp_colsq(int n, const int64_t *colptr, const double *vals, double *out,
                             cudaStream_t st);
 
+// Process-wide memo of device capability queries (rac_runtime.cu), keyed by
+// the current device, a query id and three arguments.
+bool memo_get(int fid, long long a, long long b, long long c, long long *v);
+void memo_put(int fid, long long a, long long b, long long c, long long v);
+
 // Sparse form on one thread-block cluster (rac_spcluster.cu): bytes of one
 // block's staging region, the cluster size the chain runs with (0: it does
 // not apply), the launch.

@@ -1231,11 +1231,24 @@ static int chain_grid_impl(int smax, int stage, int stage_p, int lookahead, int 
 
 int chain_max_grid(int store, bool gram, int smax, int stage, int stage_p, int lookahead,
                    int nperm, size_t *smem_out) {
-#define RAC_CG(TS, TA, GR) chain_grid_impl<TS, TA, GR>(smax, stage, stage_p, lookahead, nperm, smem_out)
-    if (store == ST_F64) return gram ? RAC_CG(double, double, true) : RAC_CG(double, double, false);
-    if (store == ST_F32) return gram ? RAC_CG(float, float, true) : RAC_CG(float, float, false);
-    return gram ? RAC_CG(__nv_bfloat16, float, true) : RAC_CG(__nv_bfloat16, float, false);
+    const long long a = store | (gram ? 16 : 0) | (stage ? 32 : 0) | (stage_p ? 64 : 0) |
+                        (lookahead ? 128 : 0);
+    long long g = 0, sm = 0;
+    if (memo_get(2, a, smax, nperm, &g) && memo_get(3, a, smax, nperm, &sm)) {
+        if (smem_out) *smem_out = (size_t)sm;
+        return (int)g;
+    }
+    size_t smem = 0;
+    int r;
+#define RAC_CG(TS, TA, GR) chain_grid_impl<TS, TA, GR>(smax, stage, stage_p, lookahead, nperm, &smem)
+    if (store == ST_F64) r = gram ? RAC_CG(double, double, true) : RAC_CG(double, double, false);
+    else if (store == ST_F32) r = gram ? RAC_CG(float, float, true) : RAC_CG(float, float, false);
+    else r = gram ? RAC_CG(__nv_bfloat16, float, true) : RAC_CG(__nv_bfloat16, float, false);
 #undef RAC_CG
+    memo_put(2, a, smax, nperm, r);
+    memo_put(3, a, smax, nperm, (long long)smem);
+    if (smem_out) *smem_out = smem;
+    return r;
 }
 
 // Staging K^{-1} (and P) needs two buffers each in shared memory.

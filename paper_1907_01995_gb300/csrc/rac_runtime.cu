@@ -13,6 +13,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "rac_internal.h"
@@ -119,6 +120,28 @@ void runtime_give_streams(StreamSet *ss) {
     }
     std::lock_guard<std::mutex> lock(g_mu);
     g_dev[ss->dev].idle.push_back(ss);
+}
+
+// Memo of device capability queries (occupancy, cluster co-residency):
+// their answers depend only on the current device and the arguments, and the
+// driver calls behind them cost tens of microseconds per handle setup.
+static std::mutex g_memo_mu;
+static std::map<std::tuple<int, int, long long, long long, long long>, long long> g_memo;
+
+bool memo_get(int fid, long long a, long long b, long long c, long long *v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_memo_mu);
+    auto it = g_memo.find(std::make_tuple(dev, fid, a, b, c));
+    if (it == g_memo.end()) return false;
+    *v = it->second;
+    return true;
+}
+void memo_put(int fid, long long a, long long b, long long c, long long v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_memo_mu);
+    g_memo[std::make_tuple(dev, fid, a, b, c)] = v;
 }
 
 }  // namespace rac

@@ -672,7 +672,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(enter(h));
     cudaStream_t st = h->st;
     const int m = h->m, n = h->n;
+    // the device error word first: the setup's own bounded waits (the
+    // tensor-core Gram build) report through it
+    RAC_ST(h->alloc(&h->err, 1));
+    RAC_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     // FP64 copies of the data
+    bool gram_built = false;   // G~ written while copying A (below)
     if (h->sparse) {
         // compressed columns: check the column starts on the host and the row
         // indices on the device before any kernel indexes by them
@@ -723,9 +728,25 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         }
     } else if (h->has_A) {
         RAC_ST(h->alloc(&h->A64, (size_t)m * n));
-        RAC_CK(cudaMemcpy2DAsync(h->A64, (size_t)m * sizeof(double), pr->A,
-                                 (size_t)pr->lda * sizeof(double), (size_t)m * sizeof(double), n,
-                                 cudaMemcpyDefault, st));
+        // BF16 Gram storage of a device-resident A: the FP64 copy is written by
+        // the pass that converts A for the tensor-core Gram build, at once
+        cudaPointerAttributes pa;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (h->gram && h->store == ST_BF16 && cudaPointerGetAttributes(&pa, pr->A) == cudaSuccess &&
+            (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) &&
+            pa.device == cur) {
+            RAC_ST(h->alloc_bytes((void **)&h->G, (size_t)n * n * store_bytes(h->store)));
+            RAC_CK(launch_gram_build_tc(m, n, pr->A, pr->lda, h->G, h->err, st, h->A64));
+            h->nlaunch += 2;
+            gram_built = true;
+        } else if (pr->lda == m)
+            RAC_CK(cudaMemcpyAsync(h->A64, pr->A, (size_t)m * n * sizeof(double),
+                                   cudaMemcpyDefault, st));
+        else
+            RAC_CK(cudaMemcpy2DAsync(h->A64, (size_t)m * sizeof(double), pr->A,
+                                     (size_t)pr->lda * sizeof(double), (size_t)m * sizeof(double),
+                                     n, cudaMemcpyDefault, st));
         RAC_ST(h->alloc(&h->b64, m));
         if (pr->b) {
             RAC_ST(copy_in(h->b64, pr->b, m, st));
@@ -734,8 +755,8 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         }
     } else {
         RAC_ST(h->alloc(&h->H64, (size_t)n * n));
-        RAC_CK(cudaMemcpy2DAsync(h->H64, (size_t)n * sizeof(double), pr->H, (size_t)n * sizeof(double),
-                                 (size_t)n * sizeof(double), n, cudaMemcpyDefault, st));
+        RAC_CK(cudaMemcpyAsync(h->H64, pr->H, (size_t)n * n * sizeof(double), cudaMemcpyDefault,
+                               st));
     }
     if (pr->c) {
         RAC_ST(h->alloc(&h->c64, n));
@@ -768,7 +789,6 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     RAC_ST(h->alloc(&h->gz, n));
     RAC_ST(h->alloc(&h->mu, std::max(1, h->k)));
     RAC_ST(h->alloc(&h->t, std::max(1, h->k)));
-    RAC_ST(h->alloc(&h->err, 1));
     RAC_ST(h->alloc(&h->stats, 1));
     RAC_ST(h->alloc(&h->bar, 1));
     RAC_ST(h->alloc(&h->sweep_dev, 1));
@@ -791,12 +811,17 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         h->nchunk = std::max(h->nchunk, resid_min_chunks(n));
         RAC_ST(h->alloc(&h->rpart, (size_t)h->nchunk * m));
     }
-    // the scale of the KKT measure: max(1, ||grad at 0||_inf)
+    // the scale of the KKT measure: max(1, ||grad at 0||_inf).  A cold start
+    // without folded rows takes it from the refresh that set_state enqueues,
+    // which evaluates exactly the gradient at z = 0 into gz.
+    const bool g0_from_refresh = !o->x0 && !h->fold && (h->sparse || h->has_A);
     {
         // gradient at z = 0 and its statistics, read back after the final sync
         h->ss->h_aux[0] = h->ss->h_aux[1] = 0.0;
         const double *g0 = nullptr;
-        if (h->sparse) {
+        if (g0_from_refresh) {
+            // (below, after set_state)
+        } else if (h->sparse) {
             RAC_CK(cudaMemsetAsync(h->z, 0, n * sizeof(double), st));
             h->nlaunch += 3;
             RAC_CK(launch_sp_resid_f64(m, n, h->sp_colptr, h->sp_rowidx, h->sp_vals64, h->z,
@@ -842,10 +867,12 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     }
     // storage-precision copy for the sweeps
     const size_t sb = store_bytes(h->store);
-    h->nlaunch += 1;
+    if (!gram_built) h->nlaunch += 1;
     if (h->gram) {
-        RAC_ST(h->alloc_bytes((void **)&h->G, (size_t)n * n * sb));
-        if (h->has_A) {
+        if (gram_built) {
+            // (written with the FP64 copy of A)
+        } else if (h->has_A) {
+            RAC_ST(h->alloc_bytes((void **)&h->G, (size_t)n * n * sb));
             if (h->store == ST_F64) {
                 RAC_CK(launch_gram_build(h->store, m, n, h->A64, m, h->G, st));
             } else {
@@ -856,6 +883,7 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
                     RAC_CK(launch_gram_build_mma(h->store, m, n, h->A64, m, h->G, st));
             }
         } else {
+            RAC_ST(h->alloc_bytes((void **)&h->G, (size_t)n * n * sb));
             RAC_CK(launch_sym_convert(h->store, n, h->H64, h->G, st));
         }
         if (h->fold) {   // the coupling rows' beta E^T E, once
@@ -1023,8 +1051,17 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
                              : "/cluster8")
                       : "",
                   h->rp ? "/rp" : "", h->boxqp ? "/boxqp" : "");
+    *h->h_err = 0;
+    RAC_CK(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     RAC_ST(set_state(h, o->x0, o->xi0));
+    if (g0_from_refresh) {
+        h->nlaunch += 1;
+        RAC_CK(launch_kkt_zero(n, h->gz, h->phi, h->lam1, h->lo, h->hi, h->kpart, st));
+        RAC_CK(cudaMemcpyAsync(h->ss->h_aux, h->kpart, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+    }
     RAC_CK(cudaStreamSynchronize(st));
+    if (*h->h_err) return (rac_status)*h->h_err;   // a setup kernel's bounded wait expired
     h->kkt_scale = std::max(1.0, h->ss->h_aux[0]);
     h->kkt_cold0 = h->ss->h_aux[1] / h->kkt_scale;
     h->setup_launches = h->nlaunch;

@@ -40,6 +40,57 @@ __global__ void k_pad_convert(int m, int n, int mp, int np, const double *__rest
     Ac[t] = from_d<TS>(r < m && c < n ? A[(size_t)c * lda + r] : 0.0);
 }
 
+// The tensor-core Gram's operand and, in the same pass, the FP64 copy that
+// the exact refreshes read: thread t of column c takes rows 4 t .. 4 t + 3
+// (mp is a multiple of 64), writes them as four BF16 values to Ac (ld = mp,
+// zeros past m and n) and, when A64 is given, as FP64 to A64 (ld = m).  With
+// an even lda and m and 16-byte aligned bases the rows go as 16-byte pairs
+// (a pair is then wholly inside or wholly past m).
+__global__ void k_copy_convert_bf16(int m, int n, int mp, int np, const double *__restrict__ A,
+                                    int64_t lda, __nv_bfloat16 *__restrict__ Ac,
+                                    double *__restrict__ A64, int vec) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = mp / 4;
+    if (t >= (int64_t)q * np) return;
+    const int c = (int)(t / q), r0 = 4 * (int)(t % q);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (c < n) {
+        const double *ac = A + (size_t)c * lda;
+        if (vec) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (r0 + 2 * h < m) {
+                    const double2 w = __ldcs(reinterpret_cast<const double2 *>(ac + r0 + 2 * h));
+                    v[2 * h] = w.x;
+                    v[2 * h + 1] = w.y;
+                }
+            if (A64) {
+                double *oc = A64 + (size_t)c * m;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (r0 + 2 * h < m)
+                        __stcs(reinterpret_cast<double2 *>(oc + r0 + 2 * h),
+                               make_double2(v[2 * h], v[2 * h + 1]));
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                if (r0 + h < m) v[h] = ac[r0 + h];
+            if (A64) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                    if (r0 + h < m) A64[(size_t)c * m + r0 + h] = v[h];
+            }
+        }
+    }
+    __nv_bfloat162 lo2 = __floats2bfloat162_rn((float)v[0], (float)v[1]);
+    __nv_bfloat162 hi2 = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+    uint2 packed;
+    packed.x = *reinterpret_cast<uint32_t *>(&lo2);
+    packed.y = *reinterpret_cast<uint32_t *>(&hi2);
+    *reinterpret_cast<uint2 *>(Ac + (size_t)c * mp + r0) = packed;
+}
+
 __device__ __forceinline__ uint32_t f2tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -425,7 +476,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 cudaError_t launch_gram_build_tc(int m, int n, const double *A, int64_t lda, void *G, int *err,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, double *A64_out) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) return cudaErrorNotSupported;
     const int mp = (m + TC_K - 1) / TC_K * TC_K, np = (n + TC_T - 1) / TC_T * TC_T;
@@ -435,9 +486,11 @@ cudaError_t launch_gram_build_tc(int m, int n, const double *A, int64_t lda, voi
     void *Ac = nullptr;
     e = cudaMallocFromPoolAsync(&Ac, (size_t)mp * np * 2, pool, st);
     if (e != cudaSuccess) return e;
-    const int64_t tot = (int64_t)mp * np;
-    k_pad_convert<__nv_bfloat16><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-        m, n, mp, np, A, lda, (__nv_bfloat16 *)Ac);
+    const int64_t tot = (int64_t)(mp / 4) * np;
+    const int vec = (lda % 2 == 0 && m % 2 == 0 && ((uintptr_t)A & 15) == 0 &&
+                     ((uintptr_t)A64_out & 15) == 0) ? 1 : 0;
+    k_copy_convert_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+        m, n, mp, np, A, lda, (__nv_bfloat16 *)Ac, A64_out, vec);
     CUtensorMap map;
     const cuuint64_t dims[2] = {(cuuint64_t)mp, (cuuint64_t)np};
     const cuuint64_t strides[1] = {(cuuint64_t)mp * 2};

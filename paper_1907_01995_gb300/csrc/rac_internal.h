@@ -323,8 +323,9 @@ cudaError_t launch_gram_build(int store, int m, int n, const double *A, int64_t 
 cudaError_t launch_sym_convert(int store, int n, const double *H, void *G, cudaStream_t st);
 // tensor-core Gram build for FP32 (three-term TF32) and BF16 storage
 // BF16 storage on tcgen05 (err: device status word for its bounded waits)
+// (A64_out, when given, receives the FP64 copy of A, ld = m, in the same pass)
 cudaError_t launch_gram_build_tc(int m, int n, const double *A, int64_t lda, void *G, int *err,
-                                 cudaStream_t st);
+                                 cudaStream_t st, double *A64_out = nullptr);
 cudaError_t launch_gram_build_mma(int store, int m, int n, const double *A, int64_t lda, void *G,
                                   cudaStream_t st);
 cudaError_t launch_to_slab(int store, int m, int n, const double *A, int64_t lda, int R,

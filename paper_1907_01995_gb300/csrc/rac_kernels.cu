@@ -1380,57 +1380,98 @@ cudaError_t launch_resid_f64(int m, int n, const double *A, int64_t lda, const d
     return cudaGetLastError();
 }
 
-// g_j = A_j^T r + c_j : one warp per column.  With an even leading dimension
-// each lane reads 16-byte pairs of rows, 8 pairs per step into independent
-// accumulators (summed in a fixed order), so a warp keeps 4 KB of its column
-// in flight; r is read through the read-only cache.
+// g_j = A_j^T r + c_j : WPC warps per column (a CTA of 8 warps takes 8 / WPC
+// columns).  With an even leading dimension each lane reads 16-byte pairs of
+// rows, 8 pairs per step into independent accumulators, so a warp keeps 4 KB
+// of its column in flight; warp s of a column takes the pair groups s, s +
+// WPC, ...  The warps' partial sums are added in warp order (deterministic);
+// r is read through the read-only cache.  WPC is chosen on the host so that a
+// few waves of CTAs cover the SMs when n alone would leave them idle.
 constexpr int kGemvtUnroll = 8;
+template <int WPC>
 __global__ void __launch_bounds__(256) k_gemvt_f64(int m, int n, const double *__restrict__ A,
                                                    int64_t lda, const double *__restrict__ r,
                                                    const double *c, double *g) {
-    const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= n) return;
-    const double *aj = A + (size_t)j * lda;
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = warp % WPC;
+    const int j = blockIdx.x * (8 / WPC) + warp / WPC;
     double acc[kGemvtUnroll];
 #pragma unroll
     for (int u = 0; u < kGemvtUnroll; ++u) acc[u] = 0.0;
-    int i0 = 0;
-    if ((lda & 1) == 0 && (((uintptr_t)A) & 15) == 0) {
-        // pairs of rows: pair k covers rows 2k, 2k + 1; lane takes pairs lane + 32 t
-        const int npair = m >> 1;
-        const double2 *a2 = reinterpret_cast<const double2 *>(aj);
-        const double2 *r2 = reinterpret_cast<const double2 *>(r);
-        const bool r_al = (((uintptr_t)r) & 15) == 0;
-        int k = lane;
-        for (; k + 32 * (kGemvtUnroll - 1) < npair; k += 32 * kGemvtUnroll) {
-            double2 av[kGemvtUnroll], rv[kGemvtUnroll];
+    if (j < n) {
+        const double *aj = A + (size_t)j * lda;
+        int i0 = 0;
+        if ((lda & 1) == 0 && (((uintptr_t)A) & 15) == 0) {
+            // pairs of rows: pair k covers rows 2k, 2k + 1
+            const int npair = m >> 1;
+            const double2 *a2 = reinterpret_cast<const double2 *>(aj);
+            const double2 *r2 = reinterpret_cast<const double2 *>(r);
+            const bool r_al = (((uintptr_t)r) & 15) == 0;
+            // whole groups of 32 x 8 pairs: group q goes to warp q mod WPC
+            const int ngroup = npair / (32 * kGemvtUnroll);
+            for (int q = sub; q < ngroup; q += WPC) {
+                const int k = q * 32 * kGemvtUnroll + lane;
+                double2 av[kGemvtUnroll], rv[kGemvtUnroll];
 #pragma unroll
-            for (int u = 0; u < kGemvtUnroll; ++u) av[u] = __ldcs(a2 + k + 32 * u);
+                for (int u = 0; u < kGemvtUnroll; ++u) av[u] = __ldcs(a2 + k + 32 * u);
 #pragma unroll
-            for (int u = 0; u < kGemvtUnroll; ++u)
-                rv[u] = r_al ? __ldg(r2 + k + 32 * u)
-                             : make_double2(__ldg(r + 2 * (k + 32 * u)), __ldg(r + 2 * (k + 32 * u) + 1));
+                for (int u = 0; u < kGemvtUnroll; ++u)
+                    rv[u] = r_al ? __ldg(r2 + k + 32 * u)
+                                 : make_double2(__ldg(r + 2 * (k + 32 * u)),
+                                                __ldg(r + 2 * (k + 32 * u) + 1));
 #pragma unroll
-            for (int u = 0; u < kGemvtUnroll; ++u)
-                acc[u] = fma(av[u].y, rv[u].y, fma(av[u].x, rv[u].x, acc[u]));
+                for (int u = 0; u < kGemvtUnroll; ++u)
+                    acc[u] = fma(av[u].y, rv[u].y, fma(av[u].x, rv[u].x, acc[u]));
+            }
+            // the ragged pairs after the last full group of the column
+            const int kfull = ngroup * 32 * kGemvtUnroll;
+            for (int kk = kfull + lane + 32 * sub; kk < npair; kk += 32 * WPC) {
+                const double2 av = __ldcs(a2 + kk);
+                acc[0] = fma(av.y, __ldg(r + 2 * kk + 1), fma(av.x, __ldg(r + 2 * kk), acc[0]));
+            }
+            i0 = 2 * npair;   // an odd last row is taken below
         }
-        for (; k < npair; k += 32) {
-            const double2 av = __ldcs(a2 + k);
-            acc[0] = fma(av.y, __ldg(r + 2 * k + 1), fma(av.x, __ldg(r + 2 * k), acc[0]));
-        }
-        i0 = 2 * npair;   // an odd last row is taken below
+        for (int i = i0 + lane + 32 * sub; i < m; i += 32 * WPC) acc[1] = fma(aj[i], __ldg(r + i), acc[1]);
     }
-    for (int i = i0 + lane; i < m; i += 32) acc[1] = fma(aj[i], __ldg(r + i), acc[1]);
     double tot = 0.0;
 #pragma unroll
     for (int u = 0; u < kGemvtUnroll; ++u) tot += acc[u];
     tot = warp_sum(tot);
-    if (lane == 0) g[j] = tot + (c ? c[j] : 0.0);
+    if (WPC == 1) {
+        if (lane == 0 && j < n) g[j] = tot + (c ? c[j] : 0.0);
+        return;
+    }
+    if (lane == 0) red[warp] = tot;
+    __syncthreads();
+    if (sub == 0 && lane == 0 && j < n) {
+        double s = red[warp];
+#pragma unroll
+        for (int w = 1; w < WPC; ++w) s += red[warp + w];
+        g[j] = s + (c ? c[j] : 0.0);
+    }
+}
+int gemvt_warps_per_column(int m, int n) {
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // a full group of pairs per warp at least; 4 CTAs of 8 warps per SM wanted
+    int wpc = 1;
+    while (wpc < 8 && (int64_t)(m / 2) >= (int64_t)2 * wpc * 32 * kGemvtUnroll &&
+           ((int64_t)n * wpc + 7) / 8 < (int64_t)4 * sms)
+        wpc *= 2;
+    return wpc;
 }
 cudaError_t launch_gemvt_f64(int m, int n, const double *A, int64_t lda, const double *r,
                              const double *c, double *g, cudaStream_t st) {
-    k_gemvt_f64<<<(n + 7) / 8, 256, 0, st>>>(m, n, A, lda, r, c, g);
+    const int wpc = gemvt_warps_per_column(m, n);
+    const unsigned grid = (unsigned)(((int64_t)n * wpc + 7) / 8);
+    switch (wpc) {
+    case 1: k_gemvt_f64<1><<<grid, 256, 0, st>>>(m, n, A, lda, r, c, g); break;
+    case 2: k_gemvt_f64<2><<<grid, 256, 0, st>>>(m, n, A, lda, r, c, g); break;
+    case 4: k_gemvt_f64<4><<<grid, 256, 0, st>>>(m, n, A, lda, r, c, g); break;
+    default: k_gemvt_f64<8><<<grid, 256, 0, st>>>(m, n, A, lda, r, c, g); break;
+    }
     return cudaGetLastError();
 }
 // Dual start consistent with the signs of x0 (see rac_options.xi0_from_grad = 2).
@@ -1465,8 +1506,7 @@ cudaError_t launch_colsq_f64(int m, int n, const double *A, int64_t lda, double 
 cudaError_t launch_symv_f64(int n, const double *H, const double *z, const double *c, double *g,
                             cudaStream_t st) {
     // symmetric H: row j is column j
-    k_gemvt_f64<<<(n + 7) / 8, 256, 0, st>>>(n, n, H, n, z, c, g);
-    return cudaGetLastError();
+    return launch_gemvt_f64(n, n, H, n, z, c, g, st);
 }
 
 // KKT reduction on z in two fixed-order stages: kKktParts CTAs reduce

@@ -269,6 +269,35 @@ def test_device_inputs_and_outputs():
     assert np.array_equal(out.cpu().numpy(), z)
 
 
+@pytest.mark.parametrize("m,ldpad", [(600, 0), (601, 0), (600, 2), (600, 3)])
+def test_bf16_gram_device_A_copy_and_conversion_in_one_pass(m, ldpad):
+    """A device-resident A in the BF16 Gram form is copied to FP64 and rounded
+    for the tensor-core Gram build in one pass (paired rows for even m and
+    lda, single rows otherwise); a host A is copied first and converted after.
+    Both handles' iterates, KKT and objective are bit-identical."""
+    rng = np.random.default_rng(m + ldpad)
+    n = 260
+    A = rng.normal(size=(m, n)) / np.sqrt(m)
+    b = rng.normal(size=m)
+    big = torch.zeros((n, m + ldpad), dtype=torch.float64, device="cuda")
+    big[:, :m] = torch.tensor(A.T, device="cuda")
+    Ad = big.t()[:m]                       # column-major, ld = m + ldpad
+    assert Ad.stride() == (1, m + ldpad)
+    kw = dict(phi="l1l2", lambda1=0.05, num_blocks=5, tol=0.0, max_sweeps=25,
+              storage="bf16", form="gram", refresh_every=5)
+    with api.Handle(Ad, torch.tensor(b, device="cuda"), **kw) as h:
+        zd, infod = h.solve()
+        std = h.state()
+    with api.Handle(A, b, **kw) as h:
+        zh, infoh = h.solve()
+        sth = h.state()
+    assert infod["form"] == infoh["form"] and infod["form"].startswith("gram/bf16")
+    assert np.array_equal(zd, zh)
+    for k in ("x", "xi"):
+        assert np.array_equal(std[k], sth[k]), k
+    assert infod["kkt"] == infoh["kkt"] and infod["obj"] == infoh["obj"]
+
+
 @pytest.mark.parametrize("storage,m,n", [("fp64", 333, 301), ("fp32", 333, 301),
                                          ("bf16", 333, 301), ("bf16", 1000, 520)])
 def test_gram_build_matches_fp64(storage, m, n):

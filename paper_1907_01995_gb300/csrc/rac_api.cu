@@ -728,16 +728,25 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
         }
     } else if (h->has_A) {
         RAC_ST(h->alloc(&h->A64, (size_t)m * n));
-        // BF16 Gram storage of a device-resident A: the FP64 copy is written by
-        // the pass that converts A for the tensor-core Gram build, at once
+        // BF16 Gram storage of a device-resident or pinned host A: the FP64
+        // copy is written by the pass that converts A for the tensor-core Gram
+        // build, at once (a pinned A is read through its mapped device address;
+        // the host link bounds that read as it bounds a copy)
         cudaPointerAttributes pa;
         int cur = 0;
         cudaGetDevice(&cur);
-        if (h->gram && h->store == ST_BF16 && cudaPointerGetAttributes(&pa, pr->A) == cudaSuccess &&
-            (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) &&
-            pa.device == cur) {
+        const double *Adev = nullptr;
+        if (h->gram && h->store == ST_BF16 && cudaPointerGetAttributes(&pa, pr->A) == cudaSuccess) {
+            if ((pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) &&
+                pa.device == cur)
+                Adev = pr->A;
+            else if (pa.type == cudaMemoryTypeHost && pa.devicePointer)
+                Adev = (const double *)pa.devicePointer;
+        }
+        (void)cudaGetLastError();   // an unregistered host pointer leaves no error behind
+        if (Adev) {
             RAC_ST(h->alloc_bytes((void **)&h->G, (size_t)n * n * store_bytes(h->store)));
-            RAC_CK(launch_gram_build_tc(m, n, pr->A, pr->lda, h->G, h->err, st, h->A64));
+            RAC_CK(launch_gram_build_tc(m, n, Adev, pr->lda, h->G, h->err, st, h->A64));
             h->nlaunch += 2;
             gram_built = true;
         } else if (pr->lda == m)

@@ -1424,11 +1424,22 @@ __global__ void __launch_bounds__(256) k_gemvt_f64(int m, int n, const double *_
                 for (int u = 0; u < kGemvtUnroll; ++u)
                     acc[u] = fma(av[u].y, rv[u].y, fma(av[u].x, rv[u].x, acc[u]));
             }
-            // the ragged pairs after the last full group of the column
+            // the ragged pairs after the last full group: one guarded group,
+            // taken by the warp next in turn
             const int kfull = ngroup * 32 * kGemvtUnroll;
-            for (int kk = kfull + lane + 32 * sub; kk < npair; kk += 32 * WPC) {
-                const double2 av = __ldcs(a2 + kk);
-                acc[0] = fma(av.y, __ldg(r + 2 * kk + 1), fma(av.x, __ldg(r + 2 * kk), acc[0]));
+            if (kfull < npair && sub == ngroup % WPC) {
+                double2 av[kGemvtUnroll];
+#pragma unroll
+                for (int u = 0; u < kGemvtUnroll; ++u) {
+                    const int k = kfull + lane + 32 * u;
+                    av[u] = k < npair ? __ldcs(a2 + k) : make_double2(0.0, 0.0);
+                }
+#pragma unroll
+                for (int u = 0; u < kGemvtUnroll; ++u) {
+                    const int k = kfull + lane + 32 * u;
+                    if (k < npair)
+                        acc[u] = fma(av[u].y, __ldg(r + 2 * k + 1), fma(av[u].x, __ldg(r + 2 * k), acc[u]));
+                }
             }
             i0 = 2 * npair;   // an odd last row is taken below
         }

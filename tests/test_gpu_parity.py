@@ -58,6 +58,11 @@ CASES = {
     "big_blocks_residual": dict(m=150, n=602, p=3, phi="l1l2", lam2=0.1, form="residual"),
     "big_blocks_coupled": dict(m=90, n=451, p=2, phi="box", coupling=True, form="residual",
                                beta=0.7, gamma=0.9),
+    # long columns: the FP64 refresh's A^T r streams whole columns per CTA in
+    # 2048-row chunks (4100 = 2 x 2048 + 4: a ragged last chunk; 300 columns
+    # split unevenly over the CTAs)
+    "long_columns_gram": dict(m=4100, n=300, p=6, phi="l1l2", form="gram"),
+    "long_columns_residual": dict(m=4100, n=300, p=6, phi="l1l2", lam2=0.05, form="residual"),
 }
 
 
@@ -269,23 +274,28 @@ def test_device_inputs_and_outputs():
     assert np.array_equal(out.cpu().numpy(), z)
 
 
+@pytest.mark.parametrize("where", ["cuda", "pinned"])
 @pytest.mark.parametrize("m,ldpad", [(600, 0), (601, 0), (600, 2), (600, 3)])
-def test_bf16_gram_device_A_copy_and_conversion_in_one_pass(m, ldpad):
-    """A device-resident A in the BF16 Gram form is copied to FP64 and rounded
-    for the tensor-core Gram build in one pass (paired rows for even m and
-    lda, single rows otherwise); a host A is copied first and converted after.
-    Both handles' iterates, KKT and objective are bit-identical."""
+def test_bf16_gram_device_A_copy_and_conversion_in_one_pass(m, ldpad, where):
+    """A device-resident (or pinned host) A in the BF16 Gram form is copied to
+    FP64 and rounded for the tensor-core Gram build in one pass (paired rows
+    for even m and lda, single rows otherwise); a pageable host A is copied
+    first and converted after.  Both handles' iterates, KKT and objective are
+    bit-identical."""
     rng = np.random.default_rng(m + ldpad)
     n = 260
     A = rng.normal(size=(m, n)) / np.sqrt(m)
     b = rng.normal(size=m)
-    big = torch.zeros((n, m + ldpad), dtype=torch.float64, device="cuda")
-    big[:, :m] = torch.tensor(A.T, device="cuda")
+    if where == "cuda":
+        big = torch.zeros((n, m + ldpad), dtype=torch.float64, device="cuda")
+    else:
+        big = torch.zeros((n, m + ldpad), dtype=torch.float64).pin_memory()
+    big[:, :m] = torch.tensor(A.T).to(big.device)
     Ad = big.t()[:m]                       # column-major, ld = m + ldpad
     assert Ad.stride() == (1, m + ldpad)
     kw = dict(phi="l1l2", lambda1=0.05, num_blocks=5, tol=0.0, max_sweeps=25,
               storage="bf16", form="gram", refresh_every=5)
-    with api.Handle(Ad, torch.tensor(b, device="cuda"), **kw) as h:
+    with api.Handle(Ad, torch.tensor(b).to(big.device), **kw) as h:
         zd, infod = h.solve()
         std = h.state()
     with api.Handle(A, b, **kw) as h:

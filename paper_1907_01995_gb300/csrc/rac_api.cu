@@ -424,7 +424,11 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
     const int nfac = (h->rp || h->boxqp) ? 0 : nb - pre_in;
     for (int q = 0; q < std::min(nfac, (int)rac_handle::kFactorStreams); ++q)
         RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[0], 0));
-    h->nlaunch += (h->rp ? 0 : 1 + (h->lookahead ? 1 : 0)) * (int64_t)nb + 1;   // + prox below
+    // (the cluster chain writes the next sweep's permuted rhs part itself, so
+    // a lookahead period launches k_prepare for its first sweep only)
+    const bool prep_fused = h->lookahead && h->cluster;
+    const int nprep = h->lookahead ? (prep_fused ? 1 : nb) : 0;
+    h->nlaunch += (h->rp ? 0 : (int64_t)nb + nprep) + 1;   // + prox below
     for (int s = pre_in; s < nb && !h->rp && !h->boxqp; ++s) {
         cudaStream_t sf = h->sfs[(s - pre_in) % rac_handle::kFactorStreams];
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
@@ -436,7 +440,7 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
     for (int s = 0; s < nb; ++s) {
         ChainArgs a = chain_args(h, s);
         cudaEvent_t *ev = pf ? &h->pev[3 + 5 * s] : nullptr;
-        if (h->lookahead)
+        if (h->lookahead && (s == 0 || !prep_fused))
             RAC_CK(launch_prepare(h->n, a.perm, h->x, h->z, h->xi, h->k == 1 ? h->e64 : nullptr,
                                   h->gamma, h->sperm, h->eperm, st));
         if (s >= pre_in && !h->rp && !h->boxqp) RAC_CK(cudaStreamWaitEvent(st, h->fev[1 + s], 0));
@@ -446,7 +450,10 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
             if (pf) RAC_CK(cudaEventRecord(ev[1], st));
         }
         if (pf) RAC_CK(cudaEventRecord(ev[2], st));
-        RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
+        // the grid chains' barrier word (the cluster chains and the one-CTA
+        // sparse chain synchronise without it)
+        if (!h->cluster && !h->sparse && !(h->big && h->rescl))
+            RAC_CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), st));
         if (h->boxqp) {
             RAC_CK(launch_box_chain(h->store, a, h->grid, st));
         } else if (h->sparse && h->sp_cl) {
@@ -460,6 +467,7 @@ static rac_status enqueue_period(rac_handle *h, int nb, int pre_in, int next_nb)
         } else if (h->cluster) {
             a.fuse_prox = 1;   // the z-step / ascent runs at the end of the chain
             a.prox = prox_args(h);
+            if (prep_fused && s + 1 < nb) a.perm_next = h->perm + (size_t)(s + 1) * h->n;
             RAC_CK(launch_cluster_chain(h->store, a, h->cluster, st));
         } else {
             RAC_CK(launch_chain(h->store, h->gram, a, h->grid, st));

@@ -442,6 +442,22 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
             q.xi[j] = xi - q.gamma * (x - z);
             a.g[j] = gown[cc] + gdef_s[cc] + gnext_s[cc];
         }
+        if (a.perm_next) {
+            // the next sweep's static rhs part -xi + gamma (x - z) and e in its
+            // order (k_prepare's work) at the positions of this CTA's columns,
+            // whose x, z, xi are final here; every CTA has read this sweep's
+            // values (cluster barrier above)
+            __syncthreads();
+            double *sp = const_cast<double *>(a.sperm);
+            double *ep = const_cast<double *>(a.eperm);
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                const int j = __ldg(a.perm_next + k);
+                if (j >= c0 && j < c0 + ncl) {
+                    sp[k] = -q.xi[j] + q.gamma * (q.x[j] - q.z[j]);
+                    if (ep) ep[k] = a.e[j];
+                }
+            }
+        }
     } else {
         for (int cc = threadIdx.x; cc < ncl; cc += blockDim.x) a.g[c0 + cc] = gown[cc];
     }

@@ -112,6 +112,8 @@ struct ChainArgs {
     int dbg_exit_cta;       // k_chain_res: this CTA returns at its start (-1: none), so the
                             // others' bounded barrier waits run out (failure-path testing)
     int fuse_prox;          // cluster chain: also run the z-step / ascent (k_prox) on its columns
+    const int *perm_next;   // fused z-step: the next sweep's permutation, whose static rhs part
+                            // (sperm, eperm) the epilogue writes for its columns (NULL: k_prepare)
     ProxArgs prox;          //   ... with these arguments (the box chain reads lo, hi here)
     unsigned long long *box_ctr;  // box chain: [0] active-set iterations, [1] capped solves
     int box_ld;             // box mode: row stride of the block matrices (W holds block i

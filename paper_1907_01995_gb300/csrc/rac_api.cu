@@ -534,8 +534,9 @@ static int64_t period_key(int nb, int pre_in, int next_nb) {
 // A period shape is captured into a CUDA graph at its kGraphAfter-th use and
 // replayed from then on: capturing and instantiating costs more than a few
 // direct launches of the same work save (a fresh handle that converges in
-// three periods runs fastest without graphs).
-constexpr int kGraphAfter = 3;
+// three periods, all of one shape since setup pre-launches the first head,
+// runs fastest without graphs).
+constexpr int kGraphAfter = 4;
 
 static rac_status run_period(rac_handle *h, int nb, int pre_in, int next_nb) {
     // Profiling brackets every kernel class with events, which is only
@@ -593,7 +594,26 @@ static rac_status read_stats(rac_handle *h, HostStats *hs, int *dev_err) {
     return RAC_OK;
 }
 
-static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) {
+// The first period's head (its assembly and first factors, on the factor
+// streams) for sweep 0: it depends on the Gram matrix and the sweep count
+// only, so it runs beside the refresh that follows; the caller rejoins it.
+static rac_status fork_head(rac_handle *h, int nb0, int npre) {
+    cudaStream_t st = h->st;
+    RAC_CK(cudaEventRecord(h->fev[0], st));
+    RAC_CK(cudaStreamWaitEvent(h->sfs[0], h->fev[0], 0));
+    RAC_CK(launch_assembly(h->n, h->p, h->seed, 0, nullptr, nb0, h->perm, h->blk, h->tkey,
+                           h->tidx, h->sfs[0]));
+    h->nlaunch += 1;
+    RAC_CK(cudaEventRecord(h->fev[1], h->sfs[0]));
+    for (int q = 1; q < npre; ++q) RAC_CK(cudaStreamWaitEvent(h->sfs[q], h->fev[1], 0));
+    for (int q = 0; q < npre; ++q) RAC_ST(enqueue_factor(h, q, h->sfs[q]));
+    return RAC_OK;
+}
+
+// head_npre > 0: fork the first period's head (fork_head) after the state's
+// reset and before its refresh.
+static rac_status set_state(rac_handle *h, const double *x0, const double *xi0, int head_nb = 0,
+                            int head_npre = 0) {
     cudaStream_t st = h->st;
     size_t nb = (size_t)h->n * sizeof(double);
     if (x0) {
@@ -617,6 +637,7 @@ static rac_status set_state(rac_handle *h, const double *x0, const double *xi0) 
     h->sweep = 0;
     h->pre = 0;   // a pre-launched period head belongs to the old sweep count
     RAC_CK(cudaMemsetAsync(h->sweep_dev, 0, sizeof(int64_t), st));
+    if (head_npre > 0) RAC_ST(fork_head(h, head_nb, head_npre));
     RAC_ST(enqueue_refresh(h));
     if (x0 && h->xi_from_grad) {
         // the refresh just evaluated the exact gradient at z = x0
@@ -1070,7 +1091,18 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
                   h->rp ? "/rp" : "", h->boxqp ? "/boxqp" : "");
     *h->h_err = 0;
     RAC_CK(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    RAC_ST(set_state(h, o->x0, o->xi0));
+    // the first solve's first period: its head runs beside the refresh
+    const int nb0 = std::min(h->refresh_every, h->max_sweeps);
+    const int npre0 = (h->profile || h->rp || h->boxqp || nb0 <= 0)
+                          ? 0
+                          : std::min(nb0, (int)rac_handle::kFactorStreams);
+    RAC_ST(set_state(h, o->x0, o->xi0, nb0, npre0));
+    for (int q = 0; q < npre0; ++q) {   // rejoin
+        RAC_CK(cudaEventRecord(h->fev[2 + q], h->sfs[q]));
+        RAC_CK(cudaStreamWaitEvent(st, h->fev[2 + q], 0));
+    }
+    h->pre = npre0;
+    h->pre_nb = nb0;
     if (g0_from_refresh) {
         h->nlaunch += 1;
         RAC_CK(launch_kkt_zero(n, h->gz, h->phi, h->lam1, h->lo, h->hi, h->kpart, st));
@@ -1146,8 +1178,10 @@ extern "C" rac_status rac_admm_solve(rac_handle *h, double *x_out, rac_info *inf
     int done = 0;
     int rejected = 0;
     rac_status status = RAC_OK;
-    if (dev_err) status = (rac_status)dev_err;
-    else if (hs.nonfinite) status = RAC_ERR_NUMERIC;   // NaN / Inf in the data or the state
+    // NaN / Inf in the data or the state come first: a head pre-launched at
+    // setup may have met them as a non-positive pivot
+    if (hs.nonfinite) status = RAC_ERR_NUMERIC;
+    else if (dev_err) status = (rac_status)dev_err;
     const bool check_ws = h->ws_fallback && h->warm && h->solves == 0;
     while (status == RAC_OK && hs.kkt > h->tol && done < h->max_sweeps) {
         int nb = std::min(h->refresh_every, h->max_sweeps - done);

@@ -29,7 +29,13 @@
 //     copy engine.)
 // Buffer reuse is ordered by the two barriers: a CTA overwrites a dx copy or
 // a rhs buffer only after a barrier phase that every reader of the previous
-// contents had to arrive at.  Every wait is an mbarrier wait bounded in time
+// contents had to arrive at.  One case rests on timing instead: the update
+// warps read dx_i from their CTA's copy right after it arrives, and the
+// dx_{i+2} stores into that copy wait for block i+2's gradient values, which
+// include this CTA's pushes only if it owns a column of block i+2.  A CTA
+// owning none is protected by the two dependent steps (dx_{i+1}, then dx_{i+2},
+// about 1.5 us each at n = 2000) that precede those stores, against reads that
+// finish within a few hundred cycles.  Every wait is an mbarrier wait bounded in time
 // (on expiry the error flag is set and the CTA carries on, so arrival counts
 // stay matched); the cluster barrier is used only at entry and exit.
 #include <cuda_runtime.h>

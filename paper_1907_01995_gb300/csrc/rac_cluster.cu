@@ -29,15 +29,15 @@
 //     copy engine.)
 // Buffer reuse is ordered by the two barriers: a CTA overwrites a dx copy or
 // a rhs buffer only after a barrier phase that every reader of the previous
-// contents had to arrive at.  One case rests on timing instead: the update
-// warps read dx_i from their CTA's copy right after it arrives, and the
-// dx_{i+2} stores into that copy wait for block i+2's gradient values, which
-// include this CTA's pushes only if it owns a column of block i+2.  A CTA
-// owning none is protected by the two dependent steps (dx_{i+1}, then dx_{i+2},
-// about 1.5 us each at n = 2000) that precede those stores, against reads that
-// finish within a few hundred cycles.  Every wait is an mbarrier wait bounded in time
-// (on expiry the error flag is set and the CTA carries on, so arrival counts
-// stay matched); the cluster barrier is used only at entry and exit.
+// contents had to arrive at.  For the dx copies the readers are also the
+// update warps of every CTA (dx_i, read right after it arrives); the dx_{i+2}
+// stores follow the wait for block i+2's gradient values, so besides its
+// values each CTA sends every CTA an 8-byte token for block i+2 once its
+// update warps have read dx_i, owner of a column of block i+2 or not, and that
+// barrier phase counts s_{i+2} values and C tokens.  Every wait is an
+// mbarrier wait bounded in time (on expiry the error flag is set and the CTA
+// carries on, so arrival counts stay matched); the cluster barrier is used
+// only at entry and exit.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cooperative_groups.h>
@@ -55,10 +55,11 @@ constexpr int kClWarps = 8;                      // warps 4..11: the gradient up
 constexpr int kClThreads = 32 * (kClSolveWarps + kClWarps);
 constexpr int kClSmax = 128;     // block size limit (a lane holds 4 of <= 128 columns)
 constexpr int kClRows = kClSmax / kClWarps;   // G rows per update warp and step (q = w + 8 j)
+constexpr int kClMaxC = 16;      // CTAs per cluster at most
 
 // Shared-memory layout (offsets in bytes, each 16-byte aligned).
 struct ClLayout {
-    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, gpark, bars, total;
+    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, gpark, bars, tok, total;
     int ncp, rmax;
     __host__ __device__ ClLayout(int n, int smax, int C) {
         // columns per CTA: 64 NK with NK in {1, 2, 4} (the kernel's template
@@ -83,6 +84,7 @@ struct ClLayout {
         red = take((size_t)kClWarps * ncp * 4);
         gpark = take(2 * (size_t)ncp * 8);
         bars = take(4 * 8);
+        tok = take(2 * (size_t)kClMaxC * 8);
         total = o;
     }
 };
@@ -183,6 +185,9 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     double *gdef_s = (double *)(sm + L.gpark);   // [ncp]: parked own-block increments (fused z-step)
     double *gnext_s = gdef_s + ncp;               // [ncp]: parked next-block increments
     uint64_t *bars = (uint64_t *)(sm + L.bars);  // dx ready [2], gradient ready [2]
+    double *tok = (double *)(sm + L.tok);        // [2][kClMaxC]: "dx read" tokens (never read)
+    // bytes of block b's gradient-ready phase: its s_b values and C tokens
+    auto gbytes = [&](int b) { return 8u * (unsigned)(lay.size(b) + C); };
     uint64_t *dready = bars, *gready = bars + 2;
     __shared__ double dred[64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
         for (int k = 0; k < 4; ++k) mbar_init(&bars[k], 1);
         mbar_init_fence();
         for (int k = 0; k < 2 && k < p; ++k) mbar_expect_tx(&dready[k], 4u * lay.size(k));
-        for (int b = 2; b < 4 && b < p; ++b) mbar_expect_tx(&gready[b & 1], 8u * lay.size(b));
+        for (int b = 2; b < 4 && b < p; ++b) mbar_expect_tx(&gready[b & 1], gbytes(b));
     }
     __syncthreads();
     cl.sync();   // every CTA is initialised and armed before remote stores arrive
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
             if (i >= 2)   // the gradient values of block i, pushed during step i-2
                 mbar_wait_cluster(&gready[i & 1], (uint32_t)((i >> 1) - 1) & 1u, a.err);
             if (i >= 2 && tid == 0 && i + 2 < p)   // arm the next phase: block i+2
-                mbar_expect_tx(&gready[i & 1], 8u * lay.size(i + 2));
+                mbar_expect_tx(&gready[i & 1], gbytes(i + 2));
             if (tid < s) {
                 double r = rhsg[(i & 1) * kClSmax + tid] + cur.sp;
                 if (a.e) r += cur.ep * (beta * t - mu);
@@ -405,6 +410,11 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
             fetch_g(i + 1);        // this step's G values are consumed
             group_sync(2, 32 * kClWarps);
             const bool push = i + 2 < p;
+            // every update warp here has read dx_i (barrier above): tell every
+            // CTA, whose dx_{i+2} stores into this CTA's copy wait for it
+            if (push && ut < C)
+                st_async_f64(cluster_addr(tok + (i & 1) * kClMaxC + c, ut), 0.0,
+                             cluster_addr(&gready[i & 1], ut));
             for (int cc = ut; cc < ncl; cc += 32 * kClWarps) {
                 float tot = 0.f;
 #pragma unroll

@@ -59,7 +59,7 @@ constexpr int kClMaxC = 16;      // CTAs per cluster at most
 
 // Shared-memory layout (offsets in bytes, each 16-byte aligned).
 struct ClLayout {
-    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, gpark, bars, tok, total;
+    size_t perm, gown, bown, qown, rhsg, dbuf, rhs, red, gpark, dxs, bars, tok, total;
     int ncp, rmax;
     __host__ __device__ ClLayout(int n, int smax, int C) {
         // columns per CTA: 64 NK with NK in {1, 2, 4} (the kernel's template
@@ -83,6 +83,7 @@ struct ClLayout {
         rhs = take((size_t)kClSmax * 4);
         red = take((size_t)kClWarps * ncp * 4);
         gpark = take(2 * (size_t)ncp * 8);
+        dxs = take((size_t)ncp * 4);
         bars = take(4 * 8);
         tok = take(2 * (size_t)kClMaxC * 8);
         total = o;
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
     float *red = (float *)(sm + L.red);          // [update warps][ncp]
     double *gdef_s = (double *)(sm + L.gpark);   // [ncp]: parked own-block increments (fused z-step)
     double *gnext_s = gdef_s + ncp;               // [ncp]: parked next-block increments
+    float *dxs = (float *)(sm + L.dxs);          // [ncp]: dx of the own columns (fused z-step)
     uint64_t *bars = (uint64_t *)(sm + L.bars);  // dx ready [2], gradient ready [2]
     double *tok = (double *)(sm + L.tok);        // [2][kClMaxC]: "dx read" tokens (never read)
     // bytes of block b's gradient-ready phase: its s_b values and C tokens
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
                     const float d = -dsum[u];
                     if (lane < C)   // lane k stores into CTA k's copy of dx_i
                         st_async_f32(rd_dbuf + 4u * ((i & 1) * kClSmax + r0 + r), d, rd_bar + 8u * (i & 1));
-                    if (lane == 0) a.dx[perm[off + r0 + r]] = (double)d;
+                    if (lane == 0 && !a.fuse_prox) a.dx[perm[off + r0 + r]] = (double)d;
                 }
             }
             group_sync(1, 32 * kClSolveWarps);   // rhs is rewritten next step
@@ -407,6 +409,9 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
                 for (int v = 0; v < GV::VEC; v += 2)
                     *reinterpret_cast<float2 *>(rw + v) = make_float2(acc[v], acc[v + 1]);
             }
+            if (a.fuse_prox)   // the z-step's dx of the own columns of block i
+                for (int cc = ut; cc < ncl; cc += 32 * kClWarps)
+                    if (bown[cc] == i) dxs[cc] = dxi[qown[cc]];
             fetch_g(i + 1);        // this step's G values are consumed
             group_sync(2, 32 * kClWarps);
             const bool push = i + 2 < p;
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_chain_cluster(ChainArgs a) {
         const double lam1 = q.lam_dev ? q.lam_dev[0] : q.lam1, lam2 = q.lam_dev ? q.lam_dev[1] : q.lam2;
         for (int cc = threadIdx.x; cc < ncl; cc += blockDim.x) {
             const int j = c0 + cc;
-            const double x = q.x[j] + q.dx[j];
+            const double x = q.x[j] + (double)dxs[cc];
             const double xi = q.xi[j];
             const double z = prox_z(q.phi, x, xi, q.gamma, lam1, lam2, q.lo, q.hi);
             q.x[j] = x;

@@ -34,7 +34,10 @@ class _Keep:
         if a is None:
             return None
         if _is_tensor(a):
-            t = a.detach().to(torch.float64).contiguous().reshape(-1)
+            if a.dtype == torch.float64 and a.is_contiguous():
+                t = a   # read in place (a contiguous tensor is one flat buffer)
+            else:
+                t = a.detach().to(torch.float64).contiguous().reshape(-1)
             if n is not None and t.numel() != n:
                 raise ValueError("vector length %d, expected %d" % (t.numel(), n))
             self.items.append(t)
@@ -48,9 +51,9 @@ class _Keep:
     def colmajor(self, a):
         """(pointer, rows, cols, ld) of a 2-D array in column-major float64."""
         if _is_tensor(a):
-            t = a.detach().to(torch.float64)
+            t = a if a.dtype == torch.float64 else a.detach().to(torch.float64)
             if not (t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0])):
-                t = t.t().contiguous().t()
+                t = t.detach().t().contiguous().t()
             self.items.append(t)
             return t.data_ptr(), t.shape[0], t.shape[1], max(1, t.stride(1))
         m = np.asfortranarray(np.asarray(a, dtype=np.float64))
@@ -58,9 +61,15 @@ class _Keep:
         return m.ctypes.data, m.shape[0], m.shape[1], max(1, m.shape[0])
 
 
+_CUDA = None   # torch.cuda.is_available(), asked once per process
+
+
 def _stream_handle(stream) -> int:
+    global _CUDA
     if stream is None:
-        if torch is not None and torch.cuda.is_available():
+        if _CUDA is None:
+            _CUDA = torch is not None and torch.cuda.is_available()
+        if _CUDA:
             return torch.cuda.current_stream().cuda_stream
         return 0
     if hasattr(stream, "cuda_stream"):

@@ -851,8 +851,9 @@ static rac_status setup_impl(const rac_problem *pr, const rac_options *o, rac_ha
     }
     // the scale of the KKT measure: max(1, ||grad at 0||_inf).  A cold start
     // without folded rows takes it from the refresh that set_state enqueues,
-    // which evaluates exactly the gradient at z = 0 into gz.
-    const bool g0_from_refresh = !o->x0 && !h->fold && (h->sparse || h->has_A);
+    // which evaluates exactly the gradient at z = 0 into gz (not in box mode,
+    // where the start is projected into the box first).
+    const bool g0_from_refresh = !o->x0 && !h->fold && !h->boxqp && (h->sparse || h->has_A);
     {
         // gradient at z = 0 and its statistics, read back after the final sync
         h->ss->h_aux[0] = h->ss->h_aux[1] = 0.0;

@@ -144,3 +144,24 @@ def test_boxqp_singular_block_reports_not_pd():
     assert info["status"] == 0, info
     P = O.Problem(H=H, q=q, phi="box", lo=0.0, hi=1.0)
     assert O.kkt(P, z)["kkt"] <= 1e-10 * 1.01
+
+
+def test_boxqp_data_form_box_excluding_zero_converges_on_the_oracle_kkt():
+    """A box that excludes 0 (bounded least squares on [2, 3]): the cold
+    start is projected into the box, while the KKT measure keeps its scale
+    max(1, ||grad f(0)||_inf) from the gradient at zero; converged to tol, the
+    point meets the oracle's KKT measure to the same tol."""
+    rng = np.random.default_rng(12)
+    A = rng.normal(size=(240, 150)) / np.sqrt(240)
+    b = 3.0 * rng.normal(size=240)
+    tol = 1e-9
+    with api.Handle(A, b, phi="box", lo=2.0, hi=3.0, num_blocks=5, box_qp=True, tol=tol,
+                    max_sweeps=20000, refresh_every=10) as h:
+        z, info = h.solve()
+    assert info["status"] == 0, info
+    assert np.all(z >= 2.0) and np.all(z <= 3.0)
+    P = O.problem_from_data(A, b, "box", lo=2.0, hi=3.0)
+    k = O.kkt(P, z)["kkt"]
+    assert k <= tol * 1.01
+    # the reported measure is the oracle's (same scale), both ways within 1%
+    assert k <= info["kkt"] * 1.01 + 1e-15 and info["kkt"] <= k * 1.01 + 1e-15, (k, info["kkt"])

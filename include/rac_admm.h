@@ -198,7 +198,9 @@ typedef struct {
     int32_t status;         /* rac_status of this problem */
     char form[32];          /* e.g. "gram/fp32" */
     int64_t kernel_launches;/* kernels this call launched (graph replays included) */
-    int64_t setup_launches; /* kernels rac_admm_setup launched for this handle */
+    int64_t setup_launches; /* kernels rac_admm_setup launched for this handle (including
+                               the first refresh period's assembly and first factors,
+                               which it runs beside its refresh) */
     /* with rac_options.profile = 1: device time of each kernel class over the
      * call, measured by CUDA events on the handle's stream (0 otherwise) */
     double t_assembly_ms, t_factor_ms, t_chain_ms, t_prox_ms, t_refresh_ms;
